@@ -1,0 +1,270 @@
+"""Throughput benchmark of the compact 8th-order GKS on GB300 (FP64 cell-updates/s).
+
+A step is one full two-stage fourth-order time step of the whole grid (CFL time step, both
+stages of reconstruction + gas-kinetic flux + Gauss-theorem update).  Default workload: the 2D
+isentropic vortex on a 2048^2 periodic grid (vortex strength 5 on free stream (1,1,1,1), [0,10]^2,
+CFL 0.5), synthetic initial data, state (3 x 12 planes, 1.2 GB) resident in HBM and larger than L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cgks|reference] [--workload NAME]
+
+--impl reference times the CPU oracle (test infrastructure, plain FP64 C) on a bounded sample of
+the same workload on the host cores.  Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "FP64 cell-updates/s on 1 GB300 (plain 2048^2 sweep); served-batched vs plain; p50/p99 solve latency"
+UNIT = "cell-updates/s"
+
+# FP64 floating-point operations per cell and stage executed by the stage kernels (FMA = 2),
+# counted with ncu (sm__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on) on a 256^2
+# isentropic-vortex grid and divided by the cells; see profiles/stage_kernels_vortex.md.
+FLOP_PER_CELL = {1: None, 2: None}
+# measured FP64 peak of this GB300 (DFMA throughput loop, FMA = 2): profiles/fp64_peak.md
+FP64_PEAK_TFLOPS = 1.010
+
+
+def workloads():
+    from paper_2001_01570_gb300 import workloads as wl
+    return {
+        "vortex2048": lambda: wl.isentropic_vortex(2048),
+        "vortex512": lambda: wl.isentropic_vortex(512),
+        "vortex256": lambda: wl.isentropic_vortex(256),
+        "shockvortex1024x512": lambda: wl.shock_vortex(1024, 512),
+    }
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.reader = threading.Thread(target=self._read, daemon=True)
+            self.reader.start()
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if args.impl == "cgks" else "gloo")
+    return world, rank, local
+
+
+def barrier_max(world, value):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_sample(seconds_target=12.0, n=96, threads=None):
+    """Time the CPU oracle (as it stands) on a bounded sample of the vortex workload: the same
+    initial condition on an n x n grid (cost per cell-update is independent of grid size)."""
+    import oracle as O
+    from paper_2001_01570_gb300 import workloads as wl
+    spec, W = wl.isentropic_vortex(n)
+    P = O.make_problem(**spec.as_kwargs())
+    cores = threads or os.cpu_count()
+    os.environ["OMP_NUM_THREADS"] = str(cores)
+    O.run(P, W, 1, threads=cores)                       # warm-up (compile/load)
+    steps, t0 = 0, time.perf_counter()
+    Wc = W
+    while True:
+        Wc, _, _, _ = O.run(P, Wc, 1, threads=cores)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds_target:
+            break
+    rate = n * n * steps / el
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"isentropic vortex {n}x{n} periodic, {steps} steps ({el:.1f} s), OpenMP over rows"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    cb = oracle_sample(seconds_target=max(5.0, min(20.0, 2.0 * args.steps)))
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload} (oracle on a bounded sample)"},
+            "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_cgks(args, world, rank, local):
+    import torch
+    from paper_2001_01570_gb300 import build as libbuild
+    from paper_2001_01570_gb300 import cgks
+
+    libbuild.build()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    spec, W = workloads()[args.workload]()
+    cells = spec.cells
+    solver = cgks.Solver(cgks.problem_from_spec(spec), stream=stream.cuda_stream)
+    solver.set_state(W)
+
+    # warm-up (also fills the per-kernel shared-memory configuration)
+    solver.step(args.warmup)
+    torch.cuda.synchronize()
+
+    # ---------------- device-resident throughput: K steps, events on the solver's stream
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        cgks.cgks_step(solver.handle, args.steps)
+        stop.record(stream)
+        torch.cuda.synchronize()
+    launches = cgks.cgks_last_launch_count()
+    ms = start.elapsed_time(stop)
+    ms = barrier_max(world, ms)
+    value = world * cells * args.steps / (ms * 1e-3)
+    clocks = clk.summary()
+
+    # ---------------- per-kernel durations (events around every launch) for the roofline
+    prof_steps = max(2, min(args.steps, 5))
+    stage_ms = cgks.cgks_step_profiled(solver.handle, prof_steps)
+    roofline = None
+    if FLOP_PER_CELL[1]:
+        flops = FLOP_PER_CELL[1] * cells
+        achieved = flops / (stage_ms[1] * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "stage_kernel<16,8,1>",
+                    "kernel_ms": stage_ms[1], "peak_source": "measured FP64 DFMA loop (FMA=2) on GB300"}
+    else:
+        roofline = {"bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": None,
+                    "traffic": None, "kernel": "stage_kernel<16,8,1>", "kernel_ms": stage_ms[1]}
+
+    # ---------------- end to end through the C ABI with host buffers
+    host_in = torch.from_numpy(np.ascontiguousarray(W)).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    e2e_reps = 1
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_reps):
+        cgks.cgks_set_state(solver.handle, host_in.numpy())
+        cgks.cgks_step(solver.handle, args.steps)
+        cgks.cgks_get_state(solver.handle, host_out.numpy())
+    el = time.perf_counter() - t0
+    el = barrier_max(world, el)
+    e2e_value = world * cells * args.steps * e2e_reps / el
+    nbytes = host_in.numel() * 8
+
+    solver.close()
+    if rank != 0:
+        return
+    cpu = None if args.no_cpu_baseline or world > 1 else oracle_sample()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "cells": cells, "grid": [spec.nx, spec.ny],
+                   "cfl": spec.cfl, "l2": "inputs larger than L2 (3 x 12 planes resident, %.2f GB)" % (36 * cells * 8 / 1e9),
+                   "parallelism": "one grid per GPU (independent replicas)" if world > 1 else "single GPU"},
+        "roofline": roofline,
+        "stage_ms": {"begin": stage_ms[0], "stage1": stage_ms[1], "stage2": stage_ms[2], "end": stage_ms[3]},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes / args.steps,
+                "d2h_bytes_per_step": nbytes / args.steps,
+                "note": "per repetition: H2D of the 12 state planes from pinned host memory, K steps, D2H of the state"},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cgks", choices=["cgks", "reference"])
+    ap.add_argument("--workload", default="vortex2048")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_cgks(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -37,8 +37,14 @@
  *   - the interface state is the psi-moment of the third-order distribution:
  *     W(t) = W0 + t W0_t + t^2/2 W0_tt + NE(t); W0_t, W0_tt are the Euler
  *     time derivatives (Cauchy-Kowalevski), NE(t) the non-equilibrium part
- *   - 2D: two Gauss points per face; normal reconstruction per row, then a
- *     tangential cubic (equilibrium) / quadratic (non-equilibrium)
+ *   - 2D: two Gauss points per face.  Each face row gets the 1D normal
+ *     reconstruction; along the face, the equilibrium value and normal
+ *     derivative at the Gauss points come from the quartic whose means over
+ *     the five segments j-2..j+2 equal the line averages of those rows, and
+ *     the non-equilibrium states from the quadratic through rows j-1..j+1.
+ *     The cell-averaged tangential gradient is used only by the faces normal
+ *     to it (a face-interpolated tangential gradient makes the 2D scheme
+ *     linearly unstable under advection)
  *   - 1D uses K = (3-gamma)/(gamma-1) internal degrees of freedom
  *   - CFL: dt = CFL * min_cells min(dx/(|U|+c), dy/(|V|+c))
  *
@@ -741,7 +747,7 @@ done:
 /* ------------------------------------------------------------------ */
 /* 2D.  Normal reconstruction of one row of one face (orientation o: 0 x-face,
  * 1 y-face), in the face frame (momentum components swapped for y-faces). */
-typedef struct { double V[4], N[4], NN[4], L[4], R[4], Ln[4], Rn[4], T[4]; } row_rec;
+typedef struct { double V[4], N[4], NN[4], L[4], R[4], Ln[4], Rn[4]; } row_rec;
 
 /* rotated variable index: frame component k reads physical component */
 static int rot_var(int o, int k) { if (o == 0) return k; return (k == 1) ? 2 : (k == 2) ? 1 : k; }
@@ -761,15 +767,14 @@ static void stencil_cell(int o, int f, int r, int c, int *i, int *j)
 static void row_recon(const oc_problem *P, const double *E, int o, int f, int r, row_rec *out)
 {
     double h = (o == 0) ? P->dx : P->dy;
-    int gn = (o == 0) ? 1 : 2, gt = (o == 0) ? 2 : 1;   /* normal / tangential gradient groups */
+    int gn = (o == 0) ? 1 : 2;   /* normal gradient group */
     for (int k = 0; k < 4; ++k) {
         int pv = rot_var(o, k);
-        double Q[4], hQp[4], s[8], lin[3], v, sl, Tg[4];
+        double Q[4], hQp[4], s[8], lin[3], v, sl;
         for (int c = 0; c < 4; ++c) {
             int i, j; stencil_cell(o, f, r, c, &i, &j);
             Q[c] = ext_at(P, E, pv, j, i);
             hQp[c] = h * ext_at(P, E, 4 * gn + pv, j, i);
-            Tg[c] = ext_at(P, E, 4 * gt + pv, j, i);
             s[c] = Q[c]; s[4 + c] = hQp[c];
         }
         oc_linear_recon(Q, hQp, lin);
@@ -778,15 +783,54 @@ static void row_recon(const oc_problem *P, const double *E, int o, int f, int r,
         out->L[k] = v; out->Ln[k] = sl / h;
         oc_weno_right(s, P->weno_eps, &v, &sl);
         out->R[k] = v; out->Rn[k] = sl / h;
-        /* cell-average -> point value at the face of the tangential-gradient averages */
-        out->T[k] = (-Tg[0] + 7.0 * Tg[1] + 7.0 * Tg[2] - Tg[3]) / 12.0;
     }
 }
 
-/* face segment: rows m=-1,0,+1 around it -> two Gauss points -> averaged result
- * (in the face frame) */
-static int face_segment(const oc_problem *P, const row_rec *rm, const row_rec *r0, const row_rec *rp,
-                        int o, double dt, face_res *res)
+/* Tangential profiles along a face.  A polynomial p(eta) in eta = (y - y_j)/h_t
+ * is fixed by its means over the unit segments centred at the neighbouring
+ * rows; SEGFIT5 maps the five means (rows j-2..j+2) to the coefficients of the
+ * quartic, SEGFIT3 the three means (rows j-1..j+1) to those of the quadratic. */
+static double SEGFIT5[5][5], SEGFIT3[3][3];
+static int SEGFIT_READY = 0;
+
+static void build_segfit(void)
+{
+    if (SEGFIT_READY) return;
+    for (int n = 3; n <= 5; n += 2) {
+        int off = n / 2;
+        for (int col = 0; col < n; ++col) {
+            double A[25], b[5];
+            for (int r = 0; r < n; ++r) {
+                double lo = (r - off) - 0.5, hi = (r - off) + 0.5;
+                for (int m = 0; m < n; ++m) A[r * n + m] = (ipow(hi, m + 1) - ipow(lo, m + 1)) / (m + 1);
+                b[r] = (r == col) ? 1.0 : 0.0;
+            }
+            solve_dense(n, A, b);
+            for (int m = 0; m < n; ++m) {
+                if (n == 5) SEGFIT5[m][col] = b[m]; else SEGFIT3[m][col] = b[m];
+            }
+        }
+    }
+    SEGFIT_READY = 1;
+}
+
+/* value, first and second derivative (per unit eta) at eta of the profile
+ * through the segment means v[0..n-1] (rows j-n/2 .. j+n/2) */
+static void seg_profile(int n, const double *v, double eta, double *p, double *dp, double *d2p)
+{
+    double c[5] = {0, 0, 0, 0, 0};
+    for (int m = 0; m < n; ++m)
+        for (int r = 0; r < n; ++r) c[m] += (n == 5 ? SEGFIT5[m][r] : SEGFIT3[m][r]) * v[r];
+    double a = 0.0, b = 0.0, cc = 0.0;
+    for (int m = 0; m < n; ++m) a += c[m] * ipow(eta, m);
+    for (int m = 1; m < n; ++m) b += m * c[m] * ipow(eta, m - 1);
+    for (int m = 2; m < n; ++m) cc += m * (m - 1) * c[m] * ipow(eta, m - 2);
+    *p = a; *dp = b; *d2p = cc;
+}
+
+/* face segment: rows m = -2..+2 around it (rr[0..4]) -> two Gauss points ->
+ * Gauss-averaged result (in the face frame) */
+static int face_segment(const oc_problem *P, const row_rec *const rr[5], int o, double dt, face_res *res)
 {
     double ht = (o == 0) ? P->dy : P->dx;
     const double g = 1.0 / (2.0 * sqrt(3.0));
@@ -794,32 +838,28 @@ static int face_segment(const oc_problem *P, const row_rec *rm, const row_rec *r
         double eta = gp ? g : -g;
         oc_point_in in;
         for (int k = 0; k < 4; ++k) {
-            /* equilibrium: tangential cubic from three line averages and the mean tangential slope */
-            double a2 = 0.5 * (rp->V[k] - 2.0 * r0->V[k] + rm->V[k]);
-            double a3 = 0.5 * ((rp->V[k] - rm->V[k]) - 2.0 * ht * r0->T[k]);
-            double a1 = ht * r0->T[k] - 0.25 * a3;
-            double a0 = r0->V[k] - a2 / 12.0;
-            in.W0[k] = a0 + a1 * eta + a2 * eta * eta + a3 * eta * eta * eta;
-            in.W0t[k] = (a1 + 2.0 * a2 * eta + 3.0 * a3 * eta * eta) / ht;
-            in.W0tt[k] = (2.0 * a2 + 6.0 * a3 * eta) / (ht * ht);
-            /* normal derivative: tangential quadratic of the line-averaged normal derivatives */
-            double b2 = 0.5 * (rp->N[k] - 2.0 * r0->N[k] + rm->N[k]);
-            double b1 = 0.5 * (rp->N[k] - rm->N[k]);
-            double b0 = r0->N[k] - b2 / 12.0;
-            in.W0n[k] = b0 + b1 * eta + b2 * eta * eta;
-            in.W0nt[k] = (b1 + 2.0 * b2 * eta) / ht;
-            in.W0nn[k] = r0->NN[k];
-            /* non-equilibrium states: tangential quadratics */
-            double l2 = 0.5 * (rp->L[k] - 2.0 * r0->L[k] + rm->L[k]), l1 = 0.5 * (rp->L[k] - rm->L[k]);
-            in.Wl[k] = r0->L[k] - l2 / 12.0 + l1 * eta + l2 * eta * eta;
-            in.Wlt[k] = (l1 + 2.0 * l2 * eta) / ht;
-            double ln2 = 0.5 * (rp->Ln[k] - 2.0 * r0->Ln[k] + rm->Ln[k]), ln1 = 0.5 * (rp->Ln[k] - rm->Ln[k]);
-            in.Wln[k] = r0->Ln[k] - ln2 / 12.0 + ln1 * eta + ln2 * eta * eta;
-            double q2 = 0.5 * (rp->R[k] - 2.0 * r0->R[k] + rm->R[k]), q1 = 0.5 * (rp->R[k] - rm->R[k]);
-            in.Wr[k] = r0->R[k] - q2 / 12.0 + q1 * eta + q2 * eta * eta;
-            in.Wrt[k] = (q1 + 2.0 * q2 * eta) / ht;
-            double rn2 = 0.5 * (rp->Rn[k] - 2.0 * r0->Rn[k] + rm->Rn[k]), rn1 = 0.5 * (rp->Rn[k] - rm->Rn[k]);
-            in.Wrn[k] = r0->Rn[k] - rn2 / 12.0 + rn1 * eta + rn2 * eta * eta;
+            double v5[5], n5[5], v3[3], p, dp, d2p;
+            for (int r = 0; r < 5; ++r) { v5[r] = rr[r]->V[k]; n5[r] = rr[r]->N[k]; }
+            /* equilibrium: value and its tangential derivatives */
+            seg_profile(5, v5, eta, &p, &dp, &d2p);
+            in.W0[k] = p; in.W0t[k] = dp / ht; in.W0tt[k] = d2p / (ht * ht);
+            /* normal derivative and its tangential derivative */
+            seg_profile(5, n5, eta, &p, &dp, &d2p);
+            in.W0n[k] = p; in.W0nt[k] = dp / ht;
+            in.W0nn[k] = rr[2]->NN[k];
+            /* non-equilibrium states: quadratics through rows j-1..j+1 */
+            for (int r = 0; r < 3; ++r) v3[r] = rr[r + 1]->L[k];
+            seg_profile(3, v3, eta, &p, &dp, &d2p);
+            in.Wl[k] = p; in.Wlt[k] = dp / ht;
+            for (int r = 0; r < 3; ++r) v3[r] = rr[r + 1]->Ln[k];
+            seg_profile(3, v3, eta, &p, &dp, &d2p);
+            in.Wln[k] = p;
+            for (int r = 0; r < 3; ++r) v3[r] = rr[r + 1]->R[k];
+            seg_profile(3, v3, eta, &p, &dp, &d2p);
+            in.Wr[k] = p; in.Wrt[k] = dp / ht;
+            for (int r = 0; r < 3; ++r) v3[r] = rr[r + 1]->Rn[k];
+            seg_profile(3, v3, eta, &p, &dp, &d2p);
+            in.Wrn[k] = p;
         }
         oc_point_out out;
         if (oc_gks_point(P, 2, &in, dt, &out)) return OC_E_NONPHYSICAL;
@@ -836,16 +876,17 @@ static int faces2d(const oc_problem *P, const double *E, double dt, face_res *fx
     for (int o = 0; o < 2; ++o) {
         int nf = (o == 0) ? nx + 1 : ny + 1;     /* faces along the normal */
         int nr = (o == 0) ? ny : nx;             /* rows along the tangent */
-        row_rec *rr = malloc((size_t)nf * (nr + 2) * sizeof(row_rec));
+        row_rec *rr = malloc((size_t)nf * (nr + 4) * sizeof(row_rec));
 #pragma omp parallel for collapse(2)
-        for (int r = -1; r <= nr; ++r)
-            for (int f = 0; f < nf; ++f) row_recon(P, E, o, f, r, &rr[(size_t)(r + 1) * nf + f]);
+        for (int r = -2; r <= nr + 1; ++r)
+            for (int f = 0; f < nf; ++f) row_recon(P, E, o, f, r, &rr[(size_t)(r + 2) * nf + f]);
 #pragma omp parallel for collapse(2) reduction(| : err)
         for (int r = 0; r < nr; ++r)
             for (int f = 0; f < nf; ++f) {
                 face_res res;
-                err |= face_segment(P, &rr[(size_t)r * nf + f], &rr[(size_t)(r + 1) * nf + f],
-                                    &rr[(size_t)(r + 2) * nf + f], o, dt, &res);
+                const row_rec *rows[5];
+                for (int m = 0; m < 5; ++m) rows[m] = &rr[(size_t)(r + m) * nf + f];
+                err |= face_segment(P, rows, o, dt, &res);
                 face_res *dst = (o == 0) ? &fx[(size_t)r * (nx + 1) + f] : &fy[(size_t)f * nx + r];
                 for (int k = 0; k < 4; ++k) {
                     int pv = rot_var(o, k);
@@ -912,6 +953,7 @@ int oc_run(const oc_problem *P, double *W, int nsteps, double t_end, double *t, 
 {
     if (!P || !W || P->nx < 1 || (P->dim == 2 && P->ny < 1) || (P->dim != 1 && P->dim != 2)) return OC_E_INVAL;
     build_coef();
+    build_segfit();
     for (int s = 0; s < nsteps; ++s) {
         if (t_end > 0.0 && *t >= t_end) break;
         double dt = oc_cfl_dt(P, W);
@@ -930,12 +972,14 @@ int oc_run(const oc_problem *P, double *W, int nsteps, double t_end, double *t, 
 int oc_step_dt(const oc_problem *P, double *W, double dt)
 {
     build_coef();
+    build_segfit();
     return (P->dim == 1) ? step1d(P, W, dt) : step2d(P, W, dt);
 }
 
 int oc_run_fixed_dt(const oc_problem *P, double *W, int nsteps, double dt)
 {
     build_coef();
+    build_segfit();
     for (int s = 0; s < nsteps; ++s) {
         int err = oc_step_dt(P, W, dt);
         if (err) return err;

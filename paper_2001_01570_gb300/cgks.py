@@ -1,0 +1,191 @@
+"""Thin ctypes binding of libcgks (include/cgks.h): argument marshalling only.
+
+Every step of the computation runs in the library's CUDA kernels.  If the
+library has not been built, :func:`load` raises; there is no fallback.
+Device buffers may be torch CUDA tensors (their data pointers are passed).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+CGKS_OK, CGKS_E_INVAL, CGKS_E_NOMEM, CGKS_E_BUDGET, CGKS_E_CUDA, CGKS_E_NONPHYSICAL, CGKS_E_TIMEOUT, \
+    CGKS_E_BUSY, CGKS_E_NOTFOUND = range(9)
+CGKS_BC_PERIODIC, CGKS_BC_REFLECT, CGKS_BC_INFLOW, CGKS_BC_OUTFLOW = range(4)
+
+_lib = None
+
+
+class CgksError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"cgks status {status}: {msg}")
+        self.status = status
+
+
+class cgks_problem(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+        ("x0", ctypes.c_double), ("x1", ctypes.c_double), ("y0", ctypes.c_double), ("y1", ctypes.c_double),
+        ("gamma", ctypes.c_double), ("cfl", ctypes.c_double),
+        ("bc", ctypes.c_int * 4), ("inflow", ctypes.c_double * 4),
+        ("eps_tau", ctypes.c_double), ("c_tau", ctypes.c_double), ("weno_eps", ctypes.c_double),
+    ]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libcgks.so (built by paper_2001_01570_gb300.build / __graft_entry__.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libcgks is not built ({path} missing): run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    vp, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+    L.cgks_create.argtypes = [ctypes.POINTER(cgks_problem), vp, ctypes.POINTER(vp)]
+    L.cgks_destroy.argtypes = [vp]
+    L.cgks_set_state.argtypes = [vp, vp, ctypes.c_int, ctypes.c_double]
+    L.cgks_get_state.argtypes = [vp, vp, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_long)]
+    L.cgks_step.argtypes = [vp, ctypes.c_int, ctypes.c_double, dp]
+    L.cgks_batch_step.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int]
+    L.cgks_step_profiled.argtypes = [vp, ctypes.c_int, dp]
+    for name in ("cgks_create", "cgks_destroy", "cgks_set_state", "cgks_get_state", "cgks_step", "cgks_batch_step",
+                 "cgks_step_profiled"):
+        getattr(L, name).restype = ctypes.c_int
+    L.cgks_status_string.argtypes = [ctypes.c_int]
+    L.cgks_status_string.restype = ctypes.c_char_p
+    L.cgks_last_error.restype = ctypes.c_char_p
+    L.cgks_last_launch_count.restype = ctypes.c_long
+    _lib = L
+    return L
+
+
+def _check(st):
+    if st != CGKS_OK:
+        L = load()
+        raise CgksError(st, L.cgks_last_error().decode())
+
+
+def make_problem(dim, nx, ny, x0, x1, y0=0.0, y1=1.0, gamma=1.4, cfl=0.5, bc=(0, 0, 0, 0),
+                 inflow=(1.0, 0.0, 0.0, 1.0), eps_tau=0.01, c_tau=1.0, weno_eps=1e-6) -> cgks_problem:
+    p = cgks_problem()
+    p.dim, p.nx, p.ny = int(dim), int(nx), int(ny)
+    p.x0, p.x1, p.y0, p.y1 = float(x0), float(x1), float(y0), float(y1)
+    p.gamma, p.cfl = float(gamma), float(cfl)
+    for k in range(4):
+        p.bc[k] = int(bc[k])
+        p.inflow[k] = float(inflow[k])
+    p.eps_tau, p.c_tau, p.weno_eps = float(eps_tau), float(c_tau), float(weno_eps)
+    return p
+
+
+def problem_from_spec(spec) -> cgks_problem:
+    """From a workloads.ProblemSpec."""
+    return make_problem(spec.dim, spec.nx, spec.ny if spec.dim == 2 else 1, spec.x0, spec.x1, spec.y0, spec.y1,
+                        spec.gamma, spec.cfl, spec.bc, spec.inflow, spec.eps_tau, spec.c_tau, spec.weno_eps)
+
+
+# ---------------------------------------------------------------------------- C-ABI names
+def cgks_create(problem: cgks_problem, stream=None):
+    L = load()
+    out = ctypes.c_void_p()
+    _check(L.cgks_create(ctypes.byref(problem), ctypes.c_void_p(stream or 0), ctypes.byref(out)))
+    return out
+
+
+def cgks_destroy(solver):
+    _check(load().cgks_destroy(solver))
+
+
+def _ptr(buf):
+    if hasattr(buf, "data_ptr"):
+        return ctypes.c_void_p(buf.data_ptr()), 1
+    arr = buf
+    if not (isinstance(arr, np.ndarray) and arr.dtype == np.float64 and arr.flags.c_contiguous):
+        raise TypeError("host planes must be a C-contiguous float64 numpy array")
+    return ctypes.c_void_p(arr.ctypes.data), 0
+
+
+def cgks_set_state(solver, planes, t=0.0):
+    p, dev = _ptr(planes)
+    _check(load().cgks_set_state(solver, p, dev, float(t)))
+
+
+def cgks_get_state(solver, planes=None):
+    """Copy the state into ``planes`` (numpy array or CUDA tensor); returns (t, steps)."""
+    t = ctypes.c_double()
+    steps = ctypes.c_long()
+    if planes is None:
+        p, dev = ctypes.c_void_p(0), 0
+    else:
+        p, dev = _ptr(planes)
+    _check(load().cgks_get_state(solver, p, dev, ctypes.byref(t), ctypes.byref(steps)))
+    return t.value, steps.value
+
+
+def cgks_step(solver, nsteps, t_end=0.0):
+    t = ctypes.c_double()
+    _check(load().cgks_step(solver, int(nsteps), float(t_end), ctypes.byref(t)))
+    return t.value
+
+
+def cgks_batch_step(solvers, nsteps):
+    arr = (ctypes.c_void_p * len(solvers))(*[s.value if isinstance(s, ctypes.c_void_p) else s for s in solvers])
+    _check(load().cgks_batch_step(arr, len(solvers), int(nsteps)))
+
+
+def cgks_step_profiled(solver, nsteps):
+    """Returns average per-launch milliseconds of (step-begin, stage 1, stage 2, step-end)."""
+    ms = (ctypes.c_double * 4)()
+    _check(load().cgks_step_profiled(solver, int(nsteps), ms))
+    return list(ms)
+
+
+def cgks_last_launch_count() -> int:
+    return int(load().cgks_last_launch_count())
+
+
+# ---------------------------------------------------------------------------- convenience
+class Solver:
+    """Owns one cgks_solver handle."""
+
+    def __init__(self, problem: cgks_problem, stream=None):
+        self.problem = problem
+        self.handle = cgks_create(problem, stream)
+        self.dim = problem.dim
+        self.nx = problem.nx
+        self.ny = problem.ny if problem.dim == 2 else 1
+
+    @property
+    def shape(self):
+        return (12, self.ny, self.nx) if self.dim == 2 else (6, self.nx)
+
+    def set_state(self, planes, t=0.0):
+        cgks_set_state(self.handle, planes, t)
+
+    def get_state(self):
+        out = np.empty(self.shape, dtype=np.float64)
+        t, steps = cgks_get_state(self.handle, out)
+        return out, t, steps
+
+    def step(self, nsteps, t_end=0.0):
+        return cgks_step(self.handle, nsteps, t_end)
+
+    def close(self):
+        if self.handle is not None:
+            cgks_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

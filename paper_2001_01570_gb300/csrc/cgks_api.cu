@@ -1,0 +1,427 @@
+// cgks_api.cu -- host runtime behind the C ABI of include/cgks.h: solver
+// objects (device planes, control block, tile queue), state transfer, the
+// plain step loop and the batched CUDA-graph step over many grids.
+#include "cgks_internal.h"
+#include "../../include/cgks.h"
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+using namespace cgks;
+
+struct cgks_solver {
+    cgks_problem prob;
+    int nx = 0, ny = 0;
+    int device = 0;
+    int nsm = 1;
+    cudaStream_t stream = nullptr;
+    double* d_planes = nullptr;   // 3 x 12 planes: buf0, buf1, ws
+    double* d_stage1d = nullptr;  // 6-plane staging for dim 1
+    Ctrl* d_ctrl = nullptr;
+    GridDev host_desc;
+    GridDev* d_desc = nullptr;
+    TileRef* d_tiles = nullptr;
+    int ntiles = 0;
+    int shape = TILE_16x8;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+thread_local long g_last_launches = 0;
+
+cgks_status fail(cgks_status st, const std::string& msg)
+{
+    g_last_error = msg;
+    return st;
+}
+
+cgks_status cuda_fail(cudaError_t e, const char* where)
+{
+    g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    return CGKS_E_CUDA;
+}
+
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+    } while (0)
+
+std::vector<TileRef> make_tiles(int nx, int ny, int shape, int grid)
+{
+    const int tw = tile_w(shape), th = tile_h(shape);
+    std::vector<TileRef> t;
+    for (int y0 = 0; y0 < ny; y0 += th)
+        for (int x0 = 0; x0 < nx; x0 += tw) t.push_back(TileRef{grid, x0, y0, 0});
+    return t;
+}
+
+cgks_status validate(const cgks_problem* p)
+{
+    if (!p) return fail(CGKS_E_INVAL, "problem is NULL");
+    if (p->dim != 1 && p->dim != 2) return fail(CGKS_E_INVAL, "dim must be 1 or 2");
+    const int ny = p->dim == 1 ? 1 : p->ny;
+    if (p->nx < 1 || ny < 1) return fail(CGKS_E_INVAL, "nx and ny must be >= 1");
+    if ((long long)p->nx * ny > (1ll << 31)) return fail(CGKS_E_INVAL, "grid too large");
+    if (!(p->x1 > p->x0) || (p->dim == 2 && !(p->y1 > p->y0))) return fail(CGKS_E_INVAL, "empty domain");
+    if (!(p->gamma > 1.0) || !(p->gamma < 3.0)) return fail(CGKS_E_INVAL, "gamma out of range");
+    if (!(p->cfl > 0.0)) return fail(CGKS_E_INVAL, "cfl must be > 0");
+    if (!(p->eps_tau >= 0.0) || !(p->c_tau >= 0.0) || !(p->weno_eps > 0.0))
+        return fail(CGKS_E_INVAL, "eps_tau, c_tau must be >= 0 and weno_eps > 0");
+    const int nb = p->dim == 1 ? 2 : 4;
+    for (int k = 0; k < nb; ++k) {
+        if (p->bc[k] < CGKS_BC_PERIODIC || p->bc[k] > CGKS_BC_OUTFLOW) return fail(CGKS_E_INVAL, "unknown bc");
+        const int n = k < 2 ? p->nx : ny;
+        if (p->bc[k] == CGKS_BC_REFLECT && n < 2) return fail(CGKS_E_INVAL, "a reflecting side needs >= 2 cells");
+    }
+    if ((p->bc[0] == CGKS_BC_PERIODIC) != (p->bc[1] == CGKS_BC_PERIODIC))
+        return fail(CGKS_E_INVAL, "periodic x needs both x sides periodic");
+    if (p->dim == 2 && ((p->bc[2] == CGKS_BC_PERIODIC) != (p->bc[3] == CGKS_BC_PERIODIC)))
+        return fail(CGKS_E_INVAL, "periodic y needs both y sides periodic");
+    for (int k = 0; k < nb; ++k)
+        if (p->bc[k] == CGKS_BC_INFLOW && (!(p->inflow[0] > 0.0) || !(p->inflow[3] > 0.0)))
+            return fail(CGKS_E_INVAL, "inflow state needs rho > 0 and p > 0");
+    return CGKS_OK;
+}
+
+cgks_status read_ctrl(cgks_solver* s, Ctrl* c)
+{
+    CK(cudaMemcpyAsync(c, s->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return CGKS_OK;
+}
+
+int pick_shape(const cgks_problem& p)
+{
+    return p.dim == 1 ? TILE_64x1 : TILE_16x8;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* cgks_status_string(cgks_status st)
+{
+    switch (st) {
+    case CGKS_OK: return "ok";
+    case CGKS_E_INVAL: return "invalid argument";
+    case CGKS_E_NOMEM: return "out of memory";
+    case CGKS_E_BUDGET: return "request can never fit the memory budget";
+    case CGKS_E_CUDA: return "CUDA error";
+    case CGKS_E_NONPHYSICAL: return "non-physical state (rho <= 0, p <= 0 or NaN)";
+    case CGKS_E_TIMEOUT: return "timeout";
+    case CGKS_E_BUSY: return "busy";
+    case CGKS_E_NOTFOUND: return "not found";
+    }
+    return "unknown status";
+}
+
+const char* cgks_last_error(void) { return g_last_error.c_str(); }
+
+long cgks_last_launch_count(void) { return g_last_launches; }
+
+cgks_status cgks_create(const cgks_problem* prob, void* cuda_stream, cgks_solver** out)
+{
+    if (!out) return fail(CGKS_E_INVAL, "out is NULL");
+    *out = nullptr;
+    cgks_status st = validate(prob);
+    if (st != CGKS_OK) return st;
+    cgks_solver* s = new (std::nothrow) cgks_solver();
+    if (!s) return fail(CGKS_E_NOMEM, "host allocation failed");
+    s->prob = *prob;
+    s->nx = prob->nx;
+    s->ny = prob->dim == 1 ? 1 : prob->ny;
+    s->stream = (cudaStream_t)cuda_stream;
+    s->shape = pick_shape(*prob);
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, s->device);
+    const size_t PL = (size_t)s->nx * s->ny;
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_planes, 3 * 12 * PL * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_ctrl, sizeof(Ctrl));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_desc, sizeof(GridDev));
+    if (e == cudaSuccess && prob->dim == 1) e = cudaMalloc(&s->d_stage1d, 6 * PL * sizeof(double));
+    std::vector<TileRef> tiles = make_tiles(s->nx, s->ny, s->shape, 0);
+    s->ntiles = (int)tiles.size();
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_tiles, tiles.size() * sizeof(TileRef));
+    if (e != cudaSuccess) {
+        cgks_destroy(s);
+        return e == cudaErrorMemoryAllocation ? fail(CGKS_E_NOMEM, "device allocation failed")
+                                              : cuda_fail(e, "cgks_create");
+    }
+    GridDev& G = s->host_desc;
+    memset(&G, 0, sizeof(G));
+    G.buf[0] = s->d_planes;
+    G.buf[1] = s->d_planes + 12 * PL;
+    G.ws = s->d_planes + 24 * PL;
+    G.ctrl = s->d_ctrl;
+    G.nx = s->nx;
+    G.ny = s->ny;
+    G.dim = prob->dim;
+    for (int k = 0; k < 4; ++k) G.bc[k] = (prob->dim == 1 && k >= 2) ? CGKS_BC_PERIODIC : prob->bc[k];
+    G.dx = (prob->x1 - prob->x0) / prob->nx;
+    G.dy = prob->dim == 1 ? 1.0 : (prob->y1 - prob->y0) / prob->ny;
+    G.inv_dx = 1.0 / G.dx;
+    G.inv_dy = 1.0 / G.dy;
+    G.gamma = prob->gamma;
+    // internal degrees of freedom of the 2D Maxwellian; a 1D problem runs as a
+    // y-uniform 2D one, whose extra velocity direction plays the role of the
+    // additional internal degree of freedom of the 1D model
+    G.K = (4.0 - 2.0 * prob->gamma) / (prob->gamma - 1.0);
+    G.cfl = prob->cfl;
+    G.eps_tau = prob->eps_tau;
+    G.c_tau = prob->c_tau;
+    G.weno_eps = prob->weno_eps;
+    {
+        const double r = prob->inflow[0], u = prob->inflow[1], v = prob->dim == 1 ? 0.0 : prob->inflow[2];
+        const double p = prob->inflow[3];
+        G.inflow[0] = r;
+        G.inflow[1] = r * u;
+        G.inflow[2] = r * v;
+        G.inflow[3] = p / (prob->gamma - 1.0) + 0.5 * r * (u * u + v * v);
+    }
+    e = cudaMemcpyAsync(s->d_desc, &G, sizeof(GridDev), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->d_tiles, tiles.data(), tiles.size() * sizeof(TileRef), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = launch_set_ctrl(s->d_ctrl, 0.0, 0.0, -1, 1, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) {
+        cgks_destroy(s);
+        return cuda_fail(e, "cgks_create");
+    }
+    *out = s;
+    return CGKS_OK;
+}
+
+cgks_status cgks_destroy(cgks_solver* s)
+{
+    if (!s) return fail(CGKS_E_INVAL, "solver is NULL");
+    if (s->d_planes || s->d_ctrl) cudaStreamSynchronize(s->stream);
+    cudaFree(s->d_planes);
+    cudaFree(s->d_stage1d);
+    cudaFree(s->d_ctrl);
+    cudaFree(s->d_desc);
+    cudaFree(s->d_tiles);
+    delete s;
+    return CGKS_OK;
+}
+
+cgks_status cgks_set_state(cgks_solver* s, const double* planes, int on_device, double t)
+{
+    if (!s || !planes) return fail(CGKS_E_INVAL, "NULL argument");
+    const size_t PL = (size_t)s->nx * s->ny;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(launch_set_ctrl(s->d_ctrl, t, 0.0, -1, 1, s->stream));
+    if (s->prob.dim == 1) {
+        CK(cudaMemcpyAsync(s->d_stage1d, planes, 6 * PL * sizeof(double), kind, s->stream));
+        CK(launch_expand1d(s->d_stage1d, s->host_desc.buf[0], s->nx, s->stream));
+    } else {
+        CK(cudaMemcpyAsync(s->host_desc.buf[0], planes, 12 * PL * sizeof(double), kind, s->stream));
+    }
+    CK(launch_cfl(s->d_desc, 0, s->host_desc, s->stream));
+    if (!on_device) CK(cudaStreamSynchronize(s->stream));
+    return CGKS_OK;
+}
+
+cgks_status cgks_get_state(cgks_solver* s, double* planes, int on_device, double* t, long* steps)
+{
+    if (!s) return fail(CGKS_E_INVAL, "solver is NULL");
+    Ctrl c;
+    cgks_status st = read_ctrl(s, &c);
+    if (st != CGKS_OK) return st;
+    if (t) *t = c.t;
+    if (steps) *steps = (long)c.steps;
+    if (planes) {
+        const size_t PL = (size_t)s->nx * s->ny;
+        const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        const double* cur = s->host_desc.buf[c.par & 1];
+        if (s->prob.dim == 1) {
+            CK(launch_compress1d(cur, s->d_stage1d, s->nx, s->stream));
+            CK(cudaMemcpyAsync(planes, s->d_stage1d, 6 * PL * sizeof(double), kind, s->stream));
+        } else {
+            CK(cudaMemcpyAsync(planes, cur, 12 * PL * sizeof(double), kind, s->stream));
+        }
+        CK(cudaStreamSynchronize(s->stream));
+    }
+    if (c.status & CGKS_E_NONPHYSICAL) return fail(CGKS_E_NONPHYSICAL, "non-physical state met; last valid state kept");
+    return CGKS_OK;
+}
+
+static cgks_status enqueue_steps(cgks_solver* s, int nsteps, long* launches)
+{
+    const int nblocks = s->ntiles < s->nsm ? s->ntiles : s->nsm;
+    for (int k = 0; k < nsteps; ++k) {
+        CK(launch_begin_step(s->d_desc, 1, s->stream));
+        CK(launch_stage(s->shape, 1, s->d_desc, s->d_tiles, s->ntiles, nblocks, s->stream));
+        CK(launch_stage(s->shape, 2, s->d_desc, s->d_tiles, s->ntiles, nblocks, s->stream));
+        CK(launch_end_step(s->d_desc, 1, s->stream));
+        *launches += 4;
+    }
+    return CGKS_OK;
+}
+
+cgks_status cgks_step(cgks_solver* s, int nsteps, double t_end, double* t_out)
+{
+    if (!s || nsteps < 0) return fail(CGKS_E_INVAL, "bad arguments");
+    g_last_launches = 0;
+    long launches = 0;
+    CK(launch_set_ctrl(s->d_ctrl, 0.0, t_end > 0.0 ? t_end : 0.0, -1, 0, s->stream));
+    launches += 1;
+    const int chunk = t_end > 0.0 ? 32 : nsteps;
+    int done_steps = 0;
+    Ctrl c;
+    while (done_steps < nsteps) {
+        const int k = (nsteps - done_steps) < chunk ? (nsteps - done_steps) : chunk;
+        cgks_status st = enqueue_steps(s, k, &launches);
+        if (st != CGKS_OK) return st;
+        done_steps += k;
+        if (t_end > 0.0 && done_steps < nsteps) {
+            st = read_ctrl(s, &c);
+            if (st != CGKS_OK) return st;
+            if (c.done) break;
+        }
+    }
+    g_last_launches = launches;
+    cgks_status st = read_ctrl(s, &c);
+    if (st != CGKS_OK) return st;
+    if (t_out) *t_out = c.t;
+    if (c.status & CGKS_E_NONPHYSICAL) return fail(CGKS_E_NONPHYSICAL, "non-physical state met; last valid state kept");
+    return CGKS_OK;
+}
+
+cgks_status cgks_step_profiled(cgks_solver* s, int nsteps, double stage_ms[4])
+{
+    if (!s || nsteps <= 0 || !stage_ms) return fail(CGKS_E_INVAL, "bad arguments");
+    g_last_launches = 0;
+    CK(launch_set_ctrl(s->d_ctrl, 0.0, 0.0, -1, 0, s->stream));
+    std::vector<cudaEvent_t> ev((size_t)nsteps * 5);
+    for (auto& e : ev) CK(cudaEventCreate(&e));
+    const int nblocks = s->ntiles < s->nsm ? s->ntiles : s->nsm;
+    for (int k = 0; k < nsteps; ++k) {
+        cudaEvent_t* e = &ev[(size_t)k * 5];
+        CK(cudaEventRecord(e[0], s->stream));
+        CK(launch_begin_step(s->d_desc, 1, s->stream));
+        CK(cudaEventRecord(e[1], s->stream));
+        CK(launch_stage(s->shape, 1, s->d_desc, s->d_tiles, s->ntiles, nblocks, s->stream));
+        CK(cudaEventRecord(e[2], s->stream));
+        CK(launch_stage(s->shape, 2, s->d_desc, s->d_tiles, s->ntiles, nblocks, s->stream));
+        CK(cudaEventRecord(e[3], s->stream));
+        CK(launch_end_step(s->d_desc, 1, s->stream));
+        CK(cudaEventRecord(e[4], s->stream));
+    }
+    CK(cudaStreamSynchronize(s->stream));
+    double acc[4] = {0, 0, 0, 0};
+    for (int k = 0; k < nsteps; ++k)
+        for (int q = 0; q < 4; ++q) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, ev[(size_t)k * 5 + q], ev[(size_t)k * 5 + q + 1]));
+            acc[q] += ms;
+        }
+    for (auto& e : ev) cudaEventDestroy(e);
+    for (int q = 0; q < 4; ++q) stage_ms[q] = acc[q] / nsteps;
+    g_last_launches = 1 + 4L * nsteps;
+    Ctrl c;
+    cgks_status st = read_ctrl(s, &c);
+    if (st != CGKS_OK) return st;
+    if (c.status & CGKS_E_NONPHYSICAL) return fail(CGKS_E_NONPHYSICAL, "non-physical state met; last valid state kept");
+    return CGKS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batched stepping: one persistent launch per stage over the tiles of all
+// grids, captured once into a CUDA graph per batch composition and replayed
+namespace {
+struct BatchPlan {
+    std::vector<cgks_solver*> solvers;
+    int shape = TILE_16x8;
+    GridDev* d_grids = nullptr;
+    TileRef* d_tiles = nullptr;
+    int ntiles = 0;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t stream = nullptr;
+};
+std::mutex g_batch_mu;
+std::map<std::vector<cgks_solver*>, BatchPlan*> g_batch_plans;
+
+cgks_status build_plan(cgks_solver* const* solvers, int n, BatchPlan** out)
+{
+    std::vector<cgks_solver*> key(solvers, solvers + n);
+    auto it = g_batch_plans.find(key);
+    if (it != g_batch_plans.end()) { *out = it->second; return CGKS_OK; }
+    BatchPlan* bp = new BatchPlan();
+    bp->solvers = key;
+    bp->stream = solvers[0]->stream;
+    bp->shape = solvers[0]->prob.dim == 1 ? TILE_64x1 : TILE_16x8;
+    std::vector<GridDev> descs;
+    std::vector<TileRef> tiles;
+    for (int g = 0; g < n; ++g) {
+        descs.push_back(solvers[g]->host_desc);
+        std::vector<TileRef> t = make_tiles(solvers[g]->nx, solvers[g]->ny, bp->shape, g);
+        tiles.insert(tiles.end(), t.begin(), t.end());
+    }
+    bp->ntiles = (int)tiles.size();
+    CK(cudaMalloc(&bp->d_grids, descs.size() * sizeof(GridDev)));
+    CK(cudaMalloc(&bp->d_tiles, tiles.size() * sizeof(TileRef)));
+    CK(cudaMemcpyAsync(bp->d_grids, descs.data(), descs.size() * sizeof(GridDev), cudaMemcpyHostToDevice, bp->stream));
+    CK(cudaMemcpyAsync(bp->d_tiles, tiles.data(), tiles.size() * sizeof(TileRef), cudaMemcpyHostToDevice, bp->stream));
+    CK(cudaStreamSynchronize(bp->stream));
+    // make sure the kernels' shared-memory attributes are set before capture
+    CK(launch_stage(bp->shape, 1, bp->d_grids, bp->d_tiles, 0, 1, bp->stream));
+    CK(launch_stage(bp->shape, 2, bp->d_grids, bp->d_tiles, 0, 1, bp->stream));
+    const int nsm = solvers[0]->nsm;
+    const int nblocks = bp->ntiles < nsm ? bp->ntiles : nsm;
+    cudaStream_t cap;
+    CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t graph;
+    CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = launch_begin_step(bp->d_grids, n, cap);
+    if (e == cudaSuccess) e = launch_stage(bp->shape, 1, bp->d_grids, bp->d_tiles, bp->ntiles, nblocks, cap);
+    if (e == cudaSuccess) e = launch_stage(bp->shape, 2, bp->d_grids, bp->d_tiles, bp->ntiles, nblocks, cap);
+    if (e == cudaSuccess) e = launch_end_step(bp->d_grids, n, cap);
+    cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess) return cuda_fail(e, "batch capture");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "batch capture end");
+    e = cudaGraphInstantiate(&bp->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    g_batch_plans[key] = bp;
+    *out = bp;
+    return CGKS_OK;
+}
+}  // namespace
+
+cgks_status cgks_batch_step(cgks_solver* const* solvers, int n, int nsteps)
+{
+    if (!solvers || n <= 0 || nsteps < 0) return fail(CGKS_E_INVAL, "bad arguments");
+    for (int g = 0; g < n; ++g) {
+        if (!solvers[g]) return fail(CGKS_E_INVAL, "NULL solver in batch");
+        if (solvers[g]->prob.dim != solvers[0]->prob.dim) return fail(CGKS_E_INVAL, "mixed dims in one batch");
+    }
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    g_last_launches = 0;
+    BatchPlan* bp = nullptr;
+    cgks_status st = build_plan(solvers, n, &bp);
+    if (st != CGKS_OK) return st;
+    long launches = 0;
+    for (int g = 0; g < n; ++g) {
+        CK(launch_set_ctrl(solvers[g]->d_ctrl, 0.0, 0.0, -1, 0, bp->stream));
+        launches += 1;
+    }
+    for (int k = 0; k < nsteps; ++k) {
+        CK(cudaGraphLaunch(bp->exec, bp->stream));
+        launches += 4;
+    }
+    CK(cudaStreamSynchronize(bp->stream));
+    g_last_launches = launches;
+    return CGKS_OK;
+}
+
+}  // extern "C"

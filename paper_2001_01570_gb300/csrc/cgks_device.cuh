@@ -1,0 +1,437 @@
+// cgks_device.cuh -- device arithmetic of the compact 8th-order gas-kinetic scheme
+// (Zhao, Ji, Shyy, Xu, arXiv 2001.01570) for sm_103a.  Everything is FP64.
+//
+// On GB300 the FP64 pipe issues about one warp instruction per 16 SM cycles, so
+// the code below is written to minimise FP64 instruction count:
+//   * WENO smoothness indicators as quadratic forms in first differences, with
+//     the 19 pair products shared by the left and the mirrored right stencil;
+//   * WENO-Z weights normalised with one reciprocal (leave-one-out products);
+//   * the Euler flux and its time derivative in closed form; only the terms that
+//     genuinely need velocity-space moments (the tau-terms and the half-line
+//     moments of the non-equilibrium states) use them;
+//   * the flux and its time derivative over [0, dt] taken from closed-form
+//     window coefficients instead of differencing two time integrals;
+//   * Euler time derivatives W_t, W_tt by Cauchy-Kowalevski in primitive form.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace cgks {
+
+// ------------------------------------------------------------------------
+// Sec. 3.2, Eq. (recons-8th-val): linear compact reconstruction at x_{i+1/2}
+// from Q_{i-1..i+2} (a, b, c, d) and h*Q' (A, B, C, D).
+__device__ __forceinline__ void linear_recon(double a, double b, double c, double d,
+                                             double A, double B, double C, double D,
+                                             double& v, double& hvx, double& h2vxx)
+{
+    v = (25.0 * (a + d) + 185.0 * (b + c) + 6.0 * (A - D) + 102.0 * (B - C)) * (1.0 / 420.0);
+    hvx = (270.0 * (c - b) + 14.0 * (d - a) - 3.0 * (A + D) - 99.0 * (B + C)) * (1.0 / 108.0);
+    h2vxx = (4.0 * ((b + c) - (a + d)) - (A - D) - 9.0 * (B - C)) * 0.25;
+}
+
+// ------------------------------------------------------------------------
+// Sec. 3.3: nonlinear compact reconstruction.  With d1 = b-a, d2 = c-b,
+// d3 = d-c the candidate values q_k - b, the interface slopes h*q_k'(x_{i+1/2})
+// and the smoothness indicators beta_k (beta_1 taken from the cubic on
+// {Q_i-1, Q_i, Q_i+1, Q'_i-1}) follow from the sub-stencil definitions; the
+// mirrored (right) stencil is d1 <-> d3, A <-> D, B <-> C with all signs flipped,
+// which leaves every pair product unchanged.
+struct PairProducts {
+    double d11, d12, d22, d23, d33, AA, Ad1, Ad2, AB, BB, Bd1, Bd2, CC, CD, Cd2, Cd3, DD, Dd2, Dd3;
+};
+
+__device__ __forceinline__ void pair_products(double d1, double d2, double d3, double A, double B, double C,
+                                              double D, PairProducts& p)
+{
+    p.d11 = d1 * d1; p.d12 = d1 * d2; p.d22 = d2 * d2; p.d23 = d2 * d3; p.d33 = d3 * d3;
+    p.AA = A * A; p.Ad1 = A * d1; p.Ad2 = A * d2; p.AB = A * B; p.BB = B * B; p.Bd1 = B * d1; p.Bd2 = B * d2;
+    p.CC = C * C; p.CD = C * D; p.Cd2 = C * d2; p.Cd3 = C * d3; p.DD = D * D; p.Dd2 = D * d2; p.Dd3 = D * d3;
+}
+
+// left-biased interface value and h*slope.  The argument order names the
+// stencil as seen from the side being reconstructed (for the right side the
+// caller passes the mirrored quantities).  Products: (x11, x12, x22, x23, x33)
+// are the difference products in that orientation, (aa, ad1, ad2, ab, bb, bd1,
+// bd2) the products of the two slopes on the near side, (cc, cd, cd2, cd3, dd,
+// dd2, dd3) those on the far side.
+__device__ __forceinline__ void weno_side(double base, double d1, double d2, double d3,
+                                          double A, double B, double C, double D,
+                                          double x11, double x12, double x22, double x23, double x33,
+                                          double aa, double ad1, double ad2, double ab, double bb, double bd1, double bd2,
+                                          double cc, double cd, double cd2, double cd3, double dd, double dd2, double dd3,
+                                          double eps, double& val, double& hslope)
+{
+    // smoothness indicators, Eq. (smooth-indicator)
+    const double b0 = (16.0 / 3.0) * aa - (38.0 / 3.0) * ad1 + (25.0 / 3.0) * x11;
+    const double b1 = (801.0 / 80.0) * aa - (2443.0 / 80.0) * ad1 + (761.0 / 80.0) * ad2
+                      + (23627.0 / 960.0) * x11 - (7769.0 / 480.0) * x12 + (3443.0 / 960.0) * x22;
+    const double b2 = (1641.0 / 80.0) * dd + (2401.0 / 80.0) * dd2 - (5523.0 / 80.0) * dd3
+                      + (12683.0 / 960.0) * x22 - (25169.0 / 480.0) * x23 + (56387.0 / 960.0) * x33;
+    const double b3 = (4.0 / 3.0) * x11 - (5.0 / 3.0) * x12 + (4.0 / 3.0) * x22;
+    const double b4 = (10.0 / 3.0) * x22 - (11.0 / 3.0) * x23 + (4.0 / 3.0) * x33;
+    const double b5 = (4405.0 / 28.0) * aa + (4405.0 / 7.0) * ab - (110433.0 / 140.0) * ad1 - (21717.0 / 140.0) * ad2
+                      + (93707.0 / 140.0) * bb - (226333.0 / 140.0) * bd1 - (48901.0 / 140.0) * bd2
+                      + (209917.0 / 210.0) * x11 + (17063.0 / 42.0) * x12 + (5153.0 / 105.0) * x22;
+    const double b6 = (265067.0 / 140.0) * cc + (11104.0 / 7.0) * cd - (160551.0 / 140.0) * cd2 - (592783.0 / 140.0) * cd3
+                      + (9529.0 / 28.0) * dd - (65327.0 / 140.0) * dd2 - (252323.0 / 140.0) * dd3
+                      + (38131.0 / 210.0) * x22 + (52763.0 / 42.0) * x23 + (251276.0 / 105.0) * x33;
+    // global reference Z_ref, Eq. (tau)
+    const double Z = fabs(3.0 * b0 - 2.0 * b4 - b3);
+    // WENO-Z: alpha_k = d_k (beta_k + eps + Z) / (beta_k + eps); normalise with
+    // one reciprocal by multiplying numerators by prod_{j != k}(beta_j + eps)
+    const double e0 = b0 + eps, e1 = b1 + eps, e2 = b2 + eps, e3 = b3 + eps, e4 = b4 + eps, e5 = b5 + eps, e6 = b6 + eps;
+    const double p01 = e0 * e1, p012 = p01 * e2, p0123 = p012 * e3, p01234 = p0123 * e4;
+    const double s56 = e5 * e6, s456 = e4 * s56, s3456 = e3 * s456, s23456 = e2 * s3456;
+    const double L0 = e1 * s23456;
+    const double L1 = e0 * s23456;
+    const double L2 = p01 * s3456;
+    const double L3 = p012 * s456;
+    const double L4 = p0123 * s56;
+    const double L5 = p01234 * e6;
+    const double L6 = p01234 * e5;
+    const double n0 = (3.0 / 98.0) * (e0 + Z) * L0;
+    const double n1 = (5.0 / 98.0) * (e1 + Z) * L1;
+    const double n2 = (4.0 / 49.0) * (e2 + Z) * L2;
+    const double n3 = (7.0 / 98.0) * (e3 + Z) * L3;
+    const double n4 = (7.0 / 98.0) * (e4 + Z) * L4;
+    const double n5 = (17.0 / 49.0) * (e5 + Z) * L5;
+    const double n6 = (17.0 / 49.0) * (e6 + Z) * L6;
+    const double inv = 1.0 / ((n0 + n1) + (n2 + n3) + (n4 + n5) + n6);
+    // candidate values minus Q_i, Eq. (sub-stencil)
+    const double q0 = (7.0 / 6.0) * d1 - (2.0 / 3.0) * A;
+    const double q13 = (1.0 / 6.0) * d1 + (1.0 / 3.0) * d2;
+    const double q2 = 0.25 * D + (19.0 / 24.0) * d2 - (13.0 / 24.0) * d3;
+    const double q4 = (2.0 / 3.0) * d2 - (1.0 / 6.0) * d3;
+    const double q5 = 0.1 * A + 0.7 * B - (1.0 / 3.0) * d1 + (1.0 / 30.0) * d2;
+    const double q6 = (29.0 / 30.0) * d2 + (1.0 / 3.0) * d3 - 0.7 * C - 0.1 * D;
+    // candidate slopes h q_k'(x_{i+1/2})
+    const double s0 = 3.0 * d1 - 2.0 * A;
+    const double s2 = 0.875 * d2 + 0.375 * d3 - 0.25 * D;
+    const double s5 = 0.5 * A + 1.5 * B - 1.5 * d1 + 0.5 * d2;
+    const double s6 = 1.5 * C + 0.5 * D + 0.5 * d2 - 1.5 * d3;
+    const double nv = n0 * q0 + (n1 + n3) * q13 + n2 * q2 + n4 * q4 + n5 * q5 + n6 * q6;
+    const double ns = n0 * s0 + (n1 + n3 + n4) * d2 + n2 * s2 + n5 * s5 + n6 * s6;
+    val = base + nv * inv;
+    hslope = ns * inv;
+}
+
+// left and right non-equilibrium values and h*slopes at x_{i+1/2}
+__device__ __forceinline__ void weno_pair(double a, double b, double c, double d, double A, double B, double C,
+                                          double D, double eps, double& vl, double& sl, double& vr, double& sr)
+{
+    const double d1 = b - a, d2 = c - b, d3 = d - c;
+    PairProducts p;
+    pair_products(d1, d2, d3, A, B, C, D, p);
+    weno_side(b, d1, d2, d3, A, B, C, D, p.d11, p.d12, p.d22, p.d23, p.d33,
+              p.AA, p.Ad1, p.Ad2, p.AB, p.BB, p.Bd1, p.Bd2, p.CC, p.CD, p.Cd2, p.Cd3, p.DD, p.Dd2, p.Dd3,
+              eps, vl, sl);
+    // mirrored stencil: (d1,d2,d3) -> -(d3,d2,d1), (A,B,C,D) -> -(D,C,B,A); products unchanged
+    double s;
+    weno_side(c, -d3, -d2, -d1, -D, -C, -B, -A, p.d33, p.d23, p.d22, p.d12, p.d11,
+              p.DD, p.Dd3, p.Dd2, p.CD, p.CC, p.Cd3, p.Cd2, p.BB, p.AB, p.Bd2, p.Bd1, p.AA, p.Ad2, p.Ad1,
+              eps, vr, s);
+    sr = -s;
+}
+
+// ------------------------------------------------------------------------
+// Sec. 2.1: Maxwellian velocity moments.  theta = p/rho = 1/(2 lambda).
+struct Moments {
+    double u[7];     // <u^n>, n = 0..6 (whole line or half line)
+    double v[6];     // <v^n>, n = 0..5 (whole line)
+    double x1, x2;   // <xi^2>, <xi^4>
+};
+
+__device__ __forceinline__ void moments_tail(Moments& m, double U, double V, double theta, double K)
+{
+    const double t2 = 2.0 * theta, t3 = 3.0 * theta, t4 = 4.0 * theta, t5 = 5.0 * theta;
+    m.u[2] = U * m.u[1] + theta * m.u[0];
+    m.u[3] = U * m.u[2] + t2 * m.u[1];
+    m.u[4] = U * m.u[3] + t3 * m.u[2];
+    m.u[5] = U * m.u[4] + t4 * m.u[3];
+    m.u[6] = U * m.u[5] + t5 * m.u[4];
+    m.v[0] = 1.0;
+    m.v[1] = V;
+    m.v[2] = V * V + theta;
+    m.v[3] = V * m.v[2] + t2 * V;
+    m.v[4] = V * m.v[3] + t3 * m.v[2];
+    m.v[5] = V * m.v[4] + t4 * m.v[3];
+    m.x1 = K * theta;
+    m.x2 = K * (K + 2.0) * theta * theta;
+}
+
+// <u^A v^B psi>
+template <int A, int B>
+__device__ __forceinline__ void psi_uv(const Moments& m, double o[4])
+{
+    const double base = m.u[A] * m.v[B];
+    o[0] = base;
+    o[1] = m.u[A + 1] * m.v[B];
+    o[2] = m.u[A] * m.v[B + 1];
+    o[3] = 0.5 * (m.u[A + 2] * m.v[B] + m.u[A] * m.v[B + 2] + base * m.x1);
+}
+
+// <u^A v^B psi (a . psi)>
+template <int A, int B>
+__device__ __forceinline__ void a_psi_uv(const Moments& m, const double a[4], double o[4])
+{
+    double t0[4], t1[4], t2[4], t3[4], t4[4];
+    psi_uv<A, B>(m, t0);
+    psi_uv<A + 1, B>(m, t1);
+    psi_uv<A, B + 1>(m, t2);
+    psi_uv<A + 2, B>(m, t3);
+    psi_uv<A, B + 2>(m, t4);
+    // <u^A v^B xi^2 psi>
+    const double base = m.u[A] * m.v[B];
+    const double t5_0 = base * m.x1;
+    const double t5_1 = m.u[A + 1] * m.v[B] * m.x1;
+    const double t5_2 = m.u[A] * m.v[B + 1] * m.x1;
+    const double t5_3 = 0.5 * ((m.u[A + 2] * m.v[B] + m.u[A] * m.v[B + 2]) * m.x1 + base * m.x2);
+    const double h = 0.5 * a[3];
+    o[0] = a[0] * t0[0] + a[1] * t1[0] + a[2] * t2[0] + h * (t3[0] + t4[0] + t5_0);
+    o[1] = a[0] * t0[1] + a[1] * t1[1] + a[2] * t2[1] + h * (t3[1] + t4[1] + t5_1);
+    o[2] = a[0] * t0[2] + a[1] * t1[2] + a[2] * t2[2] + h * (t3[2] + t4[2] + t5_2);
+    o[3] = a[0] * t0[3] + a[1] * t1[3] + a[2] * t2[3] + h * (t3[3] + t4[3] + t5_3);
+}
+
+// micro-slope coefficients a with <psi psi^T> a = b for a Maxwellian
+// (closed form of the 4x4 moment system)
+struct SlopeCtx { double U, V, Bm, inv_theta, c4; };
+
+__device__ __forceinline__ void slope_ctx(double U, double V, double theta, double inv_theta, double K, SlopeCtx& s)
+{
+    s.U = U; s.V = V;
+    s.Bm = U * U + V * V + (K + 2.0) * theta;
+    s.inv_theta = inv_theta;
+    s.c4 = inv_theta * inv_theta / (K + 2.0);
+}
+
+__device__ __forceinline__ void micro_slope(const SlopeCtx& s, const double b[4], double a[4])
+{
+    const double R4 = 2.0 * b[3] - s.Bm * b[0];
+    const double R3 = b[2] - s.V * b[0];
+    const double R2 = b[1] - s.U * b[0];
+    a[3] = s.c4 * (R4 - 2.0 * (s.U * R2 + s.V * R3));
+    a[2] = R3 * s.inv_theta - s.V * a[3];
+    a[1] = R2 * s.inv_theta - s.U * a[3];
+    a[0] = b[0] - s.U * a[1] - s.V * a[2] - 0.5 * a[3] * s.Bm;
+}
+
+// ------------------------------------------------------------------------
+// Euler time derivatives by Cauchy-Kowalevski in primitive variables.
+// Inputs: conservative W and its x (normal), y (tangential) derivatives up to
+// second order.  Outputs conservative W_t, W_tt and the flux time derivative
+// F_t of the normal Euler flux.
+struct EulerTD { double Wt[4], Wtt[4], Ft[4], F[4]; };
+
+__device__ __forceinline__ void euler_time_derivs(const double W[4], const double Wx[4], const double Wy[4],
+                                                  const double Wxx[4], const double Wxy[4], const double Wyy[4],
+                                                  double gamma, double ir, double U, double V, double p,
+                                                  EulerTD& o)
+{
+    const double gm1 = gamma - 1.0;
+    const double rho = W[0], m = W[1], n = W[2], E = W[3];
+    // primitive first derivatives
+    const double rx = Wx[0], ry = Wy[0];
+    const double Ux = (Wx[1] - U * rx) * ir, Uy = (Wy[1] - U * ry) * ir;
+    const double Vx = (Wx[2] - V * rx) * ir, Vy = (Wy[2] - V * ry) * ir;
+    const double KEx = 0.5 * (Wx[1] * U + m * Ux + Wx[2] * V + n * Vx);
+    const double KEy = 0.5 * (Wy[1] * U + m * Uy + Wy[2] * V + n * Vy);
+    const double px = gm1 * (Wx[3] - KEx), py = gm1 * (Wy[3] - KEy);
+    // primitive second derivatives
+    const double rxx = Wxx[0], rxy = Wxy[0], ryy = Wyy[0];
+    const double Uxx = (Wxx[1] - 2.0 * Ux * rx - U * rxx) * ir;
+    const double Uxy = (Wxy[1] - Ux * ry - Uy * rx - U * rxy) * ir;
+    const double Uyy = (Wyy[1] - 2.0 * Uy * ry - U * ryy) * ir;
+    const double Vxx = (Wxx[2] - 2.0 * Vx * rx - V * rxx) * ir;
+    const double Vxy = (Wxy[2] - Vx * ry - Vy * rx - V * rxy) * ir;
+    const double Vyy = (Wyy[2] - 2.0 * Vy * ry - V * ryy) * ir;
+    const double KExx = 0.5 * (Wxx[1] * U + 2.0 * Wx[1] * Ux + m * Uxx + Wxx[2] * V + 2.0 * Wx[2] * Vx + n * Vxx);
+    const double KExy = 0.5 * (Wxy[1] * U + Wx[1] * Uy + Wy[1] * Ux + m * Uxy + Wxy[2] * V + Wx[2] * Vy + Wy[2] * Vx + n * Vxy);
+    const double KEyy = 0.5 * (Wyy[1] * U + 2.0 * Wy[1] * Uy + m * Uyy + Wyy[2] * V + 2.0 * Wy[2] * Vy + n * Vyy);
+    const double pxx = gm1 * (Wxx[3] - KExx), pxy = gm1 * (Wxy[3] - KExy), pyy = gm1 * (Wyy[3] - KEyy);
+    // first time derivatives
+    const double Dv = Ux + Vy;
+    const double rt = -(U * rx + V * ry + rho * Dv);
+    const double Ut = -(U * Ux + V * Uy + px * ir);
+    const double Vt = -(U * Vx + V * Vy + py * ir);
+    const double pt = -(U * px + V * py + gamma * p * Dv);
+    // mixed derivatives d/dx, d/dy of the first time derivatives
+    const double Dx = Uxx + Vxy, Dy = Uxy + Vyy;
+    const double rxt = -(Ux * rx + U * rxx + Vx * ry + V * rxy + rx * Dv + rho * Dx);
+    const double ryt = -(Uy * rx + U * rxy + Vy * ry + V * ryy + ry * Dv + rho * Dy);
+    const double Uxt = -(Ux * Ux + U * Uxx + Vx * Uy + V * Uxy + (pxx - px * rx * ir) * ir);
+    const double Vyt = -(Uy * Vx + U * Vxy + Vy * Vy + V * Vyy + (pyy - py * ry * ir) * ir);
+    const double Uyt = -(Uy * Ux + U * Uxy + Vy * Uy + V * Uyy + (pxy - px * ry * ir) * ir);
+    const double Vxt = -(Ux * Vx + U * Vxx + Vx * Vy + V * Vxy + (pxy - py * rx * ir) * ir);
+    const double pxt = -(Ux * px + U * pxx + Vx * py + V * pxy + gamma * (px * Dv + p * Dx));
+    const double pyt = -(Uy * px + U * pxy + Vy * py + V * pyy + gamma * (py * Dv + p * Dy));
+    // second time derivatives
+    const double Dt = Uxt + Vyt;
+    const double rtt = -(Ut * rx + U * rxt + Vt * ry + V * ryt + rt * Dv + rho * Dt);
+    const double Utt = -(Ut * Ux + U * Uxt + Vt * Uy + V * Uyt + (pxt - px * rt * ir) * ir);
+    const double Vtt = -(Ut * Vx + U * Vxt + Vt * Vy + V * Vyt + (pyt - py * rt * ir) * ir);
+    const double ptt = -(Ut * px + U * pxt + Vt * py + V * pyt + gamma * (pt * Dv + p * Dt));
+    // back to conservative variables
+    const double q2 = U * U + V * V;
+    const double uut = U * Ut + V * Vt;
+    const double inv_gm1 = 1.0 / gm1;
+    o.Wt[0] = rt;
+    o.Wt[1] = rt * U + rho * Ut;
+    o.Wt[2] = rt * V + rho * Vt;
+    o.Wt[3] = pt * inv_gm1 + 0.5 * rt * q2 + rho * uut;
+    o.Wtt[0] = rtt;
+    o.Wtt[1] = rtt * U + 2.0 * rt * Ut + rho * Utt;
+    o.Wtt[2] = rtt * V + 2.0 * rt * Vt + rho * Vtt;
+    o.Wtt[3] = ptt * inv_gm1 + 0.5 * rtt * q2 + 2.0 * rt * uut + rho * (Ut * Ut + U * Utt + Vt * Vt + V * Vtt);
+    // normal Euler flux and its time derivative
+    o.F[0] = m;
+    o.F[1] = m * U + p;
+    o.F[2] = m * V;
+    o.F[3] = U * (E + p);
+    const double mt = o.Wt[1];
+    o.Ft[0] = mt;
+    o.Ft[1] = mt * U + m * Ut + pt;
+    o.Ft[2] = mt * V + m * Vt;
+    o.Ft[3] = Ut * (E + p) + U * (o.Wt[3] + pt);
+}
+
+// ------------------------------------------------------------------------
+// One interface quadrature point in the face frame (Sec. 2.1-2.2).
+struct PointIn {
+    double W0[4], W0n[4], W0t[4], W0nn[4], W0nt[4], W0tt[4];
+    double Wl[4], Wln[4], Wlt[4], Wr[4], Wrn[4], Wrt[4];
+};
+
+struct Params {
+    double gamma, K, eps_tau, c_tau, dt;
+};
+
+// STAGE 1: Fb, Ft, Wm = W(dt/2), Wb = W(dt) with W0_tt^n;  STAGE 2: Ft, Wtt
+template <int STAGE>
+__device__ __forceinline__ bool gks_point(const PointIn& in, const Params& P,
+                                          double Fb[4], double Ft[4], double Wm[4], double Wb[4], double Wtt[4])
+{
+    const double gm1 = P.gamma - 1.0, K = P.K, dt = P.dt;
+    // equilibrium state g0
+    const double ir0 = 1.0 / in.W0[0];
+    const double U0 = in.W0[1] * ir0, V0 = in.W0[2] * ir0;
+    const double p0 = gm1 * (in.W0[3] - 0.5 * (in.W0[1] * U0 + in.W0[2] * V0));
+    const double th0 = p0 * ir0;
+    // non-equilibrium states
+    const double irl = 1.0 / in.Wl[0];
+    const double Ul = in.Wl[1] * irl, Vl = in.Wl[2] * irl;
+    const double pl = gm1 * (in.Wl[3] - 0.5 * (in.Wl[1] * Ul + in.Wl[2] * Vl));
+    const double irr = 1.0 / in.Wr[0];
+    const double Ur = in.Wr[1] * irr, Vr = in.Wr[2] * irr;
+    const double pr = gm1 * (in.Wr[3] - 0.5 * (in.Wr[1] * Ur + in.Wr[2] * Vr));
+    const bool ok = (in.W0[0] > 0.0) && (p0 > 0.0) && (in.Wl[0] > 0.0) && (pl > 0.0) && (in.Wr[0] > 0.0) && (pr > 0.0);
+    const double thl = pl * irl, thr = pr * irr;
+
+    // Euler derivatives of the equilibrium state (W_t, W_tt, F, F_t)
+    EulerTD e;
+    euler_time_derivs(in.W0, in.W0n, in.W0t, in.W0nn, in.W0nt, in.W0tt, P.gamma, ir0, U0, V0, p0, e);
+
+    // tau-terms of g0: T2 = <(a_n u + a_t v) u psi> rho, T1 = F_t
+    Moments m0;
+    m0.u[0] = 1.0; m0.u[1] = U0;
+    moments_tail(m0, U0, V0, th0, K);
+    SlopeCtx s0;
+    slope_ctx(U0, V0, th0, 1.0 / th0, K, s0);
+    double bn[4], bt[4], an[4], at[4], T2[4], tmp[4];
+    for (int k = 0; k < 4; ++k) { bn[k] = in.W0n[k] * ir0; bt[k] = in.W0t[k] * ir0; }
+    micro_slope(s0, bn, an);
+    micro_slope(s0, bt, at);
+    a_psi_uv<2, 0>(m0, an, T2);
+    a_psi_uv<1, 1>(m0, at, tmp);
+    for (int k = 0; k < 4; ++k) T2[k] = in.W0[0] * (T2[k] + tmp[k]);
+
+    // half-line moments of g_l (u > 0) and g_r (u < 0)
+    double Fh[4], Th[4], Wh[4], Wsl[4];
+    {
+        Moments ml;
+        const double sq = rsqrt(2.0 * thl);            // sqrt(lambda_l)
+        const double ex = exp(-Ul * Ul * (0.5 / thl));
+        ml.u[0] = 0.5 * erfc(-sq * Ul);
+        ml.u[1] = Ul * ml.u[0] + ex * (2.0 * thl * sq) * 0.28209479177387814;  // e^{-l U^2} / (2 sqrt(pi l))
+        moments_tail(ml, Ul, Vl, thl, K);
+        SlopeCtx sl;
+        slope_ctx(Ul, Vl, thl, 1.0 / thl, K, sl);
+        double b1[4], b2[4], a1[4], a2[4], o1[4], o2[4], f[4];
+        for (int k = 0; k < 4; ++k) { b1[k] = in.Wln[k] * irl; b2[k] = in.Wlt[k] * irl; }
+        micro_slope(sl, b1, a1);
+        micro_slope(sl, b2, a2);
+        psi_uv<1, 0>(ml, f);
+        a_psi_uv<2, 0>(ml, a1, o1);
+        a_psi_uv<1, 1>(ml, a2, o2);
+        for (int k = 0; k < 4; ++k) { Fh[k] = in.Wl[0] * f[k]; Th[k] = in.Wl[0] * (o1[k] + o2[k]); }
+        if (STAGE == 1) {
+            psi_uv<0, 0>(ml, f);
+            a_psi_uv<1, 0>(ml, a1, o1);
+            a_psi_uv<0, 1>(ml, a2, o2);
+            for (int k = 0; k < 4; ++k) { Wh[k] = in.Wl[0] * f[k]; Wsl[k] = in.Wl[0] * (o1[k] + o2[k]); }
+        }
+    }
+    {
+        Moments mr;
+        const double sq = rsqrt(2.0 * thr);
+        const double ex = exp(-Ur * Ur * (0.5 / thr));
+        mr.u[0] = 0.5 * erfc(sq * Ur);
+        mr.u[1] = Ur * mr.u[0] - ex * (2.0 * thr * sq) * 0.28209479177387814;
+        moments_tail(mr, Ur, Vr, thr, K);
+        SlopeCtx sr;
+        slope_ctx(Ur, Vr, thr, 1.0 / thr, K, sr);
+        double b1[4], b2[4], a1[4], a2[4], o1[4], o2[4], f[4];
+        for (int k = 0; k < 4; ++k) { b1[k] = in.Wrn[k] * irr; b2[k] = in.Wrt[k] * irr; }
+        micro_slope(sr, b1, a1);
+        micro_slope(sr, b2, a2);
+        psi_uv<1, 0>(mr, f);
+        a_psi_uv<2, 0>(mr, a1, o1);
+        a_psi_uv<1, 1>(mr, a2, o2);
+        for (int k = 0; k < 4; ++k) { Fh[k] += in.Wr[0] * f[k]; Th[k] += in.Wr[0] * (o1[k] + o2[k]); }
+        if (STAGE == 1) {
+            psi_uv<0, 0>(mr, f);
+            a_psi_uv<1, 0>(mr, a1, o1);
+            a_psi_uv<0, 1>(mr, a2, o2);
+            for (int k = 0; k < 4; ++k) { Wh[k] += in.Wr[0] * f[k]; Wsl[k] += in.Wr[0] * (o1[k] + o2[k]); }
+        }
+    }
+
+    // Sec. 4: collision time with pressure-jump enhancement
+    const double tau = P.eps_tau * dt + P.c_tau * fabs((pl - pr) / (pl + pr)) * dt;
+    // h = exp(-dt / (2 tau)); the flux over [0,dt] reduced to F + F_t t by its
+    // integrals over [0, dt/2] and [0, dt], in closed form:
+    //   Fb = F + a (Fh - F) - tau (T2 + T1) + b4 (T2 - Th)
+    //   Ft = g (F - Fh) + T1 + f4 (T2 - Th)
+    double h = 0.0;
+    if (tau > 0.0) h = exp(-0.5 * dt / tau);
+    const double omh = 1.0 - h;
+    const double idt = 1.0 / dt;
+    const double ta = tau * omh;
+    const double a = ta * (3.0 - h) * idt;
+    const double g = 4.0 * ta * omh * idt * idt;
+    const double b4 = tau * (tau * omh * (3.0 - h) - dt * h * (2.0 - h)) * idt;
+    const double f4 = 4.0 * ta * (dt * h - ta) * idt * idt;
+    for (int k = 0; k < 4; ++k) {
+        const double dTh = T2[k] - Th[k];
+        const double dFh = Fh[k] - e.F[k];
+        Ft[k] = e.Ft[k] - g * dFh + f4 * dTh;
+        if (STAGE == 1) Fb[k] = e.F[k] + a * dFh - tau * (T2[k] + e.Ft[k]) + b4 * dTh;
+    }
+    if (STAGE == 1) {
+        // interface state W(t) = W0 + t W_t + t^2/2 W_tt + e^{-t/tau} [W_ne(t) - W0 - t W_t]
+        const double th = 0.5 * dt, h2 = h * h;
+        for (int k = 0; k < 4; ++k) {
+            const double nem = h * ((Wh[k] - th * Wsl[k]) - in.W0[k] - th * e.Wt[k]);
+            const double nef = h2 * ((Wh[k] - dt * Wsl[k]) - in.W0[k] - dt * e.Wt[k]);
+            Wm[k] = in.W0[k] + th * e.Wt[k] + (0.125 * dt * dt) * e.Wtt[k] + nem;
+            Wb[k] = in.W0[k] + dt * e.Wt[k] + (dt * dt / 6.0) * e.Wtt[k] + nef;
+        }
+    } else {
+        for (int k = 0; k < 4; ++k) Wtt[k] = e.Wtt[k];
+    }
+    return ok;
+}
+
+}  // namespace cgks

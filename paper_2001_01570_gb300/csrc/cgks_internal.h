@@ -1,0 +1,56 @@
+// cgks_internal.h -- device-side data structures shared by the kernels and the
+// host runtime of libcgks (not part of the public C ABI in include/cgks.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cgks {
+
+// Per-grid control block in device memory.  Written only by the step-control
+// kernels and the stage kernels, so a sequence of steps (or a CUDA graph of
+// them) runs without any host round trip.
+struct Ctrl {
+    double dt;                        // time step of the step in flight
+    double t;                         // simulated time of the state in buf[par]
+    double t_end;                     // > 0: clip the last step to reach t_end, then stop
+    unsigned long long dtmin_bits;    // min over cells of dx/(|U|+c) (positive double bits)
+    int status;                       // CGKS_E_* bits raised by kernels
+    int done;                         // 1: no further steps run on this grid
+    int par;                          // index of the buffer holding the current state
+    int pad;
+    long long steps;                  // steps completed
+    long long steps_target;           // < 0: unlimited
+};
+
+// Per-grid descriptor (read-only for kernels).
+struct GridDev {
+    double* buf[2];     // current state / next state ping-pong, 12 planes each
+    double* ws;         // intermediate state W* (12 planes)
+    Ctrl* ctrl;
+    int nx, ny, dim, bc0;
+    int bc[4];
+    double dx, dy, inv_dx, inv_dy;
+    double gamma, K, cfl, eps_tau, c_tau, weno_eps;
+    double inflow[4];   // conservative inflow state
+};
+
+// One unit of work of the stage kernels: a TX x TY tile of one grid.
+struct TileRef { int grid, x0, y0, pad; };
+
+// tile shapes compiled into the library
+enum TileShape { TILE_16x8 = 0, TILE_8x16 = 1, TILE_32x4 = 2, TILE_64x1 = 3, TILE_COUNT = 4 };
+inline int tile_w(int s) { return s == TILE_16x8 ? 16 : s == TILE_8x16 ? 8 : s == TILE_32x4 ? 32 : 64; }
+inline int tile_h(int s) { return s == TILE_16x8 ? 8 : s == TILE_8x16 ? 16 : s == TILE_32x4 ? 4 : 1; }
+
+// launchers (defined in the kernel translation units)
+cudaError_t launch_stage(int shape, int stage, const GridDev* grids, const TileRef* tiles, int ntiles,
+                         int nblocks, cudaStream_t st);
+size_t stage_smem_bytes(int shape, int stage);
+cudaError_t launch_begin_step(const GridDev* grids, int ngrids, cudaStream_t st);
+cudaError_t launch_end_step(const GridDev* grids, int ngrids, cudaStream_t st);
+cudaError_t launch_cfl(const GridDev* grids, int gidx, const GridDev& host, cudaStream_t st);
+cudaError_t launch_expand1d(const double* src6, double* dst12, int nx, cudaStream_t st);
+cudaError_t launch_compress1d(const double* src12, double* dst6, int nx, cudaStream_t st);
+cudaError_t launch_set_ctrl(Ctrl* c, double t, double t_end, long long steps_target, int reset, cudaStream_t st);
+
+}  // namespace cgks

@@ -1,0 +1,65 @@
+"""Write the oracle's expected values for the full-size parity tests.
+
+Calls only oracle/ (and the shared input generators).  For each case the oracle runs the stated
+number of steps on the full grid; stored are: the final time and step count, the per-plane maximum
+|value| over the whole grid (the normalisation of the relative error), and all 12 planes at a
+seeded sample of cells.
+
+  python tests/golden/make_golden.py vortex512     # isentropic vortex 512^2, 200 steps
+  python tests/golden/make_golden.py shockvortex   # shock-vortex 1024x512, 400 steps
+  python tests/golden/make_golden.py pulses        # 8 smallest grids of the 256-grid batch, 100 steps
+"""
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+import oracle as O  # noqa: E402
+from paper_2001_01570_gb300 import workloads as wl  # noqa: E402
+
+NSAMPLE = 1500
+
+
+def sample_cells(ny, nx, seed):
+    rng = np.random.default_rng(seed)
+    n = min(NSAMPLE, nx * ny)
+    flat = rng.choice(nx * ny, size=n, replace=False)
+    return np.sort(flat)
+
+
+def write_case(name, spec, W, nsteps, seed):
+    t0 = time.time()
+    Wn, t, steps, last_dt = O.run(O.make_problem(**spec.as_kwargs()), W, nsteps)
+    idx = sample_cells(spec.ny, spec.nx, seed)
+    planes = Wn.reshape(Wn.shape[0], -1)
+    np.savez_compressed(os.path.join(HERE, f"oracle_{name}.npz"), idx=idx, values=planes[:, idx],
+                        maxabs=np.abs(planes).max(axis=1), t=t, steps=steps, last_dt=last_dt,
+                        nx=spec.nx, ny=spec.ny)
+    print(f"{name}: {steps} steps to t={t:.6f} in {time.time() - t0:.0f} s", flush=True)
+
+
+def main(which):
+    if which == "vortex512":
+        spec, W = wl.isentropic_vortex(512)
+        write_case("vortex512_200", spec, W, 200, seed=512)
+    elif which == "shockvortex":
+        spec, W = wl.shock_vortex(1024, 512)
+        write_case("shockvortex1024x512_400", spec, W, 400, seed=1024)
+    elif which == "pulses":
+        params = wl.batched_pulses()
+        order = sorted(range(len(params)), key=lambda k: params[k]["N"])[:8]
+        for k in order:
+            p = params[k]
+            spec, W = wl.acoustic_pulse(p["N"], p["A"], p["b"], p["cx"], p["cy"])
+            write_case(f"pulse{k:03d}_100", spec, W, 100, seed=k)
+    else:
+        raise SystemExit(__doc__)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1])

@@ -127,7 +127,8 @@ def test_2d_reproduces_1d_on_y_uniform_data():
         b1 = np.array([b[0, r], b[1, r], b[3, r], b[4, r], b[5, r], b[7, r]])
         rel = np.abs(a - b1).max(axis=1) / np.abs(a).max(axis=1).clip(1e-300)
         assert rel[:3].max() < 1e-13 and rel[3:].max() < 1e-11
-    assert np.abs(b[2]).max() == 0.0 and np.abs(b[8:]).max() == 0.0
+    # y-momentum and y-gradients stay at roundoff (the tangential fits sum constants to ~1 ulp)
+    assert np.abs(b[2]).max() < 1e-15 and np.abs(b[8:]).max() < 1e-13
 
 
 def test_transpose_symmetry():
