@@ -31,9 +31,9 @@ METRIC = "FP64 cell-updates/s on 1 GB300 (plain 2048^2 sweep); served-batched vs
 UNIT = "cell-updates/s"
 
 # FP64 floating-point operations per cell and stage executed by the stage kernels (FMA = 2),
-# counted with ncu (sm__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on) on a 256^2
-# isentropic-vortex grid and divided by the cells; see profiles/stage_kernels_vortex.md.
-FLOP_PER_CELL = {1: None, 2: None}
+# counted with ncu (sm__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on) on the 256^2
+# isentropic vortex and divided by the cells: profiles/stage_kernels_vortex256.md.
+FLOP_PER_CELL = {1: 15414.0, 2: 13902.0}
 # measured FP64 peak of this GB300 (DFMA throughput loop, FMA = 2): profiles/fp64_peak.md
 FP64_PEAK_TFLOPS = 1.010
 

@@ -115,6 +115,12 @@ cgks_status cgks_step(cgks_solver* s, int nsteps, double t_end, double* t_out);
  * through cgks_get_state. */
 cgks_status cgks_batch_step(cgks_solver* const* solvers, int n, int nsteps);
 
+/* Tile shape (0: 16x8, 1: 8x16, 2: 32x4, 3: 64x1 cells per CTA) that the
+ * autotuner of cgks_batch_step chose for this exact batch, or -1 while it is
+ * still timing the candidates (it times each candidate shape on the first
+ * steps of a new batch composition; the shape never changes the results). */
+int cgks_batch_tile_shape(cgks_solver* const* solvers, int n);
+
 /* Same as cgks_step(s, nsteps, 0, NULL), but with CUDA events recorded on the
  * solver's stream around every kernel of every step; stage_ms[0..3] receive
  * the average duration in milliseconds of the step-begin, stage-1, stage-2 and
@@ -128,6 +134,70 @@ long cgks_last_launch_count(void);
 
 const char* cgks_status_string(cgks_status st);
 const char* cgks_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Serving: a continuous-batching solve server.  Requests (2D problems with an
+ * initial state and a step count) may be submitted from any thread at any
+ * time.  A scheduler thread admits them in arrival order while the active set
+ * has fewer than max_active solves and their device planes (3 x 12 planes of
+ * nx*ny doubles) fit hbm_budget_bytes; all active solves advance together in
+ * rounds of steps_per_round steps of the batched launch (each with its own dt
+ * and step target); a finished solve is copied to host memory and its device
+ * memory freed, so waiting requests can enter at the next round. */
+typedef struct cgks_server cgks_server;
+
+typedef struct {
+    double hbm_budget_bytes;   /* device bytes the server may hold for solver state */
+    int max_active;            /* at most this many solves share a launch */
+    int steps_per_round;       /* steps between admission / retirement points */
+    int tile_shape;            /* -1: autotune on the first batch; else a fixed shape */
+    void* cuda_stream;         /* cudaStream_t for all server work (NULL: default stream) */
+} cgks_serve_cfg;
+
+typedef struct {
+    cgks_problem prob;         /* dim must be 2 */
+    const double* init_planes; /* host, 12 planes of ny*nx; copied during the call */
+    int nsteps;                /* S2O4 steps to run */
+} cgks_request;
+
+typedef struct {
+    long submitted, completed, rejected, failed, active, pending, rounds;
+    double cell_updates;        /* completed solves: sum of cells x steps */
+    double wall_s;              /* first arrival to last completion */
+    double busy_s;              /* time spent in rounds */
+    double cell_updates_per_s;  /* cell_updates / wall_s */
+    double p50_s, p99_s, mean_s;/* solve latency, arrival to result on the host */
+    double hbm_in_use, hbm_peak;/* bytes of admitted solves */
+    int tile_shape;             /* shape in use (-1 before it is chosen) */
+} cgks_serve_stats_t;
+
+/* Start a server (spawns the scheduler thread).  Errors: CGKS_E_INVAL. */
+cgks_status cgks_serve_start(const cgks_serve_cfg* cfg, cgks_server** out);
+
+/* Queue a request; *req_id receives its id.  The initial planes are copied.
+ * Errors: CGKS_E_BUDGET if the request alone exceeds the budget (it could
+ * never be admitted), CGKS_E_INVAL, CGKS_E_BUSY while stopping.  Otherwise the
+ * request waits in the queue until it can be admitted. */
+cgks_status cgks_serve_submit(cgks_server* srv, const cgks_request* req, long* req_id);
+
+/* *done = 1 when the request has finished.  If so and out_planes is not NULL,
+ * the final state (12 planes) is copied there and the request is forgotten.
+ * Returns the request's status (CGKS_E_NOTFOUND for an unknown id). */
+cgks_status cgks_serve_poll(cgks_server* srv, long req_id, double* out_planes, int* done);
+
+/* Wait at most timeout_s seconds for a request, then behave like poll.
+ * Returns CGKS_E_TIMEOUT if it has not finished by then. */
+cgks_status cgks_serve_wait(cgks_server* srv, long req_id, double timeout_s, double* out_planes);
+
+/* Throughput and latency statistics so far. */
+cgks_status cgks_serve_stats(cgks_server* srv, cgks_serve_stats_t* out);
+
+/* Stop accepting requests, finish the queued and active ones, join the
+ * scheduler thread and free the server. */
+cgks_status cgks_serve_stop(cgks_server* srv);
+
+/* Detail of the last failing cgks_serve_* call on the calling thread. */
+const char* cgks_serve_last_error(void);
 
 #ifdef __cplusplus
 }

@@ -36,6 +36,26 @@ class cgks_problem(ctypes.Structure):
     ]
 
 
+class cgks_serve_cfg(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_double), ("max_active", ctypes.c_int),
+                ("steps_per_round", ctypes.c_int), ("tile_shape", ctypes.c_int), ("cuda_stream", ctypes.c_void_p)]
+
+
+class cgks_request(ctypes.Structure):
+    _fields_ = [("prob", cgks_problem), ("init_planes", ctypes.POINTER(ctypes.c_double)), ("nsteps", ctypes.c_int)]
+
+
+class cgks_serve_stats_t(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_long) for n in ("submitted", "completed", "rejected", "failed", "active", "pending",
+                                              "rounds")] + \
+               [(n, ctypes.c_double) for n in ("cell_updates", "wall_s", "busy_s", "cell_updates_per_s", "p50_s",
+                                                "p99_s", "mean_s", "hbm_in_use", "hbm_peak")] + \
+               [("tile_shape", ctypes.c_int)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 def library_path() -> str:
     return _build.LIB
 
@@ -60,6 +80,18 @@ def load():
     for name in ("cgks_create", "cgks_destroy", "cgks_set_state", "cgks_get_state", "cgks_step", "cgks_batch_step",
                  "cgks_step_profiled"):
         getattr(L, name).restype = ctypes.c_int
+    L.cgks_batch_tile_shape.argtypes = [ctypes.POINTER(vp), ctypes.c_int]
+    L.cgks_batch_tile_shape.restype = ctypes.c_int
+    L.cgks_serve_start.argtypes = [ctypes.POINTER(cgks_serve_cfg), ctypes.POINTER(vp)]
+    L.cgks_serve_submit.argtypes = [vp, ctypes.POINTER(cgks_request), ctypes.POINTER(ctypes.c_long)]
+    L.cgks_serve_poll.argtypes = [vp, ctypes.c_long, dp, ctypes.POINTER(ctypes.c_int)]
+    L.cgks_serve_wait.argtypes = [vp, ctypes.c_long, ctypes.c_double, dp]
+    L.cgks_serve_stats.argtypes = [vp, ctypes.POINTER(cgks_serve_stats_t)]
+    L.cgks_serve_stop.argtypes = [vp]
+    for name in ("cgks_serve_start", "cgks_serve_submit", "cgks_serve_poll", "cgks_serve_wait", "cgks_serve_stats",
+                 "cgks_serve_stop"):
+        getattr(L, name).restype = ctypes.c_int
+    L.cgks_serve_last_error.restype = ctypes.c_char_p
     L.cgks_status_string.argtypes = [ctypes.c_int]
     L.cgks_status_string.restype = ctypes.c_char_p
     L.cgks_last_error.restype = ctypes.c_char_p
@@ -147,6 +179,55 @@ def cgks_step_profiled(solver, nsteps):
     ms = (ctypes.c_double * 4)()
     _check(load().cgks_step_profiled(solver, int(nsteps), ms))
     return list(ms)
+
+
+def cgks_batch_tile_shape(solvers) -> int:
+    arr = (ctypes.c_void_p * len(solvers))(*[s.value if isinstance(s, ctypes.c_void_p) else s for s in solvers])
+    return int(load().cgks_batch_tile_shape(arr, len(solvers)))
+
+
+def _scheck(st):
+    if st != CGKS_OK:
+        raise CgksError(st, load().cgks_serve_last_error().decode())
+
+
+def cgks_serve_start(hbm_budget_bytes, max_active=64, steps_per_round=8, tile_shape=-1, stream=None):
+    cfg = cgks_serve_cfg(float(hbm_budget_bytes), int(max_active), int(steps_per_round), int(tile_shape),
+                         ctypes.c_void_p(stream or 0))
+    out = ctypes.c_void_p()
+    _scheck(load().cgks_serve_start(ctypes.byref(cfg), ctypes.byref(out)))
+    return out
+
+
+def cgks_serve_submit(server, problem: cgks_problem, planes: np.ndarray, nsteps: int) -> int:
+    planes = np.ascontiguousarray(planes, dtype=np.float64)
+    req = cgks_request(problem, planes.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(nsteps))
+    rid = ctypes.c_long()
+    _scheck(load().cgks_serve_submit(server, ctypes.byref(req), ctypes.byref(rid)))
+    return rid.value
+
+
+def cgks_serve_poll(server, req_id, out=None):
+    """Returns True when finished (copying the result into ``out`` if given)."""
+    done = ctypes.c_int()
+    p = out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if out is not None else None
+    _scheck(load().cgks_serve_poll(server, int(req_id), p, ctypes.byref(done)))
+    return bool(done.value)
+
+
+def cgks_serve_wait(server, req_id, timeout_s, out):
+    _scheck(load().cgks_serve_wait(server, int(req_id), float(timeout_s),
+                                   out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
+
+def cgks_serve_stats(server) -> dict:
+    st = cgks_serve_stats_t()
+    _scheck(load().cgks_serve_stats(server, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def cgks_serve_stop(server):
+    _scheck(load().cgks_serve_stop(server))
 
 
 def cgks_last_launch_count() -> int:

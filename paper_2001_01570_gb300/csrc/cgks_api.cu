@@ -18,6 +18,7 @@ using namespace cgks;
 
 struct cgks_solver {
     cgks_problem prob;
+    size_t device_bytes = 0;
     int nx = 0, ny = 0;
     int device = 0;
     int nsm = 1;
@@ -144,7 +145,8 @@ cgks_status cgks_create(const cgks_problem* prob, void* cuda_stream, cgks_solver
     cudaError_t e = cudaGetDevice(&s->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, s->device);
     const size_t PL = (size_t)s->nx * s->ny;
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_planes, 3 * 12 * PL * sizeof(double));
+    s->device_bytes = 3 * 12 * PL * sizeof(double);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_planes, s->device_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_ctrl, sizeof(Ctrl));
     if (e == cudaSuccess) e = cudaMalloc(&s->d_desc, sizeof(GridDev));
     if (e == cudaSuccess && prob->dim == 1) e = cudaMalloc(&s->d_stage1d, 6 * PL * sizeof(double));
@@ -200,9 +202,12 @@ cgks_status cgks_create(const cgks_problem* prob, void* cuda_stream, cgks_solver
     return CGKS_OK;
 }
 
+extern "C" void cgks_forget_solver_plans(cgks_solver* s);
+
 cgks_status cgks_destroy(cgks_solver* s)
 {
     if (!s) return fail(CGKS_E_INVAL, "solver is NULL");
+    cgks_forget_solver_plans(s);
     if (s->d_planes || s->d_ctrl) cudaStreamSynchronize(s->stream);
     cudaFree(s->d_planes);
     cudaFree(s->d_stage1d);
@@ -296,6 +301,17 @@ cgks_status cgks_step(cgks_solver* s, int nsteps, double t_end, double* t_out)
     return CGKS_OK;
 }
 
+}  // extern "C"
+
+// internal (used by the server): stop the solve after `target` steps
+cgks_status cgks_set_step_target(cgks_solver* s, long long target)
+{
+    CK(launch_set_ctrl(s->d_ctrl, 0.0, 0.0, target, 0, s->stream));
+    return CGKS_OK;
+}
+
+extern "C" {
+
 cgks_status cgks_step_profiled(cgks_solver* s, int nsteps, double stage_ms[4])
 {
     if (!s || nsteps <= 0 || !stage_ms) return fail(CGKS_E_INVAL, "bad arguments");
@@ -336,67 +352,152 @@ cgks_status cgks_step_profiled(cgks_solver* s, int nsteps, double stage_ms[4])
 
 // ---------------------------------------------------------------------------
 // batched stepping: one persistent launch per stage over the tiles of all
-// grids, captured once into a CUDA graph per batch composition and replayed
-namespace {
-struct BatchPlan {
-    std::vector<cgks_solver*> solvers;
-    int shape = TILE_16x8;
-    GridDev* d_grids = nullptr;
-    TileRef* d_tiles = nullptr;
-    int ntiles = 0;
-    cudaGraphExec_t exec = nullptr;
-    cudaStream_t stream = nullptr;
-};
-std::mutex g_batch_mu;
-std::map<std::vector<cgks_solver*>, BatchPlan*> g_batch_plans;
+// grids, captured into a CUDA graph per batch composition and replayed.  The
+// tile shape of each plan is chosen by timing the candidate shapes on its first
+// steps (the shape changes only the work decomposition, never the arithmetic of
+// a face or a cell, so results are identical whichever shape runs).
+}  // extern "C"
 
-cgks_status build_plan(cgks_solver* const* solvers, int n, BatchPlan** out)
-{
-    std::vector<cgks_solver*> key(solvers, solvers + n);
-    auto it = g_batch_plans.find(key);
-    if (it != g_batch_plans.end()) { *out = it->second; return CGKS_OK; }
-    BatchPlan* bp = new BatchPlan();
-    bp->solvers = key;
-    bp->stream = solvers[0]->stream;
-    bp->shape = solvers[0]->prob.dim == 1 ? TILE_64x1 : TILE_16x8;
-    std::vector<GridDev> descs;
-    std::vector<TileRef> tiles;
-    for (int g = 0; g < n; ++g) {
-        descs.push_back(solvers[g]->host_desc);
-        std::vector<TileRef> t = make_tiles(solvers[g]->nx, solvers[g]->ny, bp->shape, g);
-        tiles.insert(tiles.end(), t.begin(), t.end());
-    }
-    bp->ntiles = (int)tiles.size();
-    CK(cudaMalloc(&bp->d_grids, descs.size() * sizeof(GridDev)));
-    CK(cudaMalloc(&bp->d_tiles, tiles.size() * sizeof(TileRef)));
-    CK(cudaMemcpyAsync(bp->d_grids, descs.data(), descs.size() * sizeof(GridDev), cudaMemcpyHostToDevice, bp->stream));
-    CK(cudaMemcpyAsync(bp->d_tiles, tiles.data(), tiles.size() * sizeof(TileRef), cudaMemcpyHostToDevice, bp->stream));
-    CK(cudaStreamSynchronize(bp->stream));
-    // make sure the kernels' shared-memory attributes are set before capture
-    CK(launch_stage(bp->shape, 1, bp->d_grids, bp->d_tiles, 0, 1, bp->stream));
-    CK(launch_stage(bp->shape, 2, bp->d_grids, bp->d_tiles, 0, 1, bp->stream));
-    const int nsm = solvers[0]->nsm;
-    const int nblocks = bp->ntiles < nsm ? bp->ntiles : nsm;
-    cudaStream_t cap;
-    CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-    cudaGraph_t graph;
-    CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = launch_begin_step(bp->d_grids, n, cap);
-    if (e == cudaSuccess) e = launch_stage(bp->shape, 1, bp->d_grids, bp->d_tiles, bp->ntiles, nblocks, cap);
-    if (e == cudaSuccess) e = launch_stage(bp->shape, 2, bp->d_grids, bp->d_tiles, bp->ntiles, nblocks, cap);
-    if (e == cudaSuccess) e = launch_end_step(bp->d_grids, n, cap);
-    cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
-    cudaStreamDestroy(cap);
-    if (e != cudaSuccess) return cuda_fail(e, "batch capture");
-    if (e2 != cudaSuccess) return cuda_fail(e2, "batch capture end");
-    e = cudaGraphInstantiate(&bp->exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
-    g_batch_plans[key] = bp;
-    *out = bp;
-    return CGKS_OK;
-}
+namespace {
+std::mutex g_batch_mu;
+std::map<std::vector<cgks_solver*>, cgks::BatchPlan*> g_batch_plans;
 }  // namespace
+
+namespace cgks {
+
+void destroy_plan(BatchPlan* bp)
+{
+    if (!bp) return;
+    for (int k = 0; k < TILE_COUNT; ++k) {
+        if (bp->exec[k]) cudaGraphExecDestroy(bp->exec[k]);
+        cudaFree(bp->d_tiles[k]);
+    }
+    cudaFree(bp->d_grids);
+    delete bp;
+}
+
+static cudaError_t capture_graph(BatchPlan* bp, int shape)
+{
+    const int n = (int)bp->solvers.size();
+    const int nblocks = bp->ntiles[shape] < bp->nsm ? bp->ntiles[shape] : bp->nsm;
+    cudaError_t e = launch_stage(shape, 1, bp->d_grids, bp->d_tiles[shape], 0, 1, bp->stream);
+    if (e == cudaSuccess) e = launch_stage(shape, 2, bp->d_grids, bp->d_tiles[shape], 0, 1, bp->stream);
+    if (e != cudaSuccess) return e;
+    cudaStream_t cap;
+    e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    cudaGraph_t graph;
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t e1 = launch_begin_step(bp->d_grids, n, cap);
+        if (e1 == cudaSuccess) e1 = launch_stage(shape, 1, bp->d_grids, bp->d_tiles[shape], bp->ntiles[shape], nblocks, cap);
+        if (e1 == cudaSuccess) e1 = launch_stage(shape, 2, bp->d_grids, bp->d_tiles[shape], bp->ntiles[shape], nblocks, cap);
+        if (e1 == cudaSuccess) e1 = launch_end_step(bp->d_grids, n, cap);
+        e = cudaStreamEndCapture(cap, &graph);
+        if (e1 != cudaSuccess) e = e1;
+    }
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess) return e;
+    e = cudaGraphInstantiate(&bp->exec[shape], graph, 0);
+    cudaGraphDestroy(graph);
+    return e;
+}
+
+cudaError_t make_plan(cgks_solver* const* solvers, int n, cudaStream_t stream, int forced_shape, BatchPlan** out)
+{
+    BatchPlan* bp = new BatchPlan();
+    bp->solvers.assign(solvers, solvers + n);
+    bp->stream = stream;
+    bp->nsm = solvers[0]->nsm;
+    bp->dim = solvers[0]->prob.dim;
+    std::vector<GridDev> descs;
+    for (int g = 0; g < n; ++g) descs.push_back(solvers[g]->host_desc);
+    cudaError_t e = cudaMalloc(&bp->d_grids, descs.size() * sizeof(GridDev));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(bp->d_grids, descs.data(), descs.size() * sizeof(GridDev), cudaMemcpyHostToDevice, stream);
+    long long cells = 0;
+    for (int g = 0; g < n; ++g) cells += (long long)solvers[g]->nx * solvers[g]->ny;
+    bp->cells = cells;
+    if (bp->dim == 1) { bp->candidates = {TILE_64x1}; }
+    else if (forced_shape >= 0) { bp->candidates = {forced_shape}; }
+    else { bp->candidates = {TILE_16x8, TILE_8x16, TILE_32x4}; }
+    for (int shape : bp->candidates) {
+        std::vector<TileRef> tiles;
+        for (int g = 0; g < n; ++g) {
+            const int tw = tile_w(shape), th = tile_h(shape);
+            for (int y0 = 0; y0 < solvers[g]->ny; y0 += th)
+                for (int x0 = 0; x0 < solvers[g]->nx; x0 += tw) tiles.push_back(TileRef{g, x0, y0, 0});
+        }
+        bp->ntiles[shape] = (int)tiles.size();
+        if (e == cudaSuccess) e = cudaMalloc(&bp->d_tiles[shape], tiles.size() * sizeof(TileRef));
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(bp->d_tiles[shape], tiles.data(), tiles.size() * sizeof(TileRef), cudaMemcpyHostToDevice,
+                                stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        if (e == cudaSuccess) e = capture_graph(bp, shape);
+    }
+    if (e != cudaSuccess) { destroy_plan(bp); return e; }
+    bp->chosen = bp->candidates.size() == 1 ? bp->candidates[0] : -1;
+    *out = bp;
+    return cudaSuccess;
+}
+
+// run nsteps steps of the plan; while the shape is not yet chosen, each
+// candidate runs timed steps and the fastest is kept
+cudaError_t run_plan(BatchPlan* bp, int nsteps, long* launches)
+{
+    cudaError_t e = cudaSuccess;
+    int k = 0;
+    while (bp->chosen < 0 && k < nsteps) {
+        const int shape = bp->candidates[bp->trial_idx];
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        cudaEventRecord(a, bp->stream);
+        e = cudaGraphLaunch(bp->exec[shape], bp->stream);
+        cudaEventRecord(b, bp->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        if (e != cudaSuccess) return e;
+        *launches += 4;
+        ++k;
+        if (bp->trial_count[shape] > 0) bp->trial_ms[shape] += ms;   // the first run of a shape is a warm-up
+        bp->trial_count[shape] += 1;
+        if (bp->trial_count[shape] >= 2) {
+            bp->trial_idx += 1;
+            if (bp->trial_idx >= (int)bp->candidates.size()) {
+                int best = bp->candidates[0];
+                for (int s2 : bp->candidates)
+                    if (bp->trial_ms[s2] < bp->trial_ms[best]) best = s2;
+                bp->chosen = best;
+            }
+        }
+    }
+    for (; k < nsteps; ++k) {
+        e = cudaGraphLaunch(bp->exec[bp->chosen], bp->stream);
+        if (e != cudaSuccess) return e;
+        *launches += 4;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace cgks
+
+extern "C" {
+
+void cgks_forget_solver_plans(cgks_solver* s)
+{
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    for (auto it = g_batch_plans.begin(); it != g_batch_plans.end();) {
+        bool has = false;
+        for (cgks_solver* x : it->first) has |= (x == s);
+        if (has) { cgks::destroy_plan(it->second); it = g_batch_plans.erase(it); }
+        else ++it;
+    }
+}
 
 cgks_status cgks_batch_step(cgks_solver* const* solvers, int n, int nsteps)
 {
@@ -407,21 +508,31 @@ cgks_status cgks_batch_step(cgks_solver* const* solvers, int n, int nsteps)
     }
     std::lock_guard<std::mutex> lk(g_batch_mu);
     g_last_launches = 0;
+    std::vector<cgks_solver*> key(solvers, solvers + n);
     BatchPlan* bp = nullptr;
-    cgks_status st = build_plan(solvers, n, &bp);
-    if (st != CGKS_OK) return st;
+    auto it = g_batch_plans.find(key);
+    if (it != g_batch_plans.end()) bp = it->second;
+    else {
+        cudaError_t e = make_plan(solvers, n, solvers[0]->stream, -1, &bp);
+        if (e != cudaSuccess) return cuda_fail(e, "batch plan");
+        g_batch_plans[key] = bp;
+    }
     long launches = 0;
-    for (int g = 0; g < n; ++g) {
-        CK(launch_set_ctrl(solvers[g]->d_ctrl, 0.0, 0.0, -1, 0, bp->stream));
-        launches += 1;
-    }
-    for (int k = 0; k < nsteps; ++k) {
-        CK(cudaGraphLaunch(bp->exec, bp->stream));
-        launches += 4;
-    }
+    CK(launch_batch_resume(bp->d_grids, n, bp->stream));
+    launches += 1;
+    CK(run_plan(bp, nsteps, &launches));
     CK(cudaStreamSynchronize(bp->stream));
     g_last_launches = launches;
     return CGKS_OK;
+}
+
+int cgks_batch_tile_shape(cgks_solver* const* solvers, int n)
+{
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    std::vector<cgks_solver*> key(solvers, solvers + n);
+    auto it = g_batch_plans.find(key);
+    if (it == g_batch_plans.end()) return -1;
+    return it->second->chosen;
 }
 
 }  // extern "C"

@@ -114,6 +114,18 @@ __global__ void set_ctrl_kernel(Ctrl* c, double t, double t_end, long long steps
     c->steps_target = steps_target;
 }
 
+// a batch call continues every grid of the batch that has no error: no step
+// target, no end time
+__global__ void batch_resume_kernel(const GridDev* grids, int n)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    Ctrl* c = grids[g].ctrl;
+    if (!c->status) c->done = 0;
+    c->t_end = 0.0;
+    c->steps_target = -1;
+}
+
 // 1D planes (rho, rhoU, rhoE, their x-gradients) <-> the internal 2D layout
 __global__ void expand1d_kernel(const double* src, double* dst, int nx)
 {
@@ -155,6 +167,12 @@ cudaError_t launch_cfl(const GridDev* grids, int gidx, const GridDev& host, cuda
 cudaError_t launch_set_ctrl(Ctrl* c, double t, double t_end, long long steps_target, int reset, cudaStream_t st)
 {
     set_ctrl_kernel<<<1, 1, 0, st>>>(c, t, t_end, steps_target, reset);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_resume(const GridDev* grids, int n, cudaStream_t st)
+{
+    batch_resume_kernel<<<(n + 127) / 128, 128, 0, st>>>(grids, n);
     return cudaGetLastError();
 }
 

@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <vector>
 
 namespace cgks {
 
@@ -52,5 +53,33 @@ cudaError_t launch_cfl(const GridDev* grids, int gidx, const GridDev& host, cuda
 cudaError_t launch_expand1d(const double* src6, double* dst12, int nx, cudaStream_t st);
 cudaError_t launch_compress1d(const double* src12, double* dst6, int nx, cudaStream_t st);
 cudaError_t launch_set_ctrl(Ctrl* c, double t, double t_end, long long steps_target, int reset, cudaStream_t st);
+cudaError_t launch_batch_resume(const GridDev* grids, int n, cudaStream_t st);
+
+}  // namespace cgks
+
+struct cgks_solver;
+
+namespace cgks {
+
+// A batch of solvers stepped together: device descriptor array, one tile
+// queue and one captured step graph per candidate tile shape.
+struct BatchPlan {
+    std::vector<cgks_solver*> solvers;
+    cudaStream_t stream = nullptr;
+    int nsm = 1, dim = 2;
+    long long cells = 0;
+    GridDev* d_grids = nullptr;
+    TileRef* d_tiles[TILE_COUNT] = {nullptr, nullptr, nullptr, nullptr};
+    int ntiles[TILE_COUNT] = {0, 0, 0, 0};
+    cudaGraphExec_t exec[TILE_COUNT] = {nullptr, nullptr, nullptr, nullptr};
+    std::vector<int> candidates;
+    int chosen = -1, trial_idx = 0;
+    float trial_ms[TILE_COUNT] = {0, 0, 0, 0};
+    int trial_count[TILE_COUNT] = {0, 0, 0, 0};
+};
+
+cudaError_t make_plan(cgks_solver* const* solvers, int n, cudaStream_t stream, int forced_shape, BatchPlan** out);
+cudaError_t run_plan(BatchPlan* bp, int nsteps, long* launches);
+void destroy_plan(BatchPlan* bp);
 
 }  // namespace cgks
