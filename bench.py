@@ -34,7 +34,7 @@ UNIT = "cell-updates/s"
 # counted with ncu (sm__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on) on the 256^2
 # isentropic vortex and divided by the cells: profiles/stage_kernels_vortex256.md.
 FLOP_PER_CELL = {1: 15414.0, 2: 13902.0}
-# measured FP64 peak of this GB300 (DFMA throughput loop, FMA = 2): profiles/fp64_peak.md
+# measured FP64 peak of this GB300 (DFMA throughput loop, FMA = 2): profiles/fp64_peak_gb300.md
 FP64_PEAK_TFLOPS = 1.010
 
 
@@ -43,6 +43,7 @@ def workloads():
     return {
         "vortex2048": lambda: wl.isentropic_vortex(2048),
         "vortex512": lambda: wl.isentropic_vortex(512),
+        "vortex1024": lambda: wl.isentropic_vortex(1024),
         "vortex256": lambda: wl.isentropic_vortex(256),
         "shockvortex1024x512": lambda: wl.shock_vortex(1024, 512),
     }
@@ -247,6 +248,145 @@ def run_cgks(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def _pulse_ic(p):
+    from paper_2001_01570_gb300 import workloads as wl
+    spec, W = wl.acoustic_pulse(p["N"], p["A"], p["b"], p["cx"], p["cy"])
+    return spec, W
+
+
+def _request_ic(req):
+    from paper_2001_01570_gb300 import workloads as wl
+    return wl.request_problem(req)
+
+
+def _parallel_ics(fn, items):
+    """Initial conditions in a spawn pool (started before any CUDA call of this process)."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(min(len(items), os.cpu_count() or 4)) as pool:
+        return pool.map(fn, items)
+
+
+def run_batched(args, world, rank, local):
+    """Many independent grids of uneven size: one grid per launch (cgks_step per grid) against one
+    persistent launch over all grids' tiles per stage (cgks_batch_step, CUDA graph, autotuned)."""
+    from paper_2001_01570_gb300 import workloads as wl
+    params = wl.batched_pulses(seed=1570, count=args.grids)
+    ics = _parallel_ics(_pulse_ic, params)
+    import torch
+    from paper_2001_01570_gb300 import build as libbuild
+    from paper_2001_01570_gb300 import cgks
+    libbuild.build()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    solvers = []
+    for spec, W in ics:
+        s = cgks.Solver(cgks.problem_from_spec(spec), stream=stream.cuda_stream)
+        s.set_state(W)
+        solvers.append(s)
+    cells = sum(spec.cells for spec, _ in ics)
+    handles = [s.handle for s in solvers]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # plain: each grid stepped by its own launches
+    for s in solvers:
+        s.step(args.warmup)
+    torch.cuda.synchronize()
+    launches_plain = 0
+    with ClockSampler(local) as clk_plain:
+        start.record(stream)
+        for s in solvers:
+            cgks.cgks_step(s.handle, args.steps)
+            launches_plain += cgks.cgks_last_launch_count()
+        stop.record(stream)
+        torch.cuda.synchronize()
+    ms_plain = start.elapsed_time(stop)
+    # batched: warm-up covers the tile-shape autotuning (3 shapes x 2 steps)
+    cgks.cgks_batch_step(handles, max(args.warmup, 6))
+    torch.cuda.synchronize()
+    shape = cgks.cgks_batch_tile_shape(handles)
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        cgks.cgks_batch_step(handles, args.steps)
+        stop.record(stream)
+        torch.cuda.synchronize()
+    launches = cgks.cgks_last_launch_count()
+    ms_batch = start.elapsed_time(stop)
+    for s in solvers:
+        s.close()
+    plain = cells * args.steps / (ms_plain * 1e-3)
+    batched = cells * args.steps / (ms_batch * 1e-3)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "FP64 cell-updates/s, 256 uneven grids: batched persistent launch vs one grid per launch",
+            "value": batched, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_batch / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"batched{args.grids}", "grids": args.grids, "cells": cells,
+                       "sizes": "N log-uniform in [64, 512], seed 1570", "tile_shape": ["16x8", "8x16", "32x4", "64x1"][shape] if shape >= 0 else None},
+            "plain": {"value": plain, "ms_per_step": ms_plain / args.steps, "gpu_launches": launches_plain,
+                      "clocks": clk_plain.summary()},
+            "batched_vs_plain": batched / plain, "gpu_launches": launches, "clocks": clk.summary()}), flush=True)
+
+
+def run_served(args, world, rank, local):
+    """A documented prefix / scaled copy of the seeded Poisson request stream through the
+    continuous-batching server, against the same requests solved one after another."""
+    from paper_2001_01570_gb300 import workloads as wl
+    reqs = wl.served_requests(seed=2001)[: args.requests]
+    sc = args.served_scale
+    for r in reqs:
+        r["N"] = max(16, int(round(r["N"] / sc)))
+        r["steps"] = max(1, int(round(r["steps"] / sc)))
+        if "cx" in r:
+            r["cx"] /= sc
+            r["cy"] /= sc
+            r["b"] = max(1.5, r["b"] / sc)
+    ics = _parallel_ics(_request_ic, reqs)
+    import torch
+    from paper_2001_01570_gb300 import build as libbuild
+    from paper_2001_01570_gb300 import cgks
+    libbuild.build()
+    torch.cuda.set_device(local)
+    work = sum(spec.cells * r["steps"] for r, (spec, _) in zip(reqs, ics))
+    # plain: one request after another, each on its own solver
+    t0 = time.perf_counter()
+    for r, (spec, W) in zip(reqs, ics):
+        s = cgks.Solver(cgks.problem_from_spec(spec))
+        s.set_state(W)
+        s.step(r["steps"])
+        out, _, _ = s.get_state()
+        s.close()
+    plain_s = time.perf_counter() - t0
+    # served: submissions at the stream's arrival times (scaled by --arrival-scale)
+    srv = cgks.cgks_serve_start(hbm_budget_bytes=120e9, max_active=args.max_active,
+                                steps_per_round=args.steps_per_round)
+    ids = []
+    t_start = time.perf_counter()
+    with ClockSampler(local) as clk:
+        for r, (spec, W) in zip(reqs, ics):
+            delay = r["arrival"] * args.arrival_scale - (time.perf_counter() - t_start)
+            if delay > 0:
+                time.sleep(delay)
+            ids.append(cgks.cgks_serve_submit(srv, cgks.problem_from_spec(spec), W, r["steps"]))
+        for rid, (spec, W) in zip(ids, ics):
+            out = np.empty_like(W)
+            cgks.cgks_serve_wait(srv, rid, 3600.0, out)
+        stats = cgks.cgks_serve_stats(srv)
+    cgks.cgks_serve_stop(srv)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "FP64 cell-updates/s, served continuous batching vs one request after another; p50/p99 latency",
+            "value": stats["cell_updates_per_s"], "unit": UNIT, "n_gpus": world, "steps": None, "warmup": 0,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "served", "requests": len(reqs), "scale": sc, "arrival_scale": args.arrival_scale,
+                       "stream": "seed 2001, Poisson 50 req/s, N log-uniform 128..2048, steps 100..2000, "
+                                 "kinds pulse/vortex/shock-vortex, Mach 1.05..1.5; N and steps divided by scale",
+                       "max_active": args.max_active, "steps_per_round": args.steps_per_round,
+                       "cell_updates": work},
+            "served": stats, "plain": {"value": work / plain_s, "wall_s": plain_s},
+            "served_vs_plain": stats["cell_updates_per_s"] / (work / plain_s), "clocks": clk.summary()}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -255,10 +395,20 @@ def main():
     ap.add_argument("--impl", default="cgks", choices=["cgks", "reference"])
     ap.add_argument("--workload", default="vortex2048")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grids", type=int, default=256)
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--served-scale", type=float, default=8.0)
+    ap.add_argument("--arrival-scale", type=float, default=1.0)
+    ap.add_argument("--max-active", type=int, default=64)
+    ap.add_argument("--steps-per-round", type=int, default=8)
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload.startswith("batched"):
+        run_batched(args, world, rank, local)
+    elif args.workload == "served":
+        run_served(args, world, rank, local)
     else:
         run_cgks(args, world, rank, local)
     if world > 1:

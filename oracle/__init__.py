@@ -103,6 +103,7 @@ def lib():
             L.oc_run_fixed_dt.restype = ctypes.c_int
             L.oc_face1d_debug.argtypes = [ctypes.POINTER(Problem), dp, ctypes.c_int, ctypes.c_double, dp]
             L.oc_face1d_debug.restype = ctypes.c_int
+            L.oc_set_threads.argtypes = [ctypes.c_int]
             _lib = L
     return _lib
 
@@ -211,13 +212,18 @@ def cfl_dt(problem: Problem, W: np.ndarray) -> float:
 
 
 # ----------------------------------------------------------------------------- stepping
+def set_threads(n: int):
+    """OpenMP threads used by the oracle's loops from now on."""
+    lib().oc_set_threads(int(n))
+
+
 def run(problem: Problem, W: np.ndarray, nsteps: int, t_end: float = 0.0, t0: float = 0.0, threads=None):
     """Advance ``nsteps`` S2O4 steps (stopping at t_end when t_end > 0).
 
     Returns (W_new, t, steps, last_dt).  W has planes (6, nx) in 1D and
     (12, ny, nx) in 2D."""
     if threads is not None:
-        os.environ["OMP_NUM_THREADS"] = str(threads)
+        set_threads(threads)
     Wc = _f64(W).copy()
     t = np.array([t0], dtype=np.float64)
     steps = ctypes.c_long(0)

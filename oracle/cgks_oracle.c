@@ -51,6 +51,7 @@
  * Build: gcc -O2 -fPIC -shared -fopenmp -ffp-contract=off
  */
 #include <math.h>
+#include <omp.h>
 #include <stdlib.h>
 #include <string.h>
 #include <stdint.h>
@@ -966,6 +967,12 @@ int oc_run(const oc_problem *P, double *W, int nsteps, double t_end, double *t, 
         if (last_dt) *last_dt = dt;
     }
     return OC_OK;
+}
+
+/* number of OpenMP threads of the oracle's loops (0: leave the default) */
+void oc_set_threads(int n)
+{
+    if (n > 0) omp_set_num_threads(n);
 }
 
 /* one step with a given dt (used by the accuracy tests with dt = C dx^2) */

@@ -14,6 +14,12 @@ size_t smem_16x8(int);
 size_t smem_8x16(int);
 size_t smem_32x4(int);
 size_t smem_64x1(int);
+cudaError_t launch_stage_16x7(int, const GridDev*, const TileRef*, int, int, cudaStream_t);
+cudaError_t launch_stage_7x16(int, const GridDev*, const TileRef*, int, int, cudaStream_t);
+cudaError_t launch_stage_14x8(int, const GridDev*, const TileRef*, int, int, cudaStream_t);
+size_t smem_16x7(int);
+size_t smem_7x16(int);
+size_t smem_14x8(int);
 
 cudaError_t launch_stage(int shape, int stage, const GridDev* grids, const TileRef* tiles, int ntiles, int nblocks,
                          cudaStream_t st)
@@ -23,6 +29,9 @@ cudaError_t launch_stage(int shape, int stage, const GridDev* grids, const TileR
     case TILE_8x16: return launch_stage_8x16(stage, grids, tiles, ntiles, nblocks, st);
     case TILE_32x4: return launch_stage_32x4(stage, grids, tiles, ntiles, nblocks, st);
     case TILE_64x1: return launch_stage_64x1(stage, grids, tiles, ntiles, nblocks, st);
+    case TILE_16x7: return launch_stage_16x7(stage, grids, tiles, ntiles, nblocks, st);
+    case TILE_7x16: return launch_stage_7x16(stage, grids, tiles, ntiles, nblocks, st);
+    case TILE_14x8: return launch_stage_14x8(stage, grids, tiles, ntiles, nblocks, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -34,6 +43,9 @@ size_t stage_smem_bytes(int shape, int stage)
     case TILE_8x16: return smem_8x16(stage);
     case TILE_32x4: return smem_32x4(stage);
     case TILE_64x1: return smem_64x1(stage);
+    case TILE_16x7: return smem_16x7(stage);
+    case TILE_7x16: return smem_7x16(stage);
+    case TILE_14x8: return smem_14x8(stage);
     default: return 0;
     }
 }

@@ -38,10 +38,13 @@ struct GridDev {
 // One unit of work of the stage kernels: a TX x TY tile of one grid.
 struct TileRef { int grid, x0, y0, pad; };
 
-// tile shapes compiled into the library
-enum TileShape { TILE_16x8 = 0, TILE_8x16 = 1, TILE_32x4 = 2, TILE_64x1 = 3, TILE_COUNT = 4 };
-inline int tile_w(int s) { return s == TILE_16x8 ? 16 : s == TILE_8x16 ? 8 : s == TILE_32x4 ? 32 : 64; }
-inline int tile_h(int s) { return s == TILE_16x8 ? 8 : s == TILE_8x16 ? 16 : s == TILE_32x4 ? 4 : 1; }
+// tile shapes compiled into the library.  16x7, 7x16 and 14x8 give 247, 247
+// and 246 face segments per tile, i.e. one pass of the 256-thread CTA over the
+// heaviest phase (16x8 needs 280: a second pass with a single warp)
+enum TileShape { TILE_16x8 = 0, TILE_8x16 = 1, TILE_32x4 = 2, TILE_64x1 = 3, TILE_16x7 = 4, TILE_7x16 = 5,
+                 TILE_14x8 = 6, TILE_COUNT = 7 };
+inline int tile_w(int s) { static const int w[TILE_COUNT] = {16, 8, 32, 64, 16, 7, 14}; return w[s]; }
+inline int tile_h(int s) { static const int h[TILE_COUNT] = {8, 16, 4, 1, 7, 16, 8}; return h[s]; }
 
 // launchers (defined in the kernel translation units)
 cudaError_t launch_stage(int shape, int stage, const GridDev* grids, const TileRef* tiles, int ntiles,
@@ -69,13 +72,13 @@ struct BatchPlan {
     int nsm = 1, dim = 2;
     long long cells = 0;
     GridDev* d_grids = nullptr;
-    TileRef* d_tiles[TILE_COUNT] = {nullptr, nullptr, nullptr, nullptr};
-    int ntiles[TILE_COUNT] = {0, 0, 0, 0};
-    cudaGraphExec_t exec[TILE_COUNT] = {nullptr, nullptr, nullptr, nullptr};
+    TileRef* d_tiles[TILE_COUNT] = {};
+    int ntiles[TILE_COUNT] = {};
+    cudaGraphExec_t exec[TILE_COUNT] = {};
     std::vector<int> candidates;
     int chosen = -1, trial_idx = 0;
-    float trial_ms[TILE_COUNT] = {0, 0, 0, 0};
-    int trial_count[TILE_COUNT] = {0, 0, 0, 0};
+    float trial_ms[TILE_COUNT] = {};
+    int trial_count[TILE_COUNT] = {};
 };
 
 cudaError_t make_plan(cgks_solver* const* solvers, int n, cudaStream_t stream, int forced_shape, BatchPlan** out);

@@ -1,0 +1,81 @@
+"""Continuous-batching server: requests of different sizes, kinds and step counts, submitted while
+others run, with fewer slots than requests so that admission happens as slots free up; every
+result must equal the same solve run alone (bit for bit: the batched launch performs the same
+arithmetic per face and cell)."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from paper_2001_01570_gb300 import cgks, workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def _alone(spec, W, nsteps):
+    s = cgks.Solver(cgks.problem_from_spec(spec))
+    s.set_state(W)
+    s.step(nsteps)
+    out, _, steps = s.get_state()
+    s.close()
+    assert steps == nsteps
+    return out
+
+
+def _cases():
+    return [
+        (wl.acoustic_pulse(40, 1e-3, 4.0, 10.0, 30.0), 9),
+        (wl.isentropic_vortex(32), 5),
+        (wl.shock_vortex(nx=48, ny=24, mach=1.3), 12),
+        (wl.acoustic_pulse(64, 1e-5, 7.0, 50.0, 5.0), 3),
+        (wl.isentropic_vortex(24), 7),
+        (wl.shock_vortex(nx=40, ny=20, mach=1.05), 4),
+    ]
+
+
+def test_served_results_equal_alone_and_stats():
+    cases = _cases()
+    refs = [_alone(spec, W, n) for (spec, W), n in cases]
+    srv = cgks.cgks_serve_start(hbm_budget_bytes=64e6, max_active=3, steps_per_round=2)
+    ids = []
+    try:
+        def submitter():
+            for (spec, W), n in cases:
+                ids.append(cgks.cgks_serve_submit(srv, cgks.problem_from_spec(spec), W, n))
+                time.sleep(0.01)
+        th = threading.Thread(target=submitter)
+        th.start()
+        th.join()
+        outs = []
+        for rid, ((spec, W), n) in zip(ids, cases):
+            out = np.empty_like(W)
+            cgks.cgks_serve_wait(srv, rid, 120.0, out)
+            outs.append(out)
+        stats = cgks.cgks_serve_stats(srv)
+    finally:
+        cgks.cgks_serve_stop(srv)
+    for out, ref in zip(outs, refs):
+        assert np.array_equal(out, ref)
+    assert stats["completed"] == len(cases) and stats["failed"] == 0
+    assert stats["p99_s"] >= stats["p50_s"] > 0.0
+    assert stats["hbm_peak"] <= 64e6
+    expected = sum(W.shape[1] * W.shape[2] * n for (spec, W), n in cases)
+    assert stats["cell_updates"] == expected
+
+
+def test_budget_limits_concurrency():
+    """With a budget that holds one 64^2 solve at a time, requests run one after another."""
+    spec, W = wl.acoustic_pulse(64, 1e-3, 5.0, 20.0, 20.0)
+    one = 3 * 12 * 64 * 64 * 8 + 4096
+    srv = cgks.cgks_serve_start(hbm_budget_bytes=one * 1.5, max_active=8, steps_per_round=1)
+    try:
+        ids = [cgks.cgks_serve_submit(srv, cgks.problem_from_spec(spec), W, 3) for _ in range(3)]
+        out = np.empty_like(W)
+        for rid in ids:
+            cgks.cgks_serve_wait(srv, rid, 120.0, out)
+        stats = cgks.cgks_serve_stats(srv)
+    finally:
+        cgks.cgks_serve_stop(srv)
+    assert stats["hbm_peak"] <= one * 1.5 and stats["completed"] == 3
+    assert np.array_equal(out, _alone(spec, W, 3))

@@ -1,0 +1,31 @@
+"""Host-side logic of the server that needs no GPU: argument checks and budget rejection."""
+import numpy as np
+import pytest
+
+from paper_2001_01570_gb300 import cgks, workloads as wl
+
+
+def test_budget_rejection_and_bad_arguments():
+    srv = cgks.cgks_serve_start(hbm_budget_bytes=1e6, max_active=2, steps_per_round=2)
+    try:
+        spec, W = wl.acoustic_pulse(64, 1e-3, 4.0, 10.0, 10.0)     # 3 x 12 x 64^2 x 8 B > 1 MB
+        with pytest.raises(cgks.CgksError) as ei:
+            cgks.cgks_serve_submit(srv, cgks.problem_from_spec(spec), W, 5)
+        assert ei.value.status == cgks.CGKS_E_BUDGET
+        p1 = cgks.make_problem(1, 10, 1, 0.0, 1.0)
+        with pytest.raises(cgks.CgksError) as ei:
+            cgks.cgks_serve_submit(srv, p1, np.zeros((6, 10)), 5)
+        assert ei.value.status == cgks.CGKS_E_INVAL
+        with pytest.raises(cgks.CgksError) as ei:
+            cgks.cgks_serve_poll(srv, 12345)
+        assert ei.value.status == cgks.CGKS_E_NOTFOUND
+        st = cgks.cgks_serve_stats(srv)
+        assert st["rejected"] == 1 and st["submitted"] == 0 and st["completed"] == 0
+    finally:
+        cgks.cgks_serve_stop(srv)
+
+
+def test_bad_config():
+    with pytest.raises(cgks.CgksError) as ei:
+        cgks.cgks_serve_start(hbm_budget_bytes=0, max_active=2, steps_per_round=2)
+    assert ei.value.status == cgks.CGKS_E_INVAL
