@@ -136,6 +136,45 @@ const char* cgks_status_string(cgks_status st);
 const char* cgks_last_error(void);
 
 /* ------------------------------------------------------------------------
+ * Allocation-free stepping.  (The paper has no counterpart: this entry point
+ * exists for callers of this library, not for the method.)
+ *
+ * Some callers cannot let a library call cudaMalloc: applications that manage
+ * all device memory through their own pool or allocator, code that is inside a
+ * region where the allocator must not be re-entered, or embeddings with a
+ * fixed memory footprint.  cgks_step_noalloc advances a 2D problem whose state
+ * the caller already holds in device memory and allocates nothing: the second
+ * state buffer, the intermediate state, the control block and the tile queue
+ * live in fixed-size device arrays of the library (file-scope __device__
+ * storage, about 12.6 MB plus 256 KB), which every GPU that loads the library
+ * holds until the process exits.
+ *
+ * prob:        2D problem, nx*ny <= CGKS_NOALLOC_MAX_CELLS and at most
+ *              CGKS_NOALLOC_MAX_TILES tiles of 16x8 cells
+ * planes:      device pointer, 12 planes of ny*nx doubles (layout above); read
+ *              as the initial state and overwritten with the state after the
+ *              steps (or the last valid state on CGKS_E_NONPHYSICAL)
+ * nsteps:      S2O4 steps to take (dt from the CFL condition each step)
+ * t_inout:     time of the state in, time after the steps out
+ * cuda_stream: stream for all work (NULL: the legacy default stream); the
+ *              call synchronises it before returning
+ * Errors: CGKS_E_INVAL (3D/1D problem, grid larger than the maximum, bad
+ * parameters), CGKS_E_NONPHYSICAL, CGKS_E_CUDA.
+ * The first call on a device looks up the addresses of the fixed arrays and
+ * sets kernel attributes; make that first call before any stream capture.
+ * All calls share the same arrays: calls whose work overlaps on the GPU (from
+ * several threads or streams) race and must be serialised by the caller.
+ * Each call re-initialises the control block and overwrites the scratch it
+ * reads, so no state carries over from one call to the next. */
+#define CGKS_NOALLOC_MAX_CELLS 65536
+#define CGKS_NOALLOC_MAX_TILES 16384
+cgks_status cgks_step_noalloc(const cgks_problem* prob, double* planes, int nsteps, double* t_inout,
+                              void* cuda_stream);
+
+/* Detail of the last failing cgks_step_noalloc call on the calling thread. */
+const char* cgks_noalloc_last_error(void);
+
+/* ------------------------------------------------------------------------
  * Serving: a continuous-batching solve server.  Requests (2D problems with an
  * initial state and a step count) may be submitted from any thread at any
  * time.  A scheduler thread admits them in arrival order while the active set

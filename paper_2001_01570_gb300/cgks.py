@@ -92,6 +92,9 @@ def load():
                  "cgks_serve_stop"):
         getattr(L, name).restype = ctypes.c_int
     L.cgks_serve_last_error.restype = ctypes.c_char_p
+    L.cgks_step_noalloc.argtypes = [ctypes.POINTER(cgks_problem), vp, ctypes.c_int, dp, vp]
+    L.cgks_step_noalloc.restype = ctypes.c_int
+    L.cgks_noalloc_last_error.restype = ctypes.c_char_p
     L.cgks_status_string.argtypes = [ctypes.c_int]
     L.cgks_status_string.restype = ctypes.c_char_p
     L.cgks_last_error.restype = ctypes.c_char_p
@@ -228,6 +231,22 @@ def cgks_serve_stats(server) -> dict:
 
 def cgks_serve_stop(server):
     _scheck(load().cgks_serve_stop(server))
+
+
+NOALLOC_MAX_CELLS = 65536
+
+
+def cgks_step_noalloc(problem: cgks_problem, planes_device, nsteps, t=0.0, stream=None):
+    """Advance the 2D state held in ``planes_device`` (a CUDA tensor of 12 x ny x nx float64, or a
+    raw device pointer) by ``nsteps`` steps in place, without any device allocation.
+    Returns the new time."""
+    ptr = planes_device.data_ptr() if hasattr(planes_device, "data_ptr") else int(planes_device)
+    tt = ctypes.c_double(float(t))
+    st = load().cgks_step_noalloc(ctypes.byref(problem), ctypes.c_void_p(ptr), int(nsteps), ctypes.byref(tt),
+                                  ctypes.c_void_p(stream or 0))
+    if st != CGKS_OK:
+        raise CgksError(st, load().cgks_noalloc_last_error().decode())
+    return tt.value
 
 
 def cgks_last_launch_count() -> int:
