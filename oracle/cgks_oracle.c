@@ -716,7 +716,7 @@ static int step1d(const oc_problem *P, double *W, double dt)
     int err = 0;
     /* stage 1 */
     fill_ghosts1d(P, W, E);
-#pragma omp parallel for reduction(| : err)
+#pragma omp parallel for reduction(| : err) if (nx >= 4096)
     for (int f = 0; f <= nx; ++f) err |= face1d(P, E, f, dt, &fr[f]);
     if (err) goto done;
     for (int i = 0; i < nx; ++i)
@@ -731,7 +731,7 @@ static int step1d(const oc_problem *P, double *W, double dt)
         }
     /* stage 2 */
     fill_ghosts1d(P, Ws, E);
-#pragma omp parallel for reduction(| : err)
+#pragma omp parallel for reduction(| : err) if (nx >= 4096)
     for (int f = 0; f <= nx; ++f) err |= face1d(P, E, f, dt, &fr[f]);
     if (err) goto done;
     for (int i = 0; i < nx; ++i)
@@ -878,10 +878,10 @@ static int faces2d(const oc_problem *P, const double *E, double dt, face_res *fx
         int nf = (o == 0) ? nx + 1 : ny + 1;     /* faces along the normal */
         int nr = (o == 0) ? ny : nx;             /* rows along the tangent */
         row_rec *rr = malloc((size_t)nf * (nr + 4) * sizeof(row_rec));
-#pragma omp parallel for collapse(2)
+#pragma omp parallel for collapse(2) if (nf * nr >= 1024)
         for (int r = -2; r <= nr + 1; ++r)
             for (int f = 0; f < nf; ++f) row_recon(P, E, o, f, r, &rr[(size_t)(r + 2) * nf + f]);
-#pragma omp parallel for collapse(2) reduction(| : err)
+#pragma omp parallel for collapse(2) reduction(| : err) if (nf * nr >= 1024)
         for (int r = 0; r < nr; ++r)
             for (int f = 0; f < nf; ++f) {
                 face_res res;

@@ -98,7 +98,7 @@ __device__ __forceinline__ void weno_side(double base, double d1, double d2, dou
     const double n4 = (7.0 / 98.0) * (e4 + Z) * L4;
     const double n5 = (17.0 / 49.0) * (e5 + Z) * L5;
     const double n6 = (17.0 / 49.0) * (e6 + Z) * L6;
-    const double inv = 1.0 / ((n0 + n1) + (n2 + n3) + (n4 + n5) + n6);
+    const double inv = __drcp_rn((n0 + n1) + (n2 + n3) + (n4 + n5) + n6);
     // candidate values minus Q_i, Eq. (sub-stencil)
     const double q0 = (7.0 / 6.0) * d1 - (2.0 / 3.0) * A;
     const double q13 = (1.0 / 6.0) * d1 + (1.0 / 3.0) * d2;
@@ -199,12 +199,13 @@ __device__ __forceinline__ void a_psi_uv(const Moments& m, const double a[4], do
 // (closed form of the 4x4 moment system)
 struct SlopeCtx { double U, V, Bm, inv_theta, c4; };
 
-__device__ __forceinline__ void slope_ctx(double U, double V, double theta, double inv_theta, double K, SlopeCtx& s)
+__device__ __forceinline__ void slope_ctx(double U, double V, double theta, double inv_theta, double K,
+                                          double inv_K2, SlopeCtx& s)
 {
     s.U = U; s.V = V;
     s.Bm = U * U + V * V + (K + 2.0) * theta;
     s.inv_theta = inv_theta;
-    s.c4 = inv_theta * inv_theta / (K + 2.0);
+    s.c4 = inv_theta * inv_theta * inv_K2;
 }
 
 __device__ __forceinline__ void micro_slope(const SlopeCtx& s, const double b[4], double a[4])
@@ -223,12 +224,15 @@ __device__ __forceinline__ void micro_slope(const SlopeCtx& s, const double b[4]
 // Inputs: conservative W and its x (normal), y (tangential) derivatives up to
 // second order.  Outputs conservative W_t, W_tt and the flux time derivative
 // F_t of the normal Euler flux.
-struct EulerTD { double Wt[4], Wtt[4], Ft[4], F[4]; };
+// TNS is rho <(a_n u + a_t v + A) u psi> of the equilibrium state, i.e. the
+// Chapman-Enskog Navier-Stokes flux of the BGK model per unit collision time
+// (mu = tau p, bulk part 2/(K+2), heat conduction (K+4)/2 tau p grad(p/rho)).
+struct EulerTD { double Wt[4], Wtt[4], Ft[4], F[4], TNS[4]; };
 
 __device__ __forceinline__ void euler_time_derivs(const double W[4], const double Wx[4], const double Wy[4],
                                                   const double Wxx[4], const double Wxy[4], const double Wyy[4],
-                                                  double gamma, double ir, double U, double V, double p,
-                                                  EulerTD& o)
+                                                  double gamma, double inv_gm1, double K2inv2, double Kheat,
+                                                  double ir, double U, double V, double p, EulerTD& o)
 {
     const double gm1 = gamma - 1.0;
     const double rho = W[0], m = W[1], n = W[2], E = W[3];
@@ -276,7 +280,6 @@ __device__ __forceinline__ void euler_time_derivs(const double W[4], const doubl
     // back to conservative variables
     const double q2 = U * U + V * V;
     const double uut = U * Ut + V * Vt;
-    const double inv_gm1 = 1.0 / gm1;
     o.Wt[0] = rt;
     o.Wt[1] = rt * U + rho * Ut;
     o.Wt[2] = rt * V + rho * Vt;
@@ -295,6 +298,14 @@ __device__ __forceinline__ void euler_time_derivs(const double W[4], const doubl
     o.Ft[1] = mt * U + m * Ut + pt;
     o.Ft[2] = mt * V + m * Vt;
     o.Ft[3] = Ut * (E + p) + U * (o.Wt[3] + pt);
+    // BGK Navier-Stokes flux per unit tau in the face-normal direction
+    const double sxx = p * (2.0 * Ux - K2inv2 * Dv);
+    const double sxy = p * (Uy + Vx);
+    const double thx = (px - p * ir * rx) * ir;            // d/dx (p / rho)
+    o.TNS[0] = 0.0;
+    o.TNS[1] = sxx;
+    o.TNS[2] = sxy;
+    o.TNS[3] = U * sxx + V * sxy + Kheat * p * thx;
 }
 
 // ------------------------------------------------------------------------
@@ -306,6 +317,8 @@ struct PointIn {
 
 struct Params {
     double gamma, K, eps_tau, c_tau, dt;
+    double idt, inv_K2, inv_gm1;   // 1/dt, 1/(K+2), 1/(gamma-1)
+    double K2inv2, Kheat;          // 2/(K+2), (K+4)/2
 };
 
 // STAGE 1: Fb, Ft, Wm = W(dt/2), Wb = W(dt) with W0_tt^n;  STAGE 2: Ft, Wtt
@@ -315,15 +328,14 @@ __device__ __forceinline__ bool gks_point(const PointIn& in, const Params& P,
 {
     const double gm1 = P.gamma - 1.0, K = P.K, dt = P.dt;
     // equilibrium state g0
-    const double ir0 = 1.0 / in.W0[0];
+    const double ir0 = __drcp_rn(in.W0[0]);
     const double U0 = in.W0[1] * ir0, V0 = in.W0[2] * ir0;
     const double p0 = gm1 * (in.W0[3] - 0.5 * (in.W0[1] * U0 + in.W0[2] * V0));
-    const double th0 = p0 * ir0;
     // non-equilibrium states
-    const double irl = 1.0 / in.Wl[0];
+    const double irl = __drcp_rn(in.Wl[0]);
     const double Ul = in.Wl[1] * irl, Vl = in.Wl[2] * irl;
     const double pl = gm1 * (in.Wl[3] - 0.5 * (in.Wl[1] * Ul + in.Wl[2] * Vl));
-    const double irr = 1.0 / in.Wr[0];
+    const double irr = __drcp_rn(in.Wr[0]);
     const double Ur = in.Wr[1] * irr, Vr = in.Wr[2] * irr;
     const double pr = gm1 * (in.Wr[3] - 0.5 * (in.Wr[1] * Ur + in.Wr[2] * Vr));
     const bool ok = (in.W0[0] > 0.0) && (p0 > 0.0) && (in.Wl[0] > 0.0) && (pl > 0.0) && (in.Wr[0] > 0.0) && (pr > 0.0);
@@ -331,27 +343,18 @@ __device__ __forceinline__ bool gks_point(const PointIn& in, const Params& P,
 
     // Euler derivatives of the equilibrium state (W_t, W_tt, F, F_t)
     EulerTD e;
-    euler_time_derivs(in.W0, in.W0n, in.W0t, in.W0nn, in.W0nt, in.W0tt, P.gamma, ir0, U0, V0, p0, e);
+    euler_time_derivs(in.W0, in.W0n, in.W0t, in.W0nn, in.W0nt, in.W0tt, P.gamma, P.inv_gm1, P.K2inv2, P.Kheat, ir0,
+                      U0, V0, p0, e);
 
-    // tau-terms of g0: T2 = <(a_n u + a_t v) u psi> rho, T1 = F_t
-    Moments m0;
-    m0.u[0] = 1.0; m0.u[1] = U0;
-    moments_tail(m0, U0, V0, th0, K);
-    SlopeCtx s0;
-    slope_ctx(U0, V0, th0, 1.0 / th0, K, s0);
-    double bn[4], bt[4], an[4], at[4], T2[4], tmp[4];
-    for (int k = 0; k < 4; ++k) { bn[k] = in.W0n[k] * ir0; bt[k] = in.W0t[k] * ir0; }
-    micro_slope(s0, bn, an);
-    micro_slope(s0, bt, at);
-    a_psi_uv<2, 0>(m0, an, T2);
-    a_psi_uv<1, 1>(m0, at, tmp);
-    for (int k = 0; k < 4; ++k) T2[k] = in.W0[0] * (T2[k] + tmp[k]);
+    // tau-terms of g0: rho <(a_n u + a_t v) u psi> = TNS - F_t (the time part is the Euler F_t)
+    double T2[4];
+    for (int k = 0; k < 4; ++k) T2[k] = e.TNS[k] - e.Ft[k];
 
     // Sec. 4: collision time with pressure-jump enhancement
-    const double tau = P.eps_tau * dt + P.c_tau * fabs((pl - pr) / (pl + pr)) * dt;
+    const double tau = P.eps_tau * dt + P.c_tau * fabs((pl - pr) * __drcp_rn(pl + pr)) * dt;
     // h = exp(-dt / (2 tau)) weights the non-equilibrium part of the interface state
     double h = 0.0;
-    if (tau > 0.0) h = exp(-0.5 * dt / tau);
+    if (tau > 0.0) h = exp(-0.5 * dt * __drcp_rn(tau));
     // below 1e-20 that part is under 1e-20 of the state it is added to: far below one ulp,
     // so its velocity moments are not evaluated (the flux terms, weighted by O(tau), are)
     const bool need_ne = (STAGE == 1) && (h >= 1e-20);
@@ -360,13 +363,14 @@ __device__ __forceinline__ bool gks_point(const PointIn& in, const Params& P,
     double Fh[4], Th[4], Wh[4] = {0, 0, 0, 0}, Wsl[4] = {0, 0, 0, 0};
     {
         Moments ml;
+        const double ithl = __drcp_rn(thl);
         const double sq = rsqrt(2.0 * thl);            // sqrt(lambda_l)
-        const double ex = exp(-Ul * Ul * (0.5 / thl));
+        const double ex = exp(-Ul * Ul * (0.5 * ithl));
         ml.u[0] = 0.5 * erfc(-sq * Ul);
         ml.u[1] = Ul * ml.u[0] + ex * (2.0 * thl * sq) * 0.28209479177387814;  // e^{-l U^2} / (2 sqrt(pi l))
         moments_tail(ml, Ul, Vl, thl, K);
         SlopeCtx sl;
-        slope_ctx(Ul, Vl, thl, 1.0 / thl, K, sl);
+        slope_ctx(Ul, Vl, thl, ithl, K, P.inv_K2, sl);
         double b1[4], b2[4], a1[4], a2[4], o1[4], o2[4], f[4];
         for (int k = 0; k < 4; ++k) { b1[k] = in.Wln[k] * irl; b2[k] = in.Wlt[k] * irl; }
         micro_slope(sl, b1, a1);
@@ -384,13 +388,14 @@ __device__ __forceinline__ bool gks_point(const PointIn& in, const Params& P,
     }
     {
         Moments mr;
+        const double ithr = __drcp_rn(thr);
         const double sq = rsqrt(2.0 * thr);
-        const double ex = exp(-Ur * Ur * (0.5 / thr));
+        const double ex = exp(-Ur * Ur * (0.5 * ithr));
         mr.u[0] = 0.5 * erfc(sq * Ur);
         mr.u[1] = Ur * mr.u[0] - ex * (2.0 * thr * sq) * 0.28209479177387814;
         moments_tail(mr, Ur, Vr, thr, K);
         SlopeCtx sr;
-        slope_ctx(Ur, Vr, thr, 1.0 / thr, K, sr);
+        slope_ctx(Ur, Vr, thr, ithr, K, P.inv_K2, sr);
         double b1[4], b2[4], a1[4], a2[4], o1[4], o2[4], f[4];
         for (int k = 0; k < 4; ++k) { b1[k] = in.Wrn[k] * irr; b2[k] = in.Wrt[k] * irr; }
         micro_slope(sr, b1, a1);
@@ -408,7 +413,7 @@ __device__ __forceinline__ bool gks_point(const PointIn& in, const Params& P,
     }
 
     const double omh = 1.0 - h;
-    const double idt = 1.0 / dt;
+    const double idt = P.idt;
     const double ta = tau * omh;
     const double a = ta * (3.0 - h) * idt;
     const double g = 4.0 * ta * omh * idt * idt;
@@ -418,7 +423,7 @@ __device__ __forceinline__ bool gks_point(const PointIn& in, const Params& P,
         const double dTh = T2[k] - Th[k];
         const double dFh = Fh[k] - e.F[k];
         Ft[k] = e.Ft[k] - g * dFh + f4 * dTh;
-        if (STAGE == 1) Fb[k] = e.F[k] + a * dFh - tau * (T2[k] + e.Ft[k]) + b4 * dTh;
+        if (STAGE == 1) Fb[k] = e.F[k] + a * dFh - tau * e.TNS[k] + b4 * dTh;
     }
     if (STAGE == 1) {
         // interface state W(t) = W0 + t W_t + t^2/2 W_tt + e^{-t/tau} [W_ne(t) - W0 - t W_t]

@@ -165,7 +165,7 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
                 for (int f = 0; f < 4 * NREC; ++f) rec[f * nrec + ridx] = 0.0;
                 continue;
             }
-            const double ih = 1.0 / h;
+            const double ih = xo ? G.inv_dx : G.inv_dy;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 double Q[4], S[4];
@@ -195,6 +195,8 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
         // ---------------- phase 2: face segments, two Gauss points each
         Params P;
         P.gamma = G.gamma; P.K = G.K; P.eps_tau = G.eps_tau; P.c_tau = G.c_tau; P.dt = dt;
+        P.idt = __drcp_rn(dt); P.inv_K2 = __drcp_rn(G.K + 2.0); P.inv_gm1 = __drcp_rn(G.gamma - 1.0);
+        P.K2inv2 = 2.0 * P.inv_K2; P.Kheat = 0.5 * (G.K + 4.0);
         bool bad = false;
         constexpr int NSX = (TX + 1) * TY, NSY = TX * (TY + 1);
         for (int item = tid; item < NSX + NSY; item += kThreads) {
@@ -222,7 +224,7 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
                 for (int q = 0; q < NF; ++q) out[q * nout + oidx] = 0.0;
                 continue;
             }
-            const double iht = 1.0 / ht;
+            const double iht = xo ? G.inv_dy : G.inv_dx;
             double acc[NF];
 #pragma unroll
             for (int q = 0; q < NF; ++q) acc[q] = 0.0;

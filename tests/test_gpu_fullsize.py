@@ -4,7 +4,7 @@ The oracle cannot rerun these in a test, so tests/golden/make_golden.py (which c
 stored, for each case, the final time and step count, the per-plane max |value| over the whole grid
 and all 12 planes at 1500 seeded cells.  The GPU runs the same seeded inputs for the same number of
 steps; the sampled cells must agree to 1e-11 relative (per conserved variable, normalised by the
-stored max) and 1e-9 for the gradient planes."""
+scale of tests/parity_util.plane_scales) and 1e-9 for the gradient planes."""
 import multiprocessing as mp
 import os
 
@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 from conftest import GOLDEN
+from parity_util import plane_scales
 from paper_2001_01570_gb300 import cgks, workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -26,9 +27,10 @@ def _golden(name):
     return np.load(path)
 
 
-def _compare(out, g):
+def _compare(out, g, spec):
     planes = out.reshape(out.shape[0], -1)[:, g["idx"]]
-    err = np.abs(planes - g["values"]).max(axis=1) / np.where(g["maxabs"] > 0, g["maxabs"], 1.0)
+    scale = plane_scales(g["maxabs"], 2, spec.dx, spec.dy, spec.gamma)
+    err = np.abs(planes - g["values"]).max(axis=1) / np.where(scale > 0, scale, 1.0)
     assert err[:4].max() <= TOL, err
     assert err[4:].max() <= GRAD_TOL, err
     return err
@@ -48,7 +50,7 @@ def test_vortex_512_200_steps():
     spec, W = wl.isentropic_vortex(512)
     out, t, steps = _run(spec, W, 200)
     assert steps == int(g["steps"]) and abs(t - float(g["t"])) <= 1e-13 * float(g["t"])
-    _compare(out, g)
+    _compare(out, g, spec)
 
 
 def test_shock_vortex_1024x512_400_steps():
@@ -56,7 +58,7 @@ def test_shock_vortex_1024x512_400_steps():
     spec, W = wl.shock_vortex(1024, 512)
     out, t, steps = _run(spec, W, 400)
     assert steps == int(g["steps"]) and abs(t - float(g["t"])) <= 1e-12 * float(g["t"])
-    _compare(out, g)
+    _compare(out, g, spec)
 
 
 def _pulse_ic(p):
@@ -79,7 +81,7 @@ def test_batched_256_grids_100_steps():
         for k in order:
             out, t, steps = solvers[k].get_state()
             assert steps == int(goldens[k]["steps"]) == 100
-            _compare(out, goldens[k])
+            _compare(out, goldens[k], ics[k][0])
     finally:
         for s in solvers:
             s.close()

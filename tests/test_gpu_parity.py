@@ -12,8 +12,8 @@ pytestmark = pytest.mark.gpu
 GRAD_TOL = 1e-9      # cell-averaged gradient planes (reported separately, differences of interface states)
 
 
-def _check(gpu, ora, tol=TOL, grad_tol=GRAD_TOL):
-    err = rel_errors(gpu, ora)
+def _check(gpu, ora, tol=TOL, grad_tol=GRAD_TOL, spec=None):
+    err = rel_errors(gpu, ora, dx=spec.dx if spec else 1.0, dy=spec.dy if spec else 1.0)
     nv = nvars(ora)
     assert err[:nv].max() <= tol, f"conserved-variable errors {err[:nv]}"
     assert err[nv:].max() <= grad_tol, f"gradient errors {err[nv:]}"
@@ -26,7 +26,7 @@ def test_density_wave_1d_to_t2(eps_tau):
     g, tg, sg = run_gpu(spec, W, 5000, t_end=2.0)
     o, to, so = run_oracle(spec, W, 5000, t_end=2.0)
     assert sg == so and tg == pytest.approx(to, abs=1e-13) and to == 2.0
-    _check(g, o)
+    _check(g, o, spec=spec)
 
 
 def test_sod_1d():
@@ -34,7 +34,7 @@ def test_sod_1d():
     g, tg, sg = run_gpu(spec, W, 5000, t_end=0.2)
     o, to, so = run_oracle(spec, W, 5000, t_end=0.2)
     assert sg == so
-    _check(g, o)
+    _check(g, o, spec=spec)
 
 
 def test_vortex_ragged_tiles():
@@ -44,7 +44,7 @@ def test_vortex_ragged_tiles():
     W = W[:, :20, :].copy()
     g, _, _ = run_gpu(spec, W, 6)
     o, _, _ = run_oracle(spec, W, 6)
-    _check(g, o)
+    _check(g, o, spec=spec)
 
 
 def test_shock_vortex_all_boundary_types():
@@ -52,14 +52,14 @@ def test_shock_vortex_all_boundary_types():
     g, _, sg = run_gpu(spec, W, 8)
     o, _, so = run_oracle(spec, W, 8)
     assert sg == so == 8
-    _check(g, o)
+    _check(g, o, spec=spec)
 
 
 def test_acoustic_pulse():
     spec, W = wl.acoustic_pulse(40, 1e-3, 4.0, 13.0, 25.5)
     g, _, _ = run_gpu(spec, W, 10)
     o, _, _ = run_oracle(spec, W, 10)
-    _check(g, o)
+    _check(g, o, spec=spec)
 
 
 @pytest.mark.parametrize("bc", [(0, 0, 0, 0), (2, 3, 1, 1), (1, 1, 3, 3)])
