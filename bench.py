@@ -111,7 +111,8 @@ def dist_setup(args):
     if world > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
+        if args.impl == "cgks":
+            torch.cuda.set_device(local)
         dist.init_process_group("nccl" if args.impl == "cgks" else "gloo")
     return world, rank, local
 
