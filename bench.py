@@ -30,10 +30,14 @@ import numpy as np  # noqa: E402
 METRIC = "FP64 cell-updates/s on 1 GB300 (plain 2048^2 sweep); served-batched vs plain; p50/p99 solve latency"
 UNIT = "cell-updates/s"
 
-# FP64 floating-point operations per cell and stage executed by the stage kernels (FMA = 2),
+# FP64 floating-point operations per cell and stage executed by the 16x7 stage kernels (FMA = 2),
 # counted with ncu (sm__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on) on the 256^2
 # isentropic vortex and divided by the cells: profiles/stage_kernels_vortex256.md.
-FLOP_PER_CELL = {1: 15414.0, 2: 13902.0}
+FLOP_PER_CELL = {1: 12256.0, 2: 11778.0}
+# DRAM bytes (read + write) per cell of one stage-1 launch, ncu dram__bytes_{read,write}.sum on the
+# 1024^2 vortex (state larger than L2) divided by the cells; a launch on the 2048^2 bench grid moves
+# the same bytes per cell: profiles/stage_kernels_dram_vortex1024.md.
+DRAM_BYTES_PER_CELL = {1: 283.0e6 / 1048576, 2: 271.0e6 / 1048576}
 # measured FP64 peak of this GB300 (DFMA throughput loop, FMA = 2): profiles/fp64_peak_gb300.md
 FP64_PEAK_TFLOPS = 1.010
 
@@ -174,6 +178,8 @@ def run_cgks(args, world, rank, local):
     spec, W = workloads()[args.workload]()
     cells = spec.cells
     solver = cgks.Solver(cgks.problem_from_spec(spec), stream=stream.cuda_stream)
+    if args.tile:
+        cgks.cgks_set_tile_shape(solver.handle, args.tile)
     solver.set_state(W)
 
     # warm-up (also fills the per-kernel shared-memory configuration)
@@ -204,12 +210,16 @@ def run_cgks(args, world, rank, local):
     if FLOP_PER_CELL[1]:
         flops = FLOP_PER_CELL[1] * cells
         achieved = flops / (stage_ms[1] * 1e-3) / 1e12
+        same_kernel = args.tile in (None, "16x7")
         roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "stage_kernel<16,8,1>",
+                    "frac": achieved / FP64_PEAK_TFLOPS,
+                    "traffic": DRAM_BYTES_PER_CELL[1] * cells if same_kernel else None,
+                    "algorithmic_bytes": 288 * cells,
+                    "kernel": f"stage_kernel<{args.tile or '16,7'},1>",
                     "kernel_ms": stage_ms[1], "peak_source": "measured FP64 DFMA loop (FMA=2) on GB300"}
     else:
         roofline = {"bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": None,
-                    "traffic": None, "kernel": "stage_kernel<16,8,1>", "kernel_ms": stage_ms[1]}
+                    "traffic": None, "kernel": f"stage_kernel<{args.tile or '16,7'},1>", "kernel_ms": stage_ms[1]}
 
     # ---------------- end to end through the C ABI with host buffers
     host_in = torch.from_numpy(np.ascontiguousarray(W)).pin_memory()
@@ -396,6 +406,7 @@ def main():
     ap.add_argument("--impl", default="cgks", choices=["cgks", "reference"])
     ap.add_argument("--workload", default="vortex2048")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tile", default=None, help="tile shape of the plain path (e.g. 16x7, 24x8)")
     ap.add_argument("--grids", type=int, default=256)
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--served-scale", type=float, default=8.0)

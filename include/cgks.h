@@ -115,7 +115,14 @@ cgks_status cgks_step(cgks_solver* s, int nsteps, double t_end, double* t_out);
  * through cgks_get_state. */
 cgks_status cgks_batch_step(cgks_solver* const* solvers, int n, int nsteps);
 
-/* Tile shape (0: 16x8, 1: 8x16, 2: 32x4, 3: 64x1 cells per CTA) that the
+/* Cells per CTA tile of the stage kernels for this solver's plain steps:
+ * 0: 16x8, 1: 8x16, 2: 32x4, 3: 64x1, 4: 16x7, 5: 7x16, 6: 14x8, 7: 24x8; -1
+ * restores the default (16x7 in 2D, 64x1 in 1D).  The shape changes only the
+ * decomposition of the work, never the results.  Errors: CGKS_E_INVAL (1D
+ * solvers take only 64x1; 2D solvers any other shape). */
+cgks_status cgks_set_tile_shape(cgks_solver* s, int shape);
+
+/* Tile shape (numbered as for cgks_set_tile_shape) that the
  * autotuner of cgks_batch_step chose for this exact batch, or -1 while it is
  * still timing the candidates (it times each candidate shape on the first
  * steps of a new batch composition; the shape never changes the results). */

@@ -80,6 +80,8 @@ def load():
     for name in ("cgks_create", "cgks_destroy", "cgks_set_state", "cgks_get_state", "cgks_step", "cgks_batch_step",
                  "cgks_step_profiled"):
         getattr(L, name).restype = ctypes.c_int
+    L.cgks_set_tile_shape.argtypes = [vp, ctypes.c_int]
+    L.cgks_set_tile_shape.restype = ctypes.c_int
     L.cgks_batch_tile_shape.argtypes = [ctypes.POINTER(vp), ctypes.c_int]
     L.cgks_batch_tile_shape.restype = ctypes.c_int
     L.cgks_serve_start.argtypes = [ctypes.POINTER(cgks_serve_cfg), ctypes.POINTER(vp)]
@@ -182,6 +184,16 @@ def cgks_step_profiled(solver, nsteps):
     ms = (ctypes.c_double * 4)()
     _check(load().cgks_step_profiled(solver, int(nsteps), ms))
     return list(ms)
+
+
+TILE_SHAPES = ("16x8", "8x16", "32x4", "64x1", "16x7", "7x16", "14x8", "24x8")
+
+
+def cgks_set_tile_shape(solver, shape):
+    """shape: index or name from TILE_SHAPES, -1 for the default."""
+    if isinstance(shape, str):
+        shape = TILE_SHAPES.index(shape)
+    _check(load().cgks_set_tile_shape(solver, int(shape)))
 
 
 def cgks_batch_tile_shape(solvers) -> int:

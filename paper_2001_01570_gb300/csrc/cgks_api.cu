@@ -204,6 +204,25 @@ cgks_status cgks_create(const cgks_problem* prob, void* cuda_stream, cgks_solver
 
 extern "C" void cgks_forget_solver_plans(cgks_solver* s);
 
+cgks_status cgks_set_tile_shape(cgks_solver* s, int shape)
+{
+    if (!s) return fail(CGKS_E_INVAL, "solver is NULL");
+    if (shape < 0) shape = pick_shape(s->prob);
+    if (shape >= TILE_COUNT) return fail(CGKS_E_INVAL, "unknown tile shape");
+    if ((s->prob.dim == 1) != (shape == TILE_64x1)) return fail(CGKS_E_INVAL, "tile shape does not fit the dimension");
+    std::vector<TileRef> tiles = make_tiles(s->nx, s->ny, shape, 0);
+    TileRef* d = nullptr;
+    CK(cudaMalloc(&d, tiles.size() * sizeof(TileRef)));
+    cudaError_t e = cudaMemcpyAsync(d, tiles.data(), tiles.size() * sizeof(TileRef), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) { cudaFree(d); return cuda_fail(e, "cgks_set_tile_shape"); }
+    cudaFree(s->d_tiles);
+    s->d_tiles = d;
+    s->ntiles = (int)tiles.size();
+    s->shape = shape;
+    return CGKS_OK;
+}
+
 cgks_status cgks_destroy(cgks_solver* s)
 {
     if (!s) return fail(CGKS_E_INVAL, "solver is NULL");
@@ -420,7 +439,7 @@ cudaError_t make_plan(cgks_solver* const* solvers, int n, cudaStream_t stream, i
     bp->cells = cells;
     if (bp->dim == 1) { bp->candidates = {TILE_64x1}; }
     else if (forced_shape >= 0) { bp->candidates = {forced_shape}; }
-    else { bp->candidates = {TILE_16x7, TILE_14x8, TILE_16x8, TILE_7x16}; }
+    else { bp->candidates = {TILE_16x7, TILE_24x8, TILE_14x8, TILE_16x8}; }
     for (int shape : bp->candidates) {
         std::vector<TileRef> tiles;
         for (int g = 0; g < n; ++g) {

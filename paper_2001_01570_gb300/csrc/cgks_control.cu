@@ -20,6 +20,8 @@ cudaError_t launch_stage_14x8(int, const GridDev*, const TileRef*, int, int, cud
 size_t smem_16x7(int);
 size_t smem_7x16(int);
 size_t smem_14x8(int);
+cudaError_t launch_stage_24x8(int, const GridDev*, const TileRef*, int, int, cudaStream_t);
+size_t smem_24x8(int);
 
 cudaError_t launch_stage(int shape, int stage, const GridDev* grids, const TileRef* tiles, int ntiles, int nblocks,
                          cudaStream_t st)
@@ -32,6 +34,7 @@ cudaError_t launch_stage(int shape, int stage, const GridDev* grids, const TileR
     case TILE_16x7: return launch_stage_16x7(stage, grids, tiles, ntiles, nblocks, st);
     case TILE_7x16: return launch_stage_7x16(stage, grids, tiles, ntiles, nblocks, st);
     case TILE_14x8: return launch_stage_14x8(stage, grids, tiles, ntiles, nblocks, st);
+    case TILE_24x8: return launch_stage_24x8(stage, grids, tiles, ntiles, nblocks, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -46,6 +49,7 @@ size_t stage_smem_bytes(int shape, int stage)
     case TILE_16x7: return smem_16x7(stage);
     case TILE_7x16: return smem_7x16(stage);
     case TILE_14x8: return smem_14x8(stage);
+    case TILE_24x8: return smem_24x8(stage);
     default: return 0;
     }
 }

@@ -54,3 +54,20 @@ def test_nonphysical_state_is_reported_and_last_state_kept():
     s.set_state(good, t_good)
     s.step(1)
     s.close()
+
+
+@pytest.mark.parametrize("shape", ["16x8", "8x16", "32x4", "7x16", "14x8", "24x8"])
+def test_tile_shape_does_not_change_results(shape):
+    spec, W = wl.shock_vortex(nx=61, ny=37, mach=1.25)
+    ref = cgks.Solver(cgks.problem_from_spec(spec))
+    ref.set_state(W)
+    ref.step(3)
+    a, _, _ = ref.get_state()
+    ref.close()
+    s = cgks.Solver(cgks.problem_from_spec(spec))
+    cgks.cgks_set_tile_shape(s.handle, shape)
+    s.set_state(W)
+    s.step(3)
+    b, _, _ = s.get_state()
+    s.close()
+    assert np.array_equal(a, b)
