@@ -210,16 +210,16 @@ def run_cgks(args, world, rank, local):
     if FLOP_PER_CELL[1]:
         flops = FLOP_PER_CELL[1] * cells
         achieved = flops / (stage_ms[1] * 1e-3) / 1e12
-        same_kernel = args.tile in (None, "16x7")
+        same_kernel = args.tile in (None, "24x8")
         roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": achieved / FP64_PEAK_TFLOPS,
                     "traffic": DRAM_BYTES_PER_CELL[1] * cells if same_kernel else None,
                     "algorithmic_bytes": 288 * cells,
-                    "kernel": f"stage_kernel<{args.tile or '16,7'},1>",
+                    "kernel": f"stage_kernel<{args.tile or '24x8'},1>",
                     "kernel_ms": stage_ms[1], "peak_source": "measured FP64 DFMA loop (FMA=2) on GB300"}
     else:
         roofline = {"bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": None,
-                    "traffic": None, "kernel": f"stage_kernel<{args.tile or '16,7'},1>", "kernel_ms": stage_ms[1]}
+                    "traffic": None, "kernel": f"stage_kernel<{args.tile or '24x8'},1>", "kernel_ms": stage_ms[1]}
 
     # ---------------- end to end through the C ABI with host buffers
     host_in = torch.from_numpy(np.ascontiguousarray(W)).pin_memory()

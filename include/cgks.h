@@ -6,7 +6,8 @@
  *
  * What one time step computes (every step runs entirely in CUDA kernels):
  *   - dt from the CFL condition, dt = CFL * min over cells of
- *     min(dx/(|U|+c), dy/(|V|+c)) (Sec. 4);
+ *     min(dx/(|U|+c+2 nu/dx), dy/(|V|+c+2 nu/dy)) (Sec. 4; nu = mu/rho, 0 for
+ *     inviscid flow);
  *   - at every cell interface: the linear compact 8th-order reconstruction of
  *     the equilibrium state (Sec. 3.2, Eq. recons-8th-val) and the nonlinear
  *     WENO-Z compact reconstruction of the non-equilibrium left/right states
@@ -14,8 +15,10 @@
  *     averages and cell-averaged gradients on the stencil {I_i-1..I_i+2};
  *   - the gas-kinetic evolution at two Gauss points per face (Sec. 2.1,
  *     Eq. 3rd-simplify-flux) with collision time
- *     tau = eps_tau*dt + c_tau*|p_l-p_r|/(p_l+p_r)*dt (Sec. 4), giving the
- *     time-accurate flux, its time derivative and the interface state;
+ *     tau = eps_tau*dt + c_tau*|p_l-p_r|/(p_l+p_r)*dt for inviscid flow, or
+ *     tau = mu/p + c_tau*|p_l-p_r|/(p_l+p_r)*dt for viscous flow (Sec. 4),
+ *     giving the time-accurate flux, its time derivative and the interface
+ *     state;
  *   - the two-stage fourth-order update of cell averages (Sec. 2.2,
  *     Eq. step-hyper-1) and of the cell-averaged gradients by the Gauss
  *     theorem on the interface states (Sec. 3.1, Eq. compact-deriv-1).
@@ -78,6 +81,9 @@ typedef struct {
     double eps_tau;          /* tau = eps_tau*dt + c_tau*|dp|/(sum p)*dt; paper: 0.01 */
     double c_tau;            /* paper: 1 */
     double weno_eps;         /* epsilon of the WENO-Z weights; paper tests 1e-6, 1e-4 */
+    double mu;               /* dynamic viscosity; > 0 selects the viscous collision time
+                                tau = mu/p + c_tau*|dp|/(sum p)*dt (Sec. 4; Navier-Stokes with
+                                Prandtl number 1); 0: inviscid, tau from eps_tau */
 } cgks_problem;
 
 typedef struct cgks_solver cgks_solver;   /* opaque; owns the device planes of one grid */
@@ -117,7 +123,7 @@ cgks_status cgks_batch_step(cgks_solver* const* solvers, int n, int nsteps);
 
 /* Cells per CTA tile of the stage kernels for this solver's plain steps:
  * 0: 16x8, 1: 8x16, 2: 32x4, 3: 64x1, 4: 16x7, 5: 7x16, 6: 14x8, 7: 24x8; -1
- * restores the default (16x7 in 2D, 64x1 in 1D).  The shape changes only the
+ * restores the default (24x8 in 2D, 64x1 in 1D).  The shape changes only the
  * decomposition of the work, never the results.  Errors: CGKS_E_INVAL (1D
  * solvers take only 64x1; 2D solvers any other shape). */
 cgks_status cgks_set_tile_shape(cgks_solver* s, int shape);

@@ -47,11 +47,12 @@ class Problem(ctypes.Structure):
         ("gamma", ctypes.c_double), ("cfl", ctypes.c_double),
         ("bc", ctypes.c_int * 4), ("inflow", ctypes.c_double * 4),
         ("eps_tau", ctypes.c_double), ("c_tau", ctypes.c_double), ("weno_eps", ctypes.c_double),
+        ("mu", ctypes.c_double),
     ]
 
 
 def make_problem(dim, nx, ny, dx, dy, gamma=1.4, cfl=0.5, bc=(0, 0, 0, 0), inflow=(1.0, 0.0, 0.0, 1.0),
-                 eps_tau=0.01, c_tau=1.0, weno_eps=1e-6) -> Problem:
+                 eps_tau=0.01, c_tau=1.0, weno_eps=1e-6, mu=0.0) -> Problem:
     p = Problem()
     p.dim, p.nx, p.ny = int(dim), int(nx), int(ny)
     p.dx, p.dy = float(dx), float(dy)
@@ -60,6 +61,7 @@ def make_problem(dim, nx, ny, dx, dy, gamma=1.4, cfl=0.5, bc=(0, 0, 0, 0), inflo
         p.bc[k] = int(bc[k])
         p.inflow[k] = float(inflow[k])
     p.eps_tau, p.c_tau, p.weno_eps = float(eps_tau), float(c_tau), float(weno_eps)
+    p.mu = float(mu)
     return p
 
 

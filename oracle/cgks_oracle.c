@@ -46,7 +46,8 @@
  *     to it (a face-interpolated tangential gradient makes the 2D scheme
  *     linearly unstable under advection)
  *   - 1D uses K = (3-gamma)/(gamma-1) internal degrees of freedom
- *   - CFL: dt = CFL * min_cells min(dx/(|U|+c), dy/(|V|+c))
+ *   - CFL: dt = CFL * min_cells min(dx/(|U|+c), dy/(|V|+c)); with viscosity the
+ *     signal speed is |U|+c+2 nu/dx (nu = mu/rho)
  *
  * Build: gcc -O2 -fPIC -shared -fopenmp -ffp-contract=off
  */
@@ -69,6 +70,7 @@ typedef struct {
     int bc[4];          /* x-low, x-high, y-low, y-high */
     double inflow[4];   /* primitive rho, u, v, p for inflow sides */
     double eps_tau, c_tau, weno_eps;
+    double mu;          /* > 0: viscous collision time mu/p (Sec. 4) */
 } oc_problem;
 
 /* ------------------------------------------------------------------ */
@@ -518,8 +520,9 @@ int oc_gks_point(const oc_problem *P, int D, const oc_point_in *in, double dt, o
         }
     }
 
-    /* Sec. 4: collision time, enhanced by the pressure jump */
-    double tau = P->eps_tau * dt + P->c_tau * fabs((pl - pr) / (pl + pr)) * dt;
+    /* Sec. 4: collision time, enhanced by the pressure jump; for viscous flow the
+     * first part is mu/p with p the pressure of the equilibrium state at the point */
+    double tau = (P->mu > 0.0 ? P->mu / p : P->eps_tau * dt) + P->c_tau * fabs((pl - pr) / (pl + pr)) * dt;
     out->tau = tau;
 
     /* time integrals of the second-order flux over [0, dt] and [0, dt/2] */
@@ -628,8 +631,10 @@ double oc_cfl_dt(const oc_problem *P, const double *W)
         double rho, U, V, p;
         if (prim(D, P->gamma, Wc, &rho, &U, &V, &p)) return -1.0;
         double a = sqrt(P->gamma * p / rho);
-        double d = P->dx / (fabs(U) + a);
-        if (D == 2) { double dy = P->dy / (fabs(V) + a); if (dy < d) d = dy; }
+        /* viscous flow: the signal speed gains 2 nu / dx (explicit diffusion limit) */
+        double nu = P->mu / rho;
+        double d = P->dx / (fabs(U) + a + 2.0 * nu / P->dx);
+        if (D == 2) { double dy = P->dy / (fabs(V) + a + 2.0 * nu / P->dy); if (dy < d) d = dy; }
         if (d < best) best = d;
     }
     return P->cfl * best;

@@ -75,8 +75,8 @@ cgks_status validate(const cgks_problem* p)
     if (!(p->x1 > p->x0) || (p->dim == 2 && !(p->y1 > p->y0))) return fail(CGKS_E_INVAL, "empty domain");
     if (!(p->gamma > 1.0) || !(p->gamma < 3.0)) return fail(CGKS_E_INVAL, "gamma out of range");
     if (!(p->cfl > 0.0)) return fail(CGKS_E_INVAL, "cfl must be > 0");
-    if (!(p->eps_tau >= 0.0) || !(p->c_tau >= 0.0) || !(p->weno_eps > 0.0))
-        return fail(CGKS_E_INVAL, "eps_tau, c_tau must be >= 0 and weno_eps > 0");
+    if (!(p->eps_tau >= 0.0) || !(p->c_tau >= 0.0) || !(p->weno_eps > 0.0) || !(p->mu >= 0.0))
+        return fail(CGKS_E_INVAL, "eps_tau, c_tau, mu must be >= 0 and weno_eps > 0");
     const int nb = p->dim == 1 ? 2 : 4;
     for (int k = 0; k < nb; ++k) {
         if (p->bc[k] < CGKS_BC_PERIODIC || p->bc[k] > CGKS_BC_OUTFLOW) return fail(CGKS_E_INVAL, "unknown bc");
@@ -102,7 +102,7 @@ cgks_status read_ctrl(cgks_solver* s, Ctrl* c)
 
 int pick_shape(const cgks_problem& p)
 {
-    return p.dim == 1 ? TILE_64x1 : TILE_16x7;
+    return p.dim == 1 ? TILE_64x1 : TILE_24x8;
 }
 
 }  // namespace
@@ -181,6 +181,7 @@ cgks_status cgks_create(const cgks_problem* prob, void* cuda_stream, cgks_solver
     G.eps_tau = prob->eps_tau;
     G.c_tau = prob->c_tau;
     G.weno_eps = prob->weno_eps;
+    G.mu = prob->mu;
     {
         const double r = prob->inflow[0], u = prob->inflow[1], v = prob->dim == 1 ? 0.0 : prob->inflow[2];
         const double p = prob->inflow[3];
@@ -439,7 +440,7 @@ cudaError_t make_plan(cgks_solver* const* solvers, int n, cudaStream_t stream, i
     bp->cells = cells;
     if (bp->dim == 1) { bp->candidates = {TILE_64x1}; }
     else if (forced_shape >= 0) { bp->candidates = {forced_shape}; }
-    else { bp->candidates = {TILE_16x7, TILE_24x8, TILE_14x8, TILE_16x8}; }
+    else { bp->candidates = {TILE_24x8, TILE_16x7, TILE_14x8}; }
     for (int shape : bp->candidates) {
         std::vector<TileRef> tiles;
         for (int g = 0; g < n; ++g) {

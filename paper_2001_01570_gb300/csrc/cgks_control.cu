@@ -56,7 +56,7 @@ size_t stage_smem_bytes(int shape, int stage)
 
 static __device__ __forceinline__ unsigned long long inf_bits() { return 0x7ff0000000000000ull; }
 
-// Start of a step: dt = CFL * (min over cells of dx/(|U|+c)) of the current
+// Start of a step: dt = CFL * (min over cells of dx/(|U|+c+2 nu/dx)) of the current
 // state, clipped so that t does not pass t_end; marks grids that are finished.
 __global__ void begin_step_kernel(const GridDev* grids, int n)
 {
@@ -102,8 +102,9 @@ __global__ void cfl_kernel(const GridDev* grids, int gidx)
         const double p = (G.gamma - 1.0) * (E - 0.5 * (m * U + n * V));
         if (!(r > 0.0) || !(p > 0.0)) { bad = true; continue; }
         const double c0 = sqrt(G.gamma * p * ir);
-        double d = G.dx / (fabs(U) + c0);
-        if (G.dim == 2) d = fmin(d, G.dy / (fabs(V) + c0));
+        const double nu = G.mu * ir;
+        double d = G.dx / (fabs(U) + c0 + 2.0 * nu * G.inv_dx);
+        if (G.dim == 2) d = fmin(d, G.dy / (fabs(V) + c0 + 2.0 * nu * G.inv_dy));
         dmin = fmin(dmin, d);
     }
     if (bad) atomicOr(&G.ctrl->status, (int)CGKS_E_NONPHYSICAL);

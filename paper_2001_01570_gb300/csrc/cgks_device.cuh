@@ -347,7 +347,7 @@ struct PointIn {
 };
 
 struct Params {
-    double gamma, K, eps_tau, c_tau, dt;
+    double gamma, K, eps_tau, c_tau, dt, mu;
     double idt, inv_K2, inv_gm1;   // 1/dt, 1/(K+2), 1/(gamma-1)
     double K2inv2, Kheat;          // 2/(K+2), (K+4)/2
 };
@@ -381,8 +381,10 @@ __device__ __forceinline__ bool gks_point(const PointIn& in, const Params& P,
     double T2[4];
     for (int k = 0; k < 4; ++k) T2[k] = e.TNS[k] - e.Ft[k];
 
-    // Sec. 4: collision time with pressure-jump enhancement
-    const double tau = P.eps_tau * dt + P.c_tau * fabs((pl - pr) * __drcp_rn(pl + pr)) * dt;
+    // Sec. 4: collision time with pressure-jump enhancement; viscous flow: mu/p
+    // with p the equilibrium pressure at the point
+    const double tau = (P.mu > 0.0 ? P.mu * __drcp_rn(p0) : P.eps_tau * dt)
+                       + P.c_tau * fabs((pl - pr) * __drcp_rn(pl + pr)) * dt;
     // h = exp(-dt / (2 tau)) weights the non-equilibrium part of the interface state.
     // For dt > 80 tau, h < 4e-18: then 1 - h and 3 - h round to 1 and 3, and the
     // remaining h-terms change the window coefficients by under 2e-14 of a term

@@ -32,6 +32,7 @@ struct GridDev {
     int bc[4];
     double dx, dy, inv_dx, inv_dy;
     double gamma, K, cfl, eps_tau, c_tau, weno_eps;
+    double mu;          // > 0: viscous collision time mu/p
     double inflow[4];   // conservative inflow state
 };
 

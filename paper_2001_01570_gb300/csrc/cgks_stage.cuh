@@ -133,13 +133,15 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
         }
         __syncthreads();
 
-        // ---------------- phase 1: normal reconstruction per (face, row)
+        // ---------------- phase 1: normal reconstruction per (face, row, variable)
+        // items are (variable, record) pairs so the 256 threads finish together
         const double eps = G.weno_eps;
-        constexpr int NRX = (TX + 1) * (TY + 4), NRY = (TX + 4) * (TY + 1);
-        for (int item = tid; item < NRX + NRY; item += kThreads) {
-            const bool xo = item < NRX;
-            int box_i, box_j, step_i, step_j, ridx, nrec, pv[4], gn;
-            double h;
+        constexpr int NRX = (TX + 1) * (TY + 4), NRY = (TX + 4) * (TY + 1), NR = NRX + NRY;
+        for (int it = tid; it < 4 * NR; it += kThreads) {
+            const int k = it / NR, item = it - k * NR;
+            const bool xo = item < NR - NRY;
+            int box_i, box_j, step_i, step_j, ridx, nrec, pv, gn;
+            double h, ih;
             double* rec;
             bool valid, inner;
             if (xo) {
@@ -147,54 +149,50 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
                 valid = (x0 + fl <= nx) && (y0 - 2 + rl <= ny + 1);
                 inner = (rl >= 1) && (rl <= TY + 2);
                 box_i = fl; box_j = rl; step_i = 1; step_j = 0;
-                h = G.dx; gn = 4;
-                pv[0] = 0; pv[1] = 1; pv[2] = 2; pv[3] = 3;
+                h = G.dx; ih = G.inv_dx; gn = 4;
+                pv = k;
                 rec = rx; nrec = (TY + 4) * (TX + 1); ridx = rl * (TX + 1) + fl;
             } else {
-                const int it = item - NRX;
-                const int gl = it % (TY + 1), rl = it / (TY + 1);       // column x0-2+rl
+                const int itm = item - NRX;
+                const int gl = itm % (TY + 1), rl = itm / (TY + 1);       // column x0-2+rl
                 valid = !dim1 && (y0 + gl <= ny) && (x0 - 2 + rl <= nx + 1);
                 inner = (rl >= 1) && (rl <= TX + 2);
                 box_i = rl; box_j = gl; step_i = 0; step_j = 1;
-                h = G.dy; gn = 8;
-                pv[0] = 0; pv[1] = 2; pv[2] = 1; pv[3] = 3;
+                h = G.dy; ih = G.inv_dy; gn = 8;
+                pv = (k == 1) ? 2 : (k == 2) ? 1 : k;                  // face frame: normal momentum first
                 rec = ry; nrec = (TX + 4) * (TY + 1); ridx = rl * (TY + 1) + gl;
             }
             if (!valid) {
 #pragma unroll
-                for (int f = 0; f < 4 * NREC; ++f) rec[f * nrec + ridx] = 0.0;
+                for (int f = 0; f < NREC; ++f) rec[(f * 4 + k) * nrec + ridx] = 0.0;
                 continue;
             }
-            const double ih = xo ? G.inv_dx : G.inv_dy;
+            double Q[4], S[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                double Q[4], S[4];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const int bi = box_i + c * step_i, bj = box_j + c * step_j;
-                    Q[c] = sc[(pv[k] * BY + bj) * BX + bi];
-                    S[c] = h * sc[((gn + pv[k]) * BY + bj) * BX + bi];
-                }
-                double v, hvx, h2vxx;
-                linear_recon(Q[0], Q[1], Q[2], Q[3], S[0], S[1], S[2], S[3], v, hvx, h2vxx);
-                rec[(RV * 4 + k) * nrec + ridx] = v;
-                rec[(RN * 4 + k) * nrec + ridx] = hvx * ih;
-                rec[(RNN * 4 + k) * nrec + ridx] = h2vxx * ih * ih;
-                if (inner) {
-                    double vl, sl, vr, sr;
-                    weno_pair(Q[0], Q[1], Q[2], Q[3], S[0], S[1], S[2], S[3], eps, vl, sl, vr, sr);
-                    rec[(RL * 4 + k) * nrec + ridx] = vl;
-                    rec[(RR * 4 + k) * nrec + ridx] = vr;
-                    rec[(RLN * 4 + k) * nrec + ridx] = sl * ih;
-                    rec[(RRN * 4 + k) * nrec + ridx] = sr * ih;
-                }
+            for (int c = 0; c < 4; ++c) {
+                const int bi = box_i + c * step_i, bj = box_j + c * step_j;
+                Q[c] = sc[(pv * BY + bj) * BX + bi];
+                S[c] = h * sc[((gn + pv) * BY + bj) * BX + bi];
+            }
+            double v, hvx, h2vxx;
+            linear_recon(Q[0], Q[1], Q[2], Q[3], S[0], S[1], S[2], S[3], v, hvx, h2vxx);
+            rec[(RV * 4 + k) * nrec + ridx] = v;
+            rec[(RN * 4 + k) * nrec + ridx] = hvx * ih;
+            rec[(RNN * 4 + k) * nrec + ridx] = h2vxx * ih * ih;
+            if (inner) {
+                double vl, sl, vr, sr;
+                weno_pair(Q[0], Q[1], Q[2], Q[3], S[0], S[1], S[2], S[3], eps, vl, sl, vr, sr);
+                rec[(RL * 4 + k) * nrec + ridx] = vl;
+                rec[(RR * 4 + k) * nrec + ridx] = vr;
+                rec[(RLN * 4 + k) * nrec + ridx] = sl * ih;
+                rec[(RRN * 4 + k) * nrec + ridx] = sr * ih;
             }
         }
         __syncthreads();
 
         // ---------------- phase 2: face segments, two Gauss points each
         Params P;
-        P.gamma = G.gamma; P.K = G.K; P.eps_tau = G.eps_tau; P.c_tau = G.c_tau; P.dt = dt;
+        P.gamma = G.gamma; P.K = G.K; P.eps_tau = G.eps_tau; P.c_tau = G.c_tau; P.dt = dt; P.mu = G.mu;
         P.idt = __drcp_rn(dt); P.inv_K2 = __drcp_rn(G.K + 2.0); P.inv_gm1 = __drcp_rn(G.gamma - 1.0);
         P.K2inv2 = 2.0 * P.inv_K2; P.Kheat = 0.5 * (G.K + 4.0);
         bool bad = false;
@@ -347,8 +345,9 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
                 const bool ok = (Wn[0] > 0.0) && (p > 0.0);
                 bad2 |= !ok;
                 const double c = sqrt(G.gamma * p * ir);
-                double d = G.dx / (fabs(U) + c);
-                if (!dim1) d = fmin(d, G.dy / (fabs(V) + c));
+                const double nu = G.mu * ir;
+                double d = G.dx / (fabs(U) + c + 2.0 * nu * G.inv_dx);
+                if (!dim1) d = fmin(d, G.dy / (fabs(V) + c + 2.0 * nu * G.inv_dy));
                 if (ok) dtmin = fmin(dtmin, d);
             }
         }

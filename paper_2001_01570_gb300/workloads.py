@@ -50,6 +50,7 @@ class ProblemSpec:
     eps_tau: float = 0.01
     c_tau: float = 1.0
     weno_eps: float = 1e-6
+    mu: float = 0.0
     name: str = ""
     extra: dict = field(default_factory=dict)
 
@@ -68,7 +69,7 @@ class ProblemSpec:
     def as_kwargs(self) -> dict:
         return dict(dim=self.dim, nx=self.nx, ny=self.ny if self.dim == 2 else 1, dx=self.dx, dy=self.dy,
                     gamma=self.gamma, cfl=self.cfl, bc=tuple(self.bc), inflow=tuple(self.inflow),
-                    eps_tau=self.eps_tau, c_tau=self.c_tau, weno_eps=self.weno_eps)
+                    eps_tau=self.eps_tau, c_tau=self.c_tau, weno_eps=self.weno_eps, mu=self.mu)
 
 
 def prim_to_cons(rho, u, v, p, gamma):
@@ -259,6 +260,23 @@ def acoustic_pulse(N, A, b, cx, cy, gamma=1.4, cfl=0.5, eps_tau=0.01):
         return np.ones_like(x), np.zeros_like(x), np.zeros_like(x), p
 
     return spec, cell_state_2d(fun, N, N, 0.0, L, 0.0, L, gamma)
+
+
+def shear_wave(n=32, amp=1e-3, mu=0.01, gamma=1.4, cfl=0.5, kind="shear"):
+    """Viscous decay test on periodic [0,1]^2 (rho = 1, c = 1): kind "shear" has v = amp sin(2 pi x),
+    kind "entropy" has rho = 1 + amp sin(2 pi x) at constant pressure.  Both decay like
+    exp(-nu k^2 t), nu = mu / rho, k = 2 pi (Prandtl number 1)."""
+    p0 = 1.0 / gamma
+
+    def fun(x, y):
+        s = np.sin(2.0 * math.pi * x)
+        if kind == "shear":
+            return np.ones_like(x), np.zeros_like(x), amp * s, np.full_like(x, p0)
+        return 1.0 + amp * s, np.zeros_like(x), np.zeros_like(x), np.full_like(x, p0)
+
+    spec = ProblemSpec(dim=2, nx=n, ny=n, x0=0.0, x1=1.0, y0=0.0, y1=1.0, gamma=gamma, cfl=cfl, mu=mu,
+                       name=f"{kind}-wave-{n}")
+    return spec, cell_state_2d(fun, n, n, 0.0, 1.0, 0.0, 1.0, gamma)
 
 
 def tam_webb(n=200, gamma=1.4, cfl=0.3, eps_tau=0.01):

@@ -85,3 +85,19 @@ def test_conservation_periodic():
     tot0, tot1 = W[:4].sum(axis=(1, 2)), out[:4].sum(axis=(1, 2))
     assert np.all(np.abs(tot1 - tot0) <= 1e-12 * np.abs(W[:4]).sum(axis=(1, 2)))
     assert np.abs(out[4:].sum(axis=(1, 2))).max() < 1e-10
+
+
+@pytest.mark.parametrize("kind,mu", [("shear", 0.01), ("entropy", 0.002)])
+def test_viscous_waves(kind, mu):
+    spec, W = wl.shear_wave(40, amp=1e-3, mu=mu, kind=kind)
+    g, _, _ = run_gpu(spec, W, 12)
+    o, _, _ = run_oracle(spec, W, 12)
+    _check(g, o, spec=spec)
+
+
+def test_viscous_shock_vortex():
+    spec, W = wl.shock_vortex(nx=64, ny=32, mach=1.2)
+    spec.mu = 1e-4
+    g, _, _ = run_gpu(spec, W, 6)
+    o, _, _ = run_oracle(spec, W, 6)
+    _check(g, o, spec=spec)
