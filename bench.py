@@ -332,7 +332,7 @@ def run_batched(args, world, rank, local):
             "ms_per_step": ms_batch / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"batched{args.grids}", "grids": args.grids, "cells": cells,
-                       "sizes": "N log-uniform in [64, 512], seed 1570", "tile_shape": ["16x8", "8x16", "32x4", "64x1"][shape] if shape >= 0 else None},
+                       "sizes": "N log-uniform in [64, 512], seed 1570", "tile_shape": cgks.TILE_SHAPES[shape] if shape >= 0 else None},
             "plain": {"value": plain, "ms_per_step": ms_plain / args.steps, "gpu_launches": launches_plain,
                       "clocks": clk_plain.summary()},
             "batched_vs_plain": batched / plain, "gpu_launches": launches, "clocks": clk.summary()}), flush=True)

@@ -37,3 +37,35 @@ def test_status_strings_without_gpu():
     lib.cgks_status_string.restype = ctypes.c_char_p
     assert lib.cgks_status_string(0) == b"ok"
     assert b"non-physical" in lib.cgks_status_string(5)
+
+
+def test_ctypes_structs_match_the_c_layout(tmp_path):
+    """Every field of the binding's ctypes structs sits at the offset the C compiler gives it."""
+    import shutil
+    import subprocess
+
+    import pytest
+
+    from paper_2001_01570_gb300 import cgks
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"cgks_problem": cgks.cgks_problem, "cgks_serve_cfg": cgks.cgks_serve_cfg,
+               "cgks_request": cgks.cgks_request}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "cgks.h"', "int main(void) {"]
+    for name, py in structs.items():
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{name} {fname} %zu\\n", offsetof({name}, {fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for name, py in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(py), name
+        for fname, _ in py._fields_:
+            assert got[(name, fname)] == getattr(py, fname).offset, (name, fname)
