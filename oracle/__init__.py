@@ -47,12 +47,12 @@ class Problem(ctypes.Structure):
         ("gamma", ctypes.c_double), ("cfl", ctypes.c_double),
         ("bc", ctypes.c_int * 4), ("inflow", ctypes.c_double * 4),
         ("eps_tau", ctypes.c_double), ("c_tau", ctypes.c_double), ("weno_eps", ctypes.c_double),
-        ("mu", ctypes.c_double),
+        ("mu", ctypes.c_double), ("recon_vars", ctypes.c_int),
     ]
 
 
 def make_problem(dim, nx, ny, dx, dy, gamma=1.4, cfl=0.5, bc=(0, 0, 0, 0), inflow=(1.0, 0.0, 0.0, 1.0),
-                 eps_tau=0.01, c_tau=1.0, weno_eps=1e-6, mu=0.0) -> Problem:
+                 eps_tau=0.01, c_tau=1.0, weno_eps=1e-6, mu=0.0, recon_vars=0) -> Problem:
     p = Problem()
     p.dim, p.nx, p.ny = int(dim), int(nx), int(ny)
     p.dx, p.dy = float(dx), float(dy)
@@ -62,6 +62,7 @@ def make_problem(dim, nx, ny, dx, dy, gamma=1.4, cfl=0.5, bc=(0, 0, 0, 0), inflo
         p.inflow[k] = float(inflow[k])
     p.eps_tau, p.c_tau, p.weno_eps = float(eps_tau), float(c_tau), float(weno_eps)
     p.mu = float(mu)
+    p.recon_vars = int(recon_vars)
     return p
 
 
@@ -90,6 +91,8 @@ def lib():
             L.oc_weno_left.argtypes = [dp, ctypes.c_double, dp, dp, dp]
             L.oc_weno_right.argtypes = [dp, ctypes.c_double, dp, dp]
             L.oc_poly_coef_matrix.argtypes = [ctypes.c_int, dp]
+            L.oc_char_basis.argtypes = [ctypes.c_int, ctypes.c_double, dp, dp, dp]
+            L.oc_tang_weno.argtypes = [ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, dp, dp, dp]
             L.oc_moments_u.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int, dp]
             L.oc_mom_psi_poly.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp]
@@ -145,6 +148,26 @@ def weno_right(s, eps=1e-6):
     v, sl = np.zeros(1), np.zeros(1)
     lib().oc_weno_right(_dp(s), eps, _dp(v), _dp(sl))
     return v[0], sl[0]
+
+
+def char_basis(D, gamma, Wref):
+    """Right eigenvectors R (columns) of the normal Euler flux Jacobian at Wref and L = R^-1."""
+    nv = D + 2
+    Wref = _f64(Wref)
+    R, L = np.zeros(nv * nv), np.zeros(nv * nv)
+    lib().oc_char_basis(int(D), float(gamma), _dp(Wref), _dp(R), _dp(L))
+    return R.reshape(nv, nv), L.reshape(nv, nv)
+
+
+def tang_weno(v, eta, eps=1e-6):
+    """2D reading: nonlinear point value along a face at eta from n = 5 or 3 segment means.
+
+    Returns (value, derivative per unit eta, nonlinear weights omega)."""
+    v = _f64(v)
+    assert v.size in (3, 5)
+    val, dval, om = np.zeros(1), np.zeros(1), np.zeros(3)
+    lib().oc_tang_weno(int(v.size), _dp(v), float(eta), float(eps), _dp(val), _dp(dval), _dp(om))
+    return val[0], dval[0], om[: v.size // 2 + 1].copy()
 
 
 def poly_coef_matrix(p):

@@ -38,14 +38,22 @@
  *     W(t) = W0 + t W0_t + t^2/2 W0_tt + NE(t); W0_t, W0_tt are the Euler
  *     time derivatives (Cauchy-Kowalevski), NE(t) the non-equilibrium part
  *   - 2D: two Gauss points per face.  Each face row gets the 1D normal
- *     reconstruction; along the face, the equilibrium value and normal
- *     derivative at the Gauss points come from the quartic whose means over
- *     the five segments j-2..j+2 equal the line averages of those rows, and
- *     the non-equilibrium states from the quadratic through rows j-1..j+1.
+ *     reconstruction; along the face, the equilibrium derivatives at the
+ *     Gauss points come from the quartic whose means over the five segments
+ *     j-2..j+2 equal the line averages of those rows, and the normal
+ *     derivatives of the non-equilibrium states from the quadratic through
+ *     rows j-1..j+1.  The point VALUES along the face (and the tangential
+ *     slopes of the non-equilibrium states) are nonlinear: WENO-Z on the same
+ *     rows with linear weights that reproduce the quartic / quadratic at the
+ *     Gauss point, because the linear fits turn negative across a
+ *     discontinuity that runs through the faces (a normal shock seen by the
+ *     faces parallel to it).
  *     The cell-averaged tangential gradient is used only by the faces normal
  *     to it (a face-interpolated tangential gradient makes the 2D scheme
  *     linearly unstable under advection)
  *   - 1D uses K = (3-gamma)/(gamma-1) internal degrees of freedom
+ *   - characteristic reconstruction (optional): eigenvectors of the normal flux
+ *     Jacobian at the mean of the two cells sharing the face
  *   - CFL: dt = CFL * min_cells min(dx/(|U|+c), dy/(|V|+c)); with viscosity the
  *     signal speed is |U|+c+2 nu/dx (nu = mu/rho)
  *
@@ -71,6 +79,7 @@ typedef struct {
     double inflow[4];   /* primitive rho, u, v, p for inflow sides */
     double eps_tau, c_tau, weno_eps;
     double mu;          /* > 0: viscous collision time mu/p (Sec. 4) */
+    int recon_vars;     /* nonlinear reconstruction in 0: conservative, 1: characteristic variables */
 } oc_problem;
 
 /* ------------------------------------------------------------------ */
@@ -684,25 +693,103 @@ static void fill_ghosts1d(const oc_problem *P, const double *W, double *E)
         }
 }
 
+/* Sec. 3.2 allows the reconstruction in characteristic variables.  For the
+ * nonlinear reconstruction at a face the stencil data are projected on the
+ * eigenvectors of the normal Euler flux Jacobian at the arithmetic mean of the
+ * two cells sharing the face: right eigenvectors R as columns (eigenvalues
+ * U-c, U (entropy), [U (shear) in 2D], U+c), left eigenvectors = R^{-1} by
+ * elimination.  nv = 3 (1D: rho, m, E) or 4 (face frame: rho, m_n, m_t, E). */
+static void char_basis(int D, double gamma, const double *Wref, double *R, double *Linv)
+{
+    int nv = D + 2;
+    double rho = Wref[0], U = Wref[1] / rho, V = (D == 2) ? Wref[2] / rho : 0.0;
+    double q2 = U * U + V * V;
+    double p = (gamma - 1.0) * (Wref[nv - 1] - 0.5 * rho * q2);
+    double c = sqrt(gamma * p / rho), H = (Wref[nv - 1] + p) / rho;
+    memset(R, 0, sizeof(double) * nv * nv);
+    /* column 0: U - c */
+    R[0 * nv + 0] = 1.0; R[1 * nv + 0] = U - c; if (D == 2) R[2 * nv + 0] = V; R[(nv - 1) * nv + 0] = H - U * c;
+    /* column 1: entropy wave */
+    R[0 * nv + 1] = 1.0; R[1 * nv + 1] = U; if (D == 2) R[2 * nv + 1] = V; R[(nv - 1) * nv + 1] = 0.5 * q2;
+    if (D == 2) { /* column 2: shear wave */
+        R[2 * nv + 2] = 1.0; R[3 * nv + 2] = V;
+    }
+    /* last column: U + c */
+    R[0 * nv + nv - 1] = 1.0; R[1 * nv + nv - 1] = U + c; if (D == 2) R[2 * nv + nv - 1] = V;
+    R[(nv - 1) * nv + nv - 1] = H + U * c;
+    for (int col = 0; col < nv; ++col) {
+        double A[16], b[4];
+        memcpy(A, R, sizeof(double) * nv * nv);
+        for (int k = 0; k < nv; ++k) b[k] = (k == col) ? 1.0 : 0.0;
+        solve_dense(nv, A, b);
+        for (int k = 0; k < nv; ++k) Linv[k * nv + col] = b[k];
+    }
+}
+
+/* exported for the pin tests */
+void oc_char_basis(int D, double gamma, const double *Wref, double *R, double *Linv)
+{
+    char_basis(D, gamma, Wref, R, Linv);
+}
+
+/* nonlinear reconstruction of all nv variables of one face row.  Q[k][c] and
+ * hQp[k][c]: variable k, stencil cell c (i-1..i+2).  Outputs per variable. */
+static void weno_row(const oc_problem *P, int D, double Q[4][4], double hQp[4][4],
+                     double *vl, double *sl, double *vr, double *sr)
+{
+    int nv = D + 2;
+    if (P->recon_vars == 0) {
+        for (int k = 0; k < nv; ++k) {
+            double s[8];
+            for (int c = 0; c < 4; ++c) { s[c] = Q[k][c]; s[4 + c] = hQp[k][c]; }
+            oc_weno_left(s, P->weno_eps, &vl[k], &sl[k], NULL);
+            oc_weno_right(s, P->weno_eps, &vr[k], &sr[k]);
+        }
+        return;
+    }
+    double Wref[4], R[16], L[16];
+    for (int k = 0; k < nv; ++k) Wref[k] = 0.5 * (Q[k][1] + Q[k][2]);
+    char_basis(D, P->gamma, Wref, R, L);
+    double cvl[4], csl[4], cvr[4], csr[4];
+    for (int m = 0; m < nv; ++m) {
+        double s[8];
+        for (int c = 0; c < 4; ++c) {
+            double a = 0.0, b = 0.0;
+            for (int k = 0; k < nv; ++k) { a += L[m * nv + k] * Q[k][c]; b += L[m * nv + k] * hQp[k][c]; }
+            s[c] = a; s[4 + c] = b;
+        }
+        oc_weno_left(s, P->weno_eps, &cvl[m], &csl[m], NULL);
+        oc_weno_right(s, P->weno_eps, &cvr[m], &csr[m]);
+    }
+    for (int k = 0; k < nv; ++k) {
+        vl[k] = sl[k] = vr[k] = sr[k] = 0.0;
+        for (int m = 0; m < nv; ++m) {
+            vl[k] += R[k * nv + m] * cvl[m]; sl[k] += R[k * nv + m] * csl[m];
+            vr[k] += R[k * nv + m] * cvr[m]; sr[k] += R[k * nv + m] * csr[m];
+        }
+    }
+}
+
 static int face1d(const oc_problem *P, const double *E, int f, double dt, face_res *r)
 {
     int X = P->nx + 2 * NG;
     double h = P->dx;
     oc_point_in in; memset(&in, 0, sizeof(in));
+    double Q[4][4], hQp[4][4], vl[4], sl[4], vr[4], sr[4];
     for (int k = 0; k < 3; ++k) {
-        double Q[4], hQp[4], s[8], lin[3], v, sl;
+        double lin[3];
         for (int c = 0; c < 4; ++c) {
             int cell = f - 2 + c;
-            Q[c] = E[k * X + cell + NG];
-            hQp[c] = h * E[(3 + k) * X + cell + NG];
-            s[c] = Q[c]; s[4 + c] = hQp[c];
+            Q[k][c] = E[k * X + cell + NG];
+            hQp[k][c] = h * E[(3 + k) * X + cell + NG];
         }
-        oc_linear_recon(Q, hQp, lin);
+        oc_linear_recon(Q[k], hQp[k], lin);
         in.W0[k] = lin[0]; in.W0n[k] = lin[1] / h; in.W0nn[k] = lin[2] / (h * h);
-        oc_weno_left(s, P->weno_eps, &v, &sl, NULL);
-        in.Wl[k] = v; in.Wln[k] = sl / h;
-        oc_weno_right(s, P->weno_eps, &v, &sl);
-        in.Wr[k] = v; in.Wrn[k] = sl / h;
+    }
+    weno_row(P, 1, Q, hQp, vl, sl, vr, sr);
+    for (int k = 0; k < 3; ++k) {
+        in.Wl[k] = vl[k]; in.Wln[k] = sl[k] / h;
+        in.Wr[k] = vr[k]; in.Wrn[k] = sr[k] / h;
     }
     oc_point_out o;
     if (oc_gks_point(P, 1, &in, dt, &o)) return OC_E_NONPHYSICAL;
@@ -774,49 +861,59 @@ static void row_recon(const oc_problem *P, const double *E, int o, int f, int r,
 {
     double h = (o == 0) ? P->dx : P->dy;
     int gn = (o == 0) ? 1 : 2;   /* normal gradient group */
+    double Q[4][4], hQp[4][4], vl[4], sl[4], vr[4], sr[4];
     for (int k = 0; k < 4; ++k) {
         int pv = rot_var(o, k);
-        double Q[4], hQp[4], s[8], lin[3], v, sl;
+        double lin[3];
         for (int c = 0; c < 4; ++c) {
             int i, j; stencil_cell(o, f, r, c, &i, &j);
-            Q[c] = ext_at(P, E, pv, j, i);
-            hQp[c] = h * ext_at(P, E, 4 * gn + pv, j, i);
-            s[c] = Q[c]; s[4 + c] = hQp[c];
+            Q[k][c] = ext_at(P, E, pv, j, i);
+            hQp[k][c] = h * ext_at(P, E, 4 * gn + pv, j, i);
         }
-        oc_linear_recon(Q, hQp, lin);
+        oc_linear_recon(Q[k], hQp[k], lin);
         out->V[k] = lin[0]; out->N[k] = lin[1] / h; out->NN[k] = lin[2] / (h * h);
-        oc_weno_left(s, P->weno_eps, &v, &sl, NULL);
-        out->L[k] = v; out->Ln[k] = sl / h;
-        oc_weno_right(s, P->weno_eps, &v, &sl);
-        out->R[k] = v; out->Rn[k] = sl / h;
+    }
+    weno_row(P, 2, Q, hQp, vl, sl, vr, sr);
+    for (int k = 0; k < 4; ++k) {
+        out->L[k] = vl[k]; out->Ln[k] = sl[k] / h;
+        out->R[k] = vr[k]; out->Rn[k] = sr[k] / h;
     }
 }
 
 /* Tangential profiles along a face.  A polynomial p(eta) in eta = (y - y_j)/h_t
- * is fixed by its means over the unit segments centred at the neighbouring
- * rows; SEGFIT5 maps the five means (rows j-2..j+2) to the coefficients of the
- * quartic, SEGFIT3 the three means (rows j-1..j+1) to those of the quadratic. */
-static double SEGFIT5[5][5], SEGFIT3[3][3];
+ * is fixed by its means over unit segments centred at integer offsets from
+ * row j.  SEGFIT5 maps the five means (rows j-2..j+2) to the coefficients of
+ * the quartic, SEGFIT3 the three means (rows j-1..j+1) to those of the
+ * quadratic.  CAND5[k] maps the means of rows j-2+k..j+k to the quadratic on
+ * those three segments (k = 0, 1, 2); CAND3[k] maps rows j-1+k..j+k to the
+ * linear polynomial on those two segments (k = 0, 1).                       */
+static double SEGFIT5[5][5], SEGFIT3[3][3], CAND5[3][3][3], CAND3[2][2][2];
 static int SEGFIT_READY = 0;
+
+/* coefficient map of the degree-(n-1) polynomial whose means over the unit
+ * segments centred at off[0..n-1] are given: map[m][r] */
+static void seg_map(int n, const int *off, double *map)
+{
+    for (int col = 0; col < n; ++col) {
+        double A[25], b[5];
+        for (int r = 0; r < n; ++r) {
+            double lo = off[r] - 0.5, hi = off[r] + 0.5;
+            for (int m = 0; m < n; ++m) A[r * n + m] = (ipow(hi, m + 1) - ipow(lo, m + 1)) / (m + 1);
+            b[r] = (r == col) ? 1.0 : 0.0;
+        }
+        solve_dense(n, A, b);
+        for (int m = 0; m < n; ++m) map[m * n + col] = b[m];
+    }
+}
 
 static void build_segfit(void)
 {
     if (SEGFIT_READY) return;
-    for (int n = 3; n <= 5; n += 2) {
-        int off = n / 2;
-        for (int col = 0; col < n; ++col) {
-            double A[25], b[5];
-            for (int r = 0; r < n; ++r) {
-                double lo = (r - off) - 0.5, hi = (r - off) + 0.5;
-                for (int m = 0; m < n; ++m) A[r * n + m] = (ipow(hi, m + 1) - ipow(lo, m + 1)) / (m + 1);
-                b[r] = (r == col) ? 1.0 : 0.0;
-            }
-            solve_dense(n, A, b);
-            for (int m = 0; m < n; ++m) {
-                if (n == 5) SEGFIT5[m][col] = b[m]; else SEGFIT3[m][col] = b[m];
-            }
-        }
-    }
+    const int o5[5] = {-2, -1, 0, 1, 2}, o3[3] = {-1, 0, 1};
+    seg_map(5, o5, &SEGFIT5[0][0]);
+    seg_map(3, o3, &SEGFIT3[0][0]);
+    for (int k = 0; k < 3; ++k) { int o[3] = {k - 2, k - 1, k}; seg_map(3, o, &CAND5[k][0][0]); }
+    for (int k = 0; k < 2; ++k) { int o[2] = {k - 1, k}; seg_map(2, o, &CAND3[k][0][0]); }
     SEGFIT_READY = 1;
 }
 
@@ -834,6 +931,59 @@ static void seg_profile(int n, const double *v, double eta, double *p, double *d
     *p = a; *dp = b; *d2p = cc;
 }
 
+/* Nonlinear point value along a face (2D reading).  WENO-Z in the form of
+ * Sec. 3.3 over the n segment means v[0..n-1] (n = 5: rows j-2..j+2, three
+ * quadratic candidates; n = 3: rows j-1..j+1, two linear candidates):
+ *   q_k(eta)   candidate through its consecutive segments,
+ *   d_k(eta)   linear weights with sum_k d_k q_k(eta) = full-stencil
+ *              polynomial at eta for all data (fixed by the outermost
+ *              segments, which only one candidate contains; the middle
+ *              weight closes sum d_k = 1),
+ *   beta_k     Eq. (smooth-indicator) of q_k over the central segment,
+ *   Z          |beta_first - beta_last| (WENO-Z global reference),
+ *   alpha_k    d_k (1 + Z/(beta_k + eps)),  omega_k = alpha_k / sum alpha.
+ * val = sum omega_k q_k(eta); dval = sum omega_k q_k'(eta) (per unit eta).  */
+void oc_tang_weno(int n, const double *v, double eta, double eps, double *val, double *dval, double *omega)
+{
+    build_segfit();
+    int nc = n / 2 + 1, deg = n / 2;
+    double q[3], dq[3], beta[3], d[3];
+    for (int k = 0; k < nc; ++k) {
+        double c[MAXDEG + 1] = {0, 0, 0, 0, 0};
+        for (int m = 0; m <= deg; ++m)
+            for (int r = 0; r <= deg; ++r)
+                c[m] += (n == 5 ? CAND5[k][m][r] : CAND3[k][m][r]) * v[k + r];
+        q[k] = 0.0; dq[k] = 0.0;
+        for (int m = 0; m <= deg; ++m) q[k] += c[m] * ipow(eta, m);
+        for (int m = 1; m <= deg; ++m) dq[k] += m * c[m] * ipow(eta, m - 1);
+        beta[k] = poly_beta(deg, c);
+    }
+    /* weight of the first and of the last segment mean at eta in the full
+     * polynomial and in the one candidate that contains that segment */
+    double wf0 = 0.0, wfl = 0.0, wc0 = 0.0, wcl = 0.0;
+    for (int m = 0; m < n; ++m) {
+        wf0 += (n == 5 ? SEGFIT5[m][0] : SEGFIT3[m][0]) * ipow(eta, m);
+        wfl += (n == 5 ? SEGFIT5[m][n - 1] : SEGFIT3[m][n - 1]) * ipow(eta, m);
+    }
+    for (int m = 0; m <= deg; ++m) {
+        wc0 += (n == 5 ? CAND5[0][m][0] : CAND3[0][m][0]) * ipow(eta, m);
+        wcl += (n == 5 ? CAND5[nc - 1][m][deg] : CAND3[nc - 1][m][deg]) * ipow(eta, m);
+    }
+    d[0] = wf0 / wc0;
+    d[nc - 1] = wfl / wcl;
+    if (nc == 3) d[1] = 1.0 - d[0] - d[2];
+    double Z = fabs(beta[0] - beta[nc - 1]);
+    double alpha[3], asum = 0.0;
+    for (int k = 0; k < nc; ++k) { alpha[k] = d[k] * (1.0 + Z / (beta[k] + eps)); asum += alpha[k]; }
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < nc; ++k) {
+        double w = alpha[k] / asum;
+        a += w * q[k]; b += w * dq[k];
+        if (omega) omega[k] = w;
+    }
+    *val = a; *dval = b;
+}
+
 /* face segment: rows m = -2..+2 around it (rr[0..4]) -> two Gauss points ->
  * Gauss-averaged result (in the face frame) */
 static int face_segment(const oc_problem *P, const row_rec *const rr[5], int o, double dt, face_res *res)
@@ -844,25 +994,27 @@ static int face_segment(const oc_problem *P, const row_rec *const rr[5], int o, 
         double eta = gp ? g : -g;
         oc_point_in in;
         for (int k = 0; k < 4; ++k) {
-            double v5[5], n5[5], v3[3], p, dp, d2p;
+            double v5[5], n5[5], v3[3], p, dp, d2p, w, dw;
             for (int r = 0; r < 5; ++r) { v5[r] = rr[r]->V[k]; n5[r] = rr[r]->N[k]; }
-            /* equilibrium: value and its tangential derivatives */
+            /* equilibrium: nonlinear value, linear tangential derivatives */
             seg_profile(5, v5, eta, &p, &dp, &d2p);
-            in.W0[k] = p; in.W0t[k] = dp / ht; in.W0tt[k] = d2p / (ht * ht);
+            oc_tang_weno(5, v5, eta, P->weno_eps, &w, &dw, NULL);
+            in.W0[k] = w; in.W0t[k] = dp / ht; in.W0tt[k] = d2p / (ht * ht);
             /* normal derivative and its tangential derivative */
             seg_profile(5, n5, eta, &p, &dp, &d2p);
             in.W0n[k] = p; in.W0nt[k] = dp / ht;
             in.W0nn[k] = rr[2]->NN[k];
-            /* non-equilibrium states: quadratics through rows j-1..j+1 */
+            /* non-equilibrium states: nonlinear value and tangential slope
+             * from rows j-1..j+1, normal derivative from the quadratic */
             for (int r = 0; r < 3; ++r) v3[r] = rr[r + 1]->L[k];
-            seg_profile(3, v3, eta, &p, &dp, &d2p);
-            in.Wl[k] = p; in.Wlt[k] = dp / ht;
+            oc_tang_weno(3, v3, eta, P->weno_eps, &w, &dw, NULL);
+            in.Wl[k] = w; in.Wlt[k] = dw / ht;
             for (int r = 0; r < 3; ++r) v3[r] = rr[r + 1]->Ln[k];
             seg_profile(3, v3, eta, &p, &dp, &d2p);
             in.Wln[k] = p;
             for (int r = 0; r < 3; ++r) v3[r] = rr[r + 1]->R[k];
-            seg_profile(3, v3, eta, &p, &dp, &d2p);
-            in.Wr[k] = p; in.Wrt[k] = dp / ht;
+            oc_tang_weno(3, v3, eta, P->weno_eps, &w, &dw, NULL);
+            in.Wr[k] = w; in.Wrt[k] = dw / ht;
             for (int r = 0; r < 3; ++r) v3[r] = rr[r + 1]->Rn[k];
             seg_profile(3, v3, eta, &p, &dp, &d2p);
             in.Wrn[k] = p;
