@@ -84,6 +84,10 @@ typedef struct {
     double mu;               /* dynamic viscosity; > 0 selects the viscous collision time
                                 tau = mu/p + c_tau*|dp|/(sum p)*dt (Sec. 4; Navier-Stokes with
                                 Prandtl number 1); 0: inviscid, tau from eps_tau */
+    int recon_vars;          /* nonlinear (WENO-Z) reconstruction in 0: conservative variables,
+                                1: characteristic variables of the normal flux Jacobian at the
+                                mean of the two cells sharing the face (Sec. 3.2 allows either;
+                                the linear reconstruction is the same in both) */
 } cgks_problem;
 
 typedef struct cgks_solver cgks_solver;   /* opaque; owns the device planes of one grid */

@@ -77,6 +77,7 @@ cgks_status validate(const cgks_problem* p)
     if (!(p->cfl > 0.0)) return fail(CGKS_E_INVAL, "cfl must be > 0");
     if (!(p->eps_tau >= 0.0) || !(p->c_tau >= 0.0) || !(p->weno_eps > 0.0) || !(p->mu >= 0.0))
         return fail(CGKS_E_INVAL, "eps_tau, c_tau, mu must be >= 0 and weno_eps > 0");
+    if (p->recon_vars != 0 && p->recon_vars != 1) return fail(CGKS_E_INVAL, "recon_vars must be 0 or 1");
     const int nb = p->dim == 1 ? 2 : 4;
     for (int k = 0; k < nb; ++k) {
         if (p->bc[k] < CGKS_BC_PERIODIC || p->bc[k] > CGKS_BC_OUTFLOW) return fail(CGKS_E_INVAL, "unknown bc");
@@ -182,6 +183,7 @@ cgks_status cgks_create(const cgks_problem* prob, void* cuda_stream, cgks_solver
     G.c_tau = prob->c_tau;
     G.weno_eps = prob->weno_eps;
     G.mu = prob->mu;
+    G.recon_vars = prob->recon_vars;
     {
         const double r = prob->inflow[0], u = prob->inflow[1], v = prob->dim == 1 ? 0.0 : prob->inflow[2];
         const double p = prob->inflow[3];

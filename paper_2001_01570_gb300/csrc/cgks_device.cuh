@@ -167,6 +167,94 @@ __device__ __forceinline__ void weno_pair(double a, double b, double c, double d
 }
 
 // ------------------------------------------------------------------------
+// Characteristic variables (Sec. 3.2 allows them for the reconstruction):
+// eigenvectors of the normal Euler flux Jacobian in the face frame at the state
+// W (rho, m_n, m_t, E); fields 0: U-c, 1: entropy, 2: shear, 3: U+c.
+struct CharState { double U, V, c, H, q2, b1, b2, ic; };
+
+__device__ __forceinline__ void char_state(const double W[4], double gamma, CharState& s)
+{
+    const double ir = __drcp_rn(W[0]);
+    s.U = W[1] * ir;
+    s.V = W[2] * ir;
+    s.q2 = s.U * s.U + s.V * s.V;
+    const double p = (gamma - 1.0) * (W[3] - 0.5 * W[0] * s.q2);
+    s.c = sqrt(gamma * p * ir);
+    s.ic = __drcp_rn(s.c);
+    s.H = (W[3] + p) * ir;
+    s.b2 = (gamma - 1.0) * s.ic * s.ic;
+    s.b1 = 0.5 * s.b2 * s.q2;
+}
+
+// row m of the left eigenvector matrix
+__device__ __forceinline__ void char_left_row(const CharState& s, int m, double l[4])
+{
+    if (m == 0) { l[0] = 0.5 * (s.b1 + s.U * s.ic); l[1] = -0.5 * (s.b2 * s.U + s.ic); l[2] = -0.5 * s.b2 * s.V; l[3] = 0.5 * s.b2; }
+    else if (m == 1) { l[0] = 1.0 - s.b1; l[1] = s.b2 * s.U; l[2] = s.b2 * s.V; l[3] = -s.b2; }
+    else if (m == 2) { l[0] = -s.V; l[1] = 0.0; l[2] = 1.0; l[3] = 0.0; }
+    else { l[0] = 0.5 * (s.b1 - s.U * s.ic); l[1] = -0.5 * (s.b2 * s.U - s.ic); l[2] = -0.5 * s.b2 * s.V; l[3] = 0.5 * s.b2; }
+}
+
+// conservative = R . characteristic
+__device__ __forceinline__ void char_to_cons(const CharState& s, const double w[4], double out[4])
+{
+    out[0] = w[0] + w[1] + w[3];
+    out[1] = (s.U - s.c) * w[0] + s.U * w[1] + (s.U + s.c) * w[3];
+    out[2] = s.V * (w[0] + w[1] + w[3]) + w[2];
+    out[3] = (s.H - s.U * s.c) * w[0] + 0.5 * s.q2 * w[1] + s.V * w[2] + (s.H + s.U * s.c) * w[3];
+}
+
+// ------------------------------------------------------------------------
+// Nonlinear point values along a face (2D): WENO-Z over the line averages of
+// neighbouring face rows at the Gauss points eta = +-1/(2 sqrt 3) of the face
+// segment (the linear tangential fits turn negative across a discontinuity
+// that runs through the faces).
+//
+// Five means v_{-2..2}: three quadratic candidates on consecutive segments.  At
+// a Gauss point each one is v_0 + (eta/2) D_k with
+//   D_0 = 3 v_0 - 4 v_-1 + v_-2,  D_1 = v_1 - v_-1,  D_2 = 4 v_1 - v_2 - 3 v_0;
+// linear weights (d_lo, 11/18, d_hi) at eta > 0 and (d_hi, 11/18, d_lo) at
+// eta < 0, d_lo,hi = 7/36 -+ sqrt(3)/1080, make the combination the quartic
+// through the five means; beta_k = 13/12 (second difference)^2 + D_k^2 / 4 is
+// the indicator of candidate k over the central segment; Z = |beta_0 - beta_2|;
+// alpha_k = d_k (e_k + Z) / e_k with e_k = beta_k + eps, normalised with one
+// reciprocal through the common denominator e_0 e_1 e_2.
+__device__ __forceinline__ double tang_weno5(double vmm, double vm, double v0, double vp, double vpp,
+                                             double eta, double eps)
+{
+    const double D0 = (3.0 * v0 - 4.0 * vm) + vmm;
+    const double D1 = vp - vm;
+    const double D2 = (4.0 * vp - vpp) - 3.0 * v0;
+    const double s0 = (vmm - 2.0 * vm) + v0, s1 = (vm - 2.0 * v0) + vp, s2 = (v0 - 2.0 * vp) + vpp;
+    const double e0 = (13.0 / 12.0) * s0 * s0 + 0.25 * D0 * D0 + eps;
+    const double e1 = (13.0 / 12.0) * s1 * s1 + 0.25 * D1 * D1 + eps;
+    const double e2 = (13.0 / 12.0) * s2 * s2 + 0.25 * D2 * D2 + eps;
+    const double Z = fabs(e0 - e2);
+    constexpr double d_lo = 7.0 / 36.0 - 1.7320508075688772 / 1080.0;
+    constexpr double d_hi = 7.0 / 36.0 + 1.7320508075688772 / 1080.0;
+    const double w0 = eta > 0.0 ? d_lo : d_hi, w2 = eta > 0.0 ? d_hi : d_lo;
+    const double n0 = w0 * (e0 + Z) * (e1 * e2);
+    const double n1 = (11.0 / 18.0) * (e1 + Z) * (e0 * e2);
+    const double n2 = w2 * (e2 + Z) * (e0 * e1);
+    const double inv = __drcp_rn((n0 + n1) + n2);
+    return v0 + (0.5 * eta) * ((n0 * D0 + n1 * D1 + n2 * D2) * inv);
+}
+
+// Three means v_{-1..1}: two linear candidates with slopes v_0 - v_-1 and
+// v_1 - v_0, linear weights 1/2 at both Gauss points (the quadratic through the
+// three means has no eta^2 - 1/12 term there), beta_k = slope_k^2, Z = |beta_0 -
+// beta_1|.  The weights do not depend on eta: returns the nonlinear slope per
+// unit eta; the point value is v_0 + eta * slope.
+__device__ __forceinline__ double tang_weno3_slope(double vm, double v0, double vp, double eps)
+{
+    const double dm = v0 - vm, dp = vp - v0;
+    const double e0 = dm * dm + eps, e1 = dp * dp + eps;
+    const double Z = fabs(e0 - e1);
+    const double n0 = (e0 + Z) * e1, n1 = (e1 + Z) * e0;
+    return (n0 * dm + n1 * dp) * __drcp_rn(n0 + n1);
+}
+
+// ------------------------------------------------------------------------
 // Sec. 2.1: Maxwellian velocity moments.  theta = p/rho = 1/(2 lambda).
 struct Moments {
     double u[7];     // <u^n>, n = 0..6 (whole line or half line)

@@ -28,7 +28,7 @@ struct GridDev {
     double* buf[2];     // current state / next state ping-pong, 12 planes each
     double* ws;         // intermediate state W* (12 planes)
     Ctrl* ctrl;
-    int nx, ny, dim, bc0;
+    int nx, ny, dim, recon_vars;
     int bc[4];
     double dx, dy, inv_dx, inv_dy;
     double gamma, K, cfl, eps_tau, c_tau, weno_eps;

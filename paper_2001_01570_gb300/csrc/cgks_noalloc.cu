@@ -101,6 +101,7 @@ cgks_status cgks_step_noalloc(const cgks_problem* prob, double* planes, int nste
     if (!(prob->x1 > prob->x0) || !(prob->y1 > prob->y0) || !(prob->gamma > 1.0) || !(prob->gamma < 3.0) ||
         !(prob->cfl > 0.0) || !(prob->eps_tau >= 0.0) || !(prob->c_tau >= 0.0) || !(prob->weno_eps > 0.0) || !(prob->mu >= 0.0))
         return nfail(CGKS_E_INVAL, "bad problem parameters");
+    if (prob->recon_vars != 0 && prob->recon_vars != 1) return nfail(CGKS_E_INVAL, "recon_vars must be 0 or 1");
     for (int k = 0; k < 4; ++k) {
         if (prob->bc[k] < CGKS_BC_PERIODIC || prob->bc[k] > CGKS_BC_OUTFLOW) return nfail(CGKS_E_INVAL, "unknown bc");
         const int n = k < 2 ? prob->nx : prob->ny;
@@ -142,6 +143,7 @@ cgks_status cgks_step_noalloc(const cgks_problem* prob, double* planes, int nste
     G.c_tau = prob->c_tau;
     G.weno_eps = prob->weno_eps;
     G.mu = prob->mu;
+    G.recon_vars = prob->recon_vars;
     {
         const double r = prob->inflow[0], u = prob->inflow[1], v = prob->inflow[2], p = prob->inflow[3];
         G.inflow[0] = r;

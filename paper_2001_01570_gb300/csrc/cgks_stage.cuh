@@ -10,11 +10,12 @@
 //            one of a segment, the nonlinear WENO-Z left/right states with
 //            slopes (Sec. 3.3); one record per (face, row), shared by the five
 //            face segments that use it
-//   phase 2  per face segment: tangential quartic through the line averages
-//            of rows j-2..j+2 (equilibrium value and normal derivative) and
-//            quadratic through rows j-1..j+1 (non-equilibrium states) at two
-//            Gauss points, the gas-kinetic evaluation at each point, Gauss
-//            average
+//   phase 2  per face segment, at two Gauss points: WENO-Z point values along
+//            the face over rows j-2..j+2 (equilibrium) and j-1..j+1
+//            (non-equilibrium states, with their tangential slopes); tangential
+//            derivatives of the equilibrium state and normal derivatives from
+//            the quartic / quadratic through the same line averages; the
+//            gas-kinetic evaluation at each point, Gauss average
 //   phase 3  per cell: S2O4 update of cell averages by the fluxes and of the
 //            cell-averaged gradients by the Gauss theorem on interface states
 // Stage 1 writes W* and R = W^n + dt L + dt^2/6 L_t (and the gradient
@@ -180,6 +181,30 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
             rec[(RN * 4 + k) * nrec + ridx] = hvx * ih;
             rec[(RNN * 4 + k) * nrec + ridx] = h2vxx * ih * ih;
             if (inner) {
+                if (G.recon_vars) {
+                    // characteristic field k: project the stencil on the k-th left eigenvector
+                    // at the mean of the two cells sharing the face
+                    double Wref[4], Qa[4][4], Sa[4][4], l[4];
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const int pk = xo ? kk : ((kk == 1) ? 2 : (kk == 2) ? 1 : kk);
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const int bi = box_i + c * step_i, bj = box_j + c * step_j;
+                            Qa[kk][c] = sc[(pk * BY + bj) * BX + bi];
+                            Sa[kk][c] = h * sc[((gn + pk) * BY + bj) * BX + bi];
+                        }
+                        Wref[kk] = 0.5 * (Qa[kk][1] + Qa[kk][2]);
+                    }
+                    CharState cs;
+                    char_state(Wref, G.gamma, cs);
+                    char_left_row(cs, k, l);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        Q[c] = l[0] * Qa[0][c] + l[1] * Qa[1][c] + l[2] * Qa[2][c] + l[3] * Qa[3][c];
+                        S[c] = l[0] * Sa[0][c] + l[1] * Sa[1][c] + l[2] * Sa[2][c] + l[3] * Sa[3][c];
+                    }
+                }
                 double vl, sl, vr, sr;
                 weno_pair(Q[0], Q[1], Q[2], Q[3], S[0], S[1], S[2], S[3], eps, vl, sl, vr, sr);
                 rec[(RL * 4 + k) * nrec + ridx] = vl;
@@ -189,6 +214,50 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
             }
         }
         __syncthreads();
+        if (G.recon_vars) {
+            // back to conservative variables, one record per thread
+            for (int item = tid; item < NR; item += kThreads) {
+                const bool xo = item < NR - NRY;
+                int box_i, box_j, step_i, step_j, ridx, nrec;
+                double* rec;
+                bool valid, inner;
+                if (xo) {
+                    const int fl = item % (TX + 1), rl = item / (TX + 1);
+                    valid = (x0 + fl <= nx) && (y0 - 2 + rl <= ny + 1);
+                    inner = (rl >= 1) && (rl <= TY + 2);
+                    box_i = fl; box_j = rl; step_i = 1; step_j = 0;
+                    rec = rx; nrec = (TY + 4) * (TX + 1); ridx = rl * (TX + 1) + fl;
+                } else {
+                    const int itm = item - NRX;
+                    const int gl = itm % (TY + 1), rl = itm / (TY + 1);
+                    valid = !dim1 && (y0 + gl <= ny) && (x0 - 2 + rl <= nx + 1);
+                    inner = (rl >= 1) && (rl <= TX + 2);
+                    box_i = rl; box_j = gl; step_i = 0; step_j = 1;
+                    rec = ry; nrec = (TX + 4) * (TY + 1); ridx = rl * (TY + 1) + gl;
+                }
+                if (!valid || !inner) continue;
+                double Wref[4];
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const int pk = xo ? kk : ((kk == 1) ? 2 : (kk == 2) ? 1 : kk);
+                    const double a = sc[(pk * BY + box_j + step_j) * BX + box_i + step_i];
+                    const double b = sc[(pk * BY + box_j + 2 * step_j) * BX + box_i + 2 * step_i];
+                    Wref[kk] = 0.5 * (a + b);
+                }
+                CharState cs;
+                char_state(Wref, G.gamma, cs);
+#pragma unroll
+                for (int f = RL; f <= RRN; ++f) {
+                    double w[4], o[4];
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) w[m] = rec[(f * 4 + m) * nrec + ridx];
+                    char_to_cons(cs, w, o);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) rec[(f * 4 + kk) * nrec + ridx] = o[kk];
+                }
+            }
+            __syncthreads();
+        }
 
         // ---------------- phase 2: face segments, two Gauss points each
         Params P;
@@ -223,6 +292,7 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
                 continue;
             }
             const double iht = xo ? G.inv_dy : G.inv_dx;
+            const double weps = G.weno_eps;
             double acc[NF];
 #pragma unroll
             for (int q = 0; q < NF; ++q) acc[q] = 0.0;
@@ -241,7 +311,7 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
                         const double c1 = (34.0 * A1 - 5.0 * A2) * (1.0 / 48.0), c3 = (A2 - 2.0 * A1) * (1.0 / 12.0);
                         const double c2 = (12.0 * S1 - S2 - 22.0 * V0) * (1.0 / 16.0);
                         const double c4 = (S2 - 4.0 * S1 + 6.0 * V0) * (1.0 / 24.0);
-                        in.W0[k] = V0 - c4 * (1.0 / 180.0) + eta * (c1 + c3 * (1.0 / 12.0));
+                        in.W0[k] = tang_weno5(Vmm, Vm, V0, Vp, Vpp, eta, weps);
                         in.W0t[k] = (c1 + 0.25 * c3 + eta * (2.0 * c2 + c4 * (1.0 / 3.0))) * iht;
                         in.W0tt[k] = (2.0 * c2 + c4 + 6.0 * eta * c3) * iht * iht;
                     }
@@ -256,16 +326,16 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
                         in.W0nt[k] = (d1 + 0.25 * d3 + eta * (2.0 * d2 + d4 * (1.0 / 3.0))) * iht;
                     }
                     in.W0nn[k] = R(RNN, 0);
-                    // quadratics with segment means of rows j-1..j+1 at the same points
-                    const double Lm = R(RL, -rstride), L0 = R(RL, 0), Lp = R(RL, rstride);
-                    const double l1 = 0.5 * (Lp - Lm), l2 = 0.5 * ((Lp + Lm) - 2.0 * L0);
-                    in.Wl[k] = L0 + eta * l1;
-                    in.Wlt[k] = (l1 + 2.0 * eta * l2) * iht;
+                    // non-equilibrium states over rows j-1..j+1: nonlinear value and
+                    // tangential slope, normal derivative from the quadratic
+                    const double L0 = R(RL, 0), Rc = R(RR, 0);
+                    const double sl = tang_weno3_slope(R(RL, -rstride), L0, R(RL, rstride), weps);
+                    in.Wl[k] = L0 + eta * sl;
+                    in.Wlt[k] = sl * iht;
                     in.Wln[k] = R(RLN, 0) + eta * 0.5 * (R(RLN, rstride) - R(RLN, -rstride));
-                    const double Rm = R(RR, -rstride), R0 = R(RR, 0), Rp = R(RR, rstride);
-                    const double r1 = 0.5 * (Rp - Rm), r2 = 0.5 * ((Rp + Rm) - 2.0 * R0);
-                    in.Wr[k] = R0 + eta * r1;
-                    in.Wrt[k] = (r1 + 2.0 * eta * r2) * iht;
+                    const double sr = tang_weno3_slope(R(RR, -rstride), Rc, R(RR, rstride), weps);
+                    in.Wr[k] = Rc + eta * sr;
+                    in.Wrt[k] = sr * iht;
                     in.Wrn[k] = R(RRN, 0) + eta * 0.5 * (R(RRN, rstride) - R(RRN, -rstride));
                 }
                 double Fb[4], Ft[4], Wm[4], Wb[4], Wtt[4];

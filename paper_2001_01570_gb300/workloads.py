@@ -51,6 +51,7 @@ class ProblemSpec:
     c_tau: float = 1.0
     weno_eps: float = 1e-6
     mu: float = 0.0
+    recon_vars: int = 0          # nonlinear reconstruction: 0 conservative, 1 characteristic
     name: str = ""
     extra: dict = field(default_factory=dict)
 
@@ -69,7 +70,8 @@ class ProblemSpec:
     def as_kwargs(self) -> dict:
         return dict(dim=self.dim, nx=self.nx, ny=self.ny if self.dim == 2 else 1, dx=self.dx, dy=self.dy,
                     gamma=self.gamma, cfl=self.cfl, bc=tuple(self.bc), inflow=tuple(self.inflow),
-                    eps_tau=self.eps_tau, c_tau=self.c_tau, weno_eps=self.weno_eps, mu=self.mu)
+                    eps_tau=self.eps_tau, c_tau=self.c_tau, weno_eps=self.weno_eps, mu=self.mu,
+                    recon_vars=self.recon_vars)
 
 
 def prim_to_cons(rho, u, v, p, gamma):

@@ -101,3 +101,48 @@ def test_viscous_shock_vortex():
     g, _, _ = run_gpu(spec, W, 6)
     o, _, _ = run_oracle(spec, W, 6)
     _check(g, o, spec=spec)
+
+
+def test_characteristic_lax_1d():
+    spec, W = wl.shock_tube_1d(100, wl.LAX, cfl=0.5)
+    spec.recon_vars = 1
+    g, tg, sg = run_gpu(spec, W, 5000, t_end=0.16)
+    o, to, so = run_oracle(spec, W, 5000, t_end=0.16)
+    assert sg == so
+    _check(g, o, spec=spec)
+
+
+def test_characteristic_shock_vortex():
+    spec, W = wl.shock_vortex(nx=64, ny=32, mach=1.4)
+    spec.recon_vars = 1
+    g, _, _ = run_gpu(spec, W, 6)
+    o, _, _ = run_oracle(spec, W, 6)
+    _check(g, o, spec=spec)
+
+
+def _sod_2d(n, rows, along_y, recon_vars):
+    """Sod's tube on a 2D grid: the discontinuities cross every face parallel to them (the
+    nonlinear values along those faces keep the states physical).  along_y transposes it."""
+    spec1, W1 = wl.shock_tube_1d(n, wl.SOD, cfl=0.5)
+    W = np.repeat(wl.state_1d_as_2d(W1), rows, axis=1)
+    spec = wl.ProblemSpec(dim=2, nx=n, ny=rows, x0=spec1.x0, x1=spec1.x1, y0=0.0, y1=rows * spec1.dx,
+                          cfl=0.5, bc=(3, 3, 0, 0), recon_vars=recon_vars, name="sod-2d")
+    if along_y:
+        W = np.transpose(W, (0, 2, 1)).copy()
+        W[[1, 2]] = W[[2, 1]]
+        W[[5, 6]] = W[[6, 5]]
+        W[[9, 10]] = W[[10, 9]]
+        W[4:8], W[8:12] = W[8:12].copy(), W[4:8].copy()
+        spec = wl.ProblemSpec(dim=2, nx=rows, ny=n, x0=0.0, x1=rows * spec1.dx, y0=spec1.x0, y1=spec1.x1,
+                              cfl=0.5, bc=(0, 0, 3, 3), recon_vars=recon_vars, name="sod-2d-y")
+    return spec, W
+
+
+@pytest.mark.parametrize("along_y", [False, True])
+@pytest.mark.parametrize("recon_vars", [0, 1])
+def test_sod_on_a_2d_grid(along_y, recon_vars):
+    spec, W = _sod_2d(60, 11, along_y, recon_vars)
+    g, _, sg = run_gpu(spec, W, 25)
+    o, _, so = run_oracle(spec, W, 25)
+    assert sg == so == 25
+    _check(g, o, spec=spec)
