@@ -65,7 +65,7 @@ typedef enum {
 typedef enum {
     CGKS_BC_PERIODIC = 0,  /* wrap around */
     CGKS_BC_REFLECT = 1,   /* mirror, normal momentum and the matching gradients odd */
-    CGKS_BC_INFLOW = 2,    /* fixed state cgks_problem.inflow, zero gradients */
+    CGKS_BC_INFLOW = 2,    /* fixed state cgks_problem.inflow[side], zero gradients */
     CGKS_BC_OUTFLOW = 3    /* copy of the boundary cell, zero normal gradient */
 } cgks_bc;
 
@@ -77,7 +77,9 @@ typedef struct {
     double gamma;            /* ratio of specific heats, 1 < gamma < 3 (2D: < 2) */
     double cfl;              /* CFL number, > 0 */
     int bc[4];               /* cgks_bc for x-low, x-high, y-low, y-high */
-    double inflow[4];        /* primitive rho, u, v, p used on CGKS_BC_INFLOW sides */
+    double inflow[4][4];     /* per side (x-low, x-high, y-low, y-high): primitive rho, u, v, p
+                                of the fixed state on a CGKS_BC_INFLOW side (other sides ignore
+                                theirs); rho > 0 and p > 0 are required where used */
     double eps_tau;          /* tau = eps_tau*dt + c_tau*|dp|/(sum p)*dt; paper: 0.01 */
     double c_tau;            /* paper: 1 */
     double weno_eps;         /* epsilon of the WENO-Z weights; paper tests 1e-6, 1e-4 */

@@ -45,10 +45,21 @@ class Problem(ctypes.Structure):
         ("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
         ("dx", ctypes.c_double), ("dy", ctypes.c_double),
         ("gamma", ctypes.c_double), ("cfl", ctypes.c_double),
-        ("bc", ctypes.c_int * 4), ("inflow", ctypes.c_double * 4),
+        ("bc", ctypes.c_int * 4), ("inflow", (ctypes.c_double * 4) * 4),
         ("eps_tau", ctypes.c_double), ("c_tau", ctypes.c_double), ("weno_eps", ctypes.c_double),
         ("mu", ctypes.c_double), ("recon_vars", ctypes.c_int),
     ]
+
+
+def inflow_sides(inflow):
+    """One primitive state (rho, u, v, p) for every side, or four of them (x-low, x-high, y-low,
+    y-high) -> a 4 x 4 nested list."""
+    a = np.asarray(inflow, dtype=np.float64)
+    if a.shape == (4,):
+        a = np.tile(a, (4, 1))
+    if a.shape != (4, 4):
+        raise ValueError("inflow: one state (4 values) or one per side (4 x 4)")
+    return a.tolist()
 
 
 def make_problem(dim, nx, ny, dx, dy, gamma=1.4, cfl=0.5, bc=(0, 0, 0, 0), inflow=(1.0, 0.0, 0.0, 1.0),
@@ -57,9 +68,11 @@ def make_problem(dim, nx, ny, dx, dy, gamma=1.4, cfl=0.5, bc=(0, 0, 0, 0), inflo
     p.dim, p.nx, p.ny = int(dim), int(nx), int(ny)
     p.dx, p.dy = float(dx), float(dy)
     p.gamma, p.cfl = float(gamma), float(cfl)
+    sides = inflow_sides(inflow)
     for k in range(4):
         p.bc[k] = int(bc[k])
-        p.inflow[k] = float(inflow[k])
+        for m in range(4):
+            p.inflow[k][m] = sides[k][m]
     p.eps_tau, p.c_tau, p.weno_eps = float(eps_tau), float(c_tau), float(weno_eps)
     p.mu = float(mu)
     p.recon_vars = int(recon_vars)

@@ -76,7 +76,7 @@ typedef struct {
     double dx, dy;
     double gamma, cfl;
     int bc[4];          /* x-low, x-high, y-low, y-high */
-    double inflow[4];   /* primitive rho, u, v, p for inflow sides */
+    double inflow[4][4];   /* per side (x-low, x-high, y-low, y-high): primitive rho, u, v, p */
     double eps_tau, c_tau, weno_eps;
     double mu;          /* > 0: viscous collision time mu/p (Sec. 4) */
     int recon_vars;     /* nonlinear reconstruction in 0: conservative, 1: characteristic variables */
@@ -580,8 +580,8 @@ static void fill_ghosts2d(const oc_problem *P, double *E)
 {
     int nx = P->nx, ny = P->ny, X = nx + 2 * NG, Y = ny + 2 * NG;
     size_t PL = (size_t)X * Y;
-    double inflow_cons[4];
-    prim_to_cons(2, P->gamma, P->inflow, inflow_cons);
+    double inflow_cons[4][4];
+    for (int side = 0; side < 4; ++side) prim_to_cons(2, P->gamma, P->inflow[side], inflow_cons[side]);
 #define AT(p, j, i) E[(size_t)(p) * PL + (size_t)((j) + NG) * X + ((i) + NG)]
     /* x-ghosts for the real rows */
     for (int j = 0; j < ny; ++j)
@@ -598,7 +598,7 @@ static void fill_ghosts2d(const oc_problem *P, double *E)
                         v = AT(p, j, src);
                         int odd = (grp == 0 && var == 1) || (grp == 1 && var != 1) || (grp == 2 && var == 1);
                         if (odd) v = -v;
-                    } else if (bc == BC_INFLOW) v = (grp == 0) ? inflow_cons[var] : 0.0;
+                    } else if (bc == BC_INFLOW) v = (grp == 0) ? inflow_cons[side][var] : 0.0;
                     else { int src = side ? nx - 1 : 0; v = (grp == 1) ? 0.0 : AT(p, j, src); }
                     AT(p, j, g) = v;
                 }
@@ -620,7 +620,7 @@ static void fill_ghosts2d(const oc_problem *P, double *E)
                         v = AT(p, src, i);
                         int odd = (grp == 0 && var == 2) || (grp == 1 && var == 2) || (grp == 2 && var != 2);
                         if (odd) v = -v;
-                    } else if (bc == BC_INFLOW) v = (grp == 0) ? inflow_cons[var] : 0.0;
+                    } else if (bc == BC_INFLOW) v = (grp == 0) ? inflow_cons[2 + side][var] : 0.0;
                     else { int src = side ? ny - 1 : 0; v = (grp == 2) ? 0.0 : AT(p, src, i); }
                     AT(p, g, i) = v;
                 }
@@ -671,8 +671,11 @@ static void face_from_point(int nv, double dt, const double *W0, const oc_point_
 static void fill_ghosts1d(const oc_problem *P, const double *W, double *E)
 {
     int nx = P->nx, X = nx + 2 * NG;
-    double q[4] = {P->inflow[0], P->inflow[1], 0.0, P->inflow[3]}, ic[3];
-    prim_to_cons(1, P->gamma, q, ic);
+    double ic[2][3];
+    for (int side = 0; side < 2; ++side) {
+        double q[4] = {P->inflow[side][0], P->inflow[side][1], 0.0, P->inflow[side][3]};
+        prim_to_cons(1, P->gamma, q, ic[side]);
+    }
     for (int p = 0; p < 6; ++p) for (int i = 0; i < nx; ++i) E[p * X + i + NG] = W[p * nx + i];
     for (int side = 0; side < 2; ++side)
         for (int m = 0; m < NG; ++m) {
@@ -686,7 +689,7 @@ static void fill_ghosts1d(const oc_problem *P, const double *W, double *E)
                     v = E[p * X + (side ? nx - 1 - m : m) + NG];
                     int odd = (grp == 0 && var == 1) || (grp == 1 && var != 1);
                     if (odd) v = -v;
-                } else if (bc == BC_INFLOW) v = (grp == 0) ? ic[var] : 0.0;
+                } else if (bc == BC_INFLOW) v = (grp == 0) ? ic[side][var] : 0.0;
                 else v = (grp == 1) ? 0.0 : E[p * X + (side ? nx - 1 : 0) + NG];
                 E[p * X + g + NG] = v;
             }

@@ -31,7 +31,7 @@ class cgks_problem(ctypes.Structure):
         ("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
         ("x0", ctypes.c_double), ("x1", ctypes.c_double), ("y0", ctypes.c_double), ("y1", ctypes.c_double),
         ("gamma", ctypes.c_double), ("cfl", ctypes.c_double),
-        ("bc", ctypes.c_int * 4), ("inflow", ctypes.c_double * 4),
+        ("bc", ctypes.c_int * 4), ("inflow", (ctypes.c_double * 4) * 4),
         ("eps_tau", ctypes.c_double), ("c_tau", ctypes.c_double), ("weno_eps", ctypes.c_double),
         ("mu", ctypes.c_double), ("recon_vars", ctypes.c_int),
     ]
@@ -112,15 +112,28 @@ def _check(st):
         raise CgksError(st, L.cgks_last_error().decode())
 
 
+def inflow_sides(inflow):
+    """One primitive state (rho, u, v, p) for every side, or four of them (x-low, x-high, y-low,
+    y-high) -> a 4 x 4 nested list."""
+    a = np.asarray(inflow, dtype=np.float64)
+    if a.shape == (4,):
+        a = np.tile(a, (4, 1))
+    if a.shape != (4, 4):
+        raise ValueError("inflow: one state (4 values) or one per side (4 x 4)")
+    return a.tolist()
+
+
 def make_problem(dim, nx, ny, x0, x1, y0=0.0, y1=1.0, gamma=1.4, cfl=0.5, bc=(0, 0, 0, 0),
                  inflow=(1.0, 0.0, 0.0, 1.0), eps_tau=0.01, c_tau=1.0, weno_eps=1e-6, mu=0.0, recon_vars=0) -> cgks_problem:
     p = cgks_problem()
     p.dim, p.nx, p.ny = int(dim), int(nx), int(ny)
     p.x0, p.x1, p.y0, p.y1 = float(x0), float(x1), float(y0), float(y1)
     p.gamma, p.cfl = float(gamma), float(cfl)
+    sides = inflow_sides(inflow)
     for k in range(4):
         p.bc[k] = int(bc[k])
-        p.inflow[k] = float(inflow[k])
+        for m in range(4):
+            p.inflow[k][m] = sides[k][m]
     p.eps_tau, p.c_tau, p.weno_eps = float(eps_tau), float(c_tau), float(weno_eps)
     p.mu = float(mu)
     p.recon_vars = int(recon_vars)

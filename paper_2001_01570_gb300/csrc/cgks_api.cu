@@ -89,7 +89,7 @@ cgks_status validate(const cgks_problem* p)
     if (p->dim == 2 && ((p->bc[2] == CGKS_BC_PERIODIC) != (p->bc[3] == CGKS_BC_PERIODIC)))
         return fail(CGKS_E_INVAL, "periodic y needs both y sides periodic");
     for (int k = 0; k < nb; ++k)
-        if (p->bc[k] == CGKS_BC_INFLOW && (!(p->inflow[0] > 0.0) || !(p->inflow[3] > 0.0)))
+        if (p->bc[k] == CGKS_BC_INFLOW && (!(p->inflow[k][0] > 0.0) || !(p->inflow[k][3] > 0.0)))
             return fail(CGKS_E_INVAL, "inflow state needs rho > 0 and p > 0");
     return CGKS_OK;
 }
@@ -184,13 +184,13 @@ cgks_status cgks_create(const cgks_problem* prob, void* cuda_stream, cgks_solver
     G.weno_eps = prob->weno_eps;
     G.mu = prob->mu;
     G.recon_vars = prob->recon_vars;
-    {
-        const double r = prob->inflow[0], u = prob->inflow[1], v = prob->dim == 1 ? 0.0 : prob->inflow[2];
-        const double p = prob->inflow[3];
-        G.inflow[0] = r;
-        G.inflow[1] = r * u;
-        G.inflow[2] = r * v;
-        G.inflow[3] = p / (prob->gamma - 1.0) + 0.5 * r * (u * u + v * v);
+    for (int side = 0; side < 4; ++side) {
+        const double* q = prob->inflow[side];
+        const double r = q[0], u = q[1], v = prob->dim == 1 ? 0.0 : q[2], p = q[3];
+        G.inflow[side][0] = r;
+        G.inflow[side][1] = r * u;
+        G.inflow[side][2] = r * v;
+        G.inflow[side][3] = p / (prob->gamma - 1.0) + 0.5 * r * (u * u + v * v);
     }
     e = cudaMemcpyAsync(s->d_desc, &G, sizeof(GridDev), cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess)

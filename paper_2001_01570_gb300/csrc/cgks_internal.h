@@ -33,7 +33,7 @@ struct GridDev {
     double dx, dy, inv_dx, inv_dy;
     double gamma, K, cfl, eps_tau, c_tau, weno_eps;
     double mu;          // > 0: viscous collision time mu/p
-    double inflow[4];   // conservative inflow state
+    double inflow[4][4];   // conservative inflow state per side (x-low, x-high, y-low, y-high)
 };
 
 // One unit of work of the stage kernels: a TX x TY tile of one grid.

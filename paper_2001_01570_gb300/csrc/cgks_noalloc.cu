@@ -144,12 +144,13 @@ cgks_status cgks_step_noalloc(const cgks_problem* prob, double* planes, int nste
     G.weno_eps = prob->weno_eps;
     G.mu = prob->mu;
     G.recon_vars = prob->recon_vars;
-    {
-        const double r = prob->inflow[0], u = prob->inflow[1], v = prob->inflow[2], p = prob->inflow[3];
-        G.inflow[0] = r;
-        G.inflow[1] = r * u;
-        G.inflow[2] = r * v;
-        G.inflow[3] = p / (prob->gamma - 1.0) + 0.5 * r * (u * u + v * v);
+    for (int side = 0; side < 4; ++side) {
+        const double* q = prob->inflow[side];
+        const double r = q[0], u = q[1], v = q[2], p = q[3];
+        G.inflow[side][0] = r;
+        G.inflow[side][1] = r * u;
+        G.inflow[side][2] = r * v;
+        G.inflow[side][3] = p / (prob->gamma - 1.0) + 0.5 * r * (u * u + v * v);
     }
     const int nt = (int)ntiles;
     noalloc_init_kernel<<<(nt + 255) / 256, 256, 0, stream>>>(G, tw, th);

@@ -120,14 +120,16 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
             // x-boundary transform
             if (kx == 1) { v[1] = -v[1]; v[4] = -v[4]; v[6] = -v[6]; v[7] = -v[7]; v[9] = -v[9]; }
             else if (kx == 2) {
+                const double* q = G.inflow[(x0 - 2 + ii < 0) ? 0 : 1];
 #pragma unroll
-                for (int p = 0; p < 4; ++p) { v[p] = G.inflow[p]; v[4 + p] = 0.0; v[8 + p] = 0.0; }
+                for (int p = 0; p < 4; ++p) { v[p] = q[p]; v[4 + p] = 0.0; v[8 + p] = 0.0; }
             } else if (kx == 3) { v[4] = v[5] = v[6] = v[7] = 0.0; }
             // y-boundary transform
             if (ky == 1) { v[2] = -v[2]; v[6] = -v[6]; v[8] = -v[8]; v[9] = -v[9]; v[11] = -v[11]; }
             else if (ky == 2) {
+                const double* q = G.inflow[(y0 - 2 + jj < 0) ? 2 : 3];
 #pragma unroll
-                for (int p = 0; p < 4; ++p) { v[p] = G.inflow[p]; v[4 + p] = 0.0; v[8 + p] = 0.0; }
+                for (int p = 0; p < 4; ++p) { v[p] = q[p]; v[4 + p] = 0.0; v[8 + p] = 0.0; }
             } else if (ky == 3) { v[8] = v[9] = v[10] = v[11] = 0.0; }
 #pragma unroll
             for (int p = 0; p < 12; ++p) sc[(p * BY + jj) * BX + ii] = v[p];

@@ -46,7 +46,7 @@ class ProblemSpec:
     gamma: float = 1.4
     cfl: float = 0.5
     bc: tuple = (BC_PERIODIC,) * 4
-    inflow: tuple = (1.0, 0.0, 0.0, 1.0)
+    inflow: tuple = (1.0, 0.0, 0.0, 1.0)   # one primitive state, or one per side (x-lo, x-hi, y-lo, y-hi)
     eps_tau: float = 0.01
     c_tau: float = 1.0
     weno_eps: float = 1e-6
@@ -246,6 +246,38 @@ def shock_vortex(nx=1024, ny=512, mach=1.1, vortex_mach=0.3, a=0.05, b=0.2, cent
                        bc=(BC_INFLOW, BC_OUTFLOW, BC_REFLECT, BC_REFLECT), inflow=(1.0, u1, 0.0, 1.0),
                        eps_tau=eps_tau, name=f"shock-vortex-{nx}x{ny}-M{mach:g}")
     return spec, cell_state_2d(fun, nx, ny, 0.0, 2.0, 0.0, 1.0, g)
+
+
+def oblique_shock_state(mach, angle_deg, gamma=1.4):
+    """State behind a planar shock at angle_deg to a uniform stream (rho = 1, p = 1/gamma, Mach
+    `mach` along +x), the shock running down and to the right: Rankine-Hugoniot for the normal
+    component, tangential velocity unchanged.  Returns primitive (rho, u, v, p)."""
+    g = gamma
+    b = math.radians(angle_deg)
+    u1 = mach                                      # c = 1 upstream
+    un1, ut = u1 * math.sin(b), u1 * math.cos(b)
+    mn2 = un1 * un1                                # normal Mach number squared (c = 1)
+    r2 = (g + 1.0) * mn2 / ((g - 1.0) * mn2 + 2.0)
+    p2 = (1.0 / g) * (1.0 + 2.0 * g / (g + 1.0) * (mn2 - 1.0))
+    un2 = un1 / r2
+    # shock tangent (cos b, -sin b), downstream normal (sin b, cos b)
+    return r2, ut * math.cos(b) + un2 * math.sin(b), -ut * math.sin(b) + un2 * math.cos(b), p2
+
+
+def shock_reflection(nx=200, ny=50, mach=2.9, angle_deg=29.0, gamma=1.4, cfl=0.5, eps_tau=0.01):
+    """Regular shock reflection (Sec. 4, 2D shock test): [0,4] x [0,1], Mach-2.9 stream entering on
+    the left, the state behind a 29-degree incident shock entering through the top, reflecting
+    bottom wall, outflow on the right; the domain starts in the free-stream state."""
+    g = gamma
+    free = (1.0, mach, 0.0, 1.0 / g)
+    post = oblique_shock_state(mach, angle_deg, g)
+    spec = ProblemSpec(dim=2, nx=nx, ny=ny, x0=0.0, x1=4.0, y0=0.0, y1=1.0, gamma=g, cfl=cfl,
+                       bc=(BC_INFLOW, BC_OUTFLOW, BC_REFLECT, BC_INFLOW),
+                       inflow=(free, free, free, post), eps_tau=eps_tau,
+                       name=f"shock-reflection-{nx}x{ny}")
+    W = np.zeros((12, ny, nx))
+    W[:4] = np.asarray(prim_to_cons(*free, g)).reshape(4, 1, 1)
+    return spec, W
 
 
 def acoustic_pulse(N, A, b, cx, cy, gamma=1.4, cfl=0.5, eps_tau=0.01):

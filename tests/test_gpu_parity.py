@@ -146,3 +146,31 @@ def test_sod_on_a_2d_grid(along_y, recon_vars):
     o, _, so = run_oracle(spec, W, 25)
     assert sg == so == 25
     _check(g, o, spec=spec)
+
+
+@pytest.mark.parametrize("recon_vars", [0, 1])
+def test_shock_reflection_mach_2p9(recon_vars):
+    """Sec. 4's regular shock reflection: different inflow states on two sides, a reflecting wall,
+    outflow, and a Mach-2.9 stream hitting the 29-degree incident shock from the first step."""
+    spec, W = wl.shock_reflection(60, 15)
+    spec.recon_vars = recon_vars
+    g, _, sg = run_gpu(spec, W, 60)
+    o, _, so = run_oracle(spec, W, 60)
+    assert sg == so == 60
+    _check(g, o, spec=spec)
+
+
+def test_shock_reflection_paper_grid_reaches_the_exact_regions():
+    """200 x 50 (the grid of the paper's figure) to t = 10 on the GPU: the three regions reach
+    their oblique-shock states."""
+    import shock_reflection_exact as EX
+
+    spec, W = wl.shock_reflection(200, 50)
+    g, t, _ = run_gpu(spec, W, 10 ** 6, t_end=10.0)
+    assert t == 10.0
+    rho = g[0]
+    p = 0.4 * (g[3] - 0.5 * (g[1] ** 2 + g[2] ** 2) / rho)
+    (r1, p1), (r2, p2), (r3, p3) = EX.regions()
+    assert np.abs(rho[0:8, 180:] / r3 - 1.0).max() < 0.01 and np.abs(p[0:8, 180:] / p3 - 1.0).max() < 0.01
+    assert np.abs(rho[40:50, 60:110] / r2 - 1.0).max() < 0.01 and np.abs(p[40:50, 60:110] / p2 - 1.0).max() < 0.01
+    assert np.abs(rho[0:15, 0:40] / r1 - 1.0).max() < 0.01
