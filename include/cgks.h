@@ -128,8 +128,9 @@ cgks_status cgks_step(cgks_solver* s, int nsteps, double t_end, double* t_out);
 cgks_status cgks_batch_step(cgks_solver* const* solvers, int n, int nsteps);
 
 /* Cells per CTA tile of the stage kernels for this solver's plain steps:
- * 0: 16x8, 1: 8x16, 2: 32x4, 3: 64x1, 4: 16x7, 5: 7x16, 6: 14x8, 7: 24x8; -1
- * restores the default (24x8 in 2D, 64x1 in 1D).  The shape changes only the
+ * 0: 16x8, 1: 8x16, 2: 32x4, 3: 64x1, 4: 16x7, 5: 7x16, 6: 14x8, 7: 24x8,
+ * 8: 16x14, 9: 20x11, 10: 15x15, 11: 22x10, 12: 18x12; -1
+ * restores the default (15x15 in 2D, 64x1 in 1D).  The shape changes only the
  * decomposition of the work, never the results.  Errors: CGKS_E_INVAL (1D
  * solvers take only 64x1; 2D solvers any other shape). */
 cgks_status cgks_set_tile_shape(cgks_solver* s, int shape);

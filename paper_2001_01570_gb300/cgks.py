@@ -203,7 +203,8 @@ def cgks_step_profiled(solver, nsteps):
     return list(ms)
 
 
-TILE_SHAPES = ("16x8", "8x16", "32x4", "64x1", "16x7", "7x16", "14x8", "24x8")
+TILE_SHAPES = ("16x8", "8x16", "32x4", "64x1", "16x7", "7x16", "14x8", "24x8", "16x14", "20x11", "15x15",
+               "22x10", "18x12")
 
 
 def cgks_set_tile_shape(solver, shape):

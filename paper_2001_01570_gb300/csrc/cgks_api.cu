@@ -103,7 +103,7 @@ cgks_status read_ctrl(cgks_solver* s, Ctrl* c)
 
 int pick_shape(const cgks_problem& p)
 {
-    return p.dim == 1 ? TILE_64x1 : TILE_24x8;
+    return p.dim == 1 ? TILE_64x1 : TILE_15x15;
 }
 
 }  // namespace
@@ -442,7 +442,7 @@ cudaError_t make_plan(cgks_solver* const* solvers, int n, cudaStream_t stream, i
     bp->cells = cells;
     if (bp->dim == 1) { bp->candidates = {TILE_64x1}; }
     else if (forced_shape >= 0) { bp->candidates = {forced_shape}; }
-    else { bp->candidates = {TILE_24x8, TILE_16x7, TILE_14x8}; }
+    else { bp->candidates = {TILE_15x15, TILE_16x14, TILE_24x8, TILE_16x7}; }
     for (int shape : bp->candidates) {
         std::vector<TileRef> tiles;
         for (int g = 0; g < n; ++g) {

@@ -6,35 +6,20 @@
 
 namespace cgks {
 
-cudaError_t launch_stage_16x8(int, const GridDev*, const TileRef*, int, int, cudaStream_t);
-cudaError_t launch_stage_8x16(int, const GridDev*, const TileRef*, int, int, cudaStream_t);
-cudaError_t launch_stage_32x4(int, const GridDev*, const TileRef*, int, int, cudaStream_t);
-cudaError_t launch_stage_64x1(int, const GridDev*, const TileRef*, int, int, cudaStream_t);
-size_t smem_16x8(int);
-size_t smem_8x16(int);
-size_t smem_32x4(int);
-size_t smem_64x1(int);
-cudaError_t launch_stage_16x7(int, const GridDev*, const TileRef*, int, int, cudaStream_t);
-cudaError_t launch_stage_7x16(int, const GridDev*, const TileRef*, int, int, cudaStream_t);
-cudaError_t launch_stage_14x8(int, const GridDev*, const TileRef*, int, int, cudaStream_t);
-size_t smem_16x7(int);
-size_t smem_7x16(int);
-size_t smem_14x8(int);
-cudaError_t launch_stage_24x8(int, const GridDev*, const TileRef*, int, int, cudaStream_t);
-size_t smem_24x8(int);
+#define CGKS_DECLARE_TILE(w, h)                                                                          \
+    cudaError_t launch_stage_##w##x##h(int, const GridDev*, const TileRef*, int, int, cudaStream_t);  \
+    size_t smem_##w##x##h(int);
+CGKS_FOR_EACH_TILE(CGKS_DECLARE_TILE)
+#undef CGKS_DECLARE_TILE
 
 cudaError_t launch_stage(int shape, int stage, const GridDev* grids, const TileRef* tiles, int ntiles, int nblocks,
                          cudaStream_t st)
 {
     switch (shape) {
-    case TILE_16x8: return launch_stage_16x8(stage, grids, tiles, ntiles, nblocks, st);
-    case TILE_8x16: return launch_stage_8x16(stage, grids, tiles, ntiles, nblocks, st);
-    case TILE_32x4: return launch_stage_32x4(stage, grids, tiles, ntiles, nblocks, st);
-    case TILE_64x1: return launch_stage_64x1(stage, grids, tiles, ntiles, nblocks, st);
-    case TILE_16x7: return launch_stage_16x7(stage, grids, tiles, ntiles, nblocks, st);
-    case TILE_7x16: return launch_stage_7x16(stage, grids, tiles, ntiles, nblocks, st);
-    case TILE_14x8: return launch_stage_14x8(stage, grids, tiles, ntiles, nblocks, st);
-    case TILE_24x8: return launch_stage_24x8(stage, grids, tiles, ntiles, nblocks, st);
+#define CGKS_LAUNCH_CASE(w, h) \
+    case TILE_##w##x##h: return launch_stage_##w##x##h(stage, grids, tiles, ntiles, nblocks, st);
+    CGKS_FOR_EACH_TILE(CGKS_LAUNCH_CASE)
+#undef CGKS_LAUNCH_CASE
     default: return cudaErrorInvalidValue;
     }
 }
@@ -42,14 +27,10 @@ cudaError_t launch_stage(int shape, int stage, const GridDev* grids, const TileR
 size_t stage_smem_bytes(int shape, int stage)
 {
     switch (shape) {
-    case TILE_16x8: return smem_16x8(stage);
-    case TILE_8x16: return smem_8x16(stage);
-    case TILE_32x4: return smem_32x4(stage);
-    case TILE_64x1: return smem_64x1(stage);
-    case TILE_16x7: return smem_16x7(stage);
-    case TILE_7x16: return smem_7x16(stage);
-    case TILE_14x8: return smem_14x8(stage);
-    case TILE_24x8: return smem_24x8(stage);
+#define CGKS_SMEM_CASE(w, h) \
+    case TILE_##w##x##h: return smem_##w##x##h(stage);
+    CGKS_FOR_EACH_TILE(CGKS_SMEM_CASE)
+#undef CGKS_SMEM_CASE
     default: return 0;
     }
 }

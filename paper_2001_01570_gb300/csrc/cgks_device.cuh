@@ -427,47 +427,44 @@ __device__ __forceinline__ void euler_time_derivs(const double W[4], const doubl
     o.TNS[3] = U * sxx + V * sxy + Kheat * p * thx;
 }
 
-// ------------------------------------------------------------------------
-// One interface quadrature point in the face frame (Sec. 2.1-2.2).
-struct PointIn {
-    double W0[4], W0n[4], W0t[4], W0nn[4], W0nt[4], W0tt[4];
-    double Wl[4], Wln[4], Wlt[4], Wr[4], Wrn[4], Wrt[4];
-};
-
 struct Params {
     double gamma, K, eps_tau, c_tau, dt, mu;
     double idt, inv_K2, inv_gm1;   // 1/dt, 1/(K+2), 1/(gamma-1)
     double K2inv2, Kheat;          // 2/(K+2), (K+4)/2
 };
 
-// STAGE 1: Fb, Ft, Wm = W(dt/2), Wb = W(dt) with W0_tt^n;  STAGE 2: Ft, Wtt
-template <int STAGE>
-__device__ __forceinline__ bool gks_point(const PointIn& in, const Params& P,
+// ------------------------------------------------------------------------
+// One interface quadrature point in the face frame (Sec. 2.1-2.2).
+// Inputs of one Gauss point are pulled from the caller's loader when they are
+// consumed, so that the 48 reconstructed quantities are never live at once:
+//   src.eq_value(W0)                          equilibrium state
+//   src.eq_derivs(W0n, W0t, W0nn, W0nt, W0tt)  its derivatives (face frame)
+//   src.ne_value(side, W, Wt)                 left (0) / right (1) state and its
+//                                             tangential derivative
+//   src.ne_normal(side, Wn)                   its normal derivative
+template <int STAGE, class Src>
+__device__ __forceinline__ bool gks_point(const Src& src, const Params& P,
                                           double Fb[4], double Ft[4], double Wm[4], double Wb[4], double Wtt[4])
 {
     const double gm1 = P.gamma - 1.0, K = P.K, dt = P.dt;
     // equilibrium state g0
-    const double ir0 = __drcp_rn(in.W0[0]);
-    const double U0 = in.W0[1] * ir0, V0 = in.W0[2] * ir0;
-    const double p0 = gm1 * (in.W0[3] - 0.5 * (in.W0[1] * U0 + in.W0[2] * V0));
+    double W0[4];
+    src.eq_value(W0);
+    const double ir0 = __drcp_rn(W0[0]);
+    const double U0 = W0[1] * ir0, V0 = W0[2] * ir0;
+    const double p0 = gm1 * (W0[3] - 0.5 * (W0[1] * U0 + W0[2] * V0));
     // non-equilibrium states
-    const double irl = __drcp_rn(in.Wl[0]);
-    const double Ul = in.Wl[1] * irl, Vl = in.Wl[2] * irl;
-    const double pl = gm1 * (in.Wl[3] - 0.5 * (in.Wl[1] * Ul + in.Wl[2] * Vl));
-    const double irr = __drcp_rn(in.Wr[0]);
-    const double Ur = in.Wr[1] * irr, Vr = in.Wr[2] * irr;
-    const double pr = gm1 * (in.Wr[3] - 0.5 * (in.Wr[1] * Ur + in.Wr[2] * Vr));
-    const bool ok = (in.W0[0] > 0.0) && (p0 > 0.0) && (in.Wl[0] > 0.0) && (pl > 0.0) && (in.Wr[0] > 0.0) && (pr > 0.0);
+    double Wl[4], Wlt[4], Wr[4], Wrt[4];
+    src.ne_value(0, Wl, Wlt);
+    src.ne_value(1, Wr, Wrt);
+    const double irl = __drcp_rn(Wl[0]);
+    const double Ul = Wl[1] * irl, Vl = Wl[2] * irl;
+    const double pl = gm1 * (Wl[3] - 0.5 * (Wl[1] * Ul + Wl[2] * Vl));
+    const double irr = __drcp_rn(Wr[0]);
+    const double Ur = Wr[1] * irr, Vr = Wr[2] * irr;
+    const double pr = gm1 * (Wr[3] - 0.5 * (Wr[1] * Ur + Wr[2] * Vr));
+    const bool ok = (W0[0] > 0.0) && (p0 > 0.0) && (Wl[0] > 0.0) && (pl > 0.0) && (Wr[0] > 0.0) && (pr > 0.0);
     const double thl = pl * irl, thr = pr * irr;
-
-    // Euler derivatives of the equilibrium state (W_t, W_tt, F, F_t)
-    EulerTD e;
-    euler_time_derivs(in.W0, in.W0n, in.W0t, in.W0nn, in.W0nt, in.W0tt, P.gamma, P.inv_gm1, P.K2inv2, P.Kheat, ir0,
-                      U0, V0, p0, e);
-
-    // tau-terms of g0: rho <(a_n u + a_t v) u psi> = TNS - F_t (the time part is the Euler F_t)
-    double T2[4];
-    for (int k = 0; k < 4; ++k) T2[k] = e.TNS[k] - e.Ft[k];
 
     // Sec. 4: collision time with pressure-jump enhancement; viscous flow: mu/p
     // with p the equilibrium pressure at the point
@@ -494,18 +491,19 @@ __device__ __forceinline__ bool gks_point(const PointIn& in, const Params& P,
         SlopeCtx sl;
         slope_ctx(Ul, Vl, thl, ithl, K, P.inv_K2, sl);
         double b1[4], b2[4], a1[4], a2[4], o1[4], o2[4], f[4];
-        for (int k = 0; k < 4; ++k) { b1[k] = in.Wln[k] * irl; b2[k] = in.Wlt[k] * irl; }
+        src.ne_normal(0, b1);
+        for (int k = 0; k < 4; ++k) { b1[k] *= irl; b2[k] = Wlt[k] * irl; }
         micro_slope(sl, b1, a1);
         micro_slope(sl, b2, a2);
         psi_uv<1, 0>(ml, f);
         a_psi_uv<2, 0>(ml, a1, o1);
         a_psi_uv<1, 1>(ml, a2, o2);
-        for (int k = 0; k < 4; ++k) { Fh[k] = in.Wl[0] * f[k]; Th[k] = in.Wl[0] * (o1[k] + o2[k]); }
+        for (int k = 0; k < 4; ++k) { Fh[k] = Wl[0] * f[k]; Th[k] = Wl[0] * (o1[k] + o2[k]); }
         if (need_ne) {
             psi_uv<0, 0>(ml, f);
             a_psi_uv<1, 0>(ml, a1, o1);
             a_psi_uv<0, 1>(ml, a2, o2);
-            for (int k = 0; k < 4; ++k) { Wh[k] = in.Wl[0] * f[k]; Wsl[k] = in.Wl[0] * (o1[k] + o2[k]); }
+            for (int k = 0; k < 4; ++k) { Wh[k] = Wl[0] * f[k]; Wsl[k] = Wl[0] * (o1[k] + o2[k]); }
         }
     }
     {
@@ -517,20 +515,35 @@ __device__ __forceinline__ bool gks_point(const PointIn& in, const Params& P,
         SlopeCtx sr;
         slope_ctx(Ur, Vr, thr, ithr, K, P.inv_K2, sr);
         double b1[4], b2[4], a1[4], a2[4], o1[4], o2[4], f[4];
-        for (int k = 0; k < 4; ++k) { b1[k] = in.Wrn[k] * irr; b2[k] = in.Wrt[k] * irr; }
+        src.ne_normal(1, b1);
+        for (int k = 0; k < 4; ++k) { b1[k] *= irr; b2[k] = Wrt[k] * irr; }
         micro_slope(sr, b1, a1);
         micro_slope(sr, b2, a2);
         psi_uv<1, 0>(mr, f);
         a_psi_uv<2, 0>(mr, a1, o1);
         a_psi_uv<1, 1>(mr, a2, o2);
-        for (int k = 0; k < 4; ++k) { Fh[k] += in.Wr[0] * f[k]; Th[k] += in.Wr[0] * (o1[k] + o2[k]); }
+        for (int k = 0; k < 4; ++k) { Fh[k] += Wr[0] * f[k]; Th[k] += Wr[0] * (o1[k] + o2[k]); }
         if (need_ne) {
             psi_uv<0, 0>(mr, f);
             a_psi_uv<1, 0>(mr, a1, o1);
             a_psi_uv<0, 1>(mr, a2, o2);
-            for (int k = 0; k < 4; ++k) { Wh[k] += in.Wr[0] * f[k]; Wsl[k] += in.Wr[0] * (o1[k] + o2[k]); }
+            for (int k = 0; k < 4; ++k) { Wh[k] += Wr[0] * f[k]; Wsl[k] += Wr[0] * (o1[k] + o2[k]); }
         }
     }
+
+    // Euler derivatives of the equilibrium state (W_t, W_tt, F, F_t), evaluated after the
+    // half-line moments so that the two sets of intermediates are never live together
+    EulerTD e;
+    {
+        double W0n[4], W0t[4], W0nn[4], W0nt[4], W0tt[4];
+        src.eq_derivs(W0n, W0t, W0nn, W0nt, W0tt);
+        euler_time_derivs(W0, W0n, W0t, W0nn, W0nt, W0tt, P.gamma, P.inv_gm1, P.K2inv2, P.Kheat, ir0,
+                          U0, V0, p0, e);
+    }
+
+    // tau-terms of g0: rho <(a_n u + a_t v) u psi> = TNS - F_t (the time part is the Euler F_t)
+    double T2[4];
+    for (int k = 0; k < 4; ++k) T2[k] = e.TNS[k] - e.Ft[k];
 
     const double omh = 1.0 - h;
     const double idt = P.idt;
@@ -549,11 +562,11 @@ __device__ __forceinline__ bool gks_point(const PointIn& in, const Params& P,
         // interface state W(t) = W0 + t W_t + t^2/2 W_tt + e^{-t/tau} [W_ne(t) - W0 - t W_t]
         const double th = 0.5 * dt, h2 = h * h;
         for (int k = 0; k < 4; ++k) {
-            Wm[k] = in.W0[k] + th * e.Wt[k] + (0.125 * dt * dt) * e.Wtt[k];
-            Wb[k] = in.W0[k] + dt * e.Wt[k] + (dt * dt / 6.0) * e.Wtt[k];
+            Wm[k] = W0[k] + th * e.Wt[k] + (0.125 * dt * dt) * e.Wtt[k];
+            Wb[k] = W0[k] + dt * e.Wt[k] + (dt * dt / 6.0) * e.Wtt[k];
             if (need_ne) {
-                Wm[k] += h * ((Wh[k] - th * Wsl[k]) - in.W0[k] - th * e.Wt[k]);
-                Wb[k] += h2 * ((Wh[k] - dt * Wsl[k]) - in.W0[k] - dt * e.Wt[k]);
+                Wm[k] += h * ((Wh[k] - th * Wsl[k]) - W0[k] - th * e.Wt[k]);
+                Wb[k] += h2 * ((Wh[k] - dt * Wsl[k]) - W0[k] - dt * e.Wt[k]);
             }
         }
     } else {

@@ -39,15 +39,24 @@ struct GridDev {
 // One unit of work of the stage kernels: a TX x TY tile of one grid.
 struct TileRef { int grid, x0, y0, pad; };
 
-// tile shapes compiled into the library.  16x7, 7x16 and 14x8 give 247, 247
-// and 246 face segments per tile, i.e. one pass of the 256-thread CTA over the
-// heaviest phase (16x8 needs 280: a second pass with a single warp)
-// 24x8 trades a second, five-warp pass over the segments for less halo
-// recomputation (2.52 instead of 2.65 WENO records per cell).
-enum TileShape { TILE_16x8 = 0, TILE_8x16 = 1, TILE_32x4 = 2, TILE_64x1 = 3, TILE_16x7 = 4, TILE_7x16 = 5,
-                 TILE_14x8 = 6, TILE_24x8 = 7, TILE_COUNT = 8 };
-inline int tile_w(int s) { static const int w[TILE_COUNT] = {16, 8, 32, 64, 16, 7, 14, 24}; return w[s]; }
-inline int tile_h(int s) { static const int h[TILE_COUNT] = {8, 16, 4, 1, 7, 16, 8, 8}; return h[s]; }
+// tile shapes compiled into the library, in the public numbering of
+// cgks_set_tile_shape.  The heaviest phase runs one face segment per thread;
+// a TX x TY tile has 2 TX TY + TX + TY segments for 256 threads: 16x7, 7x16 and
+// 14x8 give 247, 247 and 246 (one pass); 16x8 needs 280 (a second pass with a
+// single warp); 24x8 has 416 (a second, five-warp pass) but less halo
+// recomputation per cell; 16x14, 20x11, 15x15, 22x10 and 18x12 fill two passes
+// to 90-94 % and are the largest tiles whose stage-1 shared memory fits 227 KB.
+#define CGKS_FOR_EACH_TILE(X) X(16, 8) X(8, 16) X(32, 4) X(64, 1) X(16, 7) X(7, 16) X(14, 8) X(24, 8) \
+    X(16, 14) X(20, 11) X(15, 15) X(22, 10) X(18, 12)
+#define CGKS_TILE_ENUM(w, h) TILE_##w##x##h,
+enum TileShape { CGKS_FOR_EACH_TILE(CGKS_TILE_ENUM) TILE_COUNT };
+#undef CGKS_TILE_ENUM
+#define CGKS_TILE_W(w, h) w,
+#define CGKS_TILE_H(w, h) h,
+inline int tile_w(int s) { static const int v[TILE_COUNT] = {CGKS_FOR_EACH_TILE(CGKS_TILE_W)}; return v[s]; }
+inline int tile_h(int s) { static const int v[TILE_COUNT] = {CGKS_FOR_EACH_TILE(CGKS_TILE_H)}; return v[s]; }
+#undef CGKS_TILE_W
+#undef CGKS_TILE_H
 
 // launchers (defined in the kernel translation units)
 cudaError_t launch_stage(int shape, int stage, const GridDev* grids, const TileRef* tiles, int ntiles,

@@ -71,6 +71,73 @@ __device__ __forceinline__ int map_axis(int i, int n, int bclo, int bchi, int& k
     return i;
 }
 
+// The face rows around one face segment (records of rows j-2..j+2 of one
+// face) and the reconstruction along the face at one Gauss point eta:
+// WENO-Z point values (equilibrium over five rows, non-equilibrium states over
+// three), tangential derivatives of the equilibrium state and normal
+// derivatives from the quartic / quadratic through the same line averages.
+struct SegmentRows {
+    const double* rec;
+    int nrec, r0, rstride;
+    double eta, iht, weps;
+
+    __device__ __forceinline__ double at(int f, int k, int off) const { return rec[(f * 4 + k) * nrec + r0 + off * rstride]; }
+
+    __device__ __forceinline__ void eq_value(double W0[4]) const
+    {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            W0[k] = tang_weno5(at(RV, k, -2), at(RV, k, -1), at(RV, k, 0), at(RV, k, 1), at(RV, k, 2), eta, weps);
+    }
+
+    // quartic with segment means m_{j-2..j+2}: coefficients c1..c4 of eta^1..eta^4
+    __device__ __forceinline__ static void quartic(double mm, double m, double m0, double p, double pp,
+                                                   double& c1, double& c2, double& c3, double& c4)
+    {
+        const double S1 = p + m, S2 = pp + mm, A1 = p - m, A2 = pp - mm;
+        c1 = (34.0 * A1 - 5.0 * A2) * (1.0 / 48.0);
+        c3 = (A2 - 2.0 * A1) * (1.0 / 12.0);
+        c2 = (12.0 * S1 - S2 - 22.0 * m0) * (1.0 / 16.0);
+        c4 = (S2 - 4.0 * S1 + 6.0 * m0) * (1.0 / 24.0);
+    }
+
+    __device__ __forceinline__ void eq_derivs(double W0n[4], double W0t[4], double W0nn[4], double W0nt[4],
+                                              double W0tt[4]) const
+    {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            double c1, c2, c3, c4;
+            quartic(at(RV, k, -2), at(RV, k, -1), at(RV, k, 0), at(RV, k, 1), at(RV, k, 2), c1, c2, c3, c4);
+            W0t[k] = (c1 + 0.25 * c3 + eta * (2.0 * c2 + c4 * (1.0 / 3.0))) * iht;
+            W0tt[k] = (2.0 * c2 + c4 + 6.0 * eta * c3) * iht * iht;
+            const double N0 = at(RN, k, 0);
+            quartic(at(RN, k, -2), at(RN, k, -1), N0, at(RN, k, 1), at(RN, k, 2), c1, c2, c3, c4);
+            W0n[k] = N0 - c4 * (1.0 / 180.0) + eta * (c1 + c3 * (1.0 / 12.0));
+            W0nt[k] = (c1 + 0.25 * c3 + eta * (2.0 * c2 + c4 * (1.0 / 3.0))) * iht;
+            W0nn[k] = at(RNN, k, 0);
+        }
+    }
+
+    __device__ __forceinline__ void ne_value(int side, double W[4], double Wt[4]) const
+    {
+        const int f = side ? RR : RL;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const double v0 = at(f, k, 0);
+            const double sl = tang_weno3_slope(at(f, k, -1), v0, at(f, k, 1), weps);
+            W[k] = v0 + eta * sl;
+            Wt[k] = sl * iht;
+        }
+    }
+
+    __device__ __forceinline__ void ne_normal(int side, double Wn[4]) const
+    {
+        const int f = side ? RRN : RLN;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) Wn[k] = at(f, k, 0) + eta * 0.5 * (at(f, k, 1) - at(f, k, -1));
+    }
+};
+
 template <int TX, int TY, int STAGE>
 __global__ void __launch_bounds__(kThreads, 1)
 stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tiles, int ntiles)
@@ -301,47 +368,9 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
 #pragma unroll 1
             for (int gp = 0; gp < 2; ++gp) {
                 const double eta = gp ? gq : -gq;
-                PointIn in;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    auto R = [&](int f, int off) { return rec[(f * 4 + k) * nrec + r0 + off]; };
-                    // quartic with segment means V_{j-2..j+2}: at eta = +-1/(2 sqrt 3)
-                    {
-                        const double Vmm = R(RV, -2 * rstride), Vm = R(RV, -rstride), V0 = R(RV, 0);
-                        const double Vp = R(RV, rstride), Vpp = R(RV, 2 * rstride);
-                        const double S1 = Vp + Vm, S2 = Vpp + Vmm, A1 = Vp - Vm, A2 = Vpp - Vmm;
-                        const double c1 = (34.0 * A1 - 5.0 * A2) * (1.0 / 48.0), c3 = (A2 - 2.0 * A1) * (1.0 / 12.0);
-                        const double c2 = (12.0 * S1 - S2 - 22.0 * V0) * (1.0 / 16.0);
-                        const double c4 = (S2 - 4.0 * S1 + 6.0 * V0) * (1.0 / 24.0);
-                        in.W0[k] = tang_weno5(Vmm, Vm, V0, Vp, Vpp, eta, weps);
-                        in.W0t[k] = (c1 + 0.25 * c3 + eta * (2.0 * c2 + c4 * (1.0 / 3.0))) * iht;
-                        in.W0tt[k] = (2.0 * c2 + c4 + 6.0 * eta * c3) * iht * iht;
-                    }
-                    {
-                        const double Nmm = R(RN, -2 * rstride), Nm = R(RN, -rstride), N0 = R(RN, 0);
-                        const double Np = R(RN, rstride), Npp = R(RN, 2 * rstride);
-                        const double S1 = Np + Nm, S2 = Npp + Nmm, A1 = Np - Nm, A2 = Npp - Nmm;
-                        const double d1 = (34.0 * A1 - 5.0 * A2) * (1.0 / 48.0), d3 = (A2 - 2.0 * A1) * (1.0 / 12.0);
-                        const double d2 = (12.0 * S1 - S2 - 22.0 * N0) * (1.0 / 16.0);
-                        const double d4 = (S2 - 4.0 * S1 + 6.0 * N0) * (1.0 / 24.0);
-                        in.W0n[k] = N0 - d4 * (1.0 / 180.0) + eta * (d1 + d3 * (1.0 / 12.0));
-                        in.W0nt[k] = (d1 + 0.25 * d3 + eta * (2.0 * d2 + d4 * (1.0 / 3.0))) * iht;
-                    }
-                    in.W0nn[k] = R(RNN, 0);
-                    // non-equilibrium states over rows j-1..j+1: nonlinear value and
-                    // tangential slope, normal derivative from the quadratic
-                    const double L0 = R(RL, 0), Rc = R(RR, 0);
-                    const double sl = tang_weno3_slope(R(RL, -rstride), L0, R(RL, rstride), weps);
-                    in.Wl[k] = L0 + eta * sl;
-                    in.Wlt[k] = sl * iht;
-                    in.Wln[k] = R(RLN, 0) + eta * 0.5 * (R(RLN, rstride) - R(RLN, -rstride));
-                    const double sr = tang_weno3_slope(R(RR, -rstride), Rc, R(RR, rstride), weps);
-                    in.Wr[k] = Rc + eta * sr;
-                    in.Wrt[k] = sr * iht;
-                    in.Wrn[k] = R(RRN, 0) + eta * 0.5 * (R(RRN, rstride) - R(RRN, -rstride));
-                }
+                const SegmentRows src{rec, nrec, r0, rstride, eta, iht, weps};
                 double Fb[4], Ft[4], Wm[4], Wb[4], Wtt[4];
-                bad |= !gks_point<STAGE>(in, P, Fb, Ft, Wm, Wb, Wtt);
+                bad |= !gks_point<STAGE>(src, P, Fb, Ft, Wm, Wb, Wtt);
                 if (STAGE == 1) {
                     const double c1a = 0.25 * dt, c1b = dt * dt * (1.0 / 16.0);       // half of (dt/2, dt^2/8)
                     const double c2a = 0.5 * dt, c2b = dt * dt * (1.0 / 12.0);        // half of (dt, dt^2/6)
@@ -448,5 +477,20 @@ cudaError_t launch_stage_t(const GridDev* grids, const TileRef* tiles, int ntile
     stage_kernel<TX, TY, STAGE><<<nblocks, kThreads, L::bytes, st>>>(grids, tiles, ntiles);
     return cudaGetLastError();
 }
+
+// The launcher and shared-memory size of one tile shape (one translation unit
+// per shape, so the shapes compile in parallel).
+#define CGKS_STAGE_INSTANCE(TX, TY)                                                                         \
+    static_assert(StageLayout<TX, TY, 1>::bytes + 64 <= 227 * 1024, "stage-1 tile exceeds shared memory");  \
+    cudaError_t launch_stage_##TX##x##TY(int stage, const GridDev* grids, const TileRef* tiles, int ntiles,  \
+                                         int nblocks, cudaStream_t st)                                      \
+    {                                                                                                       \
+        return stage == 1 ? launch_stage_t<TX, TY, 1>(grids, tiles, ntiles, nblocks, st)                    \
+                          : launch_stage_t<TX, TY, 2>(grids, tiles, ntiles, nblocks, st);                   \
+    }                                                                                                       \
+    size_t smem_##TX##x##TY(int stage)                                                                      \
+    {                                                                                                       \
+        return stage == 1 ? StageLayout<TX, TY, 1>::bytes : StageLayout<TX, TY, 2>::bytes;                  \
+    }
 
 }  // namespace cgks

@@ -1,0 +1,6 @@
+// Instantiation of the fused stage kernel for 15x15 cell tiles.
+#include "cgks_stage.cuh"
+
+namespace cgks {
+CGKS_STAGE_INSTANCE(15, 15)
+}  // namespace cgks

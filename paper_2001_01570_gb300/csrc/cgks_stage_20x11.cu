@@ -1,0 +1,6 @@
+// Instantiation of the fused stage kernel for 20x11 cell tiles.
+#include "cgks_stage.cuh"
+
+namespace cgks {
+CGKS_STAGE_INSTANCE(20, 11)
+}  // namespace cgks
