@@ -7,6 +7,11 @@ CFL 0.5), synthetic initial data, state (3 x 12 planes, 1.2 GB) resident in HBM 
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cgks|reference] [--workload NAME]
 
+Other workloads: vortex256/512/1024, shockvortex1024x512 (plain sweep), batched256 (256 uneven 2D
+grids, batched persistent launch vs one grid per launch), acoustic1d (2048 copies of the 1D
+acoustic-wave test, 12-48 cells each, batched vs plain), served (the Poisson request stream
+through the continuous-batching server).
+
 --impl reference times the CPU oracle (test infrastructure, plain FP64 C) on a bounded sample of
 the same workload on the host cores.  Prints one JSON line (rank 0).
 """
@@ -30,14 +35,18 @@ import numpy as np  # noqa: E402
 METRIC = "FP64 cell-updates/s on 1 GB300 (plain 2048^2 sweep); served-batched vs plain; p50/p99 solve latency"
 UNIT = "cell-updates/s"
 
-# FP64 floating-point operations per cell and stage executed by the 16x7 stage kernels (FMA = 2),
-# counted with ncu (sm__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on) on the 256^2
-# isentropic vortex and divided by the cells: profiles/stage_kernels_vortex256.md.
-FLOP_PER_CELL = {1: 12256.0, 2: 11778.0}
-# DRAM bytes (read + write) per cell of one stage-1 launch, ncu dram__bytes_{read,write}.sum on the
-# 1024^2 vortex (state larger than L2) divided by the cells; a launch on the 2048^2 bench grid moves
-# the same bytes per cell: profiles/stage_kernels_dram_vortex1024.md.
-DRAM_BYTES_PER_CELL = {1: 283.0e6 / 1048576, 2: 271.0e6 / 1048576}
+# Algorithmic FP64 operations per cell and stage (FMA = 2): the work of one cell's two face rows
+# (linear recon + WENO-Z pair per variable), its two face segments (two Gauss points each) and its
+# update, without the halo rows a tile recomputes.  Per-row costs from ncu op counts of a probe of the
+# phase-1 item, per-segment and per-cell costs fitted to the ncu op counts of seven tile shapes on
+# the 256^2 vortex: profiles/stage_kernels_flops_vortex256.md.
+FLOP_PER_CELL = {1: 11090.0, 2: 10725.0}
+# FP64 operations per cell and stage the default 15x15 tiles execute (halo rows recomputed):
+EXEC_FLOP_PER_CELL_15x15 = {1: 12543.0, 2: 12136.0}
+# DRAM bytes (read + write) per cell of one stage-1 launch with 15x15 tiles, ncu
+# dram__bytes_{read,write}.sum on the 1024^2 vortex (state larger than L2) divided by the cells; the
+# 2048^2 bench grid moves the same bytes per cell: profiles/stage_kernels_ncu_vortex1024.md.
+DRAM_BYTES_PER_CELL = {1: 292.69e6 / 1048576, 2: 274.32e6 / 1048576}
 # measured FP64 peak of this GB300 (DFMA throughput loop, FMA = 2): profiles/fp64_peak_gb300.md
 FP64_PEAK_TFLOPS = 1.010
 
@@ -206,20 +215,17 @@ def run_cgks(args, world, rank, local):
     # ---------------- per-kernel durations (events around every launch) for the roofline
     prof_steps = max(2, min(args.steps, 5))
     stage_ms = cgks.cgks_step_profiled(solver.handle, prof_steps)
-    roofline = None
-    if FLOP_PER_CELL[1]:
-        flops = FLOP_PER_CELL[1] * cells
-        achieved = flops / (stage_ms[1] * 1e-3) / 1e12
-        same_kernel = args.tile in (None, "24x8")
-        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_PEAK_TFLOPS,
-                    "traffic": DRAM_BYTES_PER_CELL[1] * cells if same_kernel else None,
-                    "algorithmic_bytes": 288 * cells,
-                    "kernel": f"stage_kernel<{args.tile or '24x8'},1>",
-                    "kernel_ms": stage_ms[1], "peak_source": "measured FP64 DFMA loop (FMA=2) on GB300"}
-    else:
-        roofline = {"bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": None,
-                    "traffic": None, "kernel": f"stage_kernel<{args.tile or '24x8'},1>", "kernel_ms": stage_ms[1]}
+    tile = args.tile or "15x15"
+    flops = FLOP_PER_CELL[1] * cells
+    achieved = flops / (stage_ms[1] * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": DRAM_BYTES_PER_CELL[1] * cells if tile == "15x15" else None,
+                "algorithmic_bytes": 288 * cells, "algorithmic_flop_per_cell": FLOP_PER_CELL[1],
+                "kernel": f"stage_kernel<{tile},1>", "kernel_ms": stage_ms[1],
+                "executed_tflops": (EXEC_FLOP_PER_CELL_15x15[1] * cells / (stage_ms[1] * 1e-3) / 1e12
+                                    if tile == "15x15" else None),
+                "peak_source": "measured FP64 DFMA loop (FMA=2) on GB300, of measured"}
 
     # ---------------- end to end through the C ABI with host buffers
     host_in = torch.from_numpy(np.ascontiguousarray(W)).pin_memory()
@@ -265,6 +271,11 @@ def _pulse_ic(p):
     return spec, W
 
 
+def _acoustic_ic(p):
+    from paper_2001_01570_gb300 import workloads as wl
+    return wl.acoustic_wave_1d(p["N"], eps_tau=0.0)
+
+
 def _request_ic(req):
     from paper_2001_01570_gb300 import workloads as wl
     return wl.request_problem(req)
@@ -281,8 +292,19 @@ def run_batched(args, world, rank, local):
     """Many independent grids of uneven size: one grid per launch (cgks_step per grid) against one
     persistent launch over all grids' tiles per stage (cgks_batch_step, CUDA graph, autotuned)."""
     from paper_2001_01570_gb300 import workloads as wl
-    params = wl.batched_pulses(seed=1570, count=args.grids)
-    ics = _parallel_ics(_pulse_ic, params)
+    if args.workload == "acoustic1d":
+        count = args.grids if args.grids_set else 2048
+        params = wl.batched_acoustic_1d(seed=618, count=count)
+        ics = _parallel_ics(_acoustic_ic, params)
+        what = (f"FP64 cell-updates/s, {count} 1D acoustic-wave grids: batched persistent launch vs one grid "
+                "per launch")
+        sizes = "N log-uniform in [12, 48], seed 618; eps_tau = 0"
+    else:
+        count = args.grids
+        params = wl.batched_pulses(seed=1570, count=count)
+        ics = _parallel_ics(_pulse_ic, params)
+        what = f"FP64 cell-updates/s, {count} uneven grids: batched persistent launch vs one grid per launch"
+        sizes = "N log-uniform in [64, 512], seed 1570"
     import torch
     from paper_2001_01570_gb300 import build as libbuild
     from paper_2001_01570_gb300 import cgks
@@ -327,12 +349,13 @@ def run_batched(args, world, rank, local):
     batched = cells * args.steps / (ms_batch * 1e-3)
     if rank == 0:
         print(json.dumps({
-            "metric": "FP64 cell-updates/s, 256 uneven grids: batched persistent launch vs one grid per launch",
+            "metric": what,
             "value": batched, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_batch / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"batched{args.grids}", "grids": args.grids, "cells": cells,
-                       "sizes": "N log-uniform in [64, 512], seed 1570", "tile_shape": cgks.TILE_SHAPES[shape] if shape >= 0 else None},
+            "config": {"workload": args.workload if args.workload == "acoustic1d" else f"batched{count}",
+                       "grids": count, "cells": cells, "sizes": sizes,
+                       "tile_shape": cgks.TILE_SHAPES[shape] if shape >= 0 else None},
             "plain": {"value": plain, "ms_per_step": ms_plain / args.steps, "gpu_launches": launches_plain,
                       "clocks": clk_plain.summary()},
             "batched_vs_plain": batched / plain, "gpu_launches": launches, "clocks": clk.summary()}), flush=True)
@@ -407,17 +430,20 @@ def main():
     ap.add_argument("--workload", default="vortex2048")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", default=None, help="tile shape of the plain path (e.g. 16x7, 24x8)")
-    ap.add_argument("--grids", type=int, default=256)
+    ap.add_argument("--grids", type=int, default=None)
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--served-scale", type=float, default=8.0)
     ap.add_argument("--arrival-scale", type=float, default=1.0)
     ap.add_argument("--max-active", type=int, default=64)
     ap.add_argument("--steps-per-round", type=int, default=8)
     args = ap.parse_args()
+    args.grids_set = args.grids is not None
+    if args.grids is None:
+        args.grids = 256
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
-    elif args.workload.startswith("batched"):
+    elif args.workload.startswith("batched") or args.workload == "acoustic1d":
         run_batched(args, world, rank, local)
     elif args.workload == "served":
         run_served(args, world, rank, local)

@@ -168,6 +168,21 @@ def density_wave_1d_exact(n, t, eps=0.2, gamma=1.4):
     return cell_state_1d(fun, n, 0.0, 2.0, gamma)
 
 
+def acoustic_wave_1d(n=16, eps=1e-5, omega=6.0 * math.pi, gamma=1.4, cfl=0.2, eps_tau=0.01):
+    """Sec. 4's 1D acoustic wave: u = eps a cos(omega x), rho = rho_inf (1 + eps cos(2 omega x)),
+    p = p_inf (rho/rho_inf)^gamma on the periodic [0, 1/3] (rho_inf = 1.1771, p_inf = 101325)."""
+    rho_inf, p_inf = 1.1771, 101325.0
+    a = math.sqrt(gamma * p_inf / rho_inf)
+    spec = ProblemSpec(dim=1, nx=n, ny=1, x0=0.0, x1=1.0 / 3.0, gamma=gamma, cfl=cfl, eps_tau=eps_tau,
+                       name=f"acoustic-wave-1d-{n}")
+
+    def fun(x):
+        rho = rho_inf * (1.0 + eps * np.cos(2.0 * omega * x))
+        return rho, eps * a * np.cos(omega * x), p_inf * (rho / rho_inf) ** gamma
+
+    return spec, cell_state_1d(fun, n, 0.0, 1.0 / 3.0, gamma)
+
+
 SOD = ((1.0, 0.0, 1.0), (0.125, 0.0, 0.1))
 LAX = ((0.445, 0.698, 3.528), (0.5, 0.0, 0.571))
 
@@ -345,6 +360,13 @@ def batched_pulses(seed=1570, count=256, nmin=64, nmax=512):
         cx, cy = rng.uniform(0.0, N), rng.uniform(0.0, N)
         out.append(dict(N=N, A=A, b=b, cx=cx, cy=cy))
     return out
+
+
+def batched_acoustic_1d(seed=618, count=2048, nmin=12, nmax=48):
+    """Parameters of the small-amplitude 1D batch: copies of the 1D acoustic-wave test with grid
+    sizes log-uniform in [nmin, nmax] cells (the coarse meshes of Sec. 4 use 12 to 24)."""
+    rng = np.random.default_rng(seed)
+    return [dict(N=int(round(math.exp(rng.uniform(math.log(nmin), math.log(nmax)))))) for _ in range(count)]
 
 
 def served_requests(seed=2001, count=2000, rate=50.0, nmin=128, nmax=2048, smin=100, smax=2000):

@@ -71,3 +71,26 @@ def test_tile_shape_does_not_change_results(shape):
     b, _, _ = s.get_state()
     s.close()
     assert np.array_equal(a, b)
+
+
+def test_batched_1d_acoustic_grids_equal_alone_bitwise():
+    params = wl.batched_acoustic_1d(count=40)
+    cases = [wl.acoustic_wave_1d(p["N"], eps_tau=0.0) for p in params]
+    alone = []
+    for spec, W in cases:
+        s = cgks.Solver(cgks.problem_from_spec(spec))
+        s.set_state(W)
+        s.step(25)
+        alone.append(s.get_state())
+        s.close()
+    solvers = []
+    for spec, W in cases:
+        s = cgks.Solver(cgks.problem_from_spec(spec))
+        s.set_state(W)
+        solvers.append(s)
+    cgks.cgks_batch_step([s.handle for s in solvers], 25)
+    for s, (ref, t, steps) in zip(solvers, alone):
+        out, tb, sb = s.get_state()
+        assert sb == steps == 25 and tb == t
+        assert np.array_equal(out, ref)
+        s.close()

@@ -174,3 +174,14 @@ def test_shock_reflection_paper_grid_reaches_the_exact_regions():
     assert np.abs(rho[0:8, 180:] / r3 - 1.0).max() < 0.01 and np.abs(p[0:8, 180:] / p3 - 1.0).max() < 0.01
     assert np.abs(rho[40:50, 60:110] / r2 - 1.0).max() < 0.01 and np.abs(p[40:50, 60:110] / p2 - 1.0).max() < 0.01
     assert np.abs(rho[0:15, 0:40] / r1 - 1.0).max() < 0.01
+
+
+@pytest.mark.parametrize("n,eps_tau", [(16, 0.0), (13, 0.01)])
+def test_acoustic_wave_1d_ten_lengths(n, eps_tau):
+    """Sec. 4's 1D acoustic wave to t = 0.01 (10 domain lengths, ~830 steps): a 1e-5 perturbation
+    on p = 101325, where the momentum is 1e-7 of the energy."""
+    spec, W = wl.acoustic_wave_1d(n, eps_tau=eps_tau)
+    g, tg, sg = run_gpu(spec, W, 10 ** 6, t_end=0.01)
+    o, to, so = run_oracle(spec, W, 10 ** 6, t_end=0.01)
+    assert sg == so and tg == to == 0.01
+    _check(g, o, spec=spec)
