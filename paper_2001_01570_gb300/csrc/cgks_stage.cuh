@@ -207,15 +207,37 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
         // items are (variable, record) pairs so the 256 threads finish together
         const double eps = G.weno_eps;
         constexpr int NRX = (TX + 1) * (TY + 4), NRY = (TX + 4) * (TY + 1), NR = NRX + NRY;
+        // the heavy items (inner rows: linear + WENO-Z) are dealt out first, then the
+        // light ones (the outer row on each side: linear only), so that no thread gets
+        // more than its share of heavy items
+        constexpr int NIX = (TX + 1) * (TY + 2), NIY = (TY + 1) * (TX + 2), NI = NIX + NIY;
+        constexpr int NOX = (TX + 1) * 2, NOY = (TY + 1) * 2, NO = NOX + NOY;
+        static_assert(NI + NO == NR, "record count");
         for (int it = tid; it < 4 * NR; it += kThreads) {
-            const int k = it / NR, item = it - k * NR;
-            const bool xo = item < NR - NRY;
+            int k, a, rl;          // variable, face index along the tile, row index of the record
+            bool xo;
+            if (it < 4 * NI) {
+                k = it / NI;
+                int r = it - k * NI;
+                xo = r < NIX;
+                if (!xo) r -= NIX;
+                const int nf = xo ? TX + 1 : TY + 1;
+                a = r % nf; rl = 1 + r / nf;
+            } else {
+                const int r2 = it - 4 * NI;
+                k = r2 / NO;
+                int r = r2 - k * NO;
+                xo = r < NOX;
+                if (!xo) r -= NOX;
+                const int nf = xo ? TX + 1 : TY + 1;
+                a = r % nf; rl = (r / nf) ? (xo ? TY + 3 : TX + 3) : 0;
+            }
             int box_i, box_j, step_i, step_j, ridx, nrec, pv, gn;
             double h, ih;
             double* rec;
             bool valid, inner;
             if (xo) {
-                const int fl = item % (TX + 1), rl = item / (TX + 1);   // row y0-2+rl
+                const int fl = a;                                       // row y0-2+rl
                 valid = (x0 + fl <= nx) && (y0 - 2 + rl <= ny + 1);
                 inner = (rl >= 1) && (rl <= TY + 2);
                 box_i = fl; box_j = rl; step_i = 1; step_j = 0;
@@ -223,8 +245,7 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
                 pv = k;
                 rec = rx; nrec = (TY + 4) * (TX + 1); ridx = rl * (TX + 1) + fl;
             } else {
-                const int itm = item - NRX;
-                const int gl = itm % (TY + 1), rl = itm / (TY + 1);       // column x0-2+rl
+                const int gl = a;                                       // column x0-2+rl
                 valid = !dim1 && (y0 + gl <= ny) && (x0 - 2 + rl <= nx + 1);
                 inner = (rl >= 1) && (rl <= TX + 2);
                 box_i = rl; box_j = gl; step_i = 0; step_j = 1;
