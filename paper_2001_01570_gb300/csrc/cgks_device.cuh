@@ -219,8 +219,11 @@ __device__ __forceinline__ void char_to_cons(const CharState& s, const double w[
 // the indicator of candidate k over the central segment; Z = |beta_0 - beta_2|;
 // alpha_k = d_k (e_k + Z) / e_k with e_k = beta_k + eps, normalised with one
 // reciprocal through the common denominator e_0 e_1 e_2.
-__device__ __forceinline__ double tang_weno5(double vmm, double vm, double v0, double vp, double vpp,
-                                             double eta, double eps)
+// Both Gauss points are evaluated at once (eta = -g and +g): the indicators
+// and the unnormalised weights are shared, only the linear weights and the
+// final normalisation differ.
+__device__ __forceinline__ void tang_weno5_pair(double vmm, double vm, double v0, double vp, double vpp, double g,
+                                                double eps, double& at_minus, double& at_plus)
 {
     const double D0 = (3.0 * v0 - 4.0 * vm) + vmm;
     const double D1 = vp - vm;
@@ -232,12 +235,11 @@ __device__ __forceinline__ double tang_weno5(double vmm, double vm, double v0, d
     const double Z = fabs(e0 - e2);
     constexpr double d_lo = 7.0 / 36.0 - 1.7320508075688772 / 1080.0;
     constexpr double d_hi = 7.0 / 36.0 + 1.7320508075688772 / 1080.0;
-    const double w0 = eta > 0.0 ? d_lo : d_hi, w2 = eta > 0.0 ? d_hi : d_lo;
-    const double n0 = w0 * (e0 + Z) * (e1 * e2);
-    const double n1 = (11.0 / 18.0) * (e1 + Z) * (e0 * e2);
-    const double n2 = w2 * (e2 + Z) * (e0 * e1);
-    const double inv = __drcp_rn((n0 + n1) + n2);
-    return v0 + (0.5 * eta) * ((n0 * D0 + n1 * D1 + n2 * D2) * inv);
+    const double P0 = (e0 + Z) * (e1 * e2), P1 = (11.0 / 18.0) * (e1 + Z) * (e0 * e2), P2 = (e2 + Z) * (e0 * e1);
+    const double Q0 = P0 * D0, Q1 = P1 * D1, Q2 = P2 * D2;
+    // eta > 0: weights (d_lo, 11/18, d_hi); eta < 0: (d_hi, 11/18, d_lo)
+    at_plus = v0 + (0.5 * g) * (((d_lo * Q0 + Q1) + d_hi * Q2) * __drcp_rn((d_lo * P0 + P1) + d_hi * P2));
+    at_minus = v0 - (0.5 * g) * (((d_hi * Q0 + Q1) + d_lo * Q2) * __drcp_rn((d_hi * P0 + P1) + d_lo * P2));
 }
 
 // Three means v_{-1..1}: two linear candidates with slopes v_0 - v_-1 and

@@ -72,22 +72,23 @@ __device__ __forceinline__ int map_axis(int i, int n, int bclo, int bchi, int& k
 }
 
 // The face rows around one face segment (records of rows j-2..j+2 of one
-// face) and the reconstruction along the face at one Gauss point eta:
-// WENO-Z point values (equilibrium over five rows, non-equilibrium states over
-// three), tangential derivatives of the equilibrium state and normal
-// derivatives from the quartic / quadratic through the same line averages.
+// face) and the reconstruction along the face at one Gauss point eta: the
+// WENO-Z point values (equilibrium over five rows, non-equilibrium slopes over
+// three) are computed once per segment for both points and carried in W0, sL,
+// sR; tangential derivatives of the equilibrium state and normal derivatives
+// come from the quartic / quadratic through the same line averages.
 struct SegmentRows {
     const double* rec;
     int nrec, r0, rstride;
     double eta, iht, weps;
+    double W0[4], sL[4], sR[4];   // WENO-Z values at this point, non-equilibrium slopes
 
     __device__ __forceinline__ double at(int f, int k, int off) const { return rec[(f * 4 + k) * nrec + r0 + off * rstride]; }
 
-    __device__ __forceinline__ void eq_value(double W0[4]) const
+    __device__ __forceinline__ void eq_value(double W[4]) const
     {
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-            W0[k] = tang_weno5(at(RV, k, -2), at(RV, k, -1), at(RV, k, 0), at(RV, k, 1), at(RV, k, 2), eta, weps);
+        for (int k = 0; k < 4; ++k) W[k] = W0[k];
     }
 
     // quartic with segment means m_{j-2..j+2}: coefficients c1..c4 of eta^1..eta^4
@@ -123,9 +124,8 @@ struct SegmentRows {
         const int f = side ? RR : RL;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const double v0 = at(f, k, 0);
-            const double sl = tang_weno3_slope(at(f, k, -1), v0, at(f, k, 1), weps);
-            W[k] = v0 + eta * sl;
+            const double sl = side ? sR[k] : sL[k];
+            W[k] = at(f, k, 0) + eta * sl;
             Wt[k] = sl * iht;
         }
     }
@@ -386,10 +386,22 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
             double acc[NF];
 #pragma unroll
             for (int q = 0; q < NF; ++q) acc[q] = 0.0;
+            // the nonlinear values along the face: both Gauss points at once
+            double W0m[4], W0p[4], sL[4], sR[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                auto R = [&](int f, int off) { return rec[(f * 4 + k) * nrec + r0 + off * rstride]; };
+                tang_weno5_pair(R(RV, -2), R(RV, -1), R(RV, 0), R(RV, 1), R(RV, 2), gq, weps, W0m[k], W0p[k]);
+                sL[k] = tang_weno3_slope(R(RL, -1), R(RL, 0), R(RL, 1), weps);
+                sR[k] = tang_weno3_slope(R(RR, -1), R(RR, 0), R(RR, 1), weps);
+            }
 #pragma unroll 1
             for (int gp = 0; gp < 2; ++gp) {
                 const double eta = gp ? gq : -gq;
-                const SegmentRows src{rec, nrec, r0, rstride, eta, iht, weps};
+                const SegmentRows src{rec, nrec, r0, rstride, eta, iht, weps,
+                                      {gp ? W0p[0] : W0m[0], gp ? W0p[1] : W0m[1], gp ? W0p[2] : W0m[2],
+                                       gp ? W0p[3] : W0m[3]},
+                                      {sL[0], sL[1], sL[2], sL[3]}, {sR[0], sR[1], sR[2], sR[3]}};
                 double Fb[4], Ft[4], Wm[4], Wb[4], Wtt[4];
                 bad |= !gks_point<STAGE>(src, P, Fb, Ft, Wm, Wb, Wtt);
                 if (STAGE == 1) {
