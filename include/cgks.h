@@ -129,8 +129,9 @@ cgks_status cgks_batch_step(cgks_solver* const* solvers, int n, int nsteps);
 
 /* Cells per CTA tile of the stage kernels for this solver's plain steps:
  * 0: 16x8, 1: 8x16, 2: 32x4, 3: 64x1, 4: 16x7, 5: 7x16, 6: 14x8, 7: 24x8,
- * 8: 16x14, 9: 20x11, 10: 15x15, 11: 22x10, 12: 18x12; -1
- * restores the default (15x15 in 2D, 64x1 in 1D).  The shape changes only the
+ * 8: 16x14, 9: 20x11, 10: 15x15, 11: 22x10, 12: 18x12, 13: 20x12, 14: 15x16,
+ * 15: 17x14; -1
+ * restores the default (15x16 in 2D, 64x1 in 1D).  The shape changes only the
  * decomposition of the work, never the results.  Errors: CGKS_E_INVAL (1D
  * solvers take only 64x1; 2D solvers any other shape). */
 cgks_status cgks_set_tile_shape(cgks_solver* s, int shape);
@@ -142,11 +143,20 @@ cgks_status cgks_set_tile_shape(cgks_solver* s, int shape);
 int cgks_batch_tile_shape(cgks_solver* const* solvers, int n);
 
 /* Same as cgks_step(s, nsteps, 0, NULL), but with CUDA events recorded on the
- * solver's stream around every kernel of every step; stage_ms[0..3] receive
- * the average duration in milliseconds of the step-begin, stage-1, stage-2 and
- * step-end kernels.  For measurement only (the events serialise nothing but
- * add host work per launch). */
-cgks_status cgks_step_profiled(cgks_solver* s, int nsteps, double stage_ms[4]);
+ * solver's stream around every kernel of every step; stage_ms[0..5] receive
+ * the average duration in milliseconds of the step-begin, stage-1 record,
+ * stage-1 flux, stage-2 record, stage-2 flux and step-end kernels.  For
+ * measurement only (the events serialise nothing but add host work per
+ * launch). */
+cgks_status cgks_step_profiled(cgks_solver* s, int nsteps, double stage_ms[6]);
+
+/* Device bytes a solver of this problem holds: three sets of 12 state planes
+ * (current, next, intermediate), the face-row records of the stage in flight
+ * (28 doubles per face row: x-faces 0..nx on rows -2..ny+1 and, in 2D, y-faces
+ * 0..ny on columns -2..nx+1) and 4 KB of descriptors.  The server admits a
+ * request while these bytes fit its budget.  Returns 0 for a NULL or empty
+ * problem. */
+double cgks_problem_device_bytes(const cgks_problem* prob);
 
 /* Kernel launch count of the most recent cgks_step / cgks_batch_step call on
  * the calling thread (for throughput accounting). */
@@ -164,13 +174,15 @@ const char* cgks_last_error(void);
  * region where the allocator must not be re-entered, or embeddings with a
  * fixed memory footprint.  cgks_step_noalloc advances a 2D problem whose state
  * the caller already holds in device memory and allocates nothing: the second
- * state buffer, the intermediate state, the control block and the tile queue
- * live in fixed-size device arrays of the library (file-scope __device__
- * storage, about 12.6 MB plus 256 KB), which every GPU that loads the library
- * holds until the process exits.
+ * state buffer, the intermediate state, the face-row records, the control
+ * block and the work queues live in fixed-size device arrays of the library
+ * (file-scope __device__ storage, about 12.6 MB of state, 34 MB of records and
+ * 300 KB of queues), which every GPU that loads the library holds until the
+ * process exits.
  *
- * prob:        2D problem, nx*ny <= CGKS_NOALLOC_MAX_CELLS and at most
- *              CGKS_NOALLOC_MAX_TILES tiles of 16x8 cells
+ * prob:        2D problem, nx*ny <= CGKS_NOALLOC_MAX_CELLS, nx and ny <=
+ *              CGKS_NOALLOC_MAX_SIDE, at most CGKS_NOALLOC_MAX_TILES tiles of
+ *              16x8 cells
  * planes:      device pointer, 12 planes of ny*nx doubles (layout above); read
  *              as the initial state and overwritten with the state after the
  *              steps (or the last valid state on CGKS_E_NONPHYSICAL)
@@ -187,6 +199,7 @@ const char* cgks_last_error(void);
  * Each call re-initialises the control block and overwrites the scratch it
  * reads, so no state carries over from one call to the next. */
 #define CGKS_NOALLOC_MAX_CELLS 65536
+#define CGKS_NOALLOC_MAX_SIDE 4096
 #define CGKS_NOALLOC_MAX_TILES 16384
 cgks_status cgks_step_noalloc(const cgks_problem* prob, double* planes, int nsteps, double* t_inout,
                               void* cuda_stream);
@@ -198,8 +211,8 @@ const char* cgks_noalloc_last_error(void);
  * Serving: a continuous-batching solve server.  Requests (2D problems with an
  * initial state and a step count) may be submitted from any thread at any
  * time.  A scheduler thread admits them in arrival order while the active set
- * has fewer than max_active solves and their device planes (3 x 12 planes of
- * nx*ny doubles) fit hbm_budget_bytes; all active solves advance together in
+ * has fewer than max_active solves and their device bytes
+ * (cgks_problem_device_bytes) fit hbm_budget_bytes; all active solves advance together in
  * rounds of steps_per_round steps of the batched launch (each with its own dt
  * and step target); a finished solve is copied to host memory and its device
  * memory freed, so waiting requests can enter at the next round. */

@@ -102,6 +102,8 @@ def load():
     L.cgks_status_string.restype = ctypes.c_char_p
     L.cgks_last_error.restype = ctypes.c_char_p
     L.cgks_last_launch_count.restype = ctypes.c_long
+    L.cgks_problem_device_bytes.argtypes = [ctypes.POINTER(cgks_problem)]
+    L.cgks_problem_device_bytes.restype = ctypes.c_double
     _lib = L
     return L
 
@@ -197,14 +199,20 @@ def cgks_batch_step(solvers, nsteps):
 
 
 def cgks_step_profiled(solver, nsteps):
-    """Returns average per-launch milliseconds of (step-begin, stage 1, stage 2, step-end)."""
-    ms = (ctypes.c_double * 4)()
+    """Average per-launch milliseconds of (step-begin, stage-1 records, stage-1 flux, stage-2 records,
+    stage-2 flux, step-end)."""
+    ms = (ctypes.c_double * 6)()
     _check(load().cgks_step_profiled(solver, int(nsteps), ms))
     return list(ms)
 
 
+def cgks_problem_device_bytes(prob) -> float:
+    """Device bytes a solver of this problem holds (the server's admission unit)."""
+    return float(load().cgks_problem_device_bytes(ctypes.byref(prob)))
+
+
 TILE_SHAPES = ("16x8", "8x16", "32x4", "64x1", "16x7", "7x16", "14x8", "24x8", "16x14", "20x11", "15x15",
-               "22x10", "18x12")
+               "22x10", "18x12", "20x12", "15x16", "17x14")
 
 
 def cgks_set_tile_shape(solver, shape):

@@ -24,6 +24,9 @@ struct cgks_solver {
     int nsm = 1;
     cudaStream_t stream = nullptr;
     double* d_planes = nullptr;   // 3 x 12 planes: buf0, buf1, ws
+    double* d_records = nullptr;  // face-row records of the stage in flight
+    TileRef* d_rchunks = nullptr; // record-kernel work queue
+    int nrchunks = 0;
     double* d_stage1d = nullptr;  // 6-plane staging for dim 1
     Ctrl* d_ctrl = nullptr;
     GridDev host_desc;
@@ -71,7 +74,8 @@ cgks_status validate(const cgks_problem* p)
     if (p->dim != 1 && p->dim != 2) return fail(CGKS_E_INVAL, "dim must be 1 or 2");
     const int ny = p->dim == 1 ? 1 : p->ny;
     if (p->nx < 1 || ny < 1) return fail(CGKS_E_INVAL, "nx and ny must be >= 1");
-    if ((long long)p->nx * ny > (1ll << 31)) return fail(CGKS_E_INVAL, "grid too large");
+    const long long rows = (long long)(p->nx + 1) * (ny + 4) + (p->dim == 2 ? (long long)(ny + 1) * (p->nx + 4) : 0);
+    if (4 * rows >= (1ll << 31)) return fail(CGKS_E_INVAL, "grid too large (face-row work items exceed 2^31)");
     if (!(p->x1 > p->x0) || (p->dim == 2 && !(p->y1 > p->y0))) return fail(CGKS_E_INVAL, "empty domain");
     if (!(p->gamma > 1.0) || !(p->gamma < 3.0)) return fail(CGKS_E_INVAL, "gamma out of range");
     if (!(p->cfl > 0.0)) return fail(CGKS_E_INVAL, "cfl must be > 0");
@@ -103,7 +107,7 @@ cgks_status read_ctrl(cgks_solver* s, Ctrl* c)
 
 int pick_shape(const cgks_problem& p)
 {
-    return p.dim == 1 ? TILE_64x1 : TILE_15x15;
+    return p.dim == 1 ? TILE_64x1 : TILE_15x16;
 }
 
 }  // namespace
@@ -130,6 +134,15 @@ const char* cgks_last_error(void) { return g_last_error.c_str(); }
 
 long cgks_last_launch_count(void) { return g_last_launches; }
 
+double cgks_problem_device_bytes(const cgks_problem* prob)
+{
+    if (!prob || prob->nx < 1 || (prob->dim == 2 && prob->ny < 1)) return 0.0;
+    const int ny = prob->dim == 1 ? 1 : prob->ny;
+    const double cells = (double)prob->nx * ny;
+    return 3.0 * 12.0 * cells * sizeof(double) + (double)record_doubles(prob->nx, ny, prob->dim) * sizeof(double)
+           + 4096.0;
+}
+
 cgks_status cgks_create(const cgks_problem* prob, void* cuda_stream, cgks_solver** out)
 {
     if (!out) return fail(CGKS_E_INVAL, "out is NULL");
@@ -146,14 +159,19 @@ cgks_status cgks_create(const cgks_problem* prob, void* cuda_stream, cgks_solver
     cudaError_t e = cudaGetDevice(&s->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, s->device);
     const size_t PL = (size_t)s->nx * s->ny;
-    s->device_bytes = 3 * 12 * PL * sizeof(double);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_planes, s->device_bytes);
+    const size_t rec = record_doubles(s->nx, s->ny, prob->dim);
+    s->device_bytes = 3 * 12 * PL * sizeof(double) + rec * sizeof(double);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_planes, 3 * 12 * PL * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_records, rec * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&s->d_ctrl, sizeof(Ctrl));
     if (e == cudaSuccess) e = cudaMalloc(&s->d_desc, sizeof(GridDev));
     if (e == cudaSuccess && prob->dim == 1) e = cudaMalloc(&s->d_stage1d, 6 * PL * sizeof(double));
     std::vector<TileRef> tiles = make_tiles(s->nx, s->ny, s->shape, 0);
     s->ntiles = (int)tiles.size();
     if (e == cudaSuccess) e = cudaMalloc(&s->d_tiles, tiles.size() * sizeof(TileRef));
+    std::vector<TileRef> rchunks = record_chunks(s->nx, s->ny, prob->dim, prob->recon_vars, 0);
+    s->nrchunks = (int)rchunks.size();
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_rchunks, rchunks.size() * sizeof(TileRef));
     if (e != cudaSuccess) {
         cgks_destroy(s);
         return e == cudaErrorMemoryAllocation ? fail(CGKS_E_NOMEM, "device allocation failed")
@@ -165,6 +183,8 @@ cgks_status cgks_create(const cgks_problem* prob, void* cuda_stream, cgks_solver
     G.buf[1] = s->d_planes + 12 * PL;
     G.ws = s->d_planes + 24 * PL;
     G.ctrl = s->d_ctrl;
+    G.recx = s->d_records;
+    G.recy = prob->dim == 2 ? s->d_records + (size_t)28 * (s->nx + 1) * (s->ny + 4) : nullptr;
     G.nx = s->nx;
     G.ny = s->ny;
     G.dim = prob->dim;
@@ -195,6 +215,9 @@ cgks_status cgks_create(const cgks_problem* prob, void* cuda_stream, cgks_solver
     e = cudaMemcpyAsync(s->d_desc, &G, sizeof(GridDev), cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(s->d_tiles, tiles.data(), tiles.size() * sizeof(TileRef), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->d_rchunks, rchunks.data(), rchunks.size() * sizeof(TileRef), cudaMemcpyHostToDevice,
+                            s->stream);
     if (e == cudaSuccess) e = launch_set_ctrl(s->d_ctrl, 0.0, 0.0, -1, 1, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) {
@@ -232,6 +255,8 @@ cgks_status cgks_destroy(cgks_solver* s)
     cgks_forget_solver_plans(s);
     if (s->d_planes || s->d_ctrl) cudaStreamSynchronize(s->stream);
     cudaFree(s->d_planes);
+    cudaFree(s->d_records);
+    cudaFree(s->d_rchunks);
     cudaFree(s->d_stage1d);
     cudaFree(s->d_ctrl);
     cudaFree(s->d_desc);
@@ -284,12 +309,16 @@ cgks_status cgks_get_state(cgks_solver* s, double* planes, int on_device, double
 static cgks_status enqueue_steps(cgks_solver* s, int nsteps, long* launches)
 {
     const int nblocks = s->ntiles < s->nsm ? s->ntiles : s->nsm;
+    const int cv = s->prob.recon_vars;
+    const int rblocks = record_blocks(s->nrchunks, s->nsm, cv);
     for (int k = 0; k < nsteps; ++k) {
         CK(launch_begin_step(s->d_desc, 1, s->stream));
+        CK(launch_records(1, cv, s->d_desc, s->d_rchunks, s->nrchunks, rblocks, s->stream));
         CK(launch_stage(s->shape, 1, s->d_desc, s->d_tiles, s->ntiles, nblocks, s->stream));
+        CK(launch_records(2, cv, s->d_desc, s->d_rchunks, s->nrchunks, rblocks, s->stream));
         CK(launch_stage(s->shape, 2, s->d_desc, s->d_tiles, s->ntiles, nblocks, s->stream));
         CK(launch_end_step(s->d_desc, 1, s->stream));
-        *launches += 4;
+        *launches += 6;
     }
     return CGKS_OK;
 }
@@ -334,37 +363,44 @@ cgks_status cgks_set_step_target(cgks_solver* s, long long target)
 
 extern "C" {
 
-cgks_status cgks_step_profiled(cgks_solver* s, int nsteps, double stage_ms[4])
+cgks_status cgks_step_profiled(cgks_solver* s, int nsteps, double stage_ms[6])
 {
     if (!s || nsteps <= 0 || !stage_ms) return fail(CGKS_E_INVAL, "bad arguments");
     g_last_launches = 0;
     CK(launch_set_ctrl(s->d_ctrl, 0.0, 0.0, -1, 0, s->stream));
-    std::vector<cudaEvent_t> ev((size_t)nsteps * 5);
+    constexpr int NK = 6;
+    std::vector<cudaEvent_t> ev((size_t)nsteps * (NK + 1));
     for (auto& e : ev) CK(cudaEventCreate(&e));
     const int nblocks = s->ntiles < s->nsm ? s->ntiles : s->nsm;
+    const int cv = s->prob.recon_vars;
+    const int rblocks = record_blocks(s->nrchunks, s->nsm, cv);
     for (int k = 0; k < nsteps; ++k) {
-        cudaEvent_t* e = &ev[(size_t)k * 5];
+        cudaEvent_t* e = &ev[(size_t)k * (NK + 1)];
         CK(cudaEventRecord(e[0], s->stream));
         CK(launch_begin_step(s->d_desc, 1, s->stream));
         CK(cudaEventRecord(e[1], s->stream));
-        CK(launch_stage(s->shape, 1, s->d_desc, s->d_tiles, s->ntiles, nblocks, s->stream));
+        CK(launch_records(1, cv, s->d_desc, s->d_rchunks, s->nrchunks, rblocks, s->stream));
         CK(cudaEventRecord(e[2], s->stream));
-        CK(launch_stage(s->shape, 2, s->d_desc, s->d_tiles, s->ntiles, nblocks, s->stream));
+        CK(launch_stage(s->shape, 1, s->d_desc, s->d_tiles, s->ntiles, nblocks, s->stream));
         CK(cudaEventRecord(e[3], s->stream));
-        CK(launch_end_step(s->d_desc, 1, s->stream));
+        CK(launch_records(2, cv, s->d_desc, s->d_rchunks, s->nrchunks, rblocks, s->stream));
         CK(cudaEventRecord(e[4], s->stream));
+        CK(launch_stage(s->shape, 2, s->d_desc, s->d_tiles, s->ntiles, nblocks, s->stream));
+        CK(cudaEventRecord(e[5], s->stream));
+        CK(launch_end_step(s->d_desc, 1, s->stream));
+        CK(cudaEventRecord(e[6], s->stream));
     }
     CK(cudaStreamSynchronize(s->stream));
-    double acc[4] = {0, 0, 0, 0};
+    double acc[NK] = {0, 0, 0, 0, 0, 0};
     for (int k = 0; k < nsteps; ++k)
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < NK; ++q) {
             float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, ev[(size_t)k * 5 + q], ev[(size_t)k * 5 + q + 1]));
+            CK(cudaEventElapsedTime(&ms, ev[(size_t)k * (NK + 1) + q], ev[(size_t)k * (NK + 1) + q + 1]));
             acc[q] += ms;
         }
     for (auto& e : ev) cudaEventDestroy(e);
-    for (int q = 0; q < 4; ++q) stage_ms[q] = acc[q] / nsteps;
-    g_last_launches = 1 + 4L * nsteps;
+    for (int q = 0; q < NK; ++q) stage_ms[q] = acc[q] / nsteps;
+    g_last_launches = 1 + (long)NK * nsteps;
     Ctrl c;
     cgks_status st = read_ctrl(s, &c);
     if (st != CGKS_OK) return st;
@@ -394,6 +430,7 @@ void destroy_plan(BatchPlan* bp)
         if (bp->exec[k]) cudaGraphExecDestroy(bp->exec[k]);
         cudaFree(bp->d_tiles[k]);
     }
+    for (int c = 0; c < 2; ++c) cudaFree(bp->d_rchunks[c]);
     cudaFree(bp->d_grids);
     delete bp;
 }
@@ -402,9 +439,17 @@ static cudaError_t capture_graph(BatchPlan* bp, int shape)
 {
     const int n = (int)bp->solvers.size();
     const int nblocks = bp->ntiles[shape] < bp->nsm ? bp->ntiles[shape] : bp->nsm;
+    // first calls configure the kernels' attributes outside the capture
     cudaError_t e = launch_stage(shape, 1, bp->d_grids, bp->d_tiles[shape], 0, 1, bp->stream);
     if (e == cudaSuccess) e = launch_stage(shape, 2, bp->d_grids, bp->d_tiles[shape], 0, 1, bp->stream);
     if (e != cudaSuccess) return e;
+    auto records = [&](int stage, cudaStream_t st) {
+        cudaError_t r = cudaSuccess;
+        for (int c = 0; c < 2 && r == cudaSuccess; ++c)
+            r = launch_records(stage, c, bp->d_grids, bp->d_rchunks[c], bp->nrchunks[c],
+                               record_blocks(bp->nrchunks[c], bp->nsm, c), st);
+        return r;
+    };
     cudaStream_t cap;
     e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) return e;
@@ -412,7 +457,9 @@ static cudaError_t capture_graph(BatchPlan* bp, int shape)
     e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         cudaError_t e1 = launch_begin_step(bp->d_grids, n, cap);
+        if (e1 == cudaSuccess) e1 = records(1, cap);
         if (e1 == cudaSuccess) e1 = launch_stage(shape, 1, bp->d_grids, bp->d_tiles[shape], bp->ntiles[shape], nblocks, cap);
+        if (e1 == cudaSuccess) e1 = records(2, cap);
         if (e1 == cudaSuccess) e1 = launch_stage(shape, 2, bp->d_grids, bp->d_tiles[shape], bp->ntiles[shape], nblocks, cap);
         if (e1 == cudaSuccess) e1 = launch_end_step(bp->d_grids, n, cap);
         e = cudaStreamEndCapture(cap, &graph);
@@ -440,9 +487,26 @@ cudaError_t make_plan(cgks_solver* const* solvers, int n, cudaStream_t stream, i
     long long cells = 0;
     for (int g = 0; g < n; ++g) cells += (long long)solvers[g]->nx * solvers[g]->ny;
     bp->cells = cells;
+    // record-kernel queues of the conservative and the characteristic grids
+    for (int c = 0; c < 2; ++c) {
+        std::vector<TileRef> q;
+        for (int g = 0; g < n; ++g) {
+            const cgks_problem& p = solvers[g]->prob;
+            if (p.recon_vars != c) continue;
+            std::vector<TileRef> r = record_chunks(solvers[g]->nx, solvers[g]->ny, p.dim, p.recon_vars, g);
+            q.insert(q.end(), r.begin(), r.end());
+        }
+        bp->nrchunks[c] = (int)q.size();
+        if (q.empty()) continue;
+        bp->launches_per_step += 2;
+        if (e == cudaSuccess) e = cudaMalloc(&bp->d_rchunks[c], q.size() * sizeof(TileRef));
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(bp->d_rchunks[c], q.data(), q.size() * sizeof(TileRef), cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    }
     if (bp->dim == 1) { bp->candidates = {TILE_64x1}; }
     else if (forced_shape >= 0) { bp->candidates = {forced_shape}; }
-    else { bp->candidates = {TILE_15x15, TILE_16x14, TILE_24x8, TILE_16x7}; }
+    else { bp->candidates = {TILE_15x16, TILE_20x12, TILE_15x15, TILE_16x7}; }
     for (int shape : bp->candidates) {
         std::vector<TileRef> tiles;
         for (int g = 0; g < n; ++g) {
@@ -484,7 +548,7 @@ cudaError_t run_plan(BatchPlan* bp, int nsteps, long* launches)
         cudaEventDestroy(a);
         cudaEventDestroy(b);
         if (e != cudaSuccess) return e;
-        *launches += 4;
+        *launches += bp->launches_per_step;
         ++k;
         if (bp->trial_count[shape] > 0) bp->trial_ms[shape] += ms;   // the first run of a shape is a warm-up
         bp->trial_count[shape] += 1;
@@ -501,7 +565,7 @@ cudaError_t run_plan(BatchPlan* bp, int nsteps, long* launches)
     for (; k < nsteps; ++k) {
         e = cudaGraphLaunch(bp->exec[bp->chosen], bp->stream);
         if (e != cudaSuccess) return e;
-        *launches += 4;
+        *launches += bp->launches_per_step;
     }
     return cudaSuccess;
 }

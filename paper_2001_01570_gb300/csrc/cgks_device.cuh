@@ -18,6 +18,7 @@
 #include <stdint.h>
 
 #include "cgks_erfcx_table.h"
+#include "../../include/cgks.h"
 
 namespace cgks {
 
@@ -48,6 +49,31 @@ __device__ __forceinline__ void half_moments01(double U, double sq, double inv_s
     const bool pos = (side > 0) ? (s >= 0.0) : (s < 0.0);
     m0 = pos ? 1.0 - hE : hE;
     m1 = U * m0 + (double)side * e * inv_sq * 0.28209479177387814;   // 1/(2 sqrt(pi))
+}
+
+// fields of a face-row record
+enum { RV = 0, RN = 1, RNN = 2, RL = 3, RR = 4, RLN = 5, RRN = 6, NREC = 7 };
+
+// boundary mapping of one index along an axis; returns the source index and
+// sets the transform kind: 0 none, 1 reflect, 2 inflow, 3 outflow
+__device__ __forceinline__ int map_axis(int i, int n, int bclo, int bchi, int& kind)
+{
+    kind = 0;
+    if (i < 0) {
+        const int m = -1 - i;
+        if (bclo == CGKS_BC_PERIODIC) { int r = i % n; return r < 0 ? r + n : r; }
+        if (bclo == CGKS_BC_REFLECT) { kind = 1; return min(m, n - 1); }
+        if (bclo == CGKS_BC_INFLOW) { kind = 2; return 0; }
+        kind = 3; return 0;
+    }
+    if (i >= n) {
+        const int m = i - n;
+        if (bchi == CGKS_BC_PERIODIC) return i % n;
+        if (bchi == CGKS_BC_REFLECT) { kind = 1; return max(n - 1 - m, 0); }
+        if (bchi == CGKS_BC_INFLOW) { kind = 2; return n - 1; }
+        kind = 3; return n - 1;
+    }
+    return i;
 }
 
 // ------------------------------------------------------------------------

@@ -23,12 +23,19 @@ namespace {
 
 constexpr size_t kMaxCells = CGKS_NOALLOC_MAX_CELLS;
 constexpr int kMaxTiles = CGKS_NOALLOC_MAX_TILES;
+constexpr int kMaxSide = CGKS_NOALLOC_MAX_SIDE;
+// face-row records of the largest admissible grid: 2 nx ny + 5 (nx + ny) + 8
+// rows is largest for nx ny = kMaxCells with one side at kMaxSide
+constexpr size_t kMaxRecordRows = 2 * kMaxCells + 5 * ((size_t)kMaxSide + kMaxCells / kMaxSide) + 8;
+constexpr int kMaxChunks = (int)((4 * kMaxRecordRows + 255) / 256);
 
 // scratch: buffer for the other state (ping-pong) and for W*, 12 planes each
 static __device__ __align__(256) double g_scratch[2 * 12 * kMaxCells];
 static __device__ __align__(256) cgks::Ctrl g_ctrl;
 static __device__ __align__(256) cgks::GridDev g_desc;
 static __device__ __align__(256) cgks::TileRef g_tiles[kMaxTiles];
+static __device__ __align__(256) double g_records[28 * kMaxRecordRows];
+static __device__ __align__(256) cgks::TileRef g_rchunks[kMaxChunks];
 
 // device addresses of the arrays above, looked up once per device with that
 // device current (host code must not use the symbols' names as addresses)
@@ -38,6 +45,8 @@ struct DeviceSymbols {
     cgks::Ctrl* ctrl = nullptr;
     cgks::GridDev* desc = nullptr;
     cgks::TileRef* tiles = nullptr;
+    double* records = nullptr;
+    cgks::TileRef* rchunks = nullptr;
 };
 constexpr int kMaxDevices = 64;
 DeviceSymbols g_syms[kMaxDevices];
@@ -60,6 +69,8 @@ cgks_status setup_device(int dev, DeviceSymbols** out)
         if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&s.ctrl, g_ctrl);
         if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&s.desc, g_desc);
         if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&s.tiles, g_tiles);
+        if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&s.records, g_records);
+        if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&s.rchunks, g_rchunks);
         if (e != cudaSuccess) return nfail(CGKS_E_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
         s.ready = true;
     }
@@ -67,14 +78,16 @@ cgks_status setup_device(int dev, DeviceSymbols** out)
     return CGKS_OK;
 }
 
-// fills the descriptor and the tile queue of this call (kernel arguments carry
-// the values, so no host buffer has to outlive the call)
-__global__ void noalloc_init_kernel(cgks::GridDev G, int tw, int th)
+// fills the descriptor, the tile queue and the record-kernel queue of this call
+// (kernel arguments carry the values, so no host buffer has to outlive the call)
+__global__ void noalloc_init_kernel(cgks::GridDev G, int tw, int th, int nchunks)
 {
     const int ntx = (G.nx + tw - 1) / tw, nty = (G.ny + th - 1) / th;
     if (blockIdx.x == 0 && threadIdx.x == 0) g_desc = G;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntx * nty; t += gridDim.x * blockDim.x)
         g_tiles[t] = cgks::TileRef{0, (t % ntx) * tw, (t / ntx) * th, 0};
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nchunks; c += gridDim.x * blockDim.x)
+        g_rchunks[c] = cgks::TileRef{0, 256 * c, 0, 0};
 }
 
 #define NCK(call)                                                                                  \
@@ -98,6 +111,7 @@ cgks_status cgks_step_noalloc(const cgks_problem* prob, double* planes, int nste
     if (prob->nx < 1 || prob->ny < 1) return nfail(CGKS_E_INVAL, "nx and ny must be >= 1");
     const size_t cells = (size_t)prob->nx * prob->ny;
     if (cells > kMaxCells) return nfail(CGKS_E_INVAL, "grid exceeds CGKS_NOALLOC_MAX_CELLS");
+    if (prob->nx > kMaxSide || prob->ny > kMaxSide) return nfail(CGKS_E_INVAL, "a side exceeds CGKS_NOALLOC_MAX_SIDE");
     if (!(prob->x1 > prob->x0) || !(prob->y1 > prob->y0) || !(prob->gamma > 1.0) || !(prob->gamma < 3.0) ||
         !(prob->cfl > 0.0) || !(prob->eps_tau >= 0.0) || !(prob->c_tau >= 0.0) || !(prob->weno_eps > 0.0) || !(prob->mu >= 0.0))
         return nfail(CGKS_E_INVAL, "bad problem parameters");
@@ -128,6 +142,8 @@ cgks_status cgks_step_noalloc(const cgks_problem* prob, double* planes, int nste
     G.buf[1] = sym->scratch;
     G.ws = sym->scratch + 12 * cells;
     G.ctrl = sym->ctrl;
+    G.recx = sym->records;
+    G.recy = sym->records + (size_t)28 * (prob->nx + 1) * (prob->ny + 4);
     G.nx = prob->nx;
     G.ny = prob->ny;
     G.dim = 2;
@@ -153,15 +169,22 @@ cgks_status cgks_step_noalloc(const cgks_problem* prob, double* planes, int nste
         G.inflow[side][3] = p / (prob->gamma - 1.0) + 0.5 * r * (u * u + v * v);
     }
     const int nt = (int)ntiles;
-    noalloc_init_kernel<<<(nt + 255) / 256, 256, 0, stream>>>(G, tw, th);
+    const int cv = prob->recon_vars;
+    const long long items = (long long)(cv ? 1 : 4) * record_rows(prob->nx, prob->ny, 2);
+    const int nrc = (int)((items + 255) / 256);
+    const int work = nt > nrc ? nt : nrc;
+    noalloc_init_kernel<<<(work + 255) / 256, 256, 0, stream>>>(G, tw, th, nrc);
     NCK(cudaGetLastError());
     // control block starts from t, step 0, no error, state in the caller's buffer
     NCK(launch_set_ctrl(sym->ctrl, *t_inout, 0.0, -1, 1, stream));
     NCK(launch_cfl(sym->desc, 0, G, stream));
     const int nblocks = nt < nsm ? nt : nsm;
+    const int rblocks = record_blocks(nrc, nsm, cv);
     for (int k = 0; k < nsteps; ++k) {
         NCK(launch_begin_step(sym->desc, 1, stream));
+        NCK(launch_records(1, cv, sym->desc, sym->rchunks, nrc, rblocks, stream));
         NCK(launch_stage(shape, 1, sym->desc, sym->tiles, nt, nblocks, stream));
+        NCK(launch_records(2, cv, sym->desc, sym->rchunks, nrc, rblocks, stream));
         NCK(launch_stage(shape, 2, sym->desc, sym->tiles, nt, nblocks, stream));
         NCK(launch_end_step(sym->desc, 1, stream));
     }

@@ -1,0 +1,197 @@
+// cgks_records.cu -- the face-row records of one stage: the normal
+// reconstruction of every face row of a grid (linear compact reconstruction,
+// Sec. 3.2, Eq. recons-8th-val; nonlinear WENO-Z left and right states with
+// their slopes, Sec. 3.3), computed once per row and written to global memory,
+// where the flux kernels of all tiles that share the row read it.
+//
+// A record holds 7 fields x 4 variables (face frame: density, normal momentum,
+// tangential momentum, energy): RV, RN, RNN (P7, P7_n, P7_nn) and, for the rows
+// the non-equilibrium states are needed on, RL, RR (WENO-Z values) and RLN, RRN
+// (their normal slopes).  x-face rows: faces 0..nx, rows -2..ny+1; y-face rows
+// (2D): faces 0..ny, columns -2..nx+1.  Ghost cells of the stencils are the
+// boundary conditions applied on the fly: x-boundaries first, then y, so the
+// corners match the oracle's ghost layers.
+#include "cgks_device.cuh"
+#include "cgks_internal.h"
+
+namespace cgks {
+
+// plane p of cell (i, j) with the boundary conditions applied outside the grid
+__device__ __forceinline__ double cell_value(const GridDev& G, const double* __restrict__ src, size_t PL, int i, int j,
+                                             int p)
+{
+    int kx, ky;
+    const int si = map_axis(i, G.nx, G.bc[0], G.bc[1], kx);
+    const int sj = map_axis(j, G.ny, G.bc[2], G.bc[3], ky);
+    double v = __ldg(src + (size_t)p * PL + (size_t)sj * G.nx + si);
+    if (kx == 1) { if (p == 1 || p == 4 || p == 6 || p == 7 || p == 9) v = -v; }
+    else if (kx == 2) v = p < 4 ? G.inflow[i < 0 ? 0 : 1][p] : 0.0;
+    else if (kx == 3) { if (p >= 4 && p < 8) v = 0.0; }
+    if (ky == 1) { if (p == 2 || p == 6 || p == 8 || p == 9 || p == 11) v = -v; }
+    else if (ky == 2) v = p < 4 ? G.inflow[j < 0 ? 2 : 3][p] : 0.0;
+    else if (ky == 3) { if (p >= 8) v = 0.0; }
+    return v;
+}
+
+// geometry of record r of a grid: orientation, stencil start cell and step,
+// frame of the variables, global record index
+struct RowRef {
+    bool xo, inner;
+    int i0, j0, di, dj;     // stencil cell c is (i0 + c di, j0 + c dj)
+    int gn;                 // first plane of the normal gradient
+    double h, ih;
+    double* base;           // record array of this orientation
+    size_t stride;          // distance between (field, variable) slices
+    size_t idx;             // index of this record inside a slice
+};
+
+__device__ __forceinline__ RowRef row_ref(const GridDev& G, int r)
+{
+    RowRef q;
+    const int nx = G.nx, ny = G.ny;
+    const int nrx = (nx + 1) * (ny + 4);
+    q.xo = r < nrx;
+    if (q.xo) {
+        const int f = r % (nx + 1), j = r / (nx + 1) - 2;
+        q.inner = (j >= -1) && (j <= ny);
+        q.i0 = f - 2; q.j0 = j; q.di = 1; q.dj = 0;
+        q.gn = 4; q.h = G.dx; q.ih = G.inv_dx;
+        q.base = G.recx; q.stride = (size_t)(ny + 4) * (nx + 1); q.idx = (size_t)r;
+    } else {
+        const int rr = r - nrx;
+        const int g = rr % (ny + 1), i = rr / (ny + 1) - 2;
+        q.inner = (i >= -1) && (i <= nx);
+        q.i0 = i; q.j0 = g - 2; q.di = 0; q.dj = 1;
+        q.gn = 8; q.h = G.dy; q.ih = G.inv_dy;
+        q.base = G.recy; q.stride = (size_t)(nx + 4) * (ny + 1); q.idx = (size_t)rr;
+    }
+    return q;
+}
+
+// CHAR = 0: conservative variables, one (record, variable) per thread;
+// CHAR = 1: characteristic variables, one record (all four variables) per thread
+template <int STAGE, int CHAR>
+__global__ void __launch_bounds__(256, CHAR ? 1 : 2) records_kernel(const GridDev* __restrict__ grids,
+                                                                    const TileRef* __restrict__ chunks, int nchunks)
+{
+    for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        const TileRef tr = chunks[ch];
+        const GridDev& G = grids[tr.grid];
+        if (G.ctrl->done) continue;
+        const double* __restrict__ src = (STAGE == 1) ? G.buf[G.ctrl->par] : G.ws;
+        const size_t PL = (size_t)G.nx * G.ny;
+        const int nrec = record_rows(G.nx, G.ny, G.dim);
+        const int item = tr.x0 + (int)threadIdx.x;
+        const double eps = G.weno_eps;
+        if (!CHAR) {
+            // one (record, variable) per thread
+            if (item >= 4 * nrec) continue;
+            const int k = item / nrec;
+            const RowRef q = row_ref(G, item - k * nrec);
+            const int pv = q.xo ? k : ((k == 1) ? 2 : (k == 2) ? 1 : k);   // face frame: normal momentum first
+            double Q[4], S[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int i = q.i0 + c * q.di, j = q.j0 + c * q.dj;
+                Q[c] = cell_value(G, src, PL, i, j, pv);
+                S[c] = q.h * cell_value(G, src, PL, i, j, q.gn + pv);
+            }
+            double v, hvx, h2vxx;
+            linear_recon(Q[0], Q[1], Q[2], Q[3], S[0], S[1], S[2], S[3], v, hvx, h2vxx);
+            double* o = q.base + q.idx;
+            o[(RV * 4 + k) * q.stride] = v;
+            o[(RN * 4 + k) * q.stride] = hvx * q.ih;
+            o[(RNN * 4 + k) * q.stride] = h2vxx * q.ih * q.ih;
+            if (q.inner) {
+                double vl, sl, vr, sr;
+                weno_pair(Q[0], Q[1], Q[2], Q[3], S[0], S[1], S[2], S[3], eps, vl, sl, vr, sr);
+                o[(RL * 4 + k) * q.stride] = vl;
+                o[(RR * 4 + k) * q.stride] = vr;
+                o[(RLN * 4 + k) * q.stride] = sl * q.ih;
+                o[(RRN * 4 + k) * q.stride] = sr * q.ih;
+            }
+        } else {
+            // characteristic variables: one record (all four variables) per thread
+            if (item >= nrec) continue;
+            const RowRef q = row_ref(G, item);
+            double Qa[4][4], Sa[4][4], Wref[4];
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const int pk = q.xo ? kk : ((kk == 1) ? 2 : (kk == 2) ? 1 : kk);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int i = q.i0 + c * q.di, j = q.j0 + c * q.dj;
+                    Qa[kk][c] = cell_value(G, src, PL, i, j, pk);
+                    Sa[kk][c] = q.h * cell_value(G, src, PL, i, j, q.gn + pk);
+                }
+                Wref[kk] = 0.5 * (Qa[kk][1] + Qa[kk][2]);
+            }
+            double* o = q.base + q.idx;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                double v, hvx, h2vxx;
+                linear_recon(Qa[k][0], Qa[k][1], Qa[k][2], Qa[k][3], Sa[k][0], Sa[k][1], Sa[k][2], Sa[k][3], v, hvx,
+                             h2vxx);
+                o[(RV * 4 + k) * q.stride] = v;
+                o[(RN * 4 + k) * q.stride] = hvx * q.ih;
+                o[(RNN * 4 + k) * q.stride] = h2vxx * q.ih * q.ih;
+            }
+            if (!q.inner) continue;
+            // project on the left eigenvectors of the normal flux Jacobian at the
+            // mean of the two cells sharing the face, WENO-Z per field, map back
+            CharState cs;
+            char_state(Wref, G.gamma, cs);
+            double cvl[4], csl[4], cvr[4], csr[4];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                double l[4], Q[4], S[4];
+                char_left_row(cs, m, l);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    Q[c] = l[0] * Qa[0][c] + l[1] * Qa[1][c] + l[2] * Qa[2][c] + l[3] * Qa[3][c];
+                    S[c] = l[0] * Sa[0][c] + l[1] * Sa[1][c] + l[2] * Sa[2][c] + l[3] * Sa[3][c];
+                }
+                weno_pair(Q[0], Q[1], Q[2], Q[3], S[0], S[1], S[2], S[3], eps, cvl[m], csl[m], cvr[m], csr[m]);
+                csl[m] *= q.ih;
+                csr[m] *= q.ih;
+            }
+            double out[4];
+            char_to_cons(cs, cvl, out);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) o[(RL * 4 + k) * q.stride] = out[k];
+            char_to_cons(cs, cvr, out);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) o[(RR * 4 + k) * q.stride] = out[k];
+            char_to_cons(cs, csl, out);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) o[(RLN * 4 + k) * q.stride] = out[k];
+            char_to_cons(cs, csr, out);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) o[(RRN * 4 + k) * q.stride] = out[k];
+        }
+    }
+}
+
+std::vector<TileRef> record_chunks(int nx, int ny, int dim, int recon_vars, int grid)
+{
+    const long long items = (long long)(recon_vars ? 1 : 4) * record_rows(nx, ny, dim);
+    std::vector<TileRef> c;
+    for (long long s = 0; s < items; s += 256) c.push_back(TileRef{grid, (int)s, 0, 0});
+    return c;
+}
+
+cudaError_t launch_records(int stage, int char_vars, const GridDev* grids, const TileRef* chunks, int nchunks,
+                           int nblocks, cudaStream_t st)
+{
+    if (nchunks <= 0) return cudaSuccess;
+    if (char_vars) {
+        if (stage == 1) records_kernel<1, 1><<<nblocks, 256, 0, st>>>(grids, chunks, nchunks);
+        else records_kernel<2, 1><<<nblocks, 256, 0, st>>>(grids, chunks, nchunks);
+    } else {
+        if (stage == 1) records_kernel<1, 0><<<nblocks, 256, 0, st>>>(grids, chunks, nchunks);
+        else records_kernel<2, 0><<<nblocks, 256, 0, st>>>(grids, chunks, nchunks);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace cgks

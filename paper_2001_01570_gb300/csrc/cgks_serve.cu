@@ -93,8 +93,7 @@ cgks_status sfail(cgks_status st, const std::string& m)
 
 size_t request_bytes(const cgks_problem& p)
 {
-    const size_t cells = (size_t)p.nx * (size_t)(p.dim == 1 ? 1 : p.ny);
-    return 3 * 12 * cells * sizeof(double) + 4096;
+    return (size_t)cgks_problem_device_bytes(&p);
 }
 
 // scheduler thread body

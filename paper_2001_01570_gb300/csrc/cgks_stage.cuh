@@ -1,15 +1,11 @@
-// cgks_stage.cuh -- the fused per-stage kernel of the two-stage fourth-order
-// compact GKS (Sec. 2.2, Eq. step-hyper-1; Sec. 3.1, Eq. compact-deriv-1).
+// cgks_stage.cuh -- the per-stage flux-and-update kernel of the two-stage
+// fourth-order compact GKS (Sec. 2.2, Eq. step-hyper-1; Sec. 3.1, Eq.
+// compact-deriv-1).  It runs after the record kernel (cgks_records.cu), which
+// did the normal reconstruction of every face row of the grid once.
 //
 // One CTA owns a TX x TY tile of cells of one grid and runs, in shared memory:
-//   phase 0  stage the tile plus a two-cell halo of all 12 planes (boundary
-//            conditions applied in the loader: periodic, reflecting, inflow,
-//            outflow; x-boundaries first, then y, corners included)
-//   phase 1  normal reconstruction of every face row the tile needs: linear
-//            8th-order values/derivatives (Sec. 3.2) and, for the rows within
-//            one of a segment, the nonlinear WENO-Z left/right states with
-//            slopes (Sec. 3.3); one record per (face, row), shared by the five
-//            face segments that use it
+//   phase 1  load the face-row records the tile needs (its faces on its rows
+//            and two rows either side)
 //   phase 2  per face segment, at two Gauss points: WENO-Z point values along
 //            the face over rows j-2..j+2 (equilibrium) and j-1..j+1
 //            (non-equilibrium states, with their tangential slopes); tangential
@@ -32,44 +28,17 @@ namespace cgks {
 
 constexpr int kThreads = 256;
 
-// fields of a face-row record
-enum { RV = 0, RN = 1, RNN = 2, RL = 3, RR = 4, RLN = 5, RRN = 6, NREC = 7 };
-
 template <int STAGE> struct FaceQ { static constexpr int n = (STAGE == 1) ? 16 : 8; };
 
 template <int TX, int TY, int STAGE>
 struct StageLayout {
-    static constexpr int BX = TX + 4, BY = TY + 4;
     static constexpr int NF = FaceQ<STAGE>::n;
-    static constexpr int n_cells = 12 * BY * BX;
     static constexpr int n_rx = 4 * NREC * (TY + 4) * (TX + 1);
     static constexpr int n_ry = 4 * NREC * (TX + 4) * (TY + 1);
     static constexpr int n_fx = NF * TY * (TX + 1);
     static constexpr int n_fy = NF * (TY + 1) * TX;
-    static constexpr size_t bytes = sizeof(double) * (size_t)(n_cells + n_rx + n_ry + n_fx + n_fy);
+    static constexpr size_t bytes = sizeof(double) * (size_t)(n_rx + n_ry + n_fx + n_fy);
 };
-
-// boundary mapping of one index along an axis; returns the source index and
-// sets the transform kind: 0 none, 1 reflect, 2 inflow, 3 outflow
-__device__ __forceinline__ int map_axis(int i, int n, int bclo, int bchi, int& kind)
-{
-    kind = 0;
-    if (i < 0) {
-        const int m = -1 - i;
-        if (bclo == CGKS_BC_PERIODIC) { int r = i % n; return r < 0 ? r + n : r; }
-        if (bclo == CGKS_BC_REFLECT) { kind = 1; return min(m, n - 1); }
-        if (bclo == CGKS_BC_INFLOW) { kind = 2; return 0; }
-        kind = 3; return 0;
-    }
-    if (i >= n) {
-        const int m = i - n;
-        if (bchi == CGKS_BC_PERIODIC) return i % n;
-        if (bchi == CGKS_BC_REFLECT) { kind = 1; return max(n - 1 - m, 0); }
-        if (bchi == CGKS_BC_INFLOW) { kind = 2; return n - 1; }
-        kind = 3; return n - 1;
-    }
-    return i;
-}
 
 // The face rows around one face segment (records of rows j-2..j+2 of one
 // face) and the reconstruction along the face at one Gauss point eta: the
@@ -143,10 +112,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tiles, int ntiles)
 {
     using L = StageLayout<TX, TY, STAGE>;
-    constexpr int BX = L::BX, BY = L::BY, NF = L::NF;
+    constexpr int NF = L::NF;
     extern __shared__ double smem[];
-    double* sc = smem;                  // [12][BY][BX]
-    double* rx = sc + L::n_cells;       // [28][TY+4][TX+1]
+    double* rx = smem;                  // [28][TY+4][TX+1]
     double* ry = rx + L::n_rx;          // [28][TX+4][TY+1]
     double* fx = ry + L::n_ry;          // [NF][TY][TX+1]
     double* fy = fx + L::n_fx;          // [NF][TY+1][TX]
@@ -174,180 +142,27 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
         const double* __restrict__ src = (STAGE == 1) ? G.buf[par] : G.ws;
         const size_t PL = (size_t)nx * ny;
 
-        // ---------------- phase 0: halo tile with boundary conditions
-        for (int idx = tid; idx < BX * BY; idx += kThreads) {
-            const int ii = idx % BX, jj = idx / BX;
-            int kx, ky;
-            const int sj = map_axis(y0 - 2 + jj, ny, G.bc[2], G.bc[3], ky);
-            const int si = map_axis(x0 - 2 + ii, nx, G.bc[0], G.bc[1], kx);
-            const size_t off = (size_t)sj * nx + si;
-            double v[12];
-#pragma unroll
-            for (int p = 0; p < 12; ++p) v[p] = __ldg(src + p * PL + off);
-            // x-boundary transform
-            if (kx == 1) { v[1] = -v[1]; v[4] = -v[4]; v[6] = -v[6]; v[7] = -v[7]; v[9] = -v[9]; }
-            else if (kx == 2) {
-                const double* q = G.inflow[(x0 - 2 + ii < 0) ? 0 : 1];
-#pragma unroll
-                for (int p = 0; p < 4; ++p) { v[p] = q[p]; v[4 + p] = 0.0; v[8 + p] = 0.0; }
-            } else if (kx == 3) { v[4] = v[5] = v[6] = v[7] = 0.0; }
-            // y-boundary transform
-            if (ky == 1) { v[2] = -v[2]; v[6] = -v[6]; v[8] = -v[8]; v[9] = -v[9]; v[11] = -v[11]; }
-            else if (ky == 2) {
-                const double* q = G.inflow[(y0 - 2 + jj < 0) ? 2 : 3];
-#pragma unroll
-                for (int p = 0; p < 4; ++p) { v[p] = q[p]; v[4 + p] = 0.0; v[8 + p] = 0.0; }
-            } else if (ky == 3) { v[8] = v[9] = v[10] = v[11] = 0.0; }
-#pragma unroll
-            for (int p = 0; p < 12; ++p) sc[(p * BY + jj) * BX + ii] = v[p];
-        }
-        __syncthreads();
-
-        // ---------------- phase 1: normal reconstruction per (face, row, variable)
-        // items are (variable, record) pairs so the 256 threads finish together
-        const double eps = G.weno_eps;
-        constexpr int NRX = (TX + 1) * (TY + 4), NRY = (TX + 4) * (TY + 1), NR = NRX + NRY;
-        // the heavy items (inner rows: linear + WENO-Z) are dealt out first, then the
-        // light ones (the outer row on each side: linear only), so that no thread gets
-        // more than its share of heavy items
-        constexpr int NIX = (TX + 1) * (TY + 2), NIY = (TY + 1) * (TX + 2), NI = NIX + NIY;
-        constexpr int NOX = (TX + 1) * 2, NOY = (TY + 1) * 2, NO = NOX + NOY;
-        static_assert(NI + NO == NR, "record count");
-        for (int it = tid; it < 4 * NR; it += kThreads) {
-            int k, a, rl;          // variable, face index along the tile, row index of the record
-            bool xo;
-            if (it < 4 * NI) {
-                k = it / NI;
-                int r = it - k * NI;
-                xo = r < NIX;
-                if (!xo) r -= NIX;
-                const int nf = xo ? TX + 1 : TY + 1;
-                a = r % nf; rl = 1 + r / nf;
-            } else {
-                const int r2 = it - 4 * NI;
-                k = r2 / NO;
-                int r = r2 - k * NO;
-                xo = r < NOX;
-                if (!xo) r -= NOX;
-                const int nf = xo ? TX + 1 : TY + 1;
-                a = r % nf; rl = (r / nf) ? (xo ? TY + 3 : TX + 3) : 0;
+        // ---------------- phase 1: the tile's face-row records (the record kernel
+        // wrote them for every face row of the grid): x-faces x0..x0+TX on rows
+        // y0-2..y0+TY+1, y-faces y0..y0+TY on columns x0-2..x0+TX+1; rows beyond
+        // the grid's last ghost row are zero and unused
+        {
+            constexpr int NRX = (TX + 1) * (TY + 4), NRY = (TY + 1) * (TX + 4);
+            const size_t sx = (size_t)(ny + 4) * (nx + 1), sy = (size_t)(nx + 4) * (ny + 1);
+            for (int idx = tid; idx < 4 * NREC * NRX; idx += kThreads) {
+                const int fk = idx / NRX, r = idx - fk * NRX;
+                const int fl = r % (TX + 1), rl = r / (TX + 1);
+                const bool valid = (x0 + fl <= nx) && (y0 - 2 + rl <= ny + 1);
+                rx[idx] = valid ? __ldg(G.recx + fk * sx + (size_t)(y0 + rl) * (nx + 1) + x0 + fl) : 0.0;
             }
-            int box_i, box_j, step_i, step_j, ridx, nrec, pv, gn;
-            double h, ih;
-            double* rec;
-            bool valid, inner;
-            if (xo) {
-                const int fl = a;                                       // row y0-2+rl
-                valid = (x0 + fl <= nx) && (y0 - 2 + rl <= ny + 1);
-                inner = (rl >= 1) && (rl <= TY + 2);
-                box_i = fl; box_j = rl; step_i = 1; step_j = 0;
-                h = G.dx; ih = G.inv_dx; gn = 4;
-                pv = k;
-                rec = rx; nrec = (TY + 4) * (TX + 1); ridx = rl * (TX + 1) + fl;
-            } else {
-                const int gl = a;                                       // column x0-2+rl
-                valid = !dim1 && (y0 + gl <= ny) && (x0 - 2 + rl <= nx + 1);
-                inner = (rl >= 1) && (rl <= TX + 2);
-                box_i = rl; box_j = gl; step_i = 0; step_j = 1;
-                h = G.dy; ih = G.inv_dy; gn = 8;
-                pv = (k == 1) ? 2 : (k == 2) ? 1 : k;                  // face frame: normal momentum first
-                rec = ry; nrec = (TX + 4) * (TY + 1); ridx = rl * (TY + 1) + gl;
-            }
-            if (!valid) {
-#pragma unroll
-                for (int f = 0; f < NREC; ++f) rec[(f * 4 + k) * nrec + ridx] = 0.0;
-                continue;
-            }
-            double Q[4], S[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int bi = box_i + c * step_i, bj = box_j + c * step_j;
-                Q[c] = sc[(pv * BY + bj) * BX + bi];
-                S[c] = h * sc[((gn + pv) * BY + bj) * BX + bi];
-            }
-            double v, hvx, h2vxx;
-            linear_recon(Q[0], Q[1], Q[2], Q[3], S[0], S[1], S[2], S[3], v, hvx, h2vxx);
-            rec[(RV * 4 + k) * nrec + ridx] = v;
-            rec[(RN * 4 + k) * nrec + ridx] = hvx * ih;
-            rec[(RNN * 4 + k) * nrec + ridx] = h2vxx * ih * ih;
-            if (inner) {
-                if (G.recon_vars) {
-                    // characteristic field k: project the stencil on the k-th left eigenvector
-                    // at the mean of the two cells sharing the face
-                    double Wref[4], Qa[4][4], Sa[4][4], l[4];
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        const int pk = xo ? kk : ((kk == 1) ? 2 : (kk == 2) ? 1 : kk);
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            const int bi = box_i + c * step_i, bj = box_j + c * step_j;
-                            Qa[kk][c] = sc[(pk * BY + bj) * BX + bi];
-                            Sa[kk][c] = h * sc[((gn + pk) * BY + bj) * BX + bi];
-                        }
-                        Wref[kk] = 0.5 * (Qa[kk][1] + Qa[kk][2]);
-                    }
-                    CharState cs;
-                    char_state(Wref, G.gamma, cs);
-                    char_left_row(cs, k, l);
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        Q[c] = l[0] * Qa[0][c] + l[1] * Qa[1][c] + l[2] * Qa[2][c] + l[3] * Qa[3][c];
-                        S[c] = l[0] * Sa[0][c] + l[1] * Sa[1][c] + l[2] * Sa[2][c] + l[3] * Sa[3][c];
-                    }
-                }
-                double vl, sl, vr, sr;
-                weno_pair(Q[0], Q[1], Q[2], Q[3], S[0], S[1], S[2], S[3], eps, vl, sl, vr, sr);
-                rec[(RL * 4 + k) * nrec + ridx] = vl;
-                rec[(RR * 4 + k) * nrec + ridx] = vr;
-                rec[(RLN * 4 + k) * nrec + ridx] = sl * ih;
-                rec[(RRN * 4 + k) * nrec + ridx] = sr * ih;
+            for (int idx = tid; idx < 4 * NREC * NRY; idx += kThreads) {
+                const int fk = idx / NRY, r = idx - fk * NRY;
+                const int gl = r % (TY + 1), rl = r / (TY + 1);
+                const bool valid = !dim1 && (y0 + gl <= ny) && (x0 - 2 + rl <= nx + 1);
+                ry[idx] = valid ? __ldg(G.recy + fk * sy + (size_t)(x0 + rl) * (ny + 1) + y0 + gl) : 0.0;
             }
         }
         __syncthreads();
-        if (G.recon_vars) {
-            // back to conservative variables, one record per thread
-            for (int item = tid; item < NR; item += kThreads) {
-                const bool xo = item < NR - NRY;
-                int box_i, box_j, step_i, step_j, ridx, nrec;
-                double* rec;
-                bool valid, inner;
-                if (xo) {
-                    const int fl = item % (TX + 1), rl = item / (TX + 1);
-                    valid = (x0 + fl <= nx) && (y0 - 2 + rl <= ny + 1);
-                    inner = (rl >= 1) && (rl <= TY + 2);
-                    box_i = fl; box_j = rl; step_i = 1; step_j = 0;
-                    rec = rx; nrec = (TY + 4) * (TX + 1); ridx = rl * (TX + 1) + fl;
-                } else {
-                    const int itm = item - NRX;
-                    const int gl = itm % (TY + 1), rl = itm / (TY + 1);
-                    valid = !dim1 && (y0 + gl <= ny) && (x0 - 2 + rl <= nx + 1);
-                    inner = (rl >= 1) && (rl <= TX + 2);
-                    box_i = rl; box_j = gl; step_i = 0; step_j = 1;
-                    rec = ry; nrec = (TX + 4) * (TY + 1); ridx = rl * (TY + 1) + gl;
-                }
-                if (!valid || !inner) continue;
-                double Wref[4];
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    const int pk = xo ? kk : ((kk == 1) ? 2 : (kk == 2) ? 1 : kk);
-                    const double a = sc[(pk * BY + box_j + step_j) * BX + box_i + step_i];
-                    const double b = sc[(pk * BY + box_j + 2 * step_j) * BX + box_i + 2 * step_i];
-                    Wref[kk] = 0.5 * (a + b);
-                }
-                CharState cs;
-                char_state(Wref, G.gamma, cs);
-#pragma unroll
-                for (int f = RL; f <= RRN; ++f) {
-                    double w[4], o[4];
-#pragma unroll
-                    for (int m = 0; m < 4; ++m) w[m] = rec[(f * 4 + m) * nrec + ridx];
-                    char_to_cons(cs, w, o);
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) rec[(f * 4 + kk) * nrec + ridx] = o[kk];
-                }
-            }
-            __syncthreads();
-        }
 
         // ---------------- phase 2: face segments, two Gauss points each
         Params P;
@@ -454,7 +269,7 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
             if (STAGE == 1) {
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const double W = sc[(k * BY + jl + 2) * BX + il + 2];
+                    const double W = __ldg(src + k * PL + off);
                     G.ws[k * PL + off] = W - (FX(k, xr) - FX(k, xl)) * idx_ - (FY(k, yt) - FY(k, yb)) * idy_;
                     G.ws[(4 + k) * PL + off] = (FX(8 + k, xr) - FX(8 + k, xl)) * idx_;
                     G.ws[(8 + k) * PL + off] = (FY(8 + k, yt) - FY(8 + k, yb)) * idy_;

@@ -1,0 +1,6 @@
+// Instantiation of the fused stage kernel for 15x16 cell tiles.
+#include "cgks_stage.cuh"
+
+namespace cgks {
+CGKS_STAGE_INSTANCE(15, 16)
+}  // namespace cgks
