@@ -90,11 +90,21 @@ __global__ void __launch_bounds__(256, CHAR ? 1 : 2) records_kernel(const GridDe
             const RowRef q = row_ref(G, item - k * nrec);
             const int pv = q.xo ? k : ((k == 1) ? 2 : (k == 2) ? 1 : k);   // face frame: normal momentum first
             double Q[4], S[4];
+            const int i3 = q.i0 + 3 * q.di, j3 = q.j0 + 3 * q.dj;
+            if (q.i0 >= 0 && q.j0 >= 0 && i3 < G.nx && j3 < G.ny) {
+                // stencil inside the grid: no boundary mapping
+                const double* v = src + (size_t)pv * PL + (size_t)q.j0 * G.nx + q.i0;
+                const double* d = src + (size_t)(q.gn + pv) * PL + (size_t)q.j0 * G.nx + q.i0;
+                const size_t step = q.di ? 1 : (size_t)G.nx;
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int i = q.i0 + c * q.di, j = q.j0 + c * q.dj;
-                Q[c] = cell_value(G, src, PL, i, j, pv);
-                S[c] = q.h * cell_value(G, src, PL, i, j, q.gn + pv);
+                for (int c = 0; c < 4; ++c) { Q[c] = __ldg(v + c * step); S[c] = q.h * __ldg(d + c * step); }
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int i = q.i0 + c * q.di, j = q.j0 + c * q.dj;
+                    Q[c] = cell_value(G, src, PL, i, j, pv);
+                    S[c] = q.h * cell_value(G, src, PL, i, j, q.gn + pv);
+                }
             }
             double v, hvx, h2vxx;
             linear_recon(Q[0], Q[1], Q[2], Q[3], S[0], S[1], S[2], S[3], v, hvx, h2vxx);
