@@ -46,12 +46,13 @@ FLOP_PER_CELL = {1: 11090.0, 2: 10725.0}
 RECORD_FLOP_PER_CELL = 2 * 148.0 + 2 * 1800.0
 FLUX_FLOP_PER_CELL = {1: FLOP_PER_CELL[1] - RECORD_FLOP_PER_CELL, 2: FLOP_PER_CELL[2] - RECORD_FLOP_PER_CELL}
 DEFAULT_TILE = "15x16"    # the library's 2D default
-# FP64 operations per cell and stage the default 15x15 tiles execute (halo rows recomputed):
-EXEC_FLOP_PER_CELL_15x15 = {1: 12543.0, 2: 12136.0}
-# DRAM bytes (read + write) per cell of one stage-1 launch with 15x15 tiles, ncu
-# dram__bytes_{read,write}.sum on the 1024^2 vortex (state larger than L2) divided by the cells; the
-# 2048^2 bench grid moves the same bytes per cell: profiles/stage_kernels_ncu_vortex1024.md.
-DRAM_BYTES_PER_CELL = {1: 292.69e6 / 1048576, 2: 274.32e6 / 1048576}
+# DRAM bytes (read + write) per cell of one stage-1 flux-kernel launch with 15x16 tiles, ncu
+# dram__bytes_{read,write}.sum on the 1024^2 vortex (records and state larger than L2) divided by the
+# cells; the 2048^2 bench grid moves the same bytes per cell: profiles/split_kernels_ncu_vortex1024.md.
+FLUX_DRAM_BYTES_PER_CELL = {1: 711.93e6 / 1048576, 2: 671.09e6 / 1048576}
+# algorithmic bytes per cell of the flux kernel: the two face rows' records (2 x 28 doubles) plus
+# the state it reads and writes (stage 1: W in, W* and R out)
+FLUX_ALGO_BYTES_PER_CELL = {1: 448 + 32 + 192, 2: 448 + 96 + 96}
 # measured FP64 peak of this GB300 (DFMA throughput loop, FMA = 2): profiles/fp64_peak_gb300.md
 FP64_PEAK_TFLOPS = 1.010
 
@@ -227,7 +228,8 @@ def run_cgks(args, world, rank, local):
     stage1 = FLOP_PER_CELL[1] * cells / ((flux_ms + rec_ms) * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": None,
+                "traffic": FLUX_DRAM_BYTES_PER_CELL[1] * cells if tile == DEFAULT_TILE else None,
+                "algorithmic_bytes": FLUX_ALGO_BYTES_PER_CELL[1] * cells,
                 "algorithmic_flop_per_cell": FLUX_FLOP_PER_CELL[1],
                 "kernel": f"stage_kernel<{tile},1>", "kernel_ms": flux_ms,
                 "stage1_records_plus_flux": {"kernels": "records_kernel<1,0> + stage_kernel<%s,1>" % tile,
