@@ -345,8 +345,8 @@ def run_batched(args, world, rank, local):
         stop.record(stream)
         torch.cuda.synchronize()
     ms_plain = start.elapsed_time(stop)
-    # batched: warm-up covers the tile-shape autotuning (3 shapes x 2 steps)
-    cgks.cgks_batch_step(handles, max(args.warmup, 6))
+    # batched: warm-up covers the tile-shape autotuning (4 candidate shapes x 2 steps)
+    cgks.cgks_batch_step(handles, max(args.warmup, 8))
     torch.cuda.synchronize()
     shape = cgks.cgks_batch_tile_shape(handles)
     with ClockSampler(local) as clk:

@@ -26,7 +26,7 @@
  *             gradients (divergence theorem in 2D)
  *   Sec. 4                          collision time tau, CFL time step
  *
- * Readings where the paper is silent (each listed in the design doc):
+ * Readings where the paper is silent:
  *   - polynomials of the sub-stencils are built from their definition (cell
  *     averages and cell-averaged slopes) by solving the small linear system;
  *     the slope of the non-equilibrium states is sum_k delta_k q_k'(x_i+1/2)
