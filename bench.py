@@ -45,7 +45,7 @@ FLOP_PER_CELL = {1: 11090.0, 2: 10725.0}
 # flux-and-update kernel (two face segments and the update)
 RECORD_FLOP_PER_CELL = 2 * 148.0 + 2 * 1800.0
 FLUX_FLOP_PER_CELL = {1: FLOP_PER_CELL[1] - RECORD_FLOP_PER_CELL, 2: FLOP_PER_CELL[2] - RECORD_FLOP_PER_CELL}
-DEFAULT_TILE = "15x16"    # the library's 2D default
+DEFAULT_TILE = "16x16"    # the library's 2D default
 # DRAM bytes (read + write) per cell of one stage-1 flux-kernel launch with 15x16 tiles, ncu
 # dram__bytes_{read,write}.sum on the 1024^2 vortex (records and state larger than L2) divided by the
 # cells; the 2048^2 bench grid moves the same bytes per cell: profiles/split_kernels_ncu_vortex1024.md.
@@ -222,18 +222,18 @@ def run_cgks(args, world, rank, local):
     prof_steps = max(2, min(args.steps, 5))
     stage_ms = cgks.cgks_step_profiled(solver.handle, prof_steps)
     tile = args.tile or DEFAULT_TILE
-    # stage_ms: begin, stage-1 records, stage-1 flux, stage-2 records, stage-2 flux, end
-    flux_ms, rec_ms = stage_ms[2], stage_ms[1]
+    # stage_ms: begin, stage-1 records, flux, update, stage-2 records, flux, update, end
+    flux_ms, rec_ms, upd_ms = stage_ms[2], stage_ms[1], stage_ms[3]
     achieved = FLUX_FLOP_PER_CELL[1] * cells / (flux_ms * 1e-3) / 1e12
-    stage1 = FLOP_PER_CELL[1] * cells / ((flux_ms + rec_ms) * 1e-3) / 1e12
+    stage1 = FLOP_PER_CELL[1] * cells / ((flux_ms + rec_ms + upd_ms) * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS,
                 "traffic": FLUX_DRAM_BYTES_PER_CELL[1] * cells if tile == DEFAULT_TILE else None,
                 "algorithmic_bytes": FLUX_ALGO_BYTES_PER_CELL[1] * cells,
                 "algorithmic_flop_per_cell": FLUX_FLOP_PER_CELL[1],
                 "kernel": f"stage_kernel<{tile},1>", "kernel_ms": flux_ms,
-                "stage1_records_plus_flux": {"kernels": "records_kernel<1,0> + stage_kernel<%s,1>" % tile,
-                                             "ms": flux_ms + rec_ms, "achieved": stage1,
+                "stage1_records_plus_flux": {"kernels": "records_kernel<1,0> + stage_kernel<%s,1> + update_kernel<1>" % tile,
+                                             "ms": flux_ms + rec_ms + upd_ms, "achieved": stage1,
                                              "frac": stage1 / FP64_PEAK_TFLOPS,
                                              "algorithmic_flop_per_cell": FLOP_PER_CELL[1],
                                              "algorithmic_bytes": 288 * cells},
@@ -266,8 +266,8 @@ def run_cgks(args, world, rank, local):
                    "cfl": spec.cfl, "l2": "inputs larger than L2 (3 x 12 planes resident, %.2f GB)" % (36 * cells * 8 / 1e9),
                    "parallelism": "one grid per GPU (independent replicas)" if world > 1 else "single GPU"},
         "roofline": roofline,
-        "stage_ms": {"begin": stage_ms[0], "records1": stage_ms[1], "flux1": stage_ms[2], "records2": stage_ms[3],
-                     "flux2": stage_ms[4], "end": stage_ms[5]},
+        "stage_ms": {"begin": stage_ms[0], "records1": stage_ms[1], "flux1": stage_ms[2], "update1": stage_ms[3],
+                     "records2": stage_ms[4], "flux2": stage_ms[5], "update2": stage_ms[6], "end": stage_ms[7]},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes / args.steps,
                 "d2h_bytes_per_step": nbytes / args.steps,
                 "note": "per repetition: H2D of the 12 state planes from pinned host memory, K steps, D2H of the state"},

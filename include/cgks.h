@@ -130,8 +130,8 @@ cgks_status cgks_batch_step(cgks_solver* const* solvers, int n, int nsteps);
 /* Cells per CTA tile of the stage kernels for this solver's plain steps:
  * 0: 16x8, 1: 8x16, 2: 32x4, 3: 64x1, 4: 16x7, 5: 7x16, 6: 14x8, 7: 24x8,
  * 8: 16x14, 9: 20x11, 10: 15x15, 11: 22x10, 12: 18x12, 13: 20x12, 14: 15x16,
- * 15: 17x14; -1
- * restores the default (15x16 in 2D, 64x1 in 1D).  The shape changes only the
+ * 15: 17x14, 16: 16x16, 17: 24x16, 18: 32x12; -1
+ * restores the default (16x16 in 2D, 64x1 in 1D).  The shape changes only the
  * decomposition of the work, never the results.  Errors: CGKS_E_INVAL (1D
  * solvers take only 64x1; 2D solvers any other shape). */
 cgks_status cgks_set_tile_shape(cgks_solver* s, int shape);
@@ -143,17 +143,18 @@ cgks_status cgks_set_tile_shape(cgks_solver* s, int shape);
 int cgks_batch_tile_shape(cgks_solver* const* solvers, int n);
 
 /* Same as cgks_step(s, nsteps, 0, NULL), but with CUDA events recorded on the
- * solver's stream around every kernel of every step; stage_ms[0..5] receive
+ * solver's stream around every kernel of every step; stage_ms[0..7] receive
  * the average duration in milliseconds of the step-begin, stage-1 record,
- * stage-1 flux, stage-2 record, stage-2 flux and step-end kernels.  For
- * measurement only (the events serialise nothing but add host work per
- * launch). */
-cgks_status cgks_step_profiled(cgks_solver* s, int nsteps, double stage_ms[6]);
+ * stage-1 flux, stage-1 update, stage-2 record, stage-2 flux, stage-2 update
+ * and step-end kernels.  For measurement only (the events serialise nothing
+ * but add host work per launch). */
+cgks_status cgks_step_profiled(cgks_solver* s, int nsteps, double stage_ms[8]);
 
 /* Device bytes a solver of this problem holds: three sets of 12 state planes
  * (current, next, intermediate), the face-row records of the stage in flight
  * (28 doubles per face row: x-faces 0..nx on rows -2..ny+1 and, in 2D, y-faces
- * 0..ny on columns -2..nx+1) and 4 KB of descriptors.  The server admits a
+ * 0..ny on columns -2..nx+1), the face results of the stage in flight (16
+ * doubles per face) and 4 KB of descriptors.  The server admits a
  * request while these bytes fit its budget.  Returns 0 for a NULL or empty
  * problem. */
 double cgks_problem_device_bytes(const cgks_problem* prob);
@@ -176,9 +177,9 @@ const char* cgks_last_error(void);
  * the caller already holds in device memory and allocates nothing: the second
  * state buffer, the intermediate state, the face-row records, the control
  * block and the work queues live in fixed-size device arrays of the library
- * (file-scope __device__ storage, about 12.6 MB of state, 34 MB of records and
- * 300 KB of queues), which every GPU that loads the library holds until the
- * process exits.
+ * (file-scope __device__ storage, about 12.6 MB of state, 34 MB of face-row
+ * records, 17 MB of face results and 300 KB of queues), which every GPU that
+ * loads the library holds until the process exits.
  *
  * prob:        2D problem, nx*ny <= CGKS_NOALLOC_MAX_CELLS, nx and ny <=
  *              CGKS_NOALLOC_MAX_SIDE, at most CGKS_NOALLOC_MAX_TILES tiles of

@@ -199,9 +199,9 @@ def cgks_batch_step(solvers, nsteps):
 
 
 def cgks_step_profiled(solver, nsteps):
-    """Average per-launch milliseconds of (step-begin, stage-1 records, stage-1 flux, stage-2 records,
-    stage-2 flux, step-end)."""
-    ms = (ctypes.c_double * 6)()
+    """Average per-launch milliseconds of (step-begin, stage-1 records, stage-1 flux, stage-1 update,
+    stage-2 records, stage-2 flux, stage-2 update, step-end)."""
+    ms = (ctypes.c_double * 8)()
     _check(load().cgks_step_profiled(solver, int(nsteps), ms))
     return list(ms)
 
@@ -212,7 +212,7 @@ def cgks_problem_device_bytes(prob) -> float:
 
 
 TILE_SHAPES = ("16x8", "8x16", "32x4", "64x1", "16x7", "7x16", "14x8", "24x8", "16x14", "20x11", "15x15",
-               "22x10", "18x12", "20x12", "15x16", "17x14")
+               "22x10", "18x12", "20x12", "15x16", "17x14", "16x16", "24x16", "32x12")
 
 
 def cgks_set_tile_shape(solver, shape):

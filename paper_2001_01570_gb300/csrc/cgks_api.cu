@@ -27,6 +27,9 @@ struct cgks_solver {
     double* d_records = nullptr;  // face-row records of the stage in flight
     TileRef* d_rchunks = nullptr; // record-kernel work queue
     int nrchunks = 0;
+    double* d_faces = nullptr;    // face results of the stage in flight
+    TileRef* d_cchunks = nullptr; // update-kernel work queue
+    int ncchunks = 0;
     double* d_stage1d = nullptr;  // 6-plane staging for dim 1
     Ctrl* d_ctrl = nullptr;
     GridDev host_desc;
@@ -107,7 +110,7 @@ cgks_status read_ctrl(cgks_solver* s, Ctrl* c)
 
 int pick_shape(const cgks_problem& p)
 {
-    return p.dim == 1 ? TILE_64x1 : TILE_15x16;
+    return p.dim == 1 ? TILE_64x1 : TILE_16x16;
 }
 
 }  // namespace
@@ -139,7 +142,8 @@ double cgks_problem_device_bytes(const cgks_problem* prob)
     if (!prob || prob->nx < 1 || (prob->dim == 2 && prob->ny < 1)) return 0.0;
     const int ny = prob->dim == 1 ? 1 : prob->ny;
     const double cells = (double)prob->nx * ny;
-    return 3.0 * 12.0 * cells * sizeof(double) + (double)record_doubles(prob->nx, ny, prob->dim) * sizeof(double)
+    return 3.0 * 12.0 * cells * sizeof(double)
+           + (double)(record_doubles(prob->nx, ny, prob->dim) + face_doubles(prob->nx, ny, prob->dim)) * sizeof(double)
            + 4096.0;
 }
 
@@ -159,10 +163,11 @@ cgks_status cgks_create(const cgks_problem* prob, void* cuda_stream, cgks_solver
     cudaError_t e = cudaGetDevice(&s->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, s->device);
     const size_t PL = (size_t)s->nx * s->ny;
-    const size_t rec = record_doubles(s->nx, s->ny, prob->dim);
-    s->device_bytes = 3 * 12 * PL * sizeof(double) + rec * sizeof(double);
+    const size_t rec = record_doubles(s->nx, s->ny, prob->dim), fac = face_doubles(s->nx, s->ny, prob->dim);
+    s->device_bytes = 3 * 12 * PL * sizeof(double) + (rec + fac) * sizeof(double);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_planes, 3 * 12 * PL * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&s->d_records, rec * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_faces, fac * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&s->d_ctrl, sizeof(Ctrl));
     if (e == cudaSuccess) e = cudaMalloc(&s->d_desc, sizeof(GridDev));
     if (e == cudaSuccess && prob->dim == 1) e = cudaMalloc(&s->d_stage1d, 6 * PL * sizeof(double));
@@ -172,6 +177,9 @@ cgks_status cgks_create(const cgks_problem* prob, void* cuda_stream, cgks_solver
     std::vector<TileRef> rchunks = record_chunks(s->nx, s->ny, prob->dim, prob->recon_vars, 0);
     s->nrchunks = (int)rchunks.size();
     if (e == cudaSuccess) e = cudaMalloc(&s->d_rchunks, rchunks.size() * sizeof(TileRef));
+    std::vector<TileRef> cchunks = cell_chunks(s->nx, s->ny, 0);
+    s->ncchunks = (int)cchunks.size();
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_cchunks, cchunks.size() * sizeof(TileRef));
     if (e != cudaSuccess) {
         cgks_destroy(s);
         return e == cudaErrorMemoryAllocation ? fail(CGKS_E_NOMEM, "device allocation failed")
@@ -185,6 +193,8 @@ cgks_status cgks_create(const cgks_problem* prob, void* cuda_stream, cgks_solver
     G.ctrl = s->d_ctrl;
     G.recx = s->d_records;
     G.recy = prob->dim == 2 ? s->d_records + (size_t)28 * (s->nx + 1) * (s->ny + 4) : nullptr;
+    G.facex = s->d_faces;
+    G.facey = prob->dim == 2 ? s->d_faces + (size_t)16 * (s->nx + 1) * s->ny : nullptr;
     G.nx = s->nx;
     G.ny = s->ny;
     G.dim = prob->dim;
@@ -217,6 +227,9 @@ cgks_status cgks_create(const cgks_problem* prob, void* cuda_stream, cgks_solver
         e = cudaMemcpyAsync(s->d_tiles, tiles.data(), tiles.size() * sizeof(TileRef), cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(s->d_rchunks, rchunks.data(), rchunks.size() * sizeof(TileRef), cudaMemcpyHostToDevice,
+                            s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->d_cchunks, cchunks.data(), cchunks.size() * sizeof(TileRef), cudaMemcpyHostToDevice,
                             s->stream);
     if (e == cudaSuccess) e = launch_set_ctrl(s->d_ctrl, 0.0, 0.0, -1, 1, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
@@ -257,6 +270,8 @@ cgks_status cgks_destroy(cgks_solver* s)
     cudaFree(s->d_planes);
     cudaFree(s->d_records);
     cudaFree(s->d_rchunks);
+    cudaFree(s->d_faces);
+    cudaFree(s->d_cchunks);
     cudaFree(s->d_stage1d);
     cudaFree(s->d_ctrl);
     cudaFree(s->d_desc);
@@ -311,14 +326,16 @@ static cgks_status enqueue_steps(cgks_solver* s, int nsteps, long* launches)
     const int nblocks = s->ntiles < s->nsm ? s->ntiles : s->nsm;
     const int cv = s->prob.recon_vars;
     const int rblocks = record_blocks(s->nrchunks, s->nsm, cv);
+    const int ublocks = update_blocks(s->ncchunks, s->nsm);
     for (int k = 0; k < nsteps; ++k) {
         CK(launch_begin_step(s->d_desc, 1, s->stream));
-        CK(launch_records(1, cv, s->d_desc, s->d_rchunks, s->nrchunks, rblocks, s->stream));
-        CK(launch_stage(s->shape, 1, s->d_desc, s->d_tiles, s->ntiles, nblocks, s->stream));
-        CK(launch_records(2, cv, s->d_desc, s->d_rchunks, s->nrchunks, rblocks, s->stream));
-        CK(launch_stage(s->shape, 2, s->d_desc, s->d_tiles, s->ntiles, nblocks, s->stream));
+        for (int stage = 1; stage <= 2; ++stage) {
+            CK(launch_records(stage, cv, s->d_desc, s->d_rchunks, s->nrchunks, rblocks, s->stream));
+            CK(launch_stage(s->shape, stage, s->d_desc, s->d_tiles, s->ntiles, nblocks, s->stream));
+            CK(launch_update(stage, s->d_desc, s->d_cchunks, s->ncchunks, ublocks, s->stream));
+        }
         CK(launch_end_step(s->d_desc, 1, s->stream));
-        *launches += 6;
+        *launches += 8;
     }
     return CGKS_OK;
 }
@@ -363,35 +380,37 @@ cgks_status cgks_set_step_target(cgks_solver* s, long long target)
 
 extern "C" {
 
-cgks_status cgks_step_profiled(cgks_solver* s, int nsteps, double stage_ms[6])
+cgks_status cgks_step_profiled(cgks_solver* s, int nsteps, double stage_ms[8])
 {
     if (!s || nsteps <= 0 || !stage_ms) return fail(CGKS_E_INVAL, "bad arguments");
     g_last_launches = 0;
     CK(launch_set_ctrl(s->d_ctrl, 0.0, 0.0, -1, 0, s->stream));
-    constexpr int NK = 6;
+    constexpr int NK = 8;
     std::vector<cudaEvent_t> ev((size_t)nsteps * (NK + 1));
     for (auto& e : ev) CK(cudaEventCreate(&e));
     const int nblocks = s->ntiles < s->nsm ? s->ntiles : s->nsm;
     const int cv = s->prob.recon_vars;
     const int rblocks = record_blocks(s->nrchunks, s->nsm, cv);
+    const int ublocks = update_blocks(s->ncchunks, s->nsm);
     for (int k = 0; k < nsteps; ++k) {
         cudaEvent_t* e = &ev[(size_t)k * (NK + 1)];
         CK(cudaEventRecord(e[0], s->stream));
         CK(launch_begin_step(s->d_desc, 1, s->stream));
         CK(cudaEventRecord(e[1], s->stream));
-        CK(launch_records(1, cv, s->d_desc, s->d_rchunks, s->nrchunks, rblocks, s->stream));
-        CK(cudaEventRecord(e[2], s->stream));
-        CK(launch_stage(s->shape, 1, s->d_desc, s->d_tiles, s->ntiles, nblocks, s->stream));
-        CK(cudaEventRecord(e[3], s->stream));
-        CK(launch_records(2, cv, s->d_desc, s->d_rchunks, s->nrchunks, rblocks, s->stream));
-        CK(cudaEventRecord(e[4], s->stream));
-        CK(launch_stage(s->shape, 2, s->d_desc, s->d_tiles, s->ntiles, nblocks, s->stream));
-        CK(cudaEventRecord(e[5], s->stream));
+        for (int stage = 1; stage <= 2; ++stage) {
+            cudaEvent_t* f = e + 1 + 3 * (stage - 1);
+            CK(launch_records(stage, cv, s->d_desc, s->d_rchunks, s->nrchunks, rblocks, s->stream));
+            CK(cudaEventRecord(f[1], s->stream));
+            CK(launch_stage(s->shape, stage, s->d_desc, s->d_tiles, s->ntiles, nblocks, s->stream));
+            CK(cudaEventRecord(f[2], s->stream));
+            CK(launch_update(stage, s->d_desc, s->d_cchunks, s->ncchunks, ublocks, s->stream));
+            CK(cudaEventRecord(f[3], s->stream));
+        }
         CK(launch_end_step(s->d_desc, 1, s->stream));
-        CK(cudaEventRecord(e[6], s->stream));
+        CK(cudaEventRecord(e[8], s->stream));
     }
     CK(cudaStreamSynchronize(s->stream));
-    double acc[NK] = {0, 0, 0, 0, 0, 0};
+    double acc[NK] = {};
     for (int k = 0; k < nsteps; ++k)
         for (int q = 0; q < NK; ++q) {
             float ms = 0.f;
@@ -431,6 +450,7 @@ void destroy_plan(BatchPlan* bp)
         cudaFree(bp->d_tiles[k]);
     }
     for (int c = 0; c < 2; ++c) cudaFree(bp->d_rchunks[c]);
+    cudaFree(bp->d_cchunks);
     cudaFree(bp->d_grids);
     delete bp;
 }
@@ -457,10 +477,14 @@ static cudaError_t capture_graph(BatchPlan* bp, int shape)
     e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         cudaError_t e1 = launch_begin_step(bp->d_grids, n, cap);
-        if (e1 == cudaSuccess) e1 = records(1, cap);
-        if (e1 == cudaSuccess) e1 = launch_stage(shape, 1, bp->d_grids, bp->d_tiles[shape], bp->ntiles[shape], nblocks, cap);
-        if (e1 == cudaSuccess) e1 = records(2, cap);
-        if (e1 == cudaSuccess) e1 = launch_stage(shape, 2, bp->d_grids, bp->d_tiles[shape], bp->ntiles[shape], nblocks, cap);
+        for (int stage = 1; stage <= 2; ++stage) {
+            if (e1 == cudaSuccess) e1 = records(stage, cap);
+            if (e1 == cudaSuccess)
+                e1 = launch_stage(shape, stage, bp->d_grids, bp->d_tiles[shape], bp->ntiles[shape], nblocks, cap);
+            if (e1 == cudaSuccess)
+                e1 = launch_update(stage, bp->d_grids, bp->d_cchunks, bp->ncchunks, update_blocks(bp->ncchunks, bp->nsm),
+                                   cap);
+        }
         if (e1 == cudaSuccess) e1 = launch_end_step(bp->d_grids, n, cap);
         e = cudaStreamEndCapture(cap, &graph);
         if (e1 != cudaSuccess) e = e1;
@@ -487,6 +511,20 @@ cudaError_t make_plan(cgks_solver* const* solvers, int n, cudaStream_t stream, i
     long long cells = 0;
     for (int g = 0; g < n; ++g) cells += (long long)solvers[g]->nx * solvers[g]->ny;
     bp->cells = cells;
+    // update-kernel queue of all grids
+    {
+        std::vector<TileRef> q;
+        for (int g = 0; g < n; ++g) {
+            std::vector<TileRef> r = cell_chunks(solvers[g]->nx, solvers[g]->ny, g);
+            q.insert(q.end(), r.begin(), r.end());
+        }
+        bp->ncchunks = (int)q.size();
+        bp->launches_per_step += 2;
+        if (e == cudaSuccess) e = cudaMalloc(&bp->d_cchunks, q.size() * sizeof(TileRef));
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(bp->d_cchunks, q.data(), q.size() * sizeof(TileRef), cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    }
     // record-kernel queues of the conservative and the characteristic grids
     for (int c = 0; c < 2; ++c) {
         std::vector<TileRef> q;
@@ -506,7 +544,7 @@ cudaError_t make_plan(cgks_solver* const* solvers, int n, cudaStream_t stream, i
     }
     if (bp->dim == 1) { bp->candidates = {TILE_64x1}; }
     else if (forced_shape >= 0) { bp->candidates = {forced_shape}; }
-    else { bp->candidates = {TILE_15x16, TILE_20x12, TILE_15x15, TILE_16x7}; }
+    else { bp->candidates = {TILE_16x16, TILE_15x16, TILE_32x12, TILE_16x8}; }
     for (int shape : bp->candidates) {
         std::vector<TileRef> tiles;
         for (int g = 0; g < n; ++g) {

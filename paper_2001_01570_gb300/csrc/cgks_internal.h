@@ -36,6 +36,8 @@ struct GridDev {
     double inflow[4][4];   // conservative inflow state per side (x-low, x-high, y-low, y-high)
     double* recx;       // face-row records of the stage in flight: x-faces [7][4][ny+4][nx+1]
     double* recy;       // y-faces [7][4][nx+4][ny+1] (2D)
+    double* facex;      // face results of the stage in flight: x-faces [16][ny][nx+1]
+    double* facey;      // y-faces [16][ny+1][nx] (2D)
 };
 
 // face rows with a record: x-faces 0..nx on rows -2..ny+1, y-faces 0..ny on
@@ -45,19 +47,22 @@ __host__ __device__ inline int record_rows(int nx, int ny, int dim)
     return (nx + 1) * (ny + 4) + (dim == 2 ? (ny + 1) * (nx + 4) : 0);
 }
 inline size_t record_doubles(int nx, int ny, int dim) { return (size_t)28 * record_rows(nx, ny, dim); }
+// per face up to 16 results (stage 1: two flux combinations, two interface states)
+inline size_t face_doubles(int nx, int ny, int dim)
+{
+    return (size_t)16 * ((size_t)(nx + 1) * ny + (dim == 2 ? (size_t)(ny + 1) * nx : 0));
+}
 
 // One unit of work of the stage kernels: a TX x TY tile of one grid.
 struct TileRef { int grid, x0, y0, pad; };
 
 // tile shapes compiled into the library, in the public numbering of
-// cgks_set_tile_shape.  The flux kernel runs one face segment per thread; a
-// TX x TY tile has 2 TX TY + TX + TY segments for 256 threads: 16x7, 7x16 and
-// 14x8 give 247, 247 and 246 (one pass), 16x8 needs 280 (a second pass with a
-// single warp); 20x12, 15x16 and 17x14 give 512, 511 and 507 (two full passes)
-// with the tile's records within 227 KB of shared memory; 24x8, 16x14, 20x11,
-// 15x15, 22x10 and 18x12 fill two passes to 81-94 %.
+// cgks_set_tile_shape.  The flux kernel runs one face segment per thread and a
+// tile owns 2 TX TY segments (plus the grid's last faces on its edges), so
+// 16x8 (256), 16x16 (512), 24x16 and 32x12 (768) fill whole passes of
+// the 256-thread CTA; a tile's records must fit 227 KB of shared memory.
 #define CGKS_FOR_EACH_TILE(X) X(16, 8) X(8, 16) X(32, 4) X(64, 1) X(16, 7) X(7, 16) X(14, 8) X(24, 8) \
-    X(16, 14) X(20, 11) X(15, 15) X(22, 10) X(18, 12) X(20, 12) X(15, 16) X(17, 14)
+    X(16, 14) X(20, 11) X(15, 15) X(22, 10) X(18, 12) X(20, 12) X(15, 16) X(17, 14) X(16, 16) X(24, 16) X(32, 12)
 #define CGKS_TILE_ENUM(w, h) TILE_##w##x##h,
 enum TileShape { CGKS_FOR_EACH_TILE(CGKS_TILE_ENUM) TILE_COUNT };
 #undef CGKS_TILE_ENUM
@@ -71,6 +76,14 @@ inline int tile_h(int s) { static const int v[TILE_COUNT] = {CGKS_FOR_EACH_TILE(
 // the record kernel's work queue: chunks of 256 (record, variable) items of one
 // grid (one record per item in characteristic mode); TileRef.x0 is the first item
 std::vector<TileRef> record_chunks(int nx, int ny, int dim, int recon_vars, int grid);
+// the update kernel's work queue: chunks of 256 cells of one grid (TileRef.x0
+// is the first cell)
+std::vector<TileRef> cell_chunks(int nx, int ny, int grid);
+cudaError_t launch_update(int stage, const GridDev* grids, const TileRef* chunks, int nchunks, int nblocks,
+                          cudaStream_t st);
+// persistent grid of the update kernel: up to 8 resident CTAs per SM
+inline int update_blocks(int nchunks, int nsm) { return nchunks < 8 * nsm ? nchunks : 8 * nsm; }
+
 // persistent grid of the record kernel: its resident CTAs (two per SM with
 // conservative variables, one with characteristic ones), at most one per chunk
 inline int record_blocks(int nchunks, int nsm, int char_vars)
@@ -111,6 +124,8 @@ struct BatchPlan {
     int ntiles[TILE_COUNT] = {};
     TileRef* d_rchunks[2] = {};   // record-kernel queues: conservative / characteristic grids
     int nrchunks[2] = {};
+    TileRef* d_cchunks = nullptr; // update-kernel queue
+    int ncchunks = 0;
     int launches_per_step = 4;
     cudaGraphExec_t exec[TILE_COUNT] = {};
     std::vector<int> candidates;

@@ -28,6 +28,9 @@ constexpr int kMaxSide = CGKS_NOALLOC_MAX_SIDE;
 // rows is largest for nx ny = kMaxCells with one side at kMaxSide
 constexpr size_t kMaxRecordRows = 2 * kMaxCells + 5 * ((size_t)kMaxSide + kMaxCells / kMaxSide) + 8;
 constexpr int kMaxChunks = (int)((4 * kMaxRecordRows + 255) / 256);
+// face results: 16 per face, (nx+1) ny + nx (ny+1) faces
+constexpr size_t kMaxFaces = 2 * kMaxCells + (size_t)kMaxSide + kMaxCells / kMaxSide;
+constexpr int kMaxCellChunks = (int)((kMaxCells + 255) / 256);
 
 // scratch: buffer for the other state (ping-pong) and for W*, 12 planes each
 static __device__ __align__(256) double g_scratch[2 * 12 * kMaxCells];
@@ -36,6 +39,8 @@ static __device__ __align__(256) cgks::GridDev g_desc;
 static __device__ __align__(256) cgks::TileRef g_tiles[kMaxTiles];
 static __device__ __align__(256) double g_records[28 * kMaxRecordRows];
 static __device__ __align__(256) cgks::TileRef g_rchunks[kMaxChunks];
+static __device__ __align__(256) double g_faces[16 * kMaxFaces];
+static __device__ __align__(256) cgks::TileRef g_cchunks[kMaxCellChunks];
 
 // device addresses of the arrays above, looked up once per device with that
 // device current (host code must not use the symbols' names as addresses)
@@ -47,6 +52,8 @@ struct DeviceSymbols {
     cgks::TileRef* tiles = nullptr;
     double* records = nullptr;
     cgks::TileRef* rchunks = nullptr;
+    double* faces = nullptr;
+    cgks::TileRef* cchunks = nullptr;
 };
 constexpr int kMaxDevices = 64;
 DeviceSymbols g_syms[kMaxDevices];
@@ -71,6 +78,8 @@ cgks_status setup_device(int dev, DeviceSymbols** out)
         if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&s.tiles, g_tiles);
         if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&s.records, g_records);
         if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&s.rchunks, g_rchunks);
+        if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&s.faces, g_faces);
+        if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&s.cchunks, g_cchunks);
         if (e != cudaSuccess) return nfail(CGKS_E_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
         s.ready = true;
     }
@@ -80,7 +89,7 @@ cgks_status setup_device(int dev, DeviceSymbols** out)
 
 // fills the descriptor, the tile queue and the record-kernel queue of this call
 // (kernel arguments carry the values, so no host buffer has to outlive the call)
-__global__ void noalloc_init_kernel(cgks::GridDev G, int tw, int th, int nchunks)
+__global__ void noalloc_init_kernel(cgks::GridDev G, int tw, int th, int nchunks, int ncchunks)
 {
     const int ntx = (G.nx + tw - 1) / tw, nty = (G.ny + th - 1) / th;
     if (blockIdx.x == 0 && threadIdx.x == 0) g_desc = G;
@@ -88,6 +97,8 @@ __global__ void noalloc_init_kernel(cgks::GridDev G, int tw, int th, int nchunks
         g_tiles[t] = cgks::TileRef{0, (t % ntx) * tw, (t / ntx) * th, 0};
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nchunks; c += gridDim.x * blockDim.x)
         g_rchunks[c] = cgks::TileRef{0, 256 * c, 0, 0};
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncchunks; c += gridDim.x * blockDim.x)
+        g_cchunks[c] = cgks::TileRef{0, 256 * c, 0, 0};
 }
 
 #define NCK(call)                                                                                  \
@@ -144,6 +155,8 @@ cgks_status cgks_step_noalloc(const cgks_problem* prob, double* planes, int nste
     G.ctrl = sym->ctrl;
     G.recx = sym->records;
     G.recy = sym->records + (size_t)28 * (prob->nx + 1) * (prob->ny + 4);
+    G.facex = sym->faces;
+    G.facey = sym->faces + (size_t)16 * (prob->nx + 1) * prob->ny;
     G.nx = prob->nx;
     G.ny = prob->ny;
     G.dim = 2;
@@ -172,20 +185,23 @@ cgks_status cgks_step_noalloc(const cgks_problem* prob, double* planes, int nste
     const int cv = prob->recon_vars;
     const long long items = (long long)(cv ? 1 : 4) * record_rows(prob->nx, prob->ny, 2);
     const int nrc = (int)((items + 255) / 256);
+    const int ncc = (int)((cells + 255) / 256);
     const int work = nt > nrc ? nt : nrc;
-    noalloc_init_kernel<<<(work + 255) / 256, 256, 0, stream>>>(G, tw, th, nrc);
+    noalloc_init_kernel<<<(work + 255) / 256, 256, 0, stream>>>(G, tw, th, nrc, ncc);
     NCK(cudaGetLastError());
     // control block starts from t, step 0, no error, state in the caller's buffer
     NCK(launch_set_ctrl(sym->ctrl, *t_inout, 0.0, -1, 1, stream));
     NCK(launch_cfl(sym->desc, 0, G, stream));
     const int nblocks = nt < nsm ? nt : nsm;
     const int rblocks = record_blocks(nrc, nsm, cv);
+    const int ublocks = update_blocks(ncc, nsm);
     for (int k = 0; k < nsteps; ++k) {
         NCK(launch_begin_step(sym->desc, 1, stream));
-        NCK(launch_records(1, cv, sym->desc, sym->rchunks, nrc, rblocks, stream));
-        NCK(launch_stage(shape, 1, sym->desc, sym->tiles, nt, nblocks, stream));
-        NCK(launch_records(2, cv, sym->desc, sym->rchunks, nrc, rblocks, stream));
-        NCK(launch_stage(shape, 2, sym->desc, sym->tiles, nt, nblocks, stream));
+        for (int stage = 1; stage <= 2; ++stage) {
+            NCK(launch_records(stage, cv, sym->desc, sym->rchunks, nrc, rblocks, stream));
+            NCK(launch_stage(shape, stage, sym->desc, sym->tiles, nt, nblocks, stream));
+            NCK(launch_update(stage, sym->desc, sym->cchunks, ncc, ublocks, stream));
+        }
         NCK(launch_end_step(sym->desc, 1, stream));
     }
     Ctrl c;

@@ -1,22 +1,23 @@
-// cgks_stage.cuh -- the per-stage flux-and-update kernel of the two-stage
-// fourth-order compact GKS (Sec. 2.2, Eq. step-hyper-1; Sec. 3.1, Eq.
-// compact-deriv-1).  It runs after the record kernel (cgks_records.cu), which
-// did the normal reconstruction of every face row of the grid once.
+// cgks_stage.cuh -- the per-stage flux kernel of the two-stage fourth-order
+// compact GKS (Sec. 2.2, Eq. step-hyper-1).  It runs after the record kernel
+// (cgks_records.cu), which did the normal reconstruction of every face row of
+// the grid once, and before the update kernel (cgks_update.cu), which applies
+// the face results to the cells.
 //
 // One CTA owns a TX x TY tile of cells of one grid and runs, in shared memory:
 //   phase 1  load the face-row records the tile needs (its faces on its rows
 //            and two rows either side)
-//   phase 2  per face segment, at two Gauss points: WENO-Z point values along
-//            the face over rows j-2..j+2 (equilibrium) and j-1..j+1
-//            (non-equilibrium states, with their tangential slopes); tangential
-//            derivatives of the equilibrium state and normal derivatives from
-//            the quartic / quadratic through the same line averages; the
-//            gas-kinetic evaluation at each point, Gauss average
-//   phase 3  per cell: S2O4 update of cell averages by the fluxes and of the
-//            cell-averaged gradients by the Gauss theorem on interface states
-// Stage 1 writes W* and R = W^n + dt L + dt^2/6 L_t (and the gradient
-// counterparts); stage 2 turns R into W^{n+1} in place and reduces the CFL
-// bound of the new state for the next step.
+//   phase 2  per face segment the tile owns (the x- and y-faces on the low side
+//            of its cells, plus the grid's last face where the tile ends on the
+//            grid's edge, so every face is evaluated once), at two Gauss points:
+//            WENO-Z point values along the face over rows j-2..j+2
+//            (equilibrium) and j-1..j+1 (non-equilibrium states, with their
+//            tangential slopes); tangential derivatives of the equilibrium state
+//            and normal derivatives from the quartic / quadratic through the same
+//            line averages; the gas-kinetic evaluation at each point; the Gauss
+//            average, weighted by the stage's time factors, written to the face
+//            results (stage 1: the W* and R flux combinations and the interface
+//            states W(dt/2), W(dt); stage 2: dt^2/3 F_t and dt^2/3 W_tt)
 // The kernel is persistent: CTAs stride over a flattened tile queue that may
 // span many grids of different sizes (each with its own dt in its Ctrl).
 #pragma once
@@ -35,9 +36,7 @@ struct StageLayout {
     static constexpr int NF = FaceQ<STAGE>::n;
     static constexpr int n_rx = 4 * NREC * (TY + 4) * (TX + 1);
     static constexpr int n_ry = 4 * NREC * (TX + 4) * (TY + 1);
-    static constexpr int n_fx = NF * TY * (TX + 1);
-    static constexpr int n_fy = NF * (TY + 1) * TX;
-    static constexpr size_t bytes = sizeof(double) * (size_t)(n_rx + n_ry + n_fx + n_fy);
+    static constexpr size_t bytes = sizeof(double) * (size_t)(n_rx + n_ry);
 };
 
 // The face rows around one face segment (records of rows j-2..j+2 of one
@@ -116,10 +115,8 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
     extern __shared__ double smem[];
     double* rx = smem;                  // [28][TY+4][TX+1]
     double* ry = rx + L::n_rx;          // [28][TX+4][TY+1]
-    double* fx = ry + L::n_ry;          // [NF][TY][TX+1]
-    double* fy = fx + L::n_fx;          // [NF][TY+1][TX]
     __shared__ double s_dt;
-    __shared__ int s_skip, s_par;
+    __shared__ int s_skip;
     const int tid = threadIdx.x;
     constexpr double gq = 0.28867513459481287;   // 1/(2 sqrt 3): Gauss points at +-gq
 
@@ -131,16 +128,12 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
             const Ctrl* C = G.ctrl;
             s_skip = C->done;
             s_dt = C->dt;
-            s_par = C->par;
         }
         __syncthreads();
         if (s_skip) continue;
         const int nx = G.nx, ny = G.ny, x0 = tr.x0, y0 = tr.y0;
         const double dt = s_dt;
-        const int par = s_par;
         const bool dim1 = (G.dim == 1);
-        const double* __restrict__ src = (STAGE == 1) ? G.buf[par] : G.ws;
-        const size_t PL = (size_t)nx * ny;
 
         // ---------------- phase 1: the tile's face-row records (the record kernel
         // wrote them for every face row of the grid): x-faces x0..x0+TX on rows
@@ -170,31 +163,34 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
         P.idt = __drcp_rn(dt); P.inv_K2 = __drcp_rn(G.K + 2.0); P.inv_gm1 = __drcp_rn(G.gamma - 1.0);
         P.K2inv2 = 2.0 * P.inv_K2; P.Kheat = 0.5 * (G.K + 4.0);
         bool bad = false;
-        constexpr int NSX = (TX + 1) * TY, NSY = TX * (TY + 1);
-        for (int item = tid; item < NSX + NSY; item += kThreads) {
-            const bool xo = item < NSX;
+        // the tile's own faces: x-faces x0..x0+TX-1 and y-faces y0..y0+TY-1 of its
+        // cells, plus the last face of the grid where the tile ends on the grid's
+        // edge; every face is evaluated by exactly one tile
+        const int xe = (x0 + TX == nx) ? TY : 0, ye = (!dim1 && y0 + TY == ny) ? TX : 0;
+        const int nseg = (dim1 ? TX * TY : 2 * TX * TY) + xe + ye;
+        const size_t nfx = (size_t)ny * (nx + 1), nfy = (size_t)(ny + 1) * nx;
+        for (int item = tid; item < nseg; item += kThreads) {
+            int fl, jl, il, gl;
+            bool xo;
+            if (item < TX * TY) { xo = true; fl = item % TX; jl = item / TX; }
+            else if (!dim1 && item < 2 * TX * TY) { xo = false; const int it = item - TX * TY; il = it % TX; gl = it / TX; }
+            else {
+                const int it = item - (dim1 ? TX * TY : 2 * TX * TY);
+                if (it < xe) { xo = true; fl = TX; jl = it; }
+                else { xo = false; il = it - xe; gl = TY; }
+            }
             const double* rec;
             int nrec, r0, rstride;
-            double ht;
             double* out;
-            int nout, oidx;
-            bool valid;
+            size_t ostride, oidx;
             if (xo) {
-                const int fl = item % (TX + 1), jl = item / (TX + 1);
-                valid = (x0 + fl <= nx) && (y0 + jl < ny);
+                if (!((x0 + fl <= nx) && (y0 + jl < ny))) continue;
                 rec = rx; nrec = (TY + 4) * (TX + 1); r0 = (jl + 2) * (TX + 1) + fl; rstride = TX + 1;
-                ht = G.dy; out = fx; nout = TY * (TX + 1); oidx = jl * (TX + 1) + fl;
+                out = G.facex; ostride = nfx; oidx = (size_t)(y0 + jl) * (nx + 1) + x0 + fl;
             } else {
-                const int it = item - NSX;
-                const int il = it % TX, gl = it / TX;
-                valid = !dim1 && (y0 + gl <= ny) && (x0 + il < nx);
+                if (!((y0 + gl <= ny) && (x0 + il < nx))) continue;
                 rec = ry; nrec = (TX + 4) * (TY + 1); r0 = (il + 2) * (TY + 1) + gl; rstride = TY + 1;
-                ht = G.dx; out = fy; nout = (TY + 1) * TX; oidx = gl * TX + il;
-            }
-            if (!valid) {
-#pragma unroll
-                for (int q = 0; q < NF; ++q) out[q * nout + oidx] = 0.0;
-                continue;
+                out = G.facey; ostride = nfy; oidx = (size_t)(y0 + gl) * nx + x0 + il;
             }
             const double iht = xo ? G.inv_dy : G.inv_dx;
             const double weps = G.weno_eps;
@@ -242,71 +238,13 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
 #pragma unroll
             for (int q = 0; q < NF; q += 4) {
                 const int k1 = xo ? 1 : 2, k2 = xo ? 2 : 1;
-                out[(q + 0) * nout + oidx] = acc[q + 0];
-                out[(q + k1) * nout + oidx] = acc[q + 1];
-                out[(q + k2) * nout + oidx] = acc[q + 2];
-                out[(q + 3) * nout + oidx] = acc[q + 3];
+                out[(q + 0) * ostride + oidx] = acc[q + 0];
+                out[(q + k1) * ostride + oidx] = acc[q + 1];
+                out[(q + k2) * ostride + oidx] = acc[q + 2];
+                out[(q + 3) * ostride + oidx] = acc[q + 3];
             }
         }
         if (bad) atomicOr(&G.ctrl->status, (int)CGKS_E_NONPHYSICAL);
-        __syncthreads();
-
-        // ---------------- phase 3: cell update
-        double* __restrict__ rbuf = G.buf[par ^ 1];
-        const double idx_ = G.inv_dx, idy_ = G.inv_dy;
-        double dtmin = INFINITY;
-        bool bad2 = false;
-        for (int item = tid; item < TX * TY; item += kThreads) {
-            const int il = item % TX, jl = item / TX;
-            const int i = x0 + il, j = y0 + jl;
-            if (i >= nx || j >= ny) continue;
-            const size_t off = (size_t)j * nx + i;
-            const int xl = jl * (TX + 1) + il, xr = xl + 1;
-            const int yb = jl * TX + il, yt = yb + TX;
-            constexpr int nfx = TY * (TX + 1), nfy = (TY + 1) * TX;
-            auto FX = [&](int q, int at) { return fx[q * nfx + at]; };
-            auto FY = [&](int q, int at) { return dim1 ? 0.0 : fy[q * nfy + at]; };
-            if (STAGE == 1) {
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const double W = __ldg(src + k * PL + off);
-                    G.ws[k * PL + off] = W - (FX(k, xr) - FX(k, xl)) * idx_ - (FY(k, yt) - FY(k, yb)) * idy_;
-                    G.ws[(4 + k) * PL + off] = (FX(8 + k, xr) - FX(8 + k, xl)) * idx_;
-                    G.ws[(8 + k) * PL + off] = (FY(8 + k, yt) - FY(8 + k, yb)) * idy_;
-                    rbuf[k * PL + off] = W - (FX(4 + k, xr) - FX(4 + k, xl)) * idx_ - (FY(4 + k, yt) - FY(4 + k, yb)) * idy_;
-                    rbuf[(4 + k) * PL + off] = (FX(12 + k, xr) - FX(12 + k, xl)) * idx_;
-                    rbuf[(8 + k) * PL + off] = (FY(12 + k, yt) - FY(12 + k, yb)) * idy_;
-                }
-            } else {
-                double Wn[4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const double R = rbuf[k * PL + off];
-                    Wn[k] = R - (FX(k, xr) - FX(k, xl)) * idx_ - (FY(k, yt) - FY(k, yb)) * idy_;
-                    rbuf[k * PL + off] = Wn[k];
-                    rbuf[(4 + k) * PL + off] += (FX(4 + k, xr) - FX(4 + k, xl)) * idx_;
-                    rbuf[(8 + k) * PL + off] += (FY(4 + k, yt) - FY(4 + k, yb)) * idy_;
-                }
-                // CFL bound of the new state (Sec. 4)
-                const double ir = 1.0 / Wn[0];
-                const double U = Wn[1] * ir, V = Wn[2] * ir;
-                const double p = (G.gamma - 1.0) * (Wn[3] - 0.5 * (Wn[1] * U + Wn[2] * V));
-                const bool ok = (Wn[0] > 0.0) && (p > 0.0);
-                bad2 |= !ok;
-                const double c = sqrt(G.gamma * p * ir);
-                const double nu = G.mu * ir;
-                double d = G.dx / (fabs(U) + c + 2.0 * nu * G.inv_dx);
-                if (!dim1) d = fmin(d, G.dy / (fabs(V) + c + 2.0 * nu * G.inv_dy));
-                if (ok) dtmin = fmin(dtmin, d);
-            }
-        }
-        if (STAGE == 2) {
-            if (bad2) atomicOr(&G.ctrl->status, (int)CGKS_E_NONPHYSICAL);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) dtmin = fmin(dtmin, __shfl_xor_sync(0xffffffffu, dtmin, o));
-            if ((tid & 31) == 0 && dtmin < INFINITY)
-                atomicMin(&G.ctrl->dtmin_bits, (unsigned long long)__double_as_longlong(dtmin));
-        }
     }
 }
 

@@ -1,4 +1,4 @@
-// Instantiation of the fused stage kernel for 14x8 cell tiles.
+// Instantiation of the flux kernel for 14x8 cell tiles.
 #include "cgks_stage.cuh"
 
 namespace cgks {

@@ -1,4 +1,4 @@
-// Instantiation of the fused stage kernel for 22x10 cell tiles.
+// Instantiation of the flux kernel for 22x10 cell tiles.
 #include "cgks_stage.cuh"
 
 namespace cgks {

@@ -1,4 +1,4 @@
-// Instantiation of the fused stage kernel for 64x1 cell tiles.
+// Instantiation of the flux kernel for 64x1 cell tiles.
 #include "cgks_stage.cuh"
 
 namespace cgks {

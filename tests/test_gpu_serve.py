@@ -68,7 +68,7 @@ def test_budget_limits_concurrency():
     """With a budget that holds one 64^2 solve at a time, requests run one after another."""
     spec, W = wl.acoustic_pulse(64, 1e-3, 5.0, 20.0, 20.0)
     one = cgks.cgks_problem_device_bytes(cgks.problem_from_spec(spec))
-    assert one == 3 * 12 * 64 * 64 * 8 + 28 * 8 * (65 * 68 * 2) + 4096
+    assert one == 3 * 12 * 64 * 64 * 8 + 28 * 8 * (65 * 68 * 2) + 16 * 8 * (65 * 64 * 2) + 4096
     srv = cgks.cgks_serve_start(hbm_budget_bytes=one * 1.5, max_active=8, steps_per_round=1)
     try:
         ids = [cgks.cgks_serve_submit(srv, cgks.problem_from_spec(spec), W, 3) for _ in range(3)]
