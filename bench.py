@@ -35,24 +35,23 @@ import numpy as np  # noqa: E402
 METRIC = "FP64 cell-updates/s on 1 GB300 (plain 2048^2 sweep); served-batched vs plain; p50/p99 solve latency"
 UNIT = "cell-updates/s"
 
-# Algorithmic FP64 operations per cell and stage (FMA = 2): the work of one cell's two face rows
-# (linear recon + WENO-Z pair per variable), its two face segments (two Gauss points each) and its
-# update, without the halo rows a tile recomputes.  Per-row costs from ncu op counts of a probe of the
-# phase-1 item, per-segment and per-cell costs fitted to the ncu op counts of seven tile shapes on
-# the 256^2 vortex: profiles/stage_kernels_flops_vortex256.md.
-FLOP_PER_CELL = {1: 11090.0, 2: 10725.0}
-# of which the record kernel (two face rows per cell: linear 148 + WENO-Z pair 1,800 each) and the
-# flux-and-update kernel (two face segments and the update)
-RECORD_FLOP_PER_CELL = 2 * 148.0 + 2 * 1800.0
-FLUX_FLOP_PER_CELL = {1: FLOP_PER_CELL[1] - RECORD_FLOP_PER_CELL, 2: FLOP_PER_CELL[2] - RECORD_FLOP_PER_CELL}
+# Algorithmic FP64 operations per cell and stage (FMA = 2), measured with ncu op counts on the 256^2
+# vortex, where every kernel does exactly the method's work (no halo recomputation, every face once):
+# two face-row records (1,912 each: linear P7 + WENO-Z pair of 4 variables), two face segments
+# (3,602.4 in stage 1, 3,388.4 in stage 2: two Gauss points each) and the update (80 / 121):
+# profiles/stage_kernels_flops_vortex256.md.
+RECORD_FLOP_PER_CELL = 3824.0
+FLUX_FLOP_PER_CELL = {1: 7205.0, 2: 6777.0}
+UPDATE_FLOP_PER_CELL = {1: 80.0, 2: 121.0}
+FLOP_PER_CELL = {s: RECORD_FLOP_PER_CELL + FLUX_FLOP_PER_CELL[s] + UPDATE_FLOP_PER_CELL[s] for s in (1, 2)}
 DEFAULT_TILE = "16x16"    # the library's 2D default
-# DRAM bytes (read + write) per cell of one stage-1 flux-kernel launch with 15x16 tiles, ncu
+# DRAM bytes (read + write) per cell of one flux-kernel launch with 16x16 tiles, ncu
 # dram__bytes_{read,write}.sum on the 1024^2 vortex (records and state larger than L2) divided by the
-# cells; the 2048^2 bench grid moves the same bytes per cell: profiles/split_kernels_ncu_vortex1024.md.
-FLUX_DRAM_BYTES_PER_CELL = {1: 711.93e6 / 1048576, 2: 671.09e6 / 1048576}
-# algorithmic bytes per cell of the flux kernel: the two face rows' records (2 x 28 doubles) plus
-# the state it reads and writes (stage 1: W in, W* and R out)
-FLUX_ALGO_BYTES_PER_CELL = {1: 448 + 32 + 192, 2: 448 + 96 + 96}
+# cells; the 2048^2 bench grid moves the same bytes per cell: profiles/flux_kernels_ncu_vortex1024.md.
+FLUX_DRAM_BYTES_PER_CELL = {1: 736.78e6 / 1048576, 2: 600.89e6 / 1048576}
+# algorithmic bytes per cell of the flux kernel: the two face rows' records (2 x 28 doubles) read and
+# the two faces' results written (stage 1: 16 doubles each, stage 2: 8)
+FLUX_ALGO_BYTES_PER_CELL = {1: 448 + 256, 2: 448 + 128}
 # measured FP64 peak of this GB300 (DFMA throughput loop, FMA = 2): profiles/fp64_peak_gb300.md
 FP64_PEAK_TFLOPS = 1.010
 
@@ -236,7 +235,7 @@ def run_cgks(args, world, rank, local):
                                              "ms": flux_ms + rec_ms + upd_ms, "achieved": stage1,
                                              "frac": stage1 / FP64_PEAK_TFLOPS,
                                              "algorithmic_flop_per_cell": FLOP_PER_CELL[1],
-                                             "algorithmic_bytes": 288 * cells},
+                                             "state_algorithmic_bytes": 288 * cells},
                 "peak_source": "measured FP64 DFMA loop (FMA=2) on GB300, of measured"}
 
     # ---------------- end to end through the C ABI with host buffers
