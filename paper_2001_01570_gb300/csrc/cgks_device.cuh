@@ -120,56 +120,56 @@ __device__ __forceinline__ void weno_side(double base, double d1, double d2, dou
                                           double cc, double cd, double cd2, double cd3, double dd, double dd2, double dd3,
                                           double eps, double& val, double& hslope)
 {
-    // smoothness indicators, Eq. (smooth-indicator)
-    const double b0 = (16.0 / 3.0) * aa - (38.0 / 3.0) * ad1 + (25.0 / 3.0) * x11;
-    const double b1 = (801.0 / 80.0) * aa - (2443.0 / 80.0) * ad1 + (761.0 / 80.0) * ad2
+    // smoothness indicators, Eq. (smooth-indicator), with the WENO epsilon
+    // already added: e_k = beta_k + eps (one multiply-add chain each)
+    const double e0 = eps + (16.0 / 3.0) * aa - (38.0 / 3.0) * ad1 + (25.0 / 3.0) * x11;
+    const double e1 = eps + (801.0 / 80.0) * aa - (2443.0 / 80.0) * ad1 + (761.0 / 80.0) * ad2
                       + (23627.0 / 960.0) * x11 - (7769.0 / 480.0) * x12 + (3443.0 / 960.0) * x22;
-    const double b2 = (1641.0 / 80.0) * dd + (2401.0 / 80.0) * dd2 - (5523.0 / 80.0) * dd3
+    const double e2 = eps + (1641.0 / 80.0) * dd + (2401.0 / 80.0) * dd2 - (5523.0 / 80.0) * dd3
                       + (12683.0 / 960.0) * x22 - (25169.0 / 480.0) * x23 + (56387.0 / 960.0) * x33;
-    const double b3 = (4.0 / 3.0) * x11 - (5.0 / 3.0) * x12 + (4.0 / 3.0) * x22;
-    const double b4 = (10.0 / 3.0) * x22 - (11.0 / 3.0) * x23 + (4.0 / 3.0) * x33;
-    const double b5 = (4405.0 / 28.0) * aa + (4405.0 / 7.0) * ab - (110433.0 / 140.0) * ad1 - (21717.0 / 140.0) * ad2
-                      + (93707.0 / 140.0) * bb - (226333.0 / 140.0) * bd1 - (48901.0 / 140.0) * bd2
-                      + (209917.0 / 210.0) * x11 + (17063.0 / 42.0) * x12 + (5153.0 / 105.0) * x22;
-    const double b6 = (265067.0 / 140.0) * cc + (11104.0 / 7.0) * cd - (160551.0 / 140.0) * cd2 - (592783.0 / 140.0) * cd3
-                      + (9529.0 / 28.0) * dd - (65327.0 / 140.0) * dd2 - (252323.0 / 140.0) * dd3
-                      + (38131.0 / 210.0) * x22 + (52763.0 / 42.0) * x23 + (251276.0 / 105.0) * x33;
-    // global reference Z_ref, Eq. (tau)
-    const double Z = fabs(3.0 * b0 - 2.0 * b4 - b3);
-    // WENO-Z: alpha_k = d_k (beta_k + eps + Z) / (beta_k + eps); normalise with
-    // one reciprocal by multiplying numerators by prod_{j != k}(beta_j + eps)
-    const double e0 = b0 + eps, e1 = b1 + eps, e2 = b2 + eps, e3 = b3 + eps, e4 = b4 + eps, e5 = b5 + eps, e6 = b6 + eps;
+    const double e3 = eps + (4.0 / 3.0) * x11 - (5.0 / 3.0) * x12 + (4.0 / 3.0) * x22;
+    const double e4 = eps + (10.0 / 3.0) * x22 - (11.0 / 3.0) * x23 + (4.0 / 3.0) * x33;
+    const double e5 = eps + (4405.0 / 28.0) * aa + (4405.0 / 7.0) * ab - (110433.0 / 140.0) * ad1
+                      - (21717.0 / 140.0) * ad2 + (93707.0 / 140.0) * bb - (226333.0 / 140.0) * bd1
+                      - (48901.0 / 140.0) * bd2 + (209917.0 / 210.0) * x11 + (17063.0 / 42.0) * x12
+                      + (5153.0 / 105.0) * x22;
+    const double e6 = eps + (265067.0 / 140.0) * cc + (11104.0 / 7.0) * cd - (160551.0 / 140.0) * cd2
+                      - (592783.0 / 140.0) * cd3 + (9529.0 / 28.0) * dd - (65327.0 / 140.0) * dd2
+                      - (252323.0 / 140.0) * dd3 + (38131.0 / 210.0) * x22 + (52763.0 / 42.0) * x23
+                      + (251276.0 / 105.0) * x33;
+    // global reference Z_ref, Eq. (tau): |3 beta_0 - 2 beta_4 - beta_3| (the epsilons cancel)
+    const double Z = fabs(3.0 * e0 - 2.0 * e4 - e3);
+    // WENO-Z: alpha_k = d_k (e_k + Z) / e_k; normalised with one reciprocal by
+    // multiplying the numerators by prod_{j != k} e_j: t_k = (e_k + Z) prod_{j != k} e_j,
+    // alpha_k proportional to d_k t_k.  The linear weights d_k are folded into the
+    // candidate coefficients below where a t_k multiplies a single candidate.
+    constexpr double d0 = 3.0 / 98.0, d1w = 5.0 / 98.0, d2w = 4.0 / 49.0, d3w = 7.0 / 98.0, d4w = 7.0 / 98.0;
+    constexpr double d5 = 17.0 / 49.0, d6 = 17.0 / 49.0;
     const double p01 = e0 * e1, p012 = p01 * e2, p0123 = p012 * e3, p01234 = p0123 * e4;
     const double s56 = e5 * e6, s456 = e4 * s56, s3456 = e3 * s456, s23456 = e2 * s3456;
-    const double L0 = e1 * s23456;
-    const double L1 = e0 * s23456;
-    const double L2 = p01 * s3456;
-    const double L3 = p012 * s456;
-    const double L4 = p0123 * s56;
-    const double L5 = p01234 * e6;
-    const double L6 = p01234 * e5;
-    const double n0 = (3.0 / 98.0) * (e0 + Z) * L0;
-    const double n1 = (5.0 / 98.0) * (e1 + Z) * L1;
-    const double n2 = (4.0 / 49.0) * (e2 + Z) * L2;
-    const double n3 = (7.0 / 98.0) * (e3 + Z) * L3;
-    const double n4 = (7.0 / 98.0) * (e4 + Z) * L4;
-    const double n5 = (17.0 / 49.0) * (e5 + Z) * L5;
-    const double n6 = (17.0 / 49.0) * (e6 + Z) * L6;
-    const double inv = __drcp_rn((n0 + n1) + (n2 + n3) + (n4 + n5) + n6);
-    // candidate values minus Q_i, Eq. (sub-stencil)
-    const double q0 = (7.0 / 6.0) * d1 - (2.0 / 3.0) * A;
+    const double t0 = (e0 + Z) * (e1 * s23456);
+    const double t1 = (e1 + Z) * (e0 * s23456);
+    const double t2 = (e2 + Z) * (p01 * s3456);
+    const double t3 = (e3 + Z) * (p012 * s456);
+    const double t4 = (e4 + Z) * (p0123 * s56);
+    const double t5 = (e5 + Z) * (p01234 * e6);
+    const double t6 = (e6 + Z) * (p01234 * e5);
+    const double n13 = d1w * t1 + d3w * t3, n4 = d4w * t4;
+    const double inv = __drcp_rn(d0 * t0 + n13 + d2w * t2 + n4 + d5 * t5 + d6 * t6);
+    // candidate values minus Q_i, Eq. (sub-stencil) (q0, q2, q5, q6 times their d_k)
+    const double q0 = (d0 * 7.0 / 6.0) * d1 - (d0 * 2.0 / 3.0) * A;
     const double q13 = (1.0 / 6.0) * d1 + (1.0 / 3.0) * d2;
-    const double q2 = 0.25 * D + (19.0 / 24.0) * d2 - (13.0 / 24.0) * d3;
+    const double q2 = (d2w * 0.25) * D + (d2w * 19.0 / 24.0) * d2 - (d2w * 13.0 / 24.0) * d3;
     const double q4 = (2.0 / 3.0) * d2 - (1.0 / 6.0) * d3;
-    const double q5 = 0.1 * A + 0.7 * B - (1.0 / 3.0) * d1 + (1.0 / 30.0) * d2;
-    const double q6 = (29.0 / 30.0) * d2 + (1.0 / 3.0) * d3 - 0.7 * C - 0.1 * D;
-    // candidate slopes h q_k'(x_{i+1/2})
-    const double s0 = 3.0 * d1 - 2.0 * A;
-    const double s2 = 0.875 * d2 + 0.375 * d3 - 0.25 * D;
-    const double s5 = 0.5 * A + 1.5 * B - 1.5 * d1 + 0.5 * d2;
-    const double s6 = 1.5 * C + 0.5 * D + 0.5 * d2 - 1.5 * d3;
-    const double nv = n0 * q0 + (n1 + n3) * q13 + n2 * q2 + n4 * q4 + n5 * q5 + n6 * q6;
-    const double ns = n0 * s0 + (n1 + n3 + n4) * d2 + n2 * s2 + n5 * s5 + n6 * s6;
+    const double q5 = (d5 * 0.1) * A + (d5 * 0.7) * B - (d5 / 3.0) * d1 + (d5 / 30.0) * d2;
+    const double q6 = (d6 * 29.0 / 30.0) * d2 + (d6 / 3.0) * d3 - (d6 * 0.7) * C - (d6 * 0.1) * D;
+    // candidate slopes h q_k'(x_{i+1/2}) (s0, s2, s5, s6 times their d_k)
+    const double s0 = (d0 * 3.0) * d1 - (d0 * 2.0) * A;
+    const double s2 = (d2w * 0.875) * d2 + (d2w * 0.375) * d3 - (d2w * 0.25) * D;
+    const double s5 = (d5 * 0.5) * A + (d5 * 1.5) * B - (d5 * 1.5) * d1 + (d5 * 0.5) * d2;
+    const double s6 = (d6 * 1.5) * C + (d6 * 0.5) * D + (d6 * 0.5) * d2 - (d6 * 1.5) * d3;
+    const double nv = t0 * q0 + n13 * q13 + t2 * q2 + n4 * q4 + t5 * q5 + t6 * q6;
+    const double ns = t0 * s0 + (n13 + n4) * d2 + t2 * s2 + t5 * s5 + t6 * s6;
     val = base + nv * inv;
     hslope = ns * inv;
 }
