@@ -37,10 +37,10 @@ UNIT = "cell-updates/s"
 
 # Algorithmic FP64 operations per cell and stage (FMA = 2), measured with ncu op counts on the 256^2
 # vortex, where every kernel does exactly the method's work (no halo recomputation, every face once):
-# two face-row records (1,912 each: linear P7 + WENO-Z pair of 4 variables), two face segments
+# two face-row records (1,888 each: linear P7 + WENO-Z pair of 4 variables), two face segments
 # (3,602.4 in stage 1, 3,388.4 in stage 2: two Gauss points each) and the update (80 / 121):
 # profiles/stage_kernels_flops_vortex256.md.
-RECORD_FLOP_PER_CELL = 3824.0
+RECORD_FLOP_PER_CELL = 3776.0
 FLUX_FLOP_PER_CELL = {1: 7205.0, 2: 6777.0}
 UPDATE_FLOP_PER_CELL = {1: 80.0, 2: 121.0}
 FLOP_PER_CELL = {s: RECORD_FLOP_PER_CELL + FLUX_FLOP_PER_CELL[s] + UPDATE_FLOP_PER_CELL[s] for s in (1, 2)}

@@ -94,3 +94,33 @@ def test_batched_1d_acoustic_grids_equal_alone_bitwise():
         assert sb == steps == 25 and tb == t
         assert np.array_equal(out, ref)
         s.close()
+
+
+def test_batched_mixed_options_equal_alone_bitwise():
+    """One batch mixing conservative and characteristic reconstruction (two record-kernel queues),
+    a viscous grid and the shock reflection's per-side inflow states."""
+    a = wl.shock_vortex(nx=40, ny=22, mach=1.3)
+    b = wl.shock_vortex(nx=33, ny=17, mach=1.2)
+    b[0].recon_vars = 1
+    c = wl.shear_wave(32, 1e-3, 0.01, kind="shear")
+    d = wl.shock_reflection(40, 10)
+    d[0].recon_vars = 1
+    cases = [a, b, c, d]
+    alone = []
+    for spec, W in cases:
+        s = cgks.Solver(cgks.problem_from_spec(spec))
+        s.set_state(W)
+        s.step(5)
+        alone.append(s.get_state())
+        s.close()
+    solvers = []
+    for spec, W in cases:
+        s = cgks.Solver(cgks.problem_from_spec(spec))
+        s.set_state(W)
+        solvers.append(s)
+    cgks.cgks_batch_step([s.handle for s in solvers], 5)
+    for s, (ref, t, steps) in zip(solvers, alone):
+        out, tb, sb = s.get_state()
+        assert sb == steps == 5 and tb == t
+        assert np.array_equal(out, ref)
+        s.close()
