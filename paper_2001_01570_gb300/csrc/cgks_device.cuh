@@ -255,9 +255,9 @@ __device__ __forceinline__ void tang_weno5_pair(double vmm, double vm, double v0
     const double D1 = vp - vm;
     const double D2 = (4.0 * vp - vpp) - 3.0 * v0;
     const double s0 = (vmm - 2.0 * vm) + v0, s1 = (vm - 2.0 * v0) + vp, s2 = (v0 - 2.0 * vp) + vpp;
-    const double e0 = (13.0 / 12.0) * s0 * s0 + 0.25 * D0 * D0 + eps;
-    const double e1 = (13.0 / 12.0) * s1 * s1 + 0.25 * D1 * D1 + eps;
-    const double e2 = (13.0 / 12.0) * s2 * s2 + 0.25 * D2 * D2 + eps;
+    const double e0 = eps + ((13.0 / 12.0) * s0) * s0 + (0.25 * D0) * D0;
+    const double e1 = eps + ((13.0 / 12.0) * s1) * s1 + (0.25 * D1) * D1;
+    const double e2 = eps + ((13.0 / 12.0) * s2) * s2 + (0.25 * D2) * D2;
     const double Z = fabs(e0 - e2);
     constexpr double d_lo = 7.0 / 36.0 - 1.7320508075688772 / 1080.0;
     constexpr double d_hi = 7.0 / 36.0 + 1.7320508075688772 / 1080.0;
@@ -276,7 +276,7 @@ __device__ __forceinline__ void tang_weno5_pair(double vmm, double vm, double v0
 __device__ __forceinline__ double tang_weno3_slope(double vm, double v0, double vp, double eps)
 {
     const double dm = v0 - vm, dp = vp - v0;
-    const double e0 = dm * dm + eps, e1 = dp * dp + eps;
+    const double e0 = eps + dm * dm, e1 = eps + dp * dp;
     const double Z = fabs(e0 - e1);
     const double n0 = (e0 + Z) * e1, n1 = (e1 + Z) * e0;
     return (n0 * dm + n1 * dp) * __drcp_rn(n0 + n1);

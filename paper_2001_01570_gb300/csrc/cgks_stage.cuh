@@ -59,30 +59,36 @@ struct SegmentRows {
         for (int k = 0; k < 4; ++k) W[k] = W0[k];
     }
 
-    // quartic with segment means m_{j-2..j+2}: coefficients c1..c4 of eta^1..eta^4
-    __device__ __forceinline__ static void quartic(double mm, double m, double m0, double p, double pp,
-                                                   double& c1, double& c2, double& c3, double& c4)
-    {
-        const double S1 = p + m, S2 = pp + mm, A1 = p - m, A2 = pp - mm;
-        c1 = (34.0 * A1 - 5.0 * A2) * (1.0 / 48.0);
-        c3 = (A2 - 2.0 * A1) * (1.0 / 12.0);
-        c2 = (12.0 * S1 - S2 - 22.0 * m0) * (1.0 / 16.0);
-        c4 = (S2 - 4.0 * S1 + 6.0 * m0) * (1.0 / 24.0);
-    }
-
+    // The quartic through the segment means m_{j-2..j+2} (m0 the centre row), written
+    // with S1 = m_1 + m_-1, S2 = m_2 + m_-2, A1 = m_1 - m_-1, A2 = m_2 - m_-2:
+    //   p(eta)   = m0 - (S2 - 4 S1 + 6 m0)/4320 + eta (50 A1 - 7 A2)/72 + O(eta^2 - 1/12)
+    //   p'(eta)  = (8 A1 - A2)/12 + eta (13 S1 - S2 - 24 m0)/9 + O(eta^2 - 1/12)
+    //   p''(eta) = (16 S1 - S2 - 30 m0)/12 + eta (A2 - 2 A1)/2 + O(eta^2 - 1/12)
+    // (exact at the Gauss points eta = +-1/(2 sqrt 3), where eta^2 = 1/12)
     __device__ __forceinline__ void eq_derivs(double W0n[4], double W0t[4], double W0nn[4], double W0nt[4],
                                               double W0tt[4]) const
     {
+        const double iht2 = iht * iht;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            double c1, c2, c3, c4;
-            quartic(at(RV, k, -2), at(RV, k, -1), at(RV, k, 0), at(RV, k, 1), at(RV, k, 2), c1, c2, c3, c4);
-            W0t[k] = (c1 + 0.25 * c3 + eta * (2.0 * c2 + c4 * (1.0 / 3.0))) * iht;
-            W0tt[k] = (2.0 * c2 + c4 + 6.0 * eta * c3) * iht * iht;
-            const double N0 = at(RN, k, 0);
-            quartic(at(RN, k, -2), at(RN, k, -1), N0, at(RN, k, 1), at(RN, k, 2), c1, c2, c3, c4);
-            W0n[k] = N0 - c4 * (1.0 / 180.0) + eta * (c1 + c3 * (1.0 / 12.0));
-            W0nt[k] = (c1 + 0.25 * c3 + eta * (2.0 * c2 + c4 * (1.0 / 3.0))) * iht;
+            {
+                const double m0 = at(RV, k, 0), mp = at(RV, k, 1), mm = at(RV, k, -1);
+                const double S1 = mp + mm, S2 = at(RV, k, 2) + at(RV, k, -2);
+                const double A1 = mp - mm, A2 = at(RV, k, 2) - at(RV, k, -2);
+                W0t[k] = ((8.0 / 12.0) * A1 - (1.0 / 12.0) * A2
+                          + eta * ((13.0 / 9.0) * S1 - (1.0 / 9.0) * S2 - (24.0 / 9.0) * m0)) * iht;
+                W0tt[k] = ((16.0 / 12.0) * S1 - (1.0 / 12.0) * S2 - (30.0 / 12.0) * m0
+                           + eta * (0.5 * A2 - A1)) * iht2;
+            }
+            {
+                const double m0 = at(RN, k, 0), mp = at(RN, k, 1), mm = at(RN, k, -1);
+                const double S1 = mp + mm, S2 = at(RN, k, 2) + at(RN, k, -2);
+                const double A1 = mp - mm, A2 = at(RN, k, 2) - at(RN, k, -2);
+                W0n[k] = m0 - (1.0 / 4320.0) * (S2 - 4.0 * S1 + 6.0 * m0)
+                         + eta * ((50.0 / 72.0) * A1 - (7.0 / 72.0) * A2);
+                W0nt[k] = ((8.0 / 12.0) * A1 - (1.0 / 12.0) * A2
+                           + eta * ((13.0 / 9.0) * S1 - (1.0 / 9.0) * S2 - (24.0 / 9.0) * m0)) * iht;
+            }
             W0nn[k] = at(RNN, k, 0);
         }
     }
