@@ -319,27 +319,40 @@ __device__ __forceinline__ void psi_uv(const Moments& m, double o[4])
     o[3] = 0.5 * (m.u[A + 2] * m.v[B] + m.u[A] * m.v[B + 2] + base * m.x1);
 }
 
-// <u^A v^B psi (a . psi)>
-template <int A, int B>
-__device__ __forceinline__ void a_psi_uv(const Moments& m, const double a[4], double o[4])
+// <psi u^A (u (a1 . psi) + v (a2 . psi))> for a Maxwellian, with a . psi =
+// a0 + a1 u + a2 v + a3 (u^2 + v^2 + xi^2)/2: the slope terms of the half-line
+// moments (A = 1: the flux part, A = 0: the interface-state part).  The
+// polynomial in the bracket, times u^A, is grouped by powers of v,
+//   v^0: a1_0 u + a1_1 u^2 + h1 u^3  (+ h1 u xi^2),  v^1: a2_0 + c12 u + h2 u^2  (+ h2 xi^2),
+//   v^2: a2_2 + h1 u,                v^3: h2,
+// (h = a_3/2, c12 = a1_2 + a2_1), so each psi component is a short sum of
+// products of the factorised u-, v- and xi-moments.
+template <int A>
+__device__ __forceinline__ void q_moments(const Moments& m, const double a1[4], const double a2[4], double o[4])
 {
-    double t0[4], t1[4], t2[4], t3[4], t4[4];
-    psi_uv<A, B>(m, t0);
-    psi_uv<A + 1, B>(m, t1);
-    psi_uv<A, B + 1>(m, t2);
-    psi_uv<A + 2, B>(m, t3);
-    psi_uv<A, B + 2>(m, t4);
-    // <u^A v^B xi^2 psi>
-    const double base = m.u[A] * m.v[B];
-    const double t5_0 = base * m.x1;
-    const double t5_1 = m.u[A + 1] * m.v[B] * m.x1;
-    const double t5_2 = m.u[A] * m.v[B + 1] * m.x1;
-    const double t5_3 = 0.5 * ((m.u[A + 2] * m.v[B] + m.u[A] * m.v[B + 2]) * m.x1 + base * m.x2);
-    const double h = 0.5 * a[3];
-    o[0] = a[0] * t0[0] + a[1] * t1[0] + a[2] * t2[0] + h * (t3[0] + t4[0] + t5_0);
-    o[1] = a[0] * t0[1] + a[1] * t1[1] + a[2] * t2[1] + h * (t3[1] + t4[1] + t5_1);
-    o[2] = a[0] * t0[2] + a[1] * t1[2] + a[2] * t2[2] + h * (t3[2] + t4[2] + t5_2);
-    o[3] = a[0] * t0[3] + a[1] * t1[3] + a[2] * t2[3] + h * (t3[3] + t4[3] + t5_3);
+    const double h1 = 0.5 * a1[3], h2 = 0.5 * a2[3], c12 = a1[2] + a2[1];
+    // sums over u for the v^j groups at u-shift s (S_j[s]) and the xi^2 parts (Z_j[s])
+    double S0[3], S1[3], S2[3], S3[3], Z0[3], Z1[3];
+#pragma unroll
+    for (int s2 = 0; s2 < 3; ++s2) {
+        S0[s2] = a1[0] * m.u[A + 1 + s2] + a1[1] * m.u[A + 2 + s2] + h1 * m.u[A + 3 + s2];
+        S1[s2] = a2[0] * m.u[A + s2] + c12 * m.u[A + 1 + s2] + h2 * m.u[A + 2 + s2];
+        S2[s2] = a2[2] * m.u[A + s2] + h1 * m.u[A + 1 + s2];
+        S3[s2] = h2 * m.u[A + s2];
+        Z0[s2] = h1 * m.u[A + 1 + s2];
+        Z1[s2] = h2 * m.u[A + s2];
+    }
+    const double x1 = m.x1, x2 = m.x2;   // m.v[0] = 1
+    auto sum = [&](int s2, int sh) {     // sum_j v[j+sh] S_j[s2] + x1 (v[sh] Z0[s2] + v[sh+1] Z1[s2])
+        return m.v[sh] * S0[s2] + m.v[sh + 1] * S1[s2] + m.v[sh + 2] * S2[s2] + m.v[sh + 3] * S3[s2]
+               + x1 * (m.v[sh] * Z0[s2] + m.v[sh + 1] * Z1[s2]);
+    };
+    const double plain0 = S0[0] + m.v[1] * S1[0] + m.v[2] * S2[0] + m.v[3] * S3[0];
+    const double xi0 = Z0[0] + m.v[1] * Z1[0];
+    o[0] = plain0 + x1 * xi0;
+    o[1] = sum(1, 0);
+    o[2] = sum(0, 1);
+    o[3] = 0.5 * (sum(2, 0) + sum(0, 2) + x1 * plain0 + x2 * xi0);
 }
 
 // micro-slope coefficients a with <psi psi^T> a = b for a Maxwellian
@@ -518,20 +531,18 @@ __device__ __forceinline__ bool gks_point(const Src& src, const Params& P,
         moments_tail(ml, Ul, Vl, thl, K);
         SlopeCtx sl;
         slope_ctx(Ul, Vl, thl, ithl, K, P.inv_K2, sl);
-        double b1[4], b2[4], a1[4], a2[4], o1[4], o2[4], f[4];
+        double b1[4], b2[4], a1[4], a2[4], o1[4], f[4];
         src.ne_normal(0, b1);
         for (int k = 0; k < 4; ++k) { b1[k] *= irl; b2[k] = Wlt[k] * irl; }
         micro_slope(sl, b1, a1);
         micro_slope(sl, b2, a2);
         psi_uv<1, 0>(ml, f);
-        a_psi_uv<2, 0>(ml, a1, o1);
-        a_psi_uv<1, 1>(ml, a2, o2);
-        for (int k = 0; k < 4; ++k) { Fh[k] = Wl[0] * f[k]; Th[k] = Wl[0] * (o1[k] + o2[k]); }
+        q_moments<1>(ml, a1, a2, o1);
+        for (int k = 0; k < 4; ++k) { Fh[k] = Wl[0] * f[k]; Th[k] = Wl[0] * o1[k]; }
         if (need_ne) {
             psi_uv<0, 0>(ml, f);
-            a_psi_uv<1, 0>(ml, a1, o1);
-            a_psi_uv<0, 1>(ml, a2, o2);
-            for (int k = 0; k < 4; ++k) { Wh[k] = Wl[0] * f[k]; Wsl[k] = Wl[0] * (o1[k] + o2[k]); }
+            q_moments<0>(ml, a1, a2, o1);
+            for (int k = 0; k < 4; ++k) { Wh[k] = Wl[0] * f[k]; Wsl[k] = Wl[0] * o1[k]; }
         }
     }
     {
@@ -542,20 +553,18 @@ __device__ __forceinline__ bool gks_point(const Src& src, const Params& P,
         moments_tail(mr, Ur, Vr, thr, K);
         SlopeCtx sr;
         slope_ctx(Ur, Vr, thr, ithr, K, P.inv_K2, sr);
-        double b1[4], b2[4], a1[4], a2[4], o1[4], o2[4], f[4];
+        double b1[4], b2[4], a1[4], a2[4], o1[4], f[4];
         src.ne_normal(1, b1);
         for (int k = 0; k < 4; ++k) { b1[k] *= irr; b2[k] = Wrt[k] * irr; }
         micro_slope(sr, b1, a1);
         micro_slope(sr, b2, a2);
         psi_uv<1, 0>(mr, f);
-        a_psi_uv<2, 0>(mr, a1, o1);
-        a_psi_uv<1, 1>(mr, a2, o2);
-        for (int k = 0; k < 4; ++k) { Fh[k] += Wr[0] * f[k]; Th[k] += Wr[0] * (o1[k] + o2[k]); }
+        q_moments<1>(mr, a1, a2, o1);
+        for (int k = 0; k < 4; ++k) { Fh[k] += Wr[0] * f[k]; Th[k] += Wr[0] * o1[k]; }
         if (need_ne) {
             psi_uv<0, 0>(mr, f);
-            a_psi_uv<1, 0>(mr, a1, o1);
-            a_psi_uv<0, 1>(mr, a2, o2);
-            for (int k = 0; k < 4; ++k) { Wh[k] += Wr[0] * f[k]; Wsl[k] += Wr[0] * (o1[k] + o2[k]); }
+            q_moments<0>(mr, a1, a2, o1);
+            for (int k = 0; k < 4; ++k) { Wh[k] += Wr[0] * f[k]; Wsl[k] += Wr[0] * o1[k]; }
         }
     }
 
