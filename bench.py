@@ -404,7 +404,8 @@ def run_served(args, world, rank, local):
     plain_s = time.perf_counter() - t0
     # served: submissions at the stream's arrival times (scaled by --arrival-scale)
     srv = cgks.cgks_serve_start(hbm_budget_bytes=120e9, max_active=args.max_active,
-                                steps_per_round=args.steps_per_round)
+                                steps_per_round=args.steps_per_round,
+                                tile_shape=cgks.TILE_SHAPES.index(args.tile) if args.tile else -1)
     ids = []
     t_start = time.perf_counter()
     with ClockSampler(local) as clk:
@@ -428,6 +429,7 @@ def run_served(args, world, rank, local):
                        "stream": "seed 2001, Poisson 50 req/s, N log-uniform 128..2048, steps 100..2000, "
                                  "kinds pulse/vortex/shock-vortex, Mach 1.05..1.5; N and steps divided by scale",
                        "max_active": args.max_active, "steps_per_round": args.steps_per_round,
+                       "tile_shape": args.tile or "autotuned",
                        "cell_updates": work},
             "served": stats, "plain": {"value": work / plain_s, "wall_s": plain_s},
             "served_vs_plain": stats["cell_updates_per_s"] / (work / plain_s), "clocks": clk.summary()}), flush=True)
