@@ -531,18 +531,19 @@ __device__ __forceinline__ bool gks_point(const Src& src, const Params& P,
         moments_tail(ml, Ul, Vl, thl, K);
         SlopeCtx sl;
         slope_ctx(Ul, Vl, thl, ithl, K, P.inv_K2, sl);
-        double b1[4], b2[4], a1[4], a2[4], o1[4], f[4];
+        // micro-slopes of g_l: M^-1 (dW / rho); the 1/rho cancels against the rho in front
+        // of the slope moments, so M^-1 is applied to dW itself
+        double b1[4], a1[4], a2[4], o1[4], f[4];
         src.ne_normal(0, b1);
-        for (int k = 0; k < 4; ++k) { b1[k] *= irl; b2[k] = Wlt[k] * irl; }
         micro_slope(sl, b1, a1);
-        micro_slope(sl, b2, a2);
+        micro_slope(sl, Wlt, a2);
         psi_uv<1, 0>(ml, f);
         q_moments<1>(ml, a1, a2, o1);
-        for (int k = 0; k < 4; ++k) { Fh[k] = Wl[0] * f[k]; Th[k] = Wl[0] * o1[k]; }
+        for (int k = 0; k < 4; ++k) { Fh[k] = Wl[0] * f[k]; Th[k] = o1[k]; }
         if (need_ne) {
             psi_uv<0, 0>(ml, f);
             q_moments<0>(ml, a1, a2, o1);
-            for (int k = 0; k < 4; ++k) { Wh[k] = Wl[0] * f[k]; Wsl[k] = Wl[0] * o1[k]; }
+            for (int k = 0; k < 4; ++k) { Wh[k] = Wl[0] * f[k]; Wsl[k] = o1[k]; }
         }
     }
     {
@@ -553,18 +554,17 @@ __device__ __forceinline__ bool gks_point(const Src& src, const Params& P,
         moments_tail(mr, Ur, Vr, thr, K);
         SlopeCtx sr;
         slope_ctx(Ur, Vr, thr, ithr, K, P.inv_K2, sr);
-        double b1[4], b2[4], a1[4], a2[4], o1[4], f[4];
+        double b1[4], a1[4], a2[4], o1[4], f[4];
         src.ne_normal(1, b1);
-        for (int k = 0; k < 4; ++k) { b1[k] *= irr; b2[k] = Wrt[k] * irr; }
         micro_slope(sr, b1, a1);
-        micro_slope(sr, b2, a2);
+        micro_slope(sr, Wrt, a2);
         psi_uv<1, 0>(mr, f);
         q_moments<1>(mr, a1, a2, o1);
-        for (int k = 0; k < 4; ++k) { Fh[k] += Wr[0] * f[k]; Th[k] += Wr[0] * o1[k]; }
+        for (int k = 0; k < 4; ++k) { Fh[k] += Wr[0] * f[k]; Th[k] += o1[k]; }
         if (need_ne) {
             psi_uv<0, 0>(mr, f);
             q_moments<0>(mr, a1, a2, o1);
-            for (int k = 0; k < 4; ++k) { Wh[k] += Wr[0] * f[k]; Wsl[k] += Wr[0] * o1[k]; }
+            for (int k = 0; k < 4; ++k) { Wh[k] += Wr[0] * f[k]; Wsl[k] += o1[k]; }
         }
     }
 
