@@ -395,13 +395,16 @@ __device__ __forceinline__ void euler_time_derivs(const double W[4], const doubl
                                                   double ir, double U, double V, double p, EulerTD& o)
 {
     const double gm1 = gamma - 1.0;
-    const double rho = W[0], m = W[1], n = W[2], E = W[3];
+    const double rho = W[0], m = W[1], E = W[3];
     // primitive first derivatives
     const double rx = Wx[0], ry = Wy[0];
     const double Ux = (Wx[1] - U * rx) * ir, Uy = (Wy[1] - U * ry) * ir;
     const double Vx = (Wx[2] - V * rx) * ir, Vy = (Wy[2] - V * ry) * ir;
-    const double KEx = 0.5 * (Wx[1] * U + m * Ux + Wx[2] * V + n * Vx);
-    const double KEy = 0.5 * (Wy[1] * U + m * Uy + Wy[2] * V + n * Vy);
+    // kinetic energy KE = rho q^2 / 2: KE_x = u . m_x - rho_x q^2/2,
+    // KE_xx = rho |u_x|^2 + u . m_xx - rho_xx q^2/2, KE_xy = rho u_x . u_y + u . m_xy - rho_xy q^2/2
+    const double hq2 = 0.5 * (U * U + V * V);
+    const double KEx = U * Wx[1] + V * Wx[2] - hq2 * rx;
+    const double KEy = U * Wy[1] + V * Wy[2] - hq2 * ry;
     const double px = gm1 * (Wx[3] - KEx), py = gm1 * (Wy[3] - KEy);
     // primitive second derivatives
     const double rxx = Wxx[0], rxy = Wxy[0], ryy = Wyy[0];
@@ -411,9 +414,9 @@ __device__ __forceinline__ void euler_time_derivs(const double W[4], const doubl
     const double Vxx = (Wxx[2] - 2.0 * Vx * rx - V * rxx) * ir;
     const double Vxy = (Wxy[2] - Vx * ry - Vy * rx - V * rxy) * ir;
     const double Vyy = (Wyy[2] - 2.0 * Vy * ry - V * ryy) * ir;
-    const double KExx = 0.5 * (Wxx[1] * U + 2.0 * Wx[1] * Ux + m * Uxx + Wxx[2] * V + 2.0 * Wx[2] * Vx + n * Vxx);
-    const double KExy = 0.5 * (Wxy[1] * U + Wx[1] * Uy + Wy[1] * Ux + m * Uxy + Wxy[2] * V + Wx[2] * Vy + Wy[2] * Vx + n * Vxy);
-    const double KEyy = 0.5 * (Wyy[1] * U + 2.0 * Wy[1] * Uy + m * Uyy + Wyy[2] * V + 2.0 * Wy[2] * Vy + n * Vyy);
+    const double KExx = rho * (Ux * Ux + Vx * Vx) + U * Wxx[1] + V * Wxx[2] - hq2 * rxx;
+    const double KExy = rho * (Ux * Uy + Vx * Vy) + U * Wxy[1] + V * Wxy[2] - hq2 * rxy;
+    const double KEyy = rho * (Uy * Uy + Vy * Vy) + U * Wyy[1] + V * Wyy[2] - hq2 * ryy;
     const double pxx = gm1 * (Wxx[3] - KExx), pxy = gm1 * (Wxy[3] - KExy), pyy = gm1 * (Wyy[3] - KEyy);
     // first time derivatives
     const double Dv = Ux + Vy;
