@@ -122,6 +122,7 @@ def lib():
             L.oc_face1d_debug.argtypes = [ctypes.POINTER(Problem), dp, ctypes.c_int, ctypes.c_double, dp]
             L.oc_face1d_debug.restype = ctypes.c_int
             L.oc_set_threads.argtypes = [ctypes.c_int]
+            L.oc_step2d_halo.argtypes = [ctypes.POINTER(Problem), dp, ctypes.c_double, EXCHANGE_FN, ctypes.c_void_p]
             _lib = L
     return _lib
 
@@ -247,6 +248,33 @@ def face1d(problem: Problem, W: np.ndarray, f: int, dt: float):
 def cfl_dt(problem: Problem, W: np.ndarray) -> float:
     W = _f64(W)
     return lib().oc_cfl_dt(ctypes.byref(problem), _dp(W))
+
+
+# ----------------------------------------------------------------------------- domain decomposition
+BC_HALO = 4   # oracle-only side type: ghost columns supplied by the caller
+EXCHANGE_FN = ctypes.CFUNCTYPE(None, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                               ctypes.c_void_p)
+
+
+def step2d_halo(problem: Problem, W: np.ndarray, dt: float, exchange):
+    """One S2O4 step of a subdomain whose x-sides may be BC_HALO.
+
+    exchange(stage, state, halo) is called before each stage with the state that stage reads
+    (12, ny, nx) and must fill halo (2 sides, 12 planes, 2 ghost columns, ny): side 0 column m is
+    ghost column -1-m, side 1 column m is ghost column nx+m.  Returns the new state."""
+    nx, ny = problem.nx, problem.ny
+    Wc = _f64(W).copy()
+
+    def cb(stage, state_p, halo_p, ctx):
+        state = np.ctypeslib.as_array(state_p, shape=(12, ny, nx))
+        halo = np.ctypeslib.as_array(halo_p, shape=(2, 12, 2, ny))
+        exchange(stage, state, halo)
+
+    fn = EXCHANGE_FN(cb)
+    st = lib().oc_step2d_halo(ctypes.byref(problem), _dp(Wc), float(dt), fn, None)
+    if st != 0:
+        raise OracleError(f"oracle step failed with status {st}")
+    return Wc
 
 
 # ----------------------------------------------------------------------------- stepping

@@ -69,7 +69,8 @@
 #define OC_E_INVAL 1
 #define OC_E_NONPHYSICAL 5
 
-enum { BC_PERIODIC = 0, BC_REFLECT = 1, BC_INFLOW = 2, BC_OUTFLOW = 3 };
+enum { BC_PERIODIC = 0, BC_REFLECT = 1, BC_INFLOW = 2, BC_OUTFLOW = 3,
+       BC_HALO = 4 /* x-sides only: ghost columns supplied by the caller (domain decomposition) */ };
 
 typedef struct {
     int dim, nx, ny;
@@ -575,8 +576,9 @@ static void prim_to_cons(int D, double gamma, const double *q, double *W)
     else W[2] = q[3] / (gamma - 1.0) + 0.5 * q[0] * q[1] * q[1];
 }
 
-/* E: extended planes [12][(ny+4)][(nx+4)], interior copied from W */
-static void fill_ghosts2d(const oc_problem *P, double *E)
+/* E: extended planes [12][(ny+4)][(nx+4)], interior copied from W.  halo (for
+ * BC_HALO x-sides): [side][12][NG][ny], ghost column -1-m (low) or nx+m (high) */
+static void fill_ghosts2d(const oc_problem *P, double *E, const double *halo)
 {
     int nx = P->nx, ny = P->ny, X = nx + 2 * NG, Y = ny + 2 * NG;
     size_t PL = (size_t)X * Y;
@@ -599,6 +601,7 @@ static void fill_ghosts2d(const oc_problem *P, double *E)
                         int odd = (grp == 0 && var == 1) || (grp == 1 && var != 1) || (grp == 2 && var == 1);
                         if (odd) v = -v;
                     } else if (bc == BC_INFLOW) v = (grp == 0) ? inflow_cons[side][var] : 0.0;
+                    else if (bc == BC_HALO) v = halo[(((size_t)side * 12 + p) * NG + m) * ny + j];
                     else { int src = side ? nx - 1 : 0; v = (grp == 1) ? 0.0 : AT(p, j, src); }
                     AT(p, j, g) = v;
                 }
@@ -1060,7 +1063,11 @@ static int faces2d(const oc_problem *P, const double *E, double dt, face_res *fx
     return err ? OC_E_NONPHYSICAL : OC_OK;
 }
 
-static int step2d(const oc_problem *P, double *W, double dt)
+/* caller-supplied ghost columns of BC_HALO sides: called before each stage with
+ * the state that stage reads (12 planes of nx*ny) and the halo array to fill */
+typedef void (*oc_exchange_fn)(int stage, const double *state, double *halo, void *ctx);
+
+static int step2d_ex(const oc_problem *P, double *W, double dt, oc_exchange_fn fn, void *ctx)
 {
     int nx = P->nx, ny = P->ny, X = nx + 2 * NG, Y = ny + 2 * NG;
     size_t PL = (size_t)nx * ny, EPL = (size_t)X * Y;
@@ -1070,13 +1077,15 @@ static int step2d(const oc_problem *P, double *W, double dt)
     double *R = malloc(12 * PL * sizeof(double));
     face_res *fx = malloc((size_t)(nx + 1) * ny * sizeof(face_res));
     face_res *fy = malloc((size_t)nx * (ny + 1) * sizeof(face_res));
+    double *halo = fn ? calloc((size_t)2 * 12 * NG * ny, sizeof(double)) : NULL;
     int err = 0;
     for (int stage = 0; stage < 2 && !err; ++stage) {
         const double *S = stage ? Ws : W;
         for (int p = 0; p < 12; ++p)
             for (int j = 0; j < ny; ++j)
                 memcpy(&E[p * EPL + (size_t)(j + NG) * X + NG], &S[p * PL + (size_t)j * nx], nx * sizeof(double));
-        fill_ghosts2d(P, E);
+        if (fn) fn(stage, S, halo, ctx);
+        fill_ghosts2d(P, E, halo);
         err = faces2d(P, E, dt, fx, fy);
         if (err) break;
         for (int j = 0; j < ny; ++j)
@@ -1103,8 +1112,21 @@ static int step2d(const oc_problem *P, double *W, double dt)
                     }
                 }
     }
-    free(E); free(Ws); free(R); free(fx); free(fy);
+    free(E); free(Ws); free(R); free(fx); free(fy); free(halo);
     return err;
+}
+
+static int step2d(const oc_problem *P, double *W, double dt) { return step2d_ex(P, W, dt, NULL, NULL); }
+
+/* one S2O4 step of a subdomain whose x-sides may be BC_HALO (its neighbours'
+ * columns, supplied through fn before each stage); dt is the caller's (the
+ * minimum of the subdomains' CFL bounds) */
+int oc_step2d_halo(const oc_problem *P, double *W, double dt, oc_exchange_fn fn, void *ctx)
+{
+    if (P->dim != 2) return OC_E_INVAL;
+    build_coef();
+    build_segfit();
+    return step2d_ex(P, W, dt, fn, ctx) ? OC_E_NONPHYSICAL : OC_OK;
 }
 
 /* ------------------------------------------------------------------ */
