@@ -9,6 +9,8 @@ import socket
 import subprocess
 import sys
 
+import multiprocessing as mp
+
 import pytest
 import torch.multiprocessing as tmp
 
@@ -37,7 +39,7 @@ def _worker(rank, world, port, out):
 
 def test_barrier_max_over_ranks():
     world = 2
-    mgr = tmp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     tmp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
     assert out[0] == out[1] == 13.0

@@ -3,8 +3,10 @@ world size 2) with the oracle: the grid is split in x, each rank steps its half 
 neighbour's two boundary columns (all 12 planes) received before each stage and the time step
 reduced to the minimum over ranks; the result equals the undivided grid bit for bit.  (Every run
 of this library uses one GPU; this pins the exchange pattern the decomposition needs.)"""
+import multiprocessing as mp
 import os
 import socket
+
 
 import numpy as np
 import torch.multiprocessing as tmp
@@ -82,7 +84,7 @@ def test_two_rank_x_split_equals_the_whole_grid():
     ref, _, steps, _ = O.run(O.make_problem(**kw), W, nsteps)
     assert steps == nsteps
     world = 2
-    mgr = tmp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     tmp.spawn(_worker, args=(world, _free_port(), nsteps, out), nprocs=world, join=True)
     parts = [np.frombuffer(out[r], dtype=np.float64).reshape(out["shape%d" % r]) for r in range(world)]
