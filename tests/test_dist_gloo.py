@@ -4,12 +4,11 @@ Every GPU run of this build uses one GPU; with N GPUs bench.py runs one independ
 workload per rank (no collective on the data path) and reduces only the timings: max over ranks.
 """
 import json
+import multiprocessing as mp
 import os
 import socket
 import subprocess
 import sys
-
-import multiprocessing as mp
 
 import pytest
 import torch.multiprocessing as tmp

@@ -7,7 +7,6 @@ import multiprocessing as mp
 import os
 import socket
 
-
 import numpy as np
 import torch.multiprocessing as tmp
 
