@@ -38,17 +38,17 @@ UNIT = "cell-updates/s"
 # Algorithmic FP64 operations per cell and stage (FMA = 2), measured with ncu op counts on the 256^2
 # vortex, where every kernel does exactly the method's work (no halo recomputation, every face once):
 # two face-row records (1,888 each: linear P7 + WENO-Z pair of 4 variables), two face segments
-# (3,348.4 in stage 1, 3,138.4 in stage 2: two Gauss points each) and the update (80 / 121):
+# (3,310.4 in stage 1, 3,100.4 in stage 2: two Gauss points each) and the update (80 / 121):
 # profiles/stage_kernels_flops_vortex256.md.
 RECORD_FLOP_PER_CELL = 3776.0
-FLUX_FLOP_PER_CELL = {1: 6697.0, 2: 6277.0}
+FLUX_FLOP_PER_CELL = {1: 6621.0, 2: 6201.0}
 UPDATE_FLOP_PER_CELL = {1: 80.0, 2: 121.0}
 FLOP_PER_CELL = {s: RECORD_FLOP_PER_CELL + FLUX_FLOP_PER_CELL[s] + UPDATE_FLOP_PER_CELL[s] for s in (1, 2)}
 DEFAULT_TILE = "16x16"    # the library's 2D default
 # DRAM bytes (read + write) per cell of one flux-kernel launch with 16x16 tiles, ncu
 # dram__bytes_{read,write}.sum on the 1024^2 vortex (records and state larger than L2) divided by the
 # cells; the 2048^2 bench grid moves the same bytes per cell: profiles/flux_kernels_ncu_vortex1024.md.
-FLUX_DRAM_BYTES_PER_CELL = {1: 731.60e6 / 1048576, 2: 596.03e6 / 1048576}
+FLUX_DRAM_BYTES_PER_CELL = {1: 733.87e6 / 1048576, 2: 601.71e6 / 1048576}
 # algorithmic bytes per cell of the flux kernel: the two face rows' records (2 x 28 doubles) read and
 # the two faces' results written (stage 1: 16 doubles each, stage 2: 8)
 FLUX_ALGO_BYTES_PER_CELL = {1: 448 + 256, 2: 448 + 128}
