@@ -11,6 +11,8 @@ module only compiles it and marshals numpy arrays through ctypes.
 
 Parity status of each oracle function (pins in ``tests/test_oracle_*.py``):
   linear reconstruction (Sec. 3.2)        pinned: polynomial exactness, degree <= 7
+  6th-order variant (named in Sec. 3.2)   pinned: exactness to degree 5, weights recover the
+                                          degree-5 fit from the printed q_k, design order 6
   candidate polynomials q_k (Sec. 3.3)    pinned: the paper's printed q_k, d_k
   WENO-Z weights, beta_k, Z_ref           pinned: beta by quadrature, recovery of P7
   Maxwellian moments (Sec. 2.1)           pinned: Gauss-Hermite / adaptive quadrature
@@ -47,7 +49,7 @@ class Problem(ctypes.Structure):
         ("gamma", ctypes.c_double), ("cfl", ctypes.c_double),
         ("bc", ctypes.c_int * 4), ("inflow", (ctypes.c_double * 4) * 4),
         ("eps_tau", ctypes.c_double), ("c_tau", ctypes.c_double), ("weno_eps", ctypes.c_double),
-        ("mu", ctypes.c_double), ("recon_vars", ctypes.c_int),
+        ("mu", ctypes.c_double), ("recon_vars", ctypes.c_int), ("order", ctypes.c_int),
     ]
 
 
@@ -63,7 +65,7 @@ def inflow_sides(inflow):
 
 
 def make_problem(dim, nx, ny, dx, dy, gamma=1.4, cfl=0.5, bc=(0, 0, 0, 0), inflow=(1.0, 0.0, 0.0, 1.0),
-                 eps_tau=0.01, c_tau=1.0, weno_eps=1e-6, mu=0.0, recon_vars=0) -> Problem:
+                 eps_tau=0.01, c_tau=1.0, weno_eps=1e-6, mu=0.0, recon_vars=0, order=8) -> Problem:
     p = Problem()
     p.dim, p.nx, p.ny = int(dim), int(nx), int(ny)
     p.dx, p.dy = float(dx), float(dy)
@@ -76,6 +78,7 @@ def make_problem(dim, nx, ny, dx, dy, gamma=1.4, cfl=0.5, bc=(0, 0, 0, 0), inflo
     p.eps_tau, p.c_tau, p.weno_eps = float(eps_tau), float(c_tau), float(weno_eps)
     p.mu = float(mu)
     p.recon_vars = int(recon_vars)
+    p.order = int(order)
     return p
 
 
@@ -103,6 +106,10 @@ def lib():
             L.oc_linear_recon.argtypes = [dp, dp, dp]
             L.oc_weno_left.argtypes = [dp, ctypes.c_double, dp, dp, dp]
             L.oc_weno_right.argtypes = [dp, ctypes.c_double, dp, dp]
+            L.oc_linear_recon_order.argtypes = [ctypes.c_int, dp, dp, dp]
+            L.oc_weno_left_order.argtypes = [ctypes.c_int, dp, ctypes.c_double, dp, dp, dp]
+            L.oc_weno_right_order.argtypes = [ctypes.c_int, dp, ctypes.c_double, dp, dp]
+            L.oc_linear_weights.argtypes = [ctypes.c_int, dp]
             L.oc_poly_coef_matrix.argtypes = [ctypes.c_int, dp]
             L.oc_char_basis.argtypes = [ctypes.c_int, ctypes.c_double, dp, dp, dp]
             L.oc_tang_weno.argtypes = [ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, dp, dp, dp]
@@ -140,27 +147,38 @@ class OracleError(RuntimeError):
 
 
 # ----------------------------------------------------------------------------- pieces
-def linear_recon(Q, hQp):
-    """Sec. 3.2: (P7, h P7_x, h^2 P7_xx) at x_{i+1/2}."""
+def linear_recon(Q, hQp, order=8):
+    """Sec. 3.2: (P7, h P7_x, h^2 P7_xx) at x_{i+1/2}; order=6: the same from the degree-5 fit
+    of the compact 6th-order variant."""
     Q, hQp, out = _f64(Q), _f64(hQp), np.zeros(3)
-    lib().oc_linear_recon(_dp(Q), _dp(hQp), _dp(out))
+    if order == 8:
+        lib().oc_linear_recon(_dp(Q), _dp(hQp), _dp(out))
+    else:
+        lib().oc_linear_recon_order(int(order), _dp(Q), _dp(hQp), _dp(out))
     return out
 
 
-def weno_left(s, eps=1e-6, diag=False):
+def linear_weights(order=8):
+    """Sec. 3.3: the linear weights d_k of the candidates q_0..q_6 for the given order."""
+    out = np.zeros(7)
+    lib().oc_linear_weights(int(order), _dp(out))
+    return out
+
+
+def weno_left(s, eps=1e-6, diag=False, order=8):
     """Sec. 3.3: left value and h*slope at x_{i+1/2} from s = (Q_{i-1..i+2}, hQ'_{i-1..i+2})."""
     s = _f64(s)
     v, sl, d = np.zeros(1), np.zeros(1), np.zeros(28)
-    lib().oc_weno_left(_dp(s), eps, _dp(v), _dp(sl), _dp(d))
+    lib().oc_weno_left_order(int(order), _dp(s), eps, _dp(v), _dp(sl), _dp(d))
     if diag:
         return v[0], sl[0], dict(q=d[0:7].copy(), qs=d[7:14].copy(), beta=d[14:21].copy(), delta=d[21:28].copy())
     return v[0], sl[0]
 
 
-def weno_right(s, eps=1e-6):
+def weno_right(s, eps=1e-6, order=8):
     s = _f64(s)
     v, sl = np.zeros(1), np.zeros(1)
-    lib().oc_weno_right(_dp(s), eps, _dp(v), _dp(sl))
+    lib().oc_weno_right_order(int(order), _dp(s), eps, _dp(v), _dp(sl))
     return v[0], sl[0]
 
 

@@ -54,6 +54,11 @@
  *   - 1D uses K = (3-gamma)/(gamma-1) internal degrees of freedom
  *   - characteristic reconstruction (optional): eigenvectors of the normal flux
  *     Jacobian at the mean of the two cells sharing the face
+ *   - compact 6th-order variant (optional; Sec. 3.2 names it without printing
+ *     it): the linear reconstruction is the degree-5 polynomial fixed by the
+ *     four cell averages and the two slopes Q'_i, Q'_i+1 next to the face; the
+ *     nonlinear one keeps the candidates q_0..q_6 with the linear weights that
+ *     recombine them into that polynomial's interface value
  *   - CFL: dt = CFL * min_cells min(dx/(|U|+c), dy/(|V|+c)); with viscosity the
  *     signal speed is |U|+c+2 nu/dx (nu = mu/rho)
  *
@@ -81,7 +86,10 @@ typedef struct {
     double eps_tau, c_tau, weno_eps;
     double mu;          /* > 0: viscous collision time mu/p (Sec. 4) */
     int recon_vars;     /* nonlinear reconstruction in 0: conservative, 1: characteristic variables */
+    int order;          /* 6: compact 6th-order variant; anything else: the 8th-order scheme */
 } oc_problem;
+
+static int recon_order(const oc_problem *P) { return P->order == 6 ? 6 : 8; }
 
 /* ------------------------------------------------------------------ */
 /* Sec. 3.2, Eq. (recons-8th-val): linear compact 8th-order reconstruction
@@ -124,6 +132,16 @@ static const poly_def POLY_DEFS[NPOLY] = {
  * a linear combination of the 8 stencil data                              */
 static double COEF[NPOLY][MAXDEG + 1][8];
 static int COEF_READY = 0;
+
+/* Compact 6th-order variant (Sec. 3.2 names it; its formulas are not printed).
+ * Reading: the degree-5 polynomial whose averages over I_i-1..I_i+2 are
+ * Q_i-1..Q_i+2 and whose cell-averaged slopes over I_i and I_i+1 are Q'_i and
+ * Q'_i+1 -- the same stencil as P7 without the two outer slopes.
+ * LIN6[r][s]: h^r times the r-th derivative of that polynomial at x_{i+1/2},
+ * as the weight of stencil datum s (r = 0, 1, 2).                           */
+static const int LIN6_KIND[6] = {0, 0, 0, 0, 1, 1};
+static const int LIN6_CELL[6] = {-1, 0, 1, 2, 0, 1};
+static double LIN6[3][8];
 
 static double ipow(double x, int m) { double r = 1.0; for (int k = 0; k < m; ++k) r *= x; return r; }
 
@@ -171,6 +189,25 @@ static void build_coef(void)
             solve_dense(n, A, b);
             for (int m = 0; m < n; ++m) COEF[p][m][sidx] = b[m];
         }
+    }
+    /* the degree-5 fit of the 6th-order variant, solved per datum the same way */
+    for (int sidx = 0; sidx < 8; ++sidx) {
+        double A[36], b[6];
+        for (int r = 0; r < 6; ++r) {
+            double lo = LIN6_CELL[r] - 0.5, hi = LIN6_CELL[r] + 0.5;
+            for (int m = 0; m < 6; ++m) {
+                if (LIN6_KIND[r] == 0) A[r * 6 + m] = (ipow(hi, m + 1) - ipow(lo, m + 1)) / (m + 1);
+                else A[r * 6 + m] = ipow(hi, m) - ipow(lo, m);
+            }
+            int datum = (LIN6_KIND[r] == 0 ? 0 : 4) + LIN6_CELL[r] + 1;
+            b[r] = (datum == sidx) ? 1.0 : 0.0;
+        }
+        solve_dense(6, A, b);
+        double v = 0.0, d1 = 0.0, d2 = 0.0;
+        for (int m = 0; m < 6; ++m) v += b[m] * ipow(0.5, m);
+        for (int m = 1; m < 6; ++m) d1 += m * b[m] * ipow(0.5, m - 1);
+        for (int m = 2; m < 6; ++m) d2 += m * (m - 1) * b[m] * ipow(0.5, m - 2);
+        LIN6[0][sidx] = v; LIN6[1][sidx] = d1; LIN6[2][sidx] = d2;
     }
     COEF_READY = 1;
 }
@@ -226,10 +263,41 @@ void oc_poly_coef_matrix(int p, double out[(MAXDEG + 1) * 8])
 /* Sec. 3.3: linear weights d^8_k */
 static const double DLIN[7] = {3.0 / 98.0, 5.0 / 98.0, 4.0 / 49.0, 7.0 / 98.0, 7.0 / 98.0, 17.0 / 49.0, 17.0 / 49.0};
 
-/* Sec. 3.3: left value at x_{i+1/2} and its scaled slope h*dQ/dx.
- * diag (may be NULL): q[7], qs[7], beta[7], delta[7]                    */
-void oc_weno_left(const double s[8], double eps, double *val, double *hslope, double *diag)
+/* Linear weights of the 6th-order variant (not printed).  Reading: the d_k
+ * for which sum_k d_k q_k(x_{i+1/2}) is the interface value of the degree-5
+ * fit above for all data.  That fixes every weight but the split between q_1
+ * and q_3 (equal point values, different indicators); the split is the one
+ * the printed d^8 has: q_0 and q_1 combine into the mirror image of q_2
+ * (d_0 + d_1 = d_2, d_0 : d_1 = 3 : 5), d_3 = d_4, d_5 = d_6.               */
+static const double DLIN6[7] = {3.0 / 70.0, 5.0 / 70.0, 8.0 / 70.0, 7.0 / 70.0, 7.0 / 70.0, 20.0 / 70.0, 20.0 / 70.0};
+
+static const double *linear_weights(int order) { return order == 6 ? DLIN6 : DLIN; }
+
+/* exported for the pin tests */
+void oc_linear_weights(int order, double out[7])
 {
+    const double *d = linear_weights(order);
+    for (int k = 0; k < 7; ++k) out[k] = d[k];
+}
+
+/* linear reconstruction of either order: out = (P, h P_x, h^2 P_xx) at x_{i+1/2} */
+void oc_linear_recon_order(int order, const double Q[4], const double hQp[4], double out[3])
+{
+    if (order != 6) { oc_linear_recon(Q, hQp, out); return; }
+    build_coef();
+    for (int r = 0; r < 3; ++r) {
+        double acc = 0.0;
+        for (int c = 0; c < 4; ++c) acc += LIN6[r][c] * Q[c] + LIN6[r][4 + c] * hQp[c];
+        out[r] = acc;
+    }
+}
+
+/* Sec. 3.3: left value at x_{i+1/2} and its scaled slope h*dQ/dx with the
+ * linear weights of the given order.
+ * diag (may be NULL): q[7], qs[7], beta[7], delta[7]                    */
+void oc_weno_left_order(int order, const double s[8], double eps, double *val, double *hslope, double *diag)
+{
+    const double *dlin = linear_weights(order);
     build_coef();
     double q[7], qs[7], beta[7], c[MAXDEG + 1];
     for (int k = 0; k < 7; ++k) {
@@ -244,7 +312,7 @@ void oc_weno_left(const double s[8], double eps, double *val, double *hslope, do
     double Z = fabs(3.0 * (beta[0] - beta[4]) + (beta[4] - beta[3]));
     /* Eq. (WENO-Z-w) */
     double alpha[7], asum = 0.0;
-    for (int k = 0; k < 7; ++k) { alpha[k] = DLIN[k] * (1.0 + Z / (beta[k] + eps)); asum += alpha[k]; }
+    for (int k = 0; k < 7; ++k) { alpha[k] = dlin[k] * (1.0 + Z / (beta[k] + eps)); asum += alpha[k]; }
     double v = 0.0, sl = 0.0, delta[7];
     for (int k = 0; k < 7; ++k) { delta[k] = alpha[k] / asum; v += delta[k] * q[k]; sl += delta[k] * qs[k]; }
     *val = v; *hslope = sl;
@@ -254,12 +322,23 @@ void oc_weno_left(const double s[8], double eps, double *val, double *hslope, do
 }
 
 /* right value at x_{i+1/2}: the left procedure on the mirrored stencil */
-void oc_weno_right(const double s[8], double eps, double *val, double *hslope)
+void oc_weno_right_order(int order, const double s[8], double eps, double *val, double *hslope)
 {
     double m[8] = {s[3], s[2], s[1], s[0], -s[7], -s[6], -s[5], -s[4]};
     double v, sl;
-    oc_weno_left(m, eps, &v, &sl, NULL);
+    oc_weno_left_order(order, m, eps, &v, &sl, NULL);
     *val = v; *hslope = -sl;
+}
+
+/* the 8th-order scheme of the paper */
+void oc_weno_left(const double s[8], double eps, double *val, double *hslope, double *diag)
+{
+    oc_weno_left_order(8, s, eps, val, hslope, diag);
+}
+
+void oc_weno_right(const double s[8], double eps, double *val, double *hslope)
+{
+    oc_weno_right_order(8, s, eps, val, hslope);
 }
 
 /* ------------------------------------------------------------------ */
@@ -748,8 +827,8 @@ static void weno_row(const oc_problem *P, int D, double Q[4][4], double hQp[4][4
         for (int k = 0; k < nv; ++k) {
             double s[8];
             for (int c = 0; c < 4; ++c) { s[c] = Q[k][c]; s[4 + c] = hQp[k][c]; }
-            oc_weno_left(s, P->weno_eps, &vl[k], &sl[k], NULL);
-            oc_weno_right(s, P->weno_eps, &vr[k], &sr[k]);
+            oc_weno_left_order(recon_order(P), s, P->weno_eps, &vl[k], &sl[k], NULL);
+            oc_weno_right_order(recon_order(P), s, P->weno_eps, &vr[k], &sr[k]);
         }
         return;
     }
@@ -764,8 +843,8 @@ static void weno_row(const oc_problem *P, int D, double Q[4][4], double hQp[4][4
             for (int k = 0; k < nv; ++k) { a += L[m * nv + k] * Q[k][c]; b += L[m * nv + k] * hQp[k][c]; }
             s[c] = a; s[4 + c] = b;
         }
-        oc_weno_left(s, P->weno_eps, &cvl[m], &csl[m], NULL);
-        oc_weno_right(s, P->weno_eps, &cvr[m], &csr[m]);
+        oc_weno_left_order(recon_order(P), s, P->weno_eps, &cvl[m], &csl[m], NULL);
+        oc_weno_right_order(recon_order(P), s, P->weno_eps, &cvr[m], &csr[m]);
     }
     for (int k = 0; k < nv; ++k) {
         vl[k] = sl[k] = vr[k] = sr[k] = 0.0;
@@ -789,7 +868,7 @@ static int face1d(const oc_problem *P, const double *E, int f, double dt, face_r
             Q[k][c] = E[k * X + cell + NG];
             hQp[k][c] = h * E[(3 + k) * X + cell + NG];
         }
-        oc_linear_recon(Q[k], hQp[k], lin);
+        oc_linear_recon_order(recon_order(P), Q[k], hQp[k], lin);
         in.W0[k] = lin[0]; in.W0n[k] = lin[1] / h; in.W0nn[k] = lin[2] / (h * h);
     }
     weno_row(P, 1, Q, hQp, vl, sl, vr, sr);
@@ -876,7 +955,7 @@ static void row_recon(const oc_problem *P, const double *E, int o, int f, int r,
             Q[k][c] = ext_at(P, E, pv, j, i);
             hQp[k][c] = h * ext_at(P, E, 4 * gn + pv, j, i);
         }
-        oc_linear_recon(Q[k], hQp[k], lin);
+        oc_linear_recon_order(recon_order(P), Q[k], hQp[k], lin);
         out->V[k] = lin[0]; out->N[k] = lin[1] / h; out->NN[k] = lin[2] / (h * h);
     }
     weno_row(P, 2, Q, hQp, vl, sl, vr, sr);

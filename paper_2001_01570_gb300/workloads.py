@@ -52,6 +52,7 @@ class ProblemSpec:
     weno_eps: float = 1e-6
     mu: float = 0.0
     recon_vars: int = 0          # nonlinear reconstruction: 0 conservative, 1 characteristic
+    order: int = 8               # 8: the paper's compact 8th-order scheme; 6: compact 6th-order variant
     name: str = ""
     extra: dict = field(default_factory=dict)
 
@@ -71,7 +72,7 @@ class ProblemSpec:
         return dict(dim=self.dim, nx=self.nx, ny=self.ny if self.dim == 2 else 1, dx=self.dx, dy=self.dy,
                     gamma=self.gamma, cfl=self.cfl, bc=tuple(self.bc), inflow=tuple(self.inflow),
                     eps_tau=self.eps_tau, c_tau=self.c_tau, weno_eps=self.weno_eps, mu=self.mu,
-                    recon_vars=self.recon_vars)
+                    recon_vars=self.recon_vars, order=self.order)
 
 
 def prim_to_cons(rho, u, v, p, gamma):
