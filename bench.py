@@ -7,7 +7,8 @@ CFL 0.5), synthetic initial data, state (3 x 12 planes, 1.2 GB) resident in HBM 
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cgks|reference] [--workload NAME]
 
-Other workloads: vortex256/512/1024, shockvortex1024x512 (plain sweep), batched256 (256 uneven 2D
+Other workloads: vortex256/512/1024, shockvortex1024x512 (plain sweep; --order 6 runs the compact
+6th-order variant of the reconstruction instead), batched256 (256 uneven 2D
 grids, batched persistent launch vs one grid per launch), acoustic1d (2048 copies of the 1D
 acoustic-wave test, 12-48 cells each, batched vs plain), served (the Poisson request stream
 through the continuous-batching server).
@@ -40,10 +41,12 @@ UNIT = "cell-updates/s"
 # two face-row records (1,888 each: linear P7 + WENO-Z pair of 4 variables), two face segments
 # (3,310.4 in stage 1, 3,100.4 in stage 2: two Gauss points each) and the update (80 / 121):
 # profiles/stage_kernels_flops_vortex256.md.
-RECORD_FLOP_PER_CELL = 3776.0
+# The compact 6th-order variant (--order 6) changes only the record kernel's linear reconstruction:
+# 1,840 per face row with WENO-Z (same ncu count, 256^2 vortex with --order 6).
+RECORD_FLOP_PER_CELL = {8: 3776.0, 6: 3680.0}
 FLUX_FLOP_PER_CELL = {1: 6621.0, 2: 6201.0}
 UPDATE_FLOP_PER_CELL = {1: 80.0, 2: 121.0}
-FLOP_PER_CELL = {s: RECORD_FLOP_PER_CELL + FLUX_FLOP_PER_CELL[s] + UPDATE_FLOP_PER_CELL[s] for s in (1, 2)}
+FLOP_PER_CELL = {s: RECORD_FLOP_PER_CELL[8] + FLUX_FLOP_PER_CELL[s] + UPDATE_FLOP_PER_CELL[s] for s in (1, 2)}
 DEFAULT_TILE = "16x16"    # the library's 2D default
 # DRAM bytes (read + write) per cell of one flux-kernel launch with 16x16 tiles, ncu
 # dram__bytes_{read,write}.sum on the 1024^2 vortex (records and state larger than L2) divided by the
@@ -145,12 +148,13 @@ def barrier_max(world, value):
     return float(t.item())
 
 
-def oracle_sample(seconds_target=12.0, n=96, threads=None):
+def oracle_sample(seconds_target=12.0, n=96, threads=None, order=8):
     """Time the CPU oracle (as it stands) on a bounded sample of the vortex workload: the same
     initial condition on an n x n grid (cost per cell-update is independent of grid size)."""
     import oracle as O
     from paper_2001_01570_gb300 import workloads as wl
     spec, W = wl.isentropic_vortex(n)
+    spec.order = order
     P = O.make_problem(**spec.as_kwargs())
     cores = threads or os.cpu_count()
     os.environ["OMP_NUM_THREADS"] = str(cores)
@@ -165,13 +169,14 @@ def oracle_sample(seconds_target=12.0, n=96, threads=None):
             break
     rate = n * n * steps / el
     return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"isentropic vortex {n}x{n} periodic, {steps} steps ({el:.1f} s), OpenMP over rows"}
+            "sample": f"isentropic vortex {n}x{n} periodic{'' if order == 8 else ', 6th-order variant'}, "
+                      f"{steps} steps ({el:.1f} s), OpenMP over rows"}
 
 
 def run_reference(args, world, rank):
     if rank != 0:
         return
-    cb = oracle_sample(seconds_target=max(5.0, min(20.0, 2.0 * args.steps)))
+    cb = oracle_sample(seconds_target=max(5.0, min(20.0, 2.0 * args.steps)), order=args.order)
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -190,6 +195,7 @@ def run_cgks(args, world, rank, local):
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
     spec, W = workloads()[args.workload]()
+    spec.order = args.order
     cells = spec.cells
     solver = cgks.Solver(cgks.problem_from_spec(spec), stream=stream.cuda_stream)
     if args.tile:
@@ -224,7 +230,9 @@ def run_cgks(args, world, rank, local):
     # stage_ms: begin, stage-1 records, flux, update, stage-2 records, flux, update, end
     flux_ms, rec_ms, upd_ms = stage_ms[2], stage_ms[1], stage_ms[3]
     achieved = FLUX_FLOP_PER_CELL[1] * cells / (flux_ms * 1e-3) / 1e12
-    stage1 = FLOP_PER_CELL[1] * cells / ((flux_ms + rec_ms + upd_ms) * 1e-3) / 1e12
+    rec_flop = RECORD_FLOP_PER_CELL[args.order]
+    stage1_flop = None if rec_flop is None else rec_flop + FLUX_FLOP_PER_CELL[1] + UPDATE_FLOP_PER_CELL[1]
+    stage1 = None if stage1_flop is None else stage1_flop * cells / ((flux_ms + rec_ms + upd_ms) * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS,
                 "traffic": FLUX_DRAM_BYTES_PER_CELL[1] * cells if tile == DEFAULT_TILE else None,
@@ -233,8 +241,8 @@ def run_cgks(args, world, rank, local):
                 "kernel": f"stage_kernel<{tile},1>", "kernel_ms": flux_ms,
                 "stage1_records_plus_flux": {"kernels": "records_kernel<1,0> + stage_kernel<%s,1> + update_kernel<1>" % tile,
                                              "ms": flux_ms + rec_ms + upd_ms, "achieved": stage1,
-                                             "frac": stage1 / FP64_PEAK_TFLOPS,
-                                             "algorithmic_flop_per_cell": FLOP_PER_CELL[1],
+                                             "frac": None if stage1 is None else stage1 / FP64_PEAK_TFLOPS,
+                                             "algorithmic_flop_per_cell": stage1_flop,
                                              "state_algorithmic_bytes": 288 * cells},
                 "peak_source": "measured FP64 DFMA loop (FMA=2) on GB300, of measured"}
 
@@ -256,12 +264,13 @@ def run_cgks(args, world, rank, local):
     solver.close()
     if rank != 0:
         return
-    cpu = None if args.no_cpu_baseline or world > 1 else oracle_sample()
+    cpu = None if args.no_cpu_baseline or world > 1 else oracle_sample(order=args.order)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "cells": cells, "grid": [spec.nx, spec.ny],
+        "config": {"workload": args.workload + ("" if args.order == 8 else " (compact 6th-order variant)"),
+                   "order": args.order, "cells": cells, "grid": [spec.nx, spec.ny],
                    "cfl": spec.cfl, "l2": "inputs larger than L2 (3 x 12 planes resident, %.2f GB)" % (36 * cells * 8 / 1e9),
                    "parallelism": "one grid per GPU (independent replicas)" if world > 1 else "single GPU"},
         "roofline": roofline,
@@ -444,6 +453,8 @@ def main():
     ap.add_argument("--workload", default="vortex2048")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", default=None, help="tile shape of the plain path (e.g. 16x7, 24x8)")
+    ap.add_argument("--order", type=int, default=8, choices=[8, 6],
+                    help="plain sweeps: 8 = the paper's scheme, 6 = its compact 6th-order variant")
     ap.add_argument("--grids", type=int, default=None)
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--served-scale", type=float, default=8.0)

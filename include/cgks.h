@@ -90,6 +90,14 @@ typedef struct {
                                 1: characteristic variables of the normal flux Jacobian at the
                                 mean of the two cells sharing the face (Sec. 3.2 allows either;
                                 the linear reconstruction is the same in both) */
+    int order;               /* spatial order of the compact reconstruction: 0 or 8 selects the
+                                paper's 8th-order scheme (Sec. 3.2-3.3); 6 the compact 6th-order
+                                variant that Sec. 3.2 names without printing: the linear
+                                reconstruction is the degree-5 polynomial fixed by the four cell
+                                averages and the slopes of the two cells next to the face, and
+                                the WENO-Z step keeps the candidates q_0..q_6 with the linear
+                                weights d = (3, 5, 8, 7, 7, 20, 20)/70 that recombine them into
+                                that polynomial's interface value */
 } cgks_problem;
 
 typedef struct cgks_solver cgks_solver;   /* opaque; owns the device planes of one grid */

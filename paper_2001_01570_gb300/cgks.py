@@ -33,7 +33,7 @@ class cgks_problem(ctypes.Structure):
         ("gamma", ctypes.c_double), ("cfl", ctypes.c_double),
         ("bc", ctypes.c_int * 4), ("inflow", (ctypes.c_double * 4) * 4),
         ("eps_tau", ctypes.c_double), ("c_tau", ctypes.c_double), ("weno_eps", ctypes.c_double),
-        ("mu", ctypes.c_double), ("recon_vars", ctypes.c_int),
+        ("mu", ctypes.c_double), ("recon_vars", ctypes.c_int), ("order", ctypes.c_int),
     ]
 
 
@@ -126,7 +126,8 @@ def inflow_sides(inflow):
 
 
 def make_problem(dim, nx, ny, x0, x1, y0=0.0, y1=1.0, gamma=1.4, cfl=0.5, bc=(0, 0, 0, 0),
-                 inflow=(1.0, 0.0, 0.0, 1.0), eps_tau=0.01, c_tau=1.0, weno_eps=1e-6, mu=0.0, recon_vars=0) -> cgks_problem:
+                 inflow=(1.0, 0.0, 0.0, 1.0), eps_tau=0.01, c_tau=1.0, weno_eps=1e-6, mu=0.0, recon_vars=0,
+                 order=8) -> cgks_problem:
     p = cgks_problem()
     p.dim, p.nx, p.ny = int(dim), int(nx), int(ny)
     p.x0, p.x1, p.y0, p.y1 = float(x0), float(x1), float(y0), float(y1)
@@ -139,6 +140,7 @@ def make_problem(dim, nx, ny, x0, x1, y0=0.0, y1=1.0, gamma=1.4, cfl=0.5, bc=(0,
     p.eps_tau, p.c_tau, p.weno_eps = float(eps_tau), float(c_tau), float(weno_eps)
     p.mu = float(mu)
     p.recon_vars = int(recon_vars)
+    p.order = int(order)
     return p
 
 
@@ -146,7 +148,7 @@ def problem_from_spec(spec) -> cgks_problem:
     """From a workloads.ProblemSpec."""
     return make_problem(spec.dim, spec.nx, spec.ny if spec.dim == 2 else 1, spec.x0, spec.x1, spec.y0, spec.y1,
                         spec.gamma, spec.cfl, spec.bc, spec.inflow, spec.eps_tau, spec.c_tau, spec.weno_eps,
-                        getattr(spec, "mu", 0.0), getattr(spec, "recon_vars", 0))
+                        getattr(spec, "mu", 0.0), getattr(spec, "recon_vars", 0), getattr(spec, "order", 8))
 
 
 # ---------------------------------------------------------------------------- C-ABI names

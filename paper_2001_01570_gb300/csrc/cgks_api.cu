@@ -85,6 +85,7 @@ cgks_status validate(const cgks_problem* p)
     if (!(p->eps_tau >= 0.0) || !(p->c_tau >= 0.0) || !(p->weno_eps > 0.0) || !(p->mu >= 0.0))
         return fail(CGKS_E_INVAL, "eps_tau, c_tau, mu must be >= 0 and weno_eps > 0");
     if (p->recon_vars != 0 && p->recon_vars != 1) return fail(CGKS_E_INVAL, "recon_vars must be 0 or 1");
+    if (p->order != 0 && p->order != 6 && p->order != 8) return fail(CGKS_E_INVAL, "order must be 0, 6 or 8");
     const int nb = p->dim == 1 ? 2 : 4;
     for (int k = 0; k < nb; ++k) {
         if (p->bc[k] < CGKS_BC_PERIODIC || p->bc[k] > CGKS_BC_OUTFLOW) return fail(CGKS_E_INVAL, "unknown bc");
@@ -214,6 +215,7 @@ cgks_status cgks_create(const cgks_problem* prob, void* cuda_stream, cgks_solver
     G.weno_eps = prob->weno_eps;
     G.mu = prob->mu;
     G.recon_vars = prob->recon_vars;
+    G.order = prob->order == 6 ? 6 : 8;
     for (int side = 0; side < 4; ++side) {
         const double* q = prob->inflow[side];
         const double r = q[0], u = q[1], v = prob->dim == 1 ? 0.0 : q[2], p = q[3];

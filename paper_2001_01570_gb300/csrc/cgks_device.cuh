@@ -79,13 +79,23 @@ __device__ __forceinline__ int map_axis(int i, int n, int bclo, int bchi, int& k
 // ------------------------------------------------------------------------
 // Sec. 3.2, Eq. (recons-8th-val): linear compact reconstruction at x_{i+1/2}
 // from Q_{i-1..i+2} (a, b, c, d) and h*Q' (A, B, C, D).
+// ORDER = 6: the compact 6th-order variant Sec. 3.2 names, read as the
+// degree-5 polynomial with the four cell averages and the cell-averaged
+// slopes of the two cells next to the face (the outer slopes A, D unused).
+template <int ORDER>
 __device__ __forceinline__ void linear_recon(double a, double b, double c, double d,
                                              double A, double B, double C, double D,
                                              double& v, double& hvx, double& h2vxx)
 {
-    v = (25.0 * (a + d) + 185.0 * (b + c) + 6.0 * (A - D) + 102.0 * (B - C)) * (1.0 / 420.0);
-    hvx = (270.0 * (c - b) + 14.0 * (d - a) - 3.0 * (A + D) - 99.0 * (B + C)) * (1.0 / 108.0);
-    h2vxx = (4.0 * ((b + c) - (a + d)) - (A - D) - 9.0 * (B - C)) * 0.25;
+    if constexpr (ORDER == 6) {
+        v = ((a + d) + 29.0 * (b + c)) * (1.0 / 60.0) + 0.2 * (B - C);
+        hvx = (d - a) * (1.0 / 36.0) + 2.25 * (c - b) - (2.0 / 3.0) * (B + C);
+        h2vxx = 0.25 * ((b + c) - (a + d)) - 1.5 * (B - C);
+    } else {
+        v = (25.0 * (a + d) + 185.0 * (b + c) + 6.0 * (A - D) + 102.0 * (B - C)) * (1.0 / 420.0);
+        hvx = (270.0 * (c - b) + 14.0 * (d - a) - 3.0 * (A + D) - 99.0 * (B + C)) * (1.0 / 108.0);
+        h2vxx = (4.0 * ((b + c) - (a + d)) - (A - D) - 9.0 * (B - C)) * 0.25;
+    }
 }
 
 // ------------------------------------------------------------------------
@@ -107,12 +117,15 @@ __device__ __forceinline__ void pair_products(double d1, double d2, double d3, d
     p.CC = C * C; p.CD = C * D; p.Cd2 = C * d2; p.Cd3 = C * d3; p.DD = D * D; p.Dd2 = D * d2; p.Dd3 = D * d3;
 }
 
-// left-biased interface value and h*slope.  The argument order names the
+// left-biased interface value and h*slope with the linear weights of the given
+// order (ORDER = 6: the weights that recombine the candidates into the degree-5
+// interface value, d = (3, 5, 8, 7, 7, 20, 20)/70).  The argument order names the
 // stencil as seen from the side being reconstructed (for the right side the
 // caller passes the mirrored quantities).  Products: (x11, x12, x22, x23, x33)
 // are the difference products in that orientation, (aa, ad1, ad2, ab, bb, bd1,
 // bd2) the products of the two slopes on the near side, (cc, cd, cd2, cd3, dd,
 // dd2, dd3) those on the far side.
+template <int ORDER>
 __device__ __forceinline__ void weno_side(double base, double d1, double d2, double d3,
                                           double A, double B, double C, double D,
                                           double x11, double x12, double x22, double x23, double x33,
@@ -143,8 +156,11 @@ __device__ __forceinline__ void weno_side(double base, double d1, double d2, dou
     // multiplying the numerators by prod_{j != k} e_j: t_k = (e_k + Z) prod_{j != k} e_j,
     // alpha_k proportional to d_k t_k.  The linear weights d_k are folded into the
     // candidate coefficients below where a t_k multiplies a single candidate.
-    constexpr double d0 = 3.0 / 98.0, d1w = 5.0 / 98.0, d2w = 4.0 / 49.0, d3w = 7.0 / 98.0, d4w = 7.0 / 98.0;
-    constexpr double d5 = 17.0 / 49.0, d6 = 17.0 / 49.0;
+    constexpr bool six = ORDER == 6;
+    constexpr double d0 = six ? 3.0 / 70.0 : 3.0 / 98.0, d1w = six ? 5.0 / 70.0 : 5.0 / 98.0;
+    constexpr double d2w = six ? 8.0 / 70.0 : 4.0 / 49.0, d3w = six ? 7.0 / 70.0 : 7.0 / 98.0;
+    constexpr double d4w = six ? 7.0 / 70.0 : 7.0 / 98.0;
+    constexpr double d5 = six ? 20.0 / 70.0 : 17.0 / 49.0, d6 = six ? 20.0 / 70.0 : 17.0 / 49.0;
     const double p01 = e0 * e1, p012 = p01 * e2, p0123 = p012 * e3, p01234 = p0123 * e4;
     const double s56 = e5 * e6, s456 = e4 * s56, s3456 = e3 * s456, s23456 = e2 * s3456;
     const double t0 = (e0 + Z) * (e1 * s23456);
@@ -175,18 +191,19 @@ __device__ __forceinline__ void weno_side(double base, double d1, double d2, dou
 }
 
 // left and right non-equilibrium values and h*slopes at x_{i+1/2}
+template <int ORDER>
 __device__ __forceinline__ void weno_pair(double a, double b, double c, double d, double A, double B, double C,
                                           double D, double eps, double& vl, double& sl, double& vr, double& sr)
 {
     const double d1 = b - a, d2 = c - b, d3 = d - c;
     PairProducts p;
     pair_products(d1, d2, d3, A, B, C, D, p);
-    weno_side(b, d1, d2, d3, A, B, C, D, p.d11, p.d12, p.d22, p.d23, p.d33,
+    weno_side<ORDER>(b, d1, d2, d3, A, B, C, D, p.d11, p.d12, p.d22, p.d23, p.d33,
               p.AA, p.Ad1, p.Ad2, p.AB, p.BB, p.Bd1, p.Bd2, p.CC, p.CD, p.Cd2, p.Cd3, p.DD, p.Dd2, p.Dd3,
               eps, vl, sl);
     // mirrored stencil: (d1,d2,d3) -> -(d3,d2,d1), (A,B,C,D) -> -(D,C,B,A); products unchanged
     double s;
-    weno_side(c, -d3, -d2, -d1, -D, -C, -B, -A, p.d33, p.d23, p.d22, p.d12, p.d11,
+    weno_side<ORDER>(c, -d3, -d2, -d1, -D, -C, -B, -A, p.d33, p.d23, p.d22, p.d12, p.d11,
               p.DD, p.Dd3, p.Dd2, p.CD, p.CC, p.Cd3, p.Cd2, p.BB, p.AB, p.Bd2, p.Bd1, p.AA, p.Ad2, p.Ad1,
               eps, vr, s);
     sr = -s;

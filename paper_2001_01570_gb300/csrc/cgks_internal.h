@@ -29,6 +29,7 @@ struct GridDev {
     double* ws;         // intermediate state W* (12 planes)
     Ctrl* ctrl;
     int nx, ny, dim, recon_vars;
+    int order;          // 8: compact 8th-order reconstruction; 6: the 6th-order variant
     int bc[4];
     double dx, dy, inv_dx, inv_dy;
     double gamma, K, cfl, eps_tau, c_tau, weno_eps;

@@ -127,6 +127,7 @@ cgks_status cgks_step_noalloc(const cgks_problem* prob, double* planes, int nste
         !(prob->cfl > 0.0) || !(prob->eps_tau >= 0.0) || !(prob->c_tau >= 0.0) || !(prob->weno_eps > 0.0) || !(prob->mu >= 0.0))
         return nfail(CGKS_E_INVAL, "bad problem parameters");
     if (prob->recon_vars != 0 && prob->recon_vars != 1) return nfail(CGKS_E_INVAL, "recon_vars must be 0 or 1");
+    if (prob->order != 0 && prob->order != 6 && prob->order != 8) return nfail(CGKS_E_INVAL, "order must be 0, 6 or 8");
     for (int k = 0; k < 4; ++k) {
         if (prob->bc[k] < CGKS_BC_PERIODIC || prob->bc[k] > CGKS_BC_OUTFLOW) return nfail(CGKS_E_INVAL, "unknown bc");
         const int n = k < 2 ? prob->nx : prob->ny;
@@ -173,6 +174,7 @@ cgks_status cgks_step_noalloc(const cgks_problem* prob, double* planes, int nste
     G.weno_eps = prob->weno_eps;
     G.mu = prob->mu;
     G.recon_vars = prob->recon_vars;
+    G.order = prob->order == 6 ? 6 : 8;
     for (int side = 0; side < 4; ++side) {
         const double* q = prob->inflow[side];
         const double r = q[0], u = q[1], v = q[2], p = q[3];

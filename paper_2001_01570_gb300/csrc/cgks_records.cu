@@ -68,8 +68,109 @@ __device__ __forceinline__ RowRef row_ref(const GridDev& G, int r)
     return q;
 }
 
+// Conservative variables: variable k of face row `row`.
+template <int ORDER>
+__device__ __forceinline__ void cons_row(const GridDev& G, const double* __restrict__ src, size_t PL, int row, int k)
+{
+    const RowRef q = row_ref(G, row);
+    const int pv = q.xo ? k : ((k == 1) ? 2 : (k == 2) ? 1 : k);   // face frame: normal momentum first
+    double Q[4], S[4];
+    const int i3 = q.i0 + 3 * q.di, j3 = q.j0 + 3 * q.dj;
+    if (q.i0 >= 0 && q.j0 >= 0 && i3 < G.nx && j3 < G.ny) {
+        // stencil inside the grid: no boundary mapping
+        const double* v = src + (size_t)pv * PL + (size_t)q.j0 * G.nx + q.i0;
+        const double* d = src + (size_t)(q.gn + pv) * PL + (size_t)q.j0 * G.nx + q.i0;
+        const size_t step = q.di ? 1 : (size_t)G.nx;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) { Q[c] = __ldg(v + c * step); S[c] = q.h * __ldg(d + c * step); }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int i = q.i0 + c * q.di, j = q.j0 + c * q.dj;
+            Q[c] = cell_value(G, src, PL, i, j, pv);
+            S[c] = q.h * cell_value(G, src, PL, i, j, q.gn + pv);
+        }
+    }
+    double v, hvx, h2vxx;
+    linear_recon<ORDER>(Q[0], Q[1], Q[2], Q[3], S[0], S[1], S[2], S[3], v, hvx, h2vxx);
+    double* o = q.base + q.idx;
+    o[(RV * 4 + k) * q.stride] = v;
+    o[(RN * 4 + k) * q.stride] = hvx * q.ih;
+    o[(RNN * 4 + k) * q.stride] = h2vxx * q.ih * q.ih;
+    if (q.inner) {
+        double vl, sl, vr, sr;
+        weno_pair<ORDER>(Q[0], Q[1], Q[2], Q[3], S[0], S[1], S[2], S[3], G.weno_eps, vl, sl, vr, sr);
+        o[(RL * 4 + k) * q.stride] = vl;
+        o[(RR * 4 + k) * q.stride] = vr;
+        o[(RLN * 4 + k) * q.stride] = sl * q.ih;
+        o[(RRN * 4 + k) * q.stride] = sr * q.ih;
+    }
+}
+
+// Characteristic variables: all four variables of face row `row`.
+template <int ORDER>
+__device__ __forceinline__ void char_row(const GridDev& G, const double* __restrict__ src, size_t PL, int row)
+{
+    const RowRef q = row_ref(G, row);
+    double Qa[4][4], Sa[4][4], Wref[4];
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        const int pk = q.xo ? kk : ((kk == 1) ? 2 : (kk == 2) ? 1 : kk);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int i = q.i0 + c * q.di, j = q.j0 + c * q.dj;
+            Qa[kk][c] = cell_value(G, src, PL, i, j, pk);
+            Sa[kk][c] = q.h * cell_value(G, src, PL, i, j, q.gn + pk);
+        }
+        Wref[kk] = 0.5 * (Qa[kk][1] + Qa[kk][2]);
+    }
+    double* o = q.base + q.idx;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        double v, hvx, h2vxx;
+        linear_recon<ORDER>(Qa[k][0], Qa[k][1], Qa[k][2], Qa[k][3], Sa[k][0], Sa[k][1], Sa[k][2], Sa[k][3], v, hvx,
+                            h2vxx);
+        o[(RV * 4 + k) * q.stride] = v;
+        o[(RN * 4 + k) * q.stride] = hvx * q.ih;
+        o[(RNN * 4 + k) * q.stride] = h2vxx * q.ih * q.ih;
+    }
+    if (!q.inner) return;
+    // project on the left eigenvectors of the normal flux Jacobian at the
+    // mean of the two cells sharing the face, WENO-Z per field, map back
+    CharState cs;
+    char_state(Wref, G.gamma, cs);
+    double cvl[4], csl[4], cvr[4], csr[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        double l[4], Q[4], S[4];
+        char_left_row(cs, m, l);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            Q[c] = l[0] * Qa[0][c] + l[1] * Qa[1][c] + l[2] * Qa[2][c] + l[3] * Qa[3][c];
+            S[c] = l[0] * Sa[0][c] + l[1] * Sa[1][c] + l[2] * Sa[2][c] + l[3] * Sa[3][c];
+        }
+        weno_pair<ORDER>(Q[0], Q[1], Q[2], Q[3], S[0], S[1], S[2], S[3], G.weno_eps, cvl[m], csl[m], cvr[m], csr[m]);
+        csl[m] *= q.ih;
+        csr[m] *= q.ih;
+    }
+    double out[4];
+    char_to_cons(cs, cvl, out);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) o[(RL * 4 + k) * q.stride] = out[k];
+    char_to_cons(cs, cvr, out);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) o[(RR * 4 + k) * q.stride] = out[k];
+    char_to_cons(cs, csl, out);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) o[(RLN * 4 + k) * q.stride] = out[k];
+    char_to_cons(cs, csr, out);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) o[(RRN * 4 + k) * q.stride] = out[k];
+}
+
 // CHAR = 0: conservative variables, one (record, variable) per thread;
-// CHAR = 1: characteristic variables, one record (all four variables) per thread
+// CHAR = 1: characteristic variables, one record (all four variables) per thread.
+// The reconstruction order is per grid (a uniform branch per chunk).
 template <int STAGE, int CHAR>
 __global__ void __launch_bounds__(256, CHAR ? 1 : 2) records_kernel(const GridDev* __restrict__ grids,
                                                                     const TileRef* __restrict__ chunks, int nchunks)
@@ -82,102 +183,15 @@ __global__ void __launch_bounds__(256, CHAR ? 1 : 2) records_kernel(const GridDe
         const size_t PL = (size_t)G.nx * G.ny;
         const int nrec = record_rows(G.nx, G.ny, G.dim);
         const int item = tr.x0 + (int)threadIdx.x;
-        const double eps = G.weno_eps;
         if (!CHAR) {
-            // one (record, variable) per thread
             if (item >= 4 * nrec) continue;
             const int k = item / nrec;
-            const RowRef q = row_ref(G, item - k * nrec);
-            const int pv = q.xo ? k : ((k == 1) ? 2 : (k == 2) ? 1 : k);   // face frame: normal momentum first
-            double Q[4], S[4];
-            const int i3 = q.i0 + 3 * q.di, j3 = q.j0 + 3 * q.dj;
-            if (q.i0 >= 0 && q.j0 >= 0 && i3 < G.nx && j3 < G.ny) {
-                // stencil inside the grid: no boundary mapping
-                const double* v = src + (size_t)pv * PL + (size_t)q.j0 * G.nx + q.i0;
-                const double* d = src + (size_t)(q.gn + pv) * PL + (size_t)q.j0 * G.nx + q.i0;
-                const size_t step = q.di ? 1 : (size_t)G.nx;
-#pragma unroll
-                for (int c = 0; c < 4; ++c) { Q[c] = __ldg(v + c * step); S[c] = q.h * __ldg(d + c * step); }
-            } else {
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const int i = q.i0 + c * q.di, j = q.j0 + c * q.dj;
-                    Q[c] = cell_value(G, src, PL, i, j, pv);
-                    S[c] = q.h * cell_value(G, src, PL, i, j, q.gn + pv);
-                }
-            }
-            double v, hvx, h2vxx;
-            linear_recon(Q[0], Q[1], Q[2], Q[3], S[0], S[1], S[2], S[3], v, hvx, h2vxx);
-            double* o = q.base + q.idx;
-            o[(RV * 4 + k) * q.stride] = v;
-            o[(RN * 4 + k) * q.stride] = hvx * q.ih;
-            o[(RNN * 4 + k) * q.stride] = h2vxx * q.ih * q.ih;
-            if (q.inner) {
-                double vl, sl, vr, sr;
-                weno_pair(Q[0], Q[1], Q[2], Q[3], S[0], S[1], S[2], S[3], eps, vl, sl, vr, sr);
-                o[(RL * 4 + k) * q.stride] = vl;
-                o[(RR * 4 + k) * q.stride] = vr;
-                o[(RLN * 4 + k) * q.stride] = sl * q.ih;
-                o[(RRN * 4 + k) * q.stride] = sr * q.ih;
-            }
+            if (G.order == 6) cons_row<6>(G, src, PL, item - k * nrec, k);
+            else cons_row<8>(G, src, PL, item - k * nrec, k);
         } else {
-            // characteristic variables: one record (all four variables) per thread
             if (item >= nrec) continue;
-            const RowRef q = row_ref(G, item);
-            double Qa[4][4], Sa[4][4], Wref[4];
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-                const int pk = q.xo ? kk : ((kk == 1) ? 2 : (kk == 2) ? 1 : kk);
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const int i = q.i0 + c * q.di, j = q.j0 + c * q.dj;
-                    Qa[kk][c] = cell_value(G, src, PL, i, j, pk);
-                    Sa[kk][c] = q.h * cell_value(G, src, PL, i, j, q.gn + pk);
-                }
-                Wref[kk] = 0.5 * (Qa[kk][1] + Qa[kk][2]);
-            }
-            double* o = q.base + q.idx;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                double v, hvx, h2vxx;
-                linear_recon(Qa[k][0], Qa[k][1], Qa[k][2], Qa[k][3], Sa[k][0], Sa[k][1], Sa[k][2], Sa[k][3], v, hvx,
-                             h2vxx);
-                o[(RV * 4 + k) * q.stride] = v;
-                o[(RN * 4 + k) * q.stride] = hvx * q.ih;
-                o[(RNN * 4 + k) * q.stride] = h2vxx * q.ih * q.ih;
-            }
-            if (!q.inner) continue;
-            // project on the left eigenvectors of the normal flux Jacobian at the
-            // mean of the two cells sharing the face, WENO-Z per field, map back
-            CharState cs;
-            char_state(Wref, G.gamma, cs);
-            double cvl[4], csl[4], cvr[4], csr[4];
-#pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                double l[4], Q[4], S[4];
-                char_left_row(cs, m, l);
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    Q[c] = l[0] * Qa[0][c] + l[1] * Qa[1][c] + l[2] * Qa[2][c] + l[3] * Qa[3][c];
-                    S[c] = l[0] * Sa[0][c] + l[1] * Sa[1][c] + l[2] * Sa[2][c] + l[3] * Sa[3][c];
-                }
-                weno_pair(Q[0], Q[1], Q[2], Q[3], S[0], S[1], S[2], S[3], eps, cvl[m], csl[m], cvr[m], csr[m]);
-                csl[m] *= q.ih;
-                csr[m] *= q.ih;
-            }
-            double out[4];
-            char_to_cons(cs, cvl, out);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) o[(RL * 4 + k) * q.stride] = out[k];
-            char_to_cons(cs, cvr, out);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) o[(RR * 4 + k) * q.stride] = out[k];
-            char_to_cons(cs, csl, out);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) o[(RLN * 4 + k) * q.stride] = out[k];
-            char_to_cons(cs, csr, out);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) o[(RRN * 4 + k) * q.stride] = out[k];
+            if (G.order == 6) char_row<6>(G, src, PL, item);
+            else char_row<8>(G, src, PL, item);
         }
     }
 }

@@ -98,14 +98,19 @@ def test_batched_1d_acoustic_grids_equal_alone_bitwise():
 
 def test_batched_mixed_options_equal_alone_bitwise():
     """One batch mixing conservative and characteristic reconstruction (two record-kernel queues),
-    a viscous grid and the shock reflection's per-side inflow states."""
+    the 8th-order scheme and its 6th-order variant, a viscous grid and the shock reflection's
+    per-side inflow states."""
     a = wl.shock_vortex(nx=40, ny=22, mach=1.3)
     b = wl.shock_vortex(nx=33, ny=17, mach=1.2)
     b[0].recon_vars = 1
     c = wl.shear_wave(32, 1e-3, 0.01, kind="shear")
     d = wl.shock_reflection(40, 10)
     d[0].recon_vars = 1
-    cases = [a, b, c, d]
+    e = wl.shock_vortex(nx=36, ny=20, mach=1.25)
+    e[0].order = 6
+    f = wl.shock_reflection(36, 9)
+    f[0].recon_vars, f[0].order = 1, 6
+    cases = [a, b, c, d, e, f]
     alone = []
     for spec, W in cases:
         s = cgks.Solver(cgks.problem_from_spec(spec))

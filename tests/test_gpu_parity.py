@@ -120,6 +120,26 @@ def test_characteristic_shock_vortex():
     _check(g, o, spec=spec)
 
 
+def test_sixth_order_density_wave_1d_to_t2():
+    """The compact 6th-order variant (Sec. 3.2 names it; reconstruction read as the degree-5 fit)."""
+    spec, W = wl.density_wave_1d(100, eps=0.2, cfl=0.3, eps_tau=0.0)
+    spec.order = 6
+    g, tg, sg = run_gpu(spec, W, 5000, t_end=2.0)
+    o, to, so = run_oracle(spec, W, 5000, t_end=2.0)
+    assert sg == so and to == 2.0
+    _check(g, o, spec=spec)
+
+
+@pytest.mark.parametrize("recon_vars", [0, 1])
+def test_sixth_order_shock_vortex(recon_vars):
+    spec, W = wl.shock_vortex(nx=70, ny=36, mach=1.3)
+    spec.order, spec.recon_vars = 6, recon_vars
+    g, _, sg = run_gpu(spec, W, 8)
+    o, _, so = run_oracle(spec, W, 8)
+    assert sg == so == 8
+    _check(g, o, spec=spec)
+
+
 def _sod_2d(n, rows, along_y, recon_vars):
     """Sod's tube on a 2D grid: the discontinuities cross every face parallel to them (the
     nonlinear values along those faces keep the states physical).  along_y transposes it."""
