@@ -22,12 +22,15 @@
 // span many grids of different sizes (each with its own dt in its Ctrl).
 #pragma once
 #include "cgks_device.cuh"
+#include "cgks_flux.cuh"
 #include "cgks_internal.h"
 #include "../../include/cgks.h"
 
 namespace cgks {
 
 constexpr int kThreads = 256;
+
+static __constant__ FluxFixed kFluxFixed = make_flux_fixed();
 
 template <int STAGE> struct FaceQ { static constexpr int n = (STAGE == 1) ? 16 : 8; };
 
@@ -46,9 +49,10 @@ struct StageLayout {
 // sR; tangential derivatives of the equilibrium state and normal derivatives
 // come from the quartic / quadratic through the same line averages.
 struct SegmentRows {
+    RegK r;
     const double* rec;
     int nrec, r0, rstride;
-    double eta, iht, weps;
+    double eta, iht;
     double W0[4], sL[4], sR[4];   // WENO-Z values at this point, non-equilibrium slopes
 
     __device__ __forceinline__ double at(int f, int k, int off) const { return rec[(f * 4 + k) * nrec + r0 + off * rstride]; }
@@ -68,26 +72,28 @@ struct SegmentRows {
     __device__ __forceinline__ void eq_derivs(double W0n[4], double W0t[4], double W0nn[4], double W0nt[4],
                                               double W0tt[4]) const
     {
-        const double iht2 = iht * iht;
+        const double iht2 = r.mul(iht, iht);
+        auto dp = [&](double m0, double S1, double S2, double A1, double A2) {   // p'(eta) / h_t
+            return r.mul(fma(eta, r.kfma(FK_S1T, S1, r.kfma(FK_S2T, S2, r.kmul(FK_M0T, m0))),
+                             r.kfma(FK_A1T, A1, r.kmul(FK_A2T, A2))), iht);
+        };
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             {
                 const double m0 = at(RV, k, 0), mp = at(RV, k, 1), mm = at(RV, k, -1);
-                const double S1 = mp + mm, S2 = at(RV, k, 2) + at(RV, k, -2);
-                const double A1 = mp - mm, A2 = at(RV, k, 2) - at(RV, k, -2);
-                W0t[k] = ((8.0 / 12.0) * A1 - (1.0 / 12.0) * A2
-                          + eta * ((13.0 / 9.0) * S1 - (1.0 / 9.0) * S2 - (24.0 / 9.0) * m0)) * iht;
-                W0tt[k] = ((16.0 / 12.0) * S1 - (1.0 / 12.0) * S2 - (30.0 / 12.0) * m0
-                           + eta * (0.5 * A2 - A1)) * iht2;
+                const double m2p = at(RV, k, 2), m2m = at(RV, k, -2);
+                const double S1 = r.add(mp, mm), S2 = r.add(m2p, m2m), A1 = r.sub(mp, mm), A2 = r.sub(m2p, m2m);
+                W0t[k] = dp(m0, S1, S2, A1, A2);
+                W0tt[k] = r.mul(fma(eta, r.kfma(FK_HALF, A2, -A1),
+                                    r.kfma(FK_S1TT, S1, r.kfma(FK_S2TT, S2, r.kmul(FK_M0TT, m0)))), iht2);
             }
             {
                 const double m0 = at(RN, k, 0), mp = at(RN, k, 1), mm = at(RN, k, -1);
-                const double S1 = mp + mm, S2 = at(RN, k, 2) + at(RN, k, -2);
-                const double A1 = mp - mm, A2 = at(RN, k, 2) - at(RN, k, -2);
-                W0n[k] = m0 - (1.0 / 4320.0) * (S2 - 4.0 * S1 + 6.0 * m0)
-                         + eta * ((50.0 / 72.0) * A1 - (7.0 / 72.0) * A2);
-                W0nt[k] = ((8.0 / 12.0) * A1 - (1.0 / 12.0) * A2
-                           + eta * ((13.0 / 9.0) * S1 - (1.0 / 9.0) * S2 - (24.0 / 9.0) * m0)) * iht;
+                const double m2p = at(RN, k, 2), m2m = at(RN, k, -2);
+                const double S1 = r.add(mp, mm), S2 = r.add(m2p, m2m), A1 = r.sub(mp, mm), A2 = r.sub(m2p, m2m);
+                W0n[k] = fma(eta, r.kfma(FK_A1N, A1, r.kmul(FK_A2N, A2)),
+                             r.kfma(FK_M0N, m0, r.kfma(FK_S1N, S1, r.kmul(FK_S2N, S2))));
+                W0nt[k] = dp(m0, S1, S2, A1, A2);
             }
             W0nn[k] = at(RNN, k, 0);
         }
@@ -99,16 +105,17 @@ struct SegmentRows {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const double sl = side ? sR[k] : sL[k];
-            W[k] = at(f, k, 0) + eta * sl;
-            Wt[k] = sl * iht;
+            W[k] = fma(eta, sl, at(f, k, 0));
+            Wt[k] = r.mul(sl, iht);
         }
     }
 
     __device__ __forceinline__ void ne_normal(int side, double Wn[4]) const
     {
         const int f = side ? RRN : RLN;
+        const double he = r.kmul(FK_HALF, eta);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) Wn[k] = at(f, k, 0) + eta * 0.5 * (at(f, k, 1) - at(f, k, -1));
+        for (int k = 0; k < 4; ++k) Wn[k] = fma(he, r.sub(at(f, k, 1), at(f, k, -1)), at(f, k, 0));
     }
 };
 
@@ -121,10 +128,13 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
     extern __shared__ double smem[];
     double* rx = smem;                  // [28][TY+4][TX+1]
     double* ry = rx + L::n_rx;          // [28][TX+4][TY+1]
-    __shared__ double s_dt;
+    __shared__ double s_fk[FK_N];       // coefficient table (fixed part, then the tile's grid and dt)
     __shared__ int s_skip;
     const int tid = threadIdx.x;
     constexpr double gq = 0.28867513459481287;   // 1/(2 sqrt 3): Gauss points at +-gq
+    for (int i = tid; i < FK_NFIX; i += kThreads) s_fk[i] = kFluxFixed.v[i];
+    __syncthreads();
+    const RegK r{s_fk, ((volatile const double*)s_fk)[FK_ONE], ((volatile const double*)s_fk)[FK_NZERO]};
 
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         __syncthreads();
@@ -133,12 +143,11 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
         if (tid == 0) {
             const Ctrl* C = G.ctrl;
             s_skip = C->done;
-            s_dt = C->dt;
+            if (!C->done) flux_table_tile(s_fk, G, C->dt);
         }
         __syncthreads();
         if (s_skip) continue;
         const int nx = G.nx, ny = G.ny, x0 = tr.x0, y0 = tr.y0;
-        const double dt = s_dt;
         const bool dim1 = (G.dim == 1);
 
         // ---------------- phase 1: the tile's face-row records (the record kernel
@@ -164,10 +173,6 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
         __syncthreads();
 
         // ---------------- phase 2: face segments, two Gauss points each
-        Params P;
-        P.gamma = G.gamma; P.K = G.K; P.eps_tau = G.eps_tau; P.c_tau = G.c_tau; P.dt = dt; P.mu = G.mu;
-        P.idt = __drcp_rn(dt); P.inv_K2 = __drcp_rn(G.K + 2.0); P.inv_gm1 = __drcp_rn(G.gamma - 1.0);
-        P.K2inv2 = 2.0 * P.inv_K2; P.Kheat = 0.5 * (G.K + 4.0);
         bool bad = false;
         // the tile's own faces: x-faces x0..x0+TX-1 and y-faces y0..y0+TY-1 of its
         // cells, plus the last face of the grid where the tile ends on the grid's
@@ -198,8 +203,8 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
                 rec = ry; nrec = (TX + 4) * (TY + 1); r0 = (il + 2) * (TY + 1) + gl; rstride = TY + 1;
                 out = G.facey; ostride = nfy; oidx = (size_t)(y0 + gl) * nx + x0 + il;
             }
-            const double iht = xo ? G.inv_dy : G.inv_dx;
-            const double weps = G.weno_eps;
+            const double iht = r.k(xo ? FK_IDY : FK_IDX);
+            const double weps = r.k(FK_WEPS);
             double acc[NF];
 #pragma unroll
             for (int q = 0; q < NF; ++q) acc[q] = 0.0;
@@ -208,35 +213,33 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 auto R = [&](int f, int off) { return rec[(f * 4 + k) * nrec + r0 + off * rstride]; };
-                tang_weno5_pair(R(RV, -2), R(RV, -1), R(RV, 0), R(RV, 1), R(RV, 2), gq, weps, W0m[k], W0p[k]);
-                sL[k] = tang_weno3_slope(R(RL, -1), R(RL, 0), R(RL, 1), weps);
-                sR[k] = tang_weno3_slope(R(RR, -1), R(RR, 0), R(RR, 1), weps);
+                tang_weno5_pair(r, R(RV, -2), R(RV, -1), R(RV, 0), R(RV, 1), R(RV, 2), weps, W0m[k], W0p[k]);
+                sL[k] = tang_weno3_slope(r, R(RL, -1), R(RL, 0), R(RL, 1), weps);
+                sR[k] = tang_weno3_slope(r, R(RR, -1), R(RR, 0), R(RR, 1), weps);
             }
 #pragma unroll 1
             for (int gp = 0; gp < 2; ++gp) {
                 const double eta = gp ? gq : -gq;
-                const SegmentRows src{rec, nrec, r0, rstride, eta, iht, weps,
+                const SegmentRows src{r, rec, nrec, r0, rstride, eta, iht,
                                       {gp ? W0p[0] : W0m[0], gp ? W0p[1] : W0m[1], gp ? W0p[2] : W0m[2],
                                        gp ? W0p[3] : W0m[3]},
                                       {sL[0], sL[1], sL[2], sL[3]}, {sR[0], sR[1], sR[2], sR[3]}};
                 double Fb[4], Ft[4], Wm[4], Wb[4], Wtt[4];
-                bad |= !gks_point<STAGE>(src, P, Fb, Ft, Wm, Wb, Wtt);
+                bad |= !gks_point<STAGE>(r, src, Fb, Ft, Wm, Wb, Wtt);
+                // Gauss average (weight 1/2 per point) times the stage's time factors
                 if (STAGE == 1) {
-                    const double c1a = 0.25 * dt, c1b = dt * dt * (1.0 / 16.0);       // half of (dt/2, dt^2/8)
-                    const double c2a = 0.5 * dt, c2b = dt * dt * (1.0 / 12.0);        // half of (dt, dt^2/6)
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        acc[k] += c1a * Fb[k] + c1b * Ft[k];
-                        acc[4 + k] += c2a * Fb[k] + c2b * Ft[k];
-                        acc[8 + k] += 0.5 * Wm[k];
-                        acc[12 + k] += 0.5 * Wb[k];
+                        acc[k] = r.kfma(FK_W1B, Ft[k], r.kfma(FK_W1A, Fb[k], acc[k]));
+                        acc[4 + k] = r.kfma(FK_W2B, Ft[k], r.kfma(FK_W2A, Fb[k], acc[4 + k]));
+                        acc[8 + k] = r.kfma(FK_HALF, Wm[k], acc[8 + k]);
+                        acc[12 + k] = r.kfma(FK_HALF, Wb[k], acc[12 + k]);
                     }
                 } else {
-                    const double c3 = dt * dt * (1.0 / 6.0);                           // half of dt^2/3
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        acc[k] += c3 * Ft[k];
-                        acc[4 + k] += c3 * Wtt[k];
+                        acc[k] = r.kfma(FK_W3, Ft[k], acc[k]);
+                        acc[4 + k] = r.kfma(FK_W3, Wtt[k], acc[4 + k]);
                     }
                 }
             }
