@@ -55,8 +55,15 @@ FLUX_DRAM_BYTES_PER_CELL = {1: 733.87e6 / 1048576, 2: 601.71e6 / 1048576}
 # algorithmic bytes per cell of the flux kernel: the two face rows' records (2 x 28 doubles) read and
 # the two faces' results written (stage 1: 16 doubles each, stage 2: 8)
 FLUX_ALGO_BYTES_PER_CELL = {1: 448 + 256, 2: 448 + 128}
-# measured FP64 peak of this GB300 (DFMA throughput loop, FMA = 2): profiles/fp64_peak_gb300.md
-FP64_PEAK_TFLOPS = 1.010
+# measured FP64 peak of this GB300: DFMA with register operands issues 1.99 per SM and cycle
+# (throughput loop, FMA = 2 flops): profiles/fp64_peak_gb300.md.  The peak is taken at the median
+# SM clock sampled during the timed region (1.252 TFLOP/s at 2070 MHz).
+FP64_DFMA_PER_SM_CYCLE = 1.99
+DEFAULT_SM_MHZ = 2070.0
+
+
+def fp64_peak_tflops(nsm, sm_mhz):
+    return 2.0 * FP64_DFMA_PER_SM_CYCLE * nsm * sm_mhz * 1e6 / 1e12
 
 
 def workloads():
@@ -229,22 +236,27 @@ def run_cgks(args, world, rank, local):
     tile = args.tile or DEFAULT_TILE
     # stage_ms: begin, stage-1 records, flux, update, stage-2 records, flux, update, end
     flux_ms, rec_ms, upd_ms = stage_ms[2], stage_ms[1], stage_ms[3]
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    peak_mhz = clocks["sm_mhz"] if clocks else DEFAULT_SM_MHZ
+    peak = fp64_peak_tflops(nsm, peak_mhz)
     achieved = FLUX_FLOP_PER_CELL[1] * cells / (flux_ms * 1e-3) / 1e12
     rec_flop = RECORD_FLOP_PER_CELL[args.order]
     stage1_flop = None if rec_flop is None else rec_flop + FLUX_FLOP_PER_CELL[1] + UPDATE_FLOP_PER_CELL[1]
     stage1 = None if stage1_flop is None else stage1_flop * cells / ((flux_ms + rec_ms + upd_ms) * 1e-3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS,
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak,
                 "traffic": FLUX_DRAM_BYTES_PER_CELL[1] * cells if tile == DEFAULT_TILE else None,
                 "algorithmic_bytes": FLUX_ALGO_BYTES_PER_CELL[1] * cells,
                 "algorithmic_flop_per_cell": FLUX_FLOP_PER_CELL[1],
                 "kernel": f"stage_kernel<{tile},1>", "kernel_ms": flux_ms,
                 "stage1_records_plus_flux": {"kernels": "records_kernel<1,0> + stage_kernel<%s,1> + update_kernel<1>" % tile,
                                              "ms": flux_ms + rec_ms + upd_ms, "achieved": stage1,
-                                             "frac": None if stage1 is None else stage1 / FP64_PEAK_TFLOPS,
+                                             "frac": None if stage1 is None else stage1 / peak,
                                              "algorithmic_flop_per_cell": stage1_flop,
                                              "state_algorithmic_bytes": 288 * cells},
-                "peak_source": "measured FP64 DFMA loop (FMA=2) on GB300, of measured"}
+                "peak_source": "measured FP64 DFMA rate (register operands, FMA = 2): %.2f per SM and cycle x %d SMs "
+                               "x %.0f MHz (median SM clock in the timed region), of measured"
+                               % (FP64_DFMA_PER_SM_CYCLE, nsm, peak_mhz)}
 
     # ---------------- end to end through the C ABI with host buffers
     host_in = torch.from_numpy(np.ascontiguousarray(W)).pin_memory()

@@ -71,6 +71,18 @@ struct RegK {
     // c_i * x + y and c_i * x with c_i from the table
     __device__ __forceinline__ double kfma(int i, double x, double y) const { return fma(k(i), x, y); }
     __device__ __forceinline__ double kmul(int i, double x) const { return fma(k(i), x, nzero); }
+    // 1/x for normal positive or negative x: the hardware approximation
+    // (rcp.approx.ftz.f64, about 20 correct bits) refined by two Newton-Raphson
+    // steps y <- y + y (1 - x y), each doubling the correct bits
+    __device__ __forceinline__ double rcp(double x) const
+    {
+        double y;
+        asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+        double e = fma(-x, y, one);
+        y = fma(y, e, y);
+        e = fma(-x, y, one);
+        return fma(y, e, y);
+    }
 };
 
 // Layout of the reconstruction coefficient table: one block per order (8, 6),
@@ -191,7 +203,7 @@ __device__ __forceinline__ void weno_side_rk(const RegK& r, double base, double 
     const double t6 = r.mul(r.add(e6, Z), r.mul(p01234, e5));
     const double n13 = r.kfma(RK_W + 1, t1, r.kmul(RK_W + 3, t3)), n4 = r.kmul(RK_W + 4, t4);
     const double den = r.kfma(RK_W + 6, t6, r.kfma(RK_W + 5, t5, r.add(r.kfma(RK_W + 2, t2, r.kfma(RK_W + 0, t0, n13)), n4)));
-    const double inv = __drcp_rn(den);
+    const double inv = r.rcp(den);
     const double q0 = r.kfma(RK_Q0 + 0, d1, r.kmul(RK_Q0 + 1, A));
     const double q13 = r.kfma(RK_Q13 + 0, d1, r.kmul(RK_Q13 + 1, d2));
     const double q2 = r.kfma(RK_Q2 + 0, D, r.kfma(RK_Q2 + 1, d2, r.kmul(RK_Q2 + 2, d3)));

@@ -128,8 +128,8 @@ __device__ __forceinline__ void tang_weno5_pair(const RegK& r, double vmm, doubl
     const double Q0 = r.mul(P0, D0), Q1 = r.mul(P1, D1), Q2 = r.mul(P2, D2);
     const double np = r.kfma(FK_DHI, Q2, r.kfma(FK_DLO, Q0, Q1)), dp = r.kfma(FK_DHI, P2, r.kfma(FK_DLO, P0, P1));
     const double nm = r.kfma(FK_DLO, Q2, r.kfma(FK_DHI, Q0, Q1)), dm = r.kfma(FK_DLO, P2, r.kfma(FK_DHI, P0, P1));
-    at_plus = r.kfma(FK_HG, r.mul(np, __drcp_rn(dp)), v0);
-    at_minus = r.kfma(FK_MHG, r.mul(nm, __drcp_rn(dm)), v0);
+    at_plus = r.kfma(FK_HG, r.mul(np, r.rcp(dp)), v0);
+    at_minus = r.kfma(FK_MHG, r.mul(nm, r.rcp(dm)), v0);
 }
 
 // Three means v_{-1..1}: two linear candidates with slopes v_0 - v_-1 and
@@ -143,7 +143,7 @@ __device__ __forceinline__ double tang_weno3_slope(const RegK& r, double vm, dou
     const double e0 = fma(dm, dm, eps), e1 = fma(dp, dp, eps);
     const double Z = fabs(r.sub(e0, e1));
     const double n0 = r.mul(r.add(e0, Z), e1), n1 = r.mul(r.add(e1, Z), e0);
-    return r.mul(fma(n1, dp, r.mul(n0, dm)), __drcp_rn(r.add(n0, n1)));
+    return r.mul(fma(n1, dp, r.mul(n0, dm)), r.rcp(r.add(n0, n1)));
 }
 
 // ------------------------------------------------------------------------
@@ -392,17 +392,17 @@ __device__ __forceinline__ bool gks_point(const RegK& r, const Src& src, double 
     // equilibrium state g0
     double W0[4];
     src.eq_value(W0);
-    const double ir0 = __drcp_rn(W0[0]);
+    const double ir0 = r.rcp(W0[0]);
     const double U0 = r.mul(W0[1], ir0), V0 = r.mul(W0[2], ir0);
     const double p0 = r.mul(r.k(FK_GM1), r.kfma(FK_MHALF, fma(W0[2], V0, r.mul(W0[1], U0)), W0[3]));
     // non-equilibrium states
     double Wl[4], Wlt[4], Wr[4], Wrt[4];
     src.ne_value(0, Wl, Wlt);
     src.ne_value(1, Wr, Wrt);
-    const double irl = __drcp_rn(Wl[0]);
+    const double irl = r.rcp(Wl[0]);
     const double Ul = r.mul(Wl[1], irl), Vl = r.mul(Wl[2], irl);
     const double pl = r.mul(r.k(FK_GM1), r.kfma(FK_MHALF, fma(Wl[2], Vl, r.mul(Wl[1], Ul)), Wl[3]));
-    const double irr = __drcp_rn(Wr[0]);
+    const double irr = r.rcp(Wr[0]);
     const double Ur = r.mul(Wr[1], irr), Vr = r.mul(Wr[2], irr);
     const double pr = r.mul(r.k(FK_GM1), r.kfma(FK_MHALF, fma(Wr[2], Vr, r.mul(Wr[1], Ur)), Wr[3]));
     const bool ok = (W0[0] > 0.0) && (p0 > 0.0) && (Wl[0] > 0.0) && (pl > 0.0) && (Wr[0] > 0.0) && (pr > 0.0);
@@ -411,14 +411,14 @@ __device__ __forceinline__ bool gks_point(const RegK& r, const Src& src, double 
     // Sec. 4: collision time with pressure-jump enhancement; viscous flow: mu/p
     // with p the equilibrium pressure at the point
     const double mu = r.k(FK_MU), dt = r.k(FK_DT);
-    const double tau = fma(r.k(FK_CTAUDT), fabs(r.mul(r.sub(pl, pr), __drcp_rn(r.add(pl, pr)))),
-                           mu > 0.0 ? r.mul(mu, __drcp_rn(p0)) : r.k(FK_EPSDT));
+    const double tau = fma(r.k(FK_CTAUDT), fabs(r.mul(r.sub(pl, pr), r.rcp(r.add(pl, pr)))),
+                           mu > 0.0 ? r.mul(mu, r.rcp(p0)) : r.k(FK_EPSDT));
     // h = exp(-dt / (2 tau)) weights the non-equilibrium part of the interface state.
     // For dt > 80 tau, h < 4e-18: then 1 - h and 3 - h round to 1 and 3, and the
     // remaining h-terms change the window coefficients by under 2e-14 of a term
     // that is itself O(tau^2), so h is taken as 0 without evaluating the exponential
     double h = 0.0;
-    if (tau > 0.0 && dt < 80.0 * tau) h = exp(r.mul(r.k(FK_MHDT), __drcp_rn(tau)));
+    if (tau > 0.0 && dt < 80.0 * tau) h = exp(r.mul(r.k(FK_MHDT), r.rcp(tau)));
     // below 1e-20 that part is under 1e-20 of the state it is added to: far below one ulp,
     // so its velocity moments are not evaluated (the flux terms, weighted by O(tau), are)
     const bool need_ne = (STAGE == 1) && (h >= 1e-20);
@@ -427,7 +427,7 @@ __device__ __forceinline__ bool gks_point(const RegK& r, const Src& src, double 
     double Fh[4], Th[4], Wh[4] = {0, 0, 0, 0}, Wsl[4] = {0, 0, 0, 0};
     {
         Moments ml;
-        const double ithl = __drcp_rn(thl);
+        const double ithl = r.rcp(thl);
         const double th2 = r.add(thl, thl);
         const double sq = rsqrt(th2);                     // sqrt(lambda_l)
         half_moments01<+1>(r, Ul, sq, r.mul(th2, sq), ml.u[0], ml.u[1]);
@@ -451,7 +451,7 @@ __device__ __forceinline__ bool gks_point(const RegK& r, const Src& src, double 
     }
     {
         Moments mr;
-        const double ithr = __drcp_rn(thr);
+        const double ithr = r.rcp(thr);
         const double th2 = r.add(thr, thr);
         const double sq = rsqrt(th2);
         half_moments01<-1>(r, Ur, sq, r.mul(th2, sq), mr.u[0], mr.u[1]);

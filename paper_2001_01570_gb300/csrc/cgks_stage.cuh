@@ -157,36 +157,25 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
         {
             constexpr int NRX = (TX + 1) * (TY + 4), NRY = (TY + 1) * (TX + 4);
             const size_t sx = (size_t)(ny + 4) * (nx + 1), sy = (size_t)(nx + 4) * (ny + 1);
-            // eight loads in flight per thread before their stores
-            constexpr int NB = 8;
-            for (int base = tid; base < 4 * NREC * NRX; base += NB * kThreads) {
-                double v[NB];
-#pragma unroll
-                for (int u = 0; u < NB; ++u) {
-                    const int idx = base + u * kThreads;
-                    const int fk = idx / NRX, r = idx - fk * NRX;
-                    const int fl = r % (TX + 1), rl = r / (TX + 1);
-                    const bool valid = (idx < 4 * NREC * NRX) && (x0 + fl <= nx) && (y0 - 2 + rl <= ny + 1);
-                    v[u] = valid ? __ldg(G.recx + fk * sx + (size_t)(y0 + rl) * (nx + 1) + x0 + fl) : 0.0;
-                }
-#pragma unroll
-                for (int u = 0; u < NB; ++u)
-                    if (base + u * kThreads < 4 * NREC * NRX) rx[base + u * kThreads] = v[u];
+            // asynchronous 8-byte copies (zero-filled where the row lies outside the grid)
+            const unsigned sbx = (unsigned)__cvta_generic_to_shared(rx), sby = (unsigned)__cvta_generic_to_shared(ry);
+            for (int idx = tid; idx < 4 * NREC * NRX; idx += kThreads) {
+                const int fk = idx / NRX, r = idx - fk * NRX;
+                const int fl = r % (TX + 1), rl = r / (TX + 1);
+                const bool valid = (x0 + fl <= nx) && (y0 - 2 + rl <= ny + 1);
+                const double* src = valid ? G.recx + fk * sx + (size_t)(y0 + rl) * (nx + 1) + x0 + fl : G.recx;
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(sbx + 8u * (unsigned)idx), "l"(src),
+                             "r"(valid ? 8 : 0) : "memory");
             }
-            for (int base = tid; base < 4 * NREC * NRY; base += NB * kThreads) {
-                double v[NB];
-#pragma unroll
-                for (int u = 0; u < NB; ++u) {
-                    const int idx = base + u * kThreads;
-                    const int fk = idx / NRY, r = idx - fk * NRY;
-                    const int gl = r % (TY + 1), rl = r / (TY + 1);
-                    const bool valid = (idx < 4 * NREC * NRY) && !dim1 && (y0 + gl <= ny) && (x0 - 2 + rl <= nx + 1);
-                    v[u] = valid ? __ldg(G.recy + fk * sy + (size_t)(x0 + rl) * (ny + 1) + y0 + gl) : 0.0;
-                }
-#pragma unroll
-                for (int u = 0; u < NB; ++u)
-                    if (base + u * kThreads < 4 * NREC * NRY) ry[base + u * kThreads] = v[u];
+            for (int idx = tid; idx < 4 * NREC * NRY; idx += kThreads) {
+                const int fk = idx / NRY, r = idx - fk * NRY;
+                const int gl = r % (TY + 1), rl = r / (TY + 1);
+                const bool valid = !dim1 && (y0 + gl <= ny) && (x0 - 2 + rl <= nx + 1);
+                const double* src = valid ? G.recy + fk * sy + (size_t)(x0 + rl) * (ny + 1) + y0 + gl : G.recx;
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(sby + 8u * (unsigned)idx), "l"(src),
+                             "r"(valid ? 8 : 0) : "memory");
             }
+            asm volatile("cp.async.wait_all;" ::: "memory");
         }
         __syncthreads();
 
