@@ -39,7 +39,12 @@ struct StageLayout {
     static constexpr int NF = FaceQ<STAGE>::n;
     static constexpr int n_rx = 4 * NREC * (TY + 4) * (TX + 1);
     static constexpr int n_ry = 4 * NREC * (TX + 4) * (TY + 1);
-    static constexpr size_t bytes = sizeof(double) * (size_t)(n_rx + n_ry);
+    // where it fits, a per-thread slice of 32 doubles holds the Gauss-point-independent
+    // parts of the tangential / normal derivatives of one segment (shared by its two points)
+    static constexpr int n_dc_full = 32 * kThreads;
+    static constexpr bool share = sizeof(double) * (size_t)(n_rx + n_ry + n_dc_full) + 1024 <= 227 * 1024;
+    static constexpr int n_dc = share ? n_dc_full : 0;
+    static constexpr size_t bytes = sizeof(double) * (size_t)(n_rx + n_ry + n_dc);
 };
 
 // The face rows around one face segment (records of rows j-2..j+2 of one
@@ -48,12 +53,14 @@ struct StageLayout {
 // three) are computed once per segment for both points and carried in W0, sL,
 // sR; tangential derivatives of the equilibrium state and normal derivatives
 // come from the quartic / quadratic through the same line averages.
+template <bool SHARE>
 struct SegmentRows {
     RegK r;
     const double* rec;
     int nrec, r0, rstride;
     double eta, iht;
     double W0[4], sL[4], sR[4];   // WENO-Z values at this point, non-equilibrium slopes
+    const double* dc;             // SHARE: this thread's slice of the segment's derivative parts
 
     __device__ __forceinline__ double at(int f, int k, int off) const { return rec[(f * 4 + k) * nrec + r0 + off * rstride]; }
 
@@ -73,6 +80,19 @@ struct SegmentRows {
                                               double W0tt[4]) const
     {
         const double iht2 = r.mul(iht, iht);
+        if constexpr (SHARE) {
+            // the parts computed once per segment by seg_deriv_parts: value + eta * slope
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                auto P = [&](int j) { return dc[(8 * k + j) * kThreads]; };
+                W0t[k] = r.mul(fma(eta, P(1), P(0)), iht);
+                W0tt[k] = r.mul(fma(eta, P(3), P(2)), iht2);
+                W0n[k] = fma(eta, P(5), P(4));
+                W0nt[k] = r.mul(fma(eta, P(7), P(6)), iht);
+                W0nn[k] = at(RNN, k, 0);
+            }
+            return;
+        }
         auto dp = [&](double m0, double S1, double S2, double A1, double A2) {   // p'(eta) / h_t
             return r.mul(fma(eta, r.kfma(FK_S1T, S1, r.kfma(FK_S2T, S2, r.kmul(FK_M0T, m0))),
                              r.kfma(FK_A1T, A1, r.kmul(FK_A2T, A2))), iht);
@@ -97,6 +117,24 @@ struct SegmentRows {
             }
             W0nn[k] = at(RNN, k, 0);
         }
+    }
+
+    // the eta-independent parts of the quartic's derivatives above for variable k
+    // (rows m_{-2..2} of the values and of the normal derivatives), stored at dc
+    __device__ __forceinline__ static void seg_deriv_parts(const RegK& r, double* dc, double m2m, double mm, double m0,
+                                                           double mp, double m2p, double n2m, double nm, double n0,
+                                                           double np, double n2p)
+    {
+        const double S1 = r.add(mp, mm), S2 = r.add(m2p, m2m), A1 = r.sub(mp, mm), A2 = r.sub(m2p, m2m);
+        dc[0 * kThreads] = r.kfma(FK_A1T, A1, r.kmul(FK_A2T, A2));
+        dc[1 * kThreads] = r.kfma(FK_S1T, S1, r.kfma(FK_S2T, S2, r.kmul(FK_M0T, m0)));
+        dc[2 * kThreads] = r.kfma(FK_S1TT, S1, r.kfma(FK_S2TT, S2, r.kmul(FK_M0TT, m0)));
+        dc[3 * kThreads] = r.kfma(FK_HALF, A2, -A1);
+        const double T1 = r.add(np, nm), T2 = r.add(n2p, n2m), B1 = r.sub(np, nm), B2 = r.sub(n2p, n2m);
+        dc[4 * kThreads] = r.kfma(FK_M0N, n0, r.kfma(FK_S1N, T1, r.kmul(FK_S2N, T2)));
+        dc[5 * kThreads] = r.kfma(FK_A1N, B1, r.kmul(FK_A2N, B2));
+        dc[6 * kThreads] = r.kfma(FK_A1T, B1, r.kmul(FK_A2T, B2));
+        dc[7 * kThreads] = r.kfma(FK_S1T, T1, r.kfma(FK_S2T, T2, r.kmul(FK_M0T, n0)));
     }
 
     __device__ __forceinline__ void ne_value(int side, double W[4], double Wt[4]) const
@@ -128,6 +166,7 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
     extern __shared__ double smem[];
     double* rx = smem;                  // [28][TY+4][TX+1]
     double* ry = rx + L::n_rx;          // [28][TX+4][TY+1]
+    double* dc = ry + L::n_ry + threadIdx.x;   // [32][kThreads] when L::share
     __shared__ double s_fk[FK_N];       // coefficient table (fixed part, then the tile's grid and dt)
     __shared__ int s_skip;
     const int tid = threadIdx.x;
@@ -220,17 +259,21 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 auto R = [&](int f, int off) { return rec[(f * 4 + k) * nrec + r0 + off * rstride]; };
-                tang_weno5_pair(r, R(RV, -2), R(RV, -1), R(RV, 0), R(RV, 1), R(RV, 2), weps, W0m[k], W0p[k]);
+                const double m2m = R(RV, -2), mm = R(RV, -1), m0 = R(RV, 0), mp = R(RV, 1), m2p = R(RV, 2);
+                tang_weno5_pair(r, m2m, mm, m0, mp, m2p, weps, W0m[k], W0p[k]);
+                if constexpr (L::share)
+                    SegmentRows<true>::seg_deriv_parts(r, dc + 8 * k * kThreads, m2m, mm, m0, mp, m2p, R(RN, -2),
+                                                       R(RN, -1), R(RN, 0), R(RN, 1), R(RN, 2));
                 sL[k] = tang_weno3_slope(r, R(RL, -1), R(RL, 0), R(RL, 1), weps);
                 sR[k] = tang_weno3_slope(r, R(RR, -1), R(RR, 0), R(RR, 1), weps);
             }
 #pragma unroll 1
             for (int gp = 0; gp < 2; ++gp) {
                 const double eta = gp ? gq : -gq;
-                const SegmentRows src{r, rec, nrec, r0, rstride, eta, iht,
-                                      {gp ? W0p[0] : W0m[0], gp ? W0p[1] : W0m[1], gp ? W0p[2] : W0m[2],
-                                       gp ? W0p[3] : W0m[3]},
-                                      {sL[0], sL[1], sL[2], sL[3]}, {sR[0], sR[1], sR[2], sR[3]}};
+                const SegmentRows<L::share> src{r, rec, nrec, r0, rstride, eta, iht,
+                                                {gp ? W0p[0] : W0m[0], gp ? W0p[1] : W0m[1], gp ? W0p[2] : W0m[2],
+                                                 gp ? W0p[3] : W0m[3]},
+                                                {sL[0], sL[1], sL[2], sL[3]}, {sR[0], sR[1], sR[2], sR[3]}, dc};
                 double Fb[4], Ft[4], Wm[4], Wb[4], Wtt[4];
                 bad |= !gks_point<STAGE>(r, src, Fb, Ft, Wm, Wb, Wtt);
                 // Gauss average (weight 1/2 per point) times the stage's time factors
