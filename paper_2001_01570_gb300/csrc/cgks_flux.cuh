@@ -26,9 +26,13 @@ enum FluxK {
     FK_S1TT, FK_S2TT, FK_M0TT,                      // quartic: d^2/deta^2 coefficients
     FK_M0N, FK_S1N, FK_S2N, FK_A1N, FK_A2N,         // quartic: value at the Gauss points
     FK_C0P, FK_C0M,                                  // +-1/(2 sqrt(pi))
+    FK_X32LN2, FK_SHIFT, FK_LN2HI, FK_LN2LO,         // exponential: argument reduction
+    FK_P2, FK_P3, FK_P4, FK_P5, FK_P6,               // exponential: 1/k! of the Taylor polynomial
     FK_NFIX,
+    FK_EXP2 = FK_NFIX,                               // 2^(j/32), j = 0..31 (computed per CTA)
+    FK_NFIX2 = FK_EXP2 + 32,
     // per grid and tile
-    FK_DT = FK_NFIX, FK_IDT, FK_HDT, FK_MHDT, FK_EPSDT, FK_CTAUDT, FK_C8, FK_C6,
+    FK_DT = FK_NFIX2, FK_IDT, FK_HDT, FK_MHDT, FK_EPSDT, FK_CTAUDT, FK_C8, FK_C6,
     FK_W1A, FK_W1B, FK_W2A, FK_W2B, FK_W3,          // Gauss-average weights of the face results
     FK_GAMMA, FK_GM1, FK_INVGM1, FK_K, FK_K2, FK_KK2, FK_INVK2, FK_K2INV2, FK_KHEAT, FK_MU,
     FK_IDX, FK_IDY, FK_WEPS,
@@ -56,6 +60,12 @@ constexpr FluxFixed make_flux_fixed()
     k[FK_M0N] = 1.0 - 6.0 / 4320.0; k[FK_S1N] = 4.0 / 4320.0; k[FK_S2N] = -1.0 / 4320.0;
     k[FK_A1N] = 50.0 / 72.0; k[FK_A2N] = -7.0 / 72.0;
     k[FK_C0P] = 0.28209479177387814; k[FK_C0M] = -0.28209479177387814;
+    k[FK_X32LN2] = 32.0 / 0.6931471805599453;             // 32 / ln 2
+    k[FK_SHIFT] = 6755399441055744.0;                      // 1.5 * 2^52: rounds to an integer in the low bits
+    k[FK_LN2HI] = 0.6931471805599453 / 32.0;               // ln 2 / 32 and the remainder of its rounding
+    k[FK_LN2LO] = 2.3190468138462996e-17 / 32.0;
+    k[FK_P2] = 1.0 / 2.0; k[FK_P3] = 1.0 / 6.0; k[FK_P4] = 1.0 / 24.0; k[FK_P5] = 1.0 / 120.0;
+    k[FK_P6] = 1.0 / 720.0;
     return t;
 }
 
@@ -147,6 +157,28 @@ __device__ __forceinline__ double tang_weno3_slope(const RegK& r, double vm, dou
 }
 
 // ------------------------------------------------------------------------
+// e^x for x <= 0 by Tang's table-driven method (ACM TOMS 15, 1989): x = (32 m +
+// j) ln2/32 + r with |r| <= ln2/64, e^x = 2^m 2^(j/32) e^r, e^r from its Taylor
+// polynomial of degree 6 (truncation below 4e-18 relative), 2^(j/32) from the
+// table, 2^m added to the exponent field.  Below -700 (e^x < 1e-304) it returns 0.
+__device__ __forceinline__ double exp_neg(const RegK& r, double x)
+{
+    if (x < -700.0) return 0.0;
+    const double t = r.kfma(FK_X32LN2, x, r.k(FK_SHIFT));
+    const double n = r.sub(t, r.k(FK_SHIFT));             // round(32 x / ln 2), exactly
+    const int ni = (int)(unsigned)__double_as_longlong(t);
+    const double q = r.kfma(FK_LN2LO, -n, r.kfma(FK_LN2HI, -n, x));
+    double p = fma(r.k(FK_P6), q, r.k(FK_P5));
+    p = fma(p, q, r.k(FK_P4));
+    p = fma(p, q, r.k(FK_P3));
+    p = fma(p, q, r.k(FK_P2));
+    p = fma(p, q, r.one);
+    p = fma(p, q, r.one);
+    const double y = r.mul(r.k(FK_EXP2 + (ni & 31)), p);
+    return __longlong_as_double(__double_as_longlong(y) + ((long long)(ni >> 5) << 52));
+}
+
+// ------------------------------------------------------------------------
 // erfc(t) for t >= 0 from e = exp(-t^2): e * erfcx(t), erfcx from the piecewise
 // polynomials of cgks_erfcx_table.h (relative error ~2e-16); 11 FMAs instead
 // of a full erfc evaluation, since the half-line moments need e anyway.  Past
@@ -170,7 +202,7 @@ __device__ __forceinline__ void half_moments01(const RegK& r, double U, double s
                                                double& m1)
 {
     const double s = r.mul(U, sq);
-    const double e = exp(-r.mul(s, s));
+    const double e = exp_neg(r, -r.mul(s, s));
     const double hE = r.kmul(FK_HALF, erfc_scaled(r, fabs(s), e));    // erfc(|s|)/2
     // SIDE +1: erfc(-s)/2 = 1 - erfc(s)/2 for s >= 0, erfc(|s|)/2 for s < 0; SIDE -1 mirrored
     const bool pos = (SIDE > 0) ? (s >= 0.0) : (s < 0.0);
@@ -418,7 +450,7 @@ __device__ __forceinline__ bool gks_point(const RegK& r, const Src& src, double 
     // remaining h-terms change the window coefficients by under 2e-14 of a term
     // that is itself O(tau^2), so h is taken as 0 without evaluating the exponential
     double h = 0.0;
-    if (tau > 0.0 && dt < 80.0 * tau) h = exp(r.mul(r.k(FK_MHDT), r.rcp(tau)));
+    if (tau > 0.0 && dt < 80.0 * tau) h = exp_neg(r, r.mul(r.k(FK_MHDT), r.rcp(tau)));
     // below 1e-20 that part is under 1e-20 of the state it is added to: far below one ulp,
     // so its velocity moments are not evaluated (the flux terms, weighted by O(tau), are)
     const bool need_ne = (STAGE == 1) && (h >= 1e-20);

@@ -172,6 +172,7 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
     const int tid = threadIdx.x;
     constexpr double gq = 0.28867513459481287;   // 1/(2 sqrt 3): Gauss points at +-gq
     for (int i = tid; i < FK_NFIX; i += kThreads) s_fk[i] = kFluxFixed.v[i];
+    if (tid < 32) s_fk[FK_EXP2 + tid] = exp2((double)tid * (1.0 / 32.0));
     __syncthreads();
     const RegK r{s_fk, ((volatile const double*)s_fk)[FK_ONE], ((volatile const double*)s_fk)[FK_NZERO]};
 
