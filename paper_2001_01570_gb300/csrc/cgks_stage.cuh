@@ -5,8 +5,8 @@
 // the face results to the cells.
 //
 // One CTA owns a TX x TY tile of cells of one grid and runs, in shared memory:
-//   phase 1  load the face-row records the tile needs (its faces on its rows
-//            and two rows either side)
+//   phase 1  stage the face-row records the tile needs (its faces on its rows
+//            and two rows either side) with asynchronous copies
 //   phase 2  per face segment the tile owns (the x- and y-faces on the low side
 //            of its cells, plus the grid's last face where the tile ends on the
 //            grid's edge, so every face is evaluated once), at two Gauss points:
@@ -14,10 +14,13 @@
 //            (equilibrium) and j-1..j+1 (non-equilibrium states, with their
 //            tangential slopes); tangential derivatives of the equilibrium state
 //            and normal derivatives from the quartic / quadratic through the same
-//            line averages; the gas-kinetic evaluation at each point; the Gauss
+//            line averages (their Gauss-point-independent parts once per
+//            segment); the gas-kinetic evaluation at each point; the Gauss
 //            average, weighted by the stage's time factors, written to the face
 //            results (stage 1: the W* and R flux combinations and the interface
 //            states W(dt/2), W(dt); stage 2: dt^2/3 F_t and dt^2/3 W_tt)
+// Coefficients (fixed, and the tile's grid and dt) come from the shared-memory
+// table of cgks_flux.cuh; all arithmetic is in the register-only DFMA forms.
 // The kernel is persistent: CTAs stride over a flattened tile queue that may
 // span many grids of different sizes (each with its own dt in its Ctrl).
 #pragma once
