@@ -50,7 +50,7 @@ RECORD_FLOP_PER_CELL = {8: 3776.0, 6: 3680.0}
 FLUX_FLOP_PER_CELL = {1: 6322.4, 2: 5862.4}
 UPDATE_FLOP_PER_CELL = {1: 80.0, 2: 121.0}
 FLOP_PER_CELL = {s: RECORD_FLOP_PER_CELL[8] + FLUX_FLOP_PER_CELL[s] + UPDATE_FLOP_PER_CELL[s] for s in (1, 2)}
-DEFAULT_TILE = "16x16"    # the library's 2D default
+DEFAULT_TILE = "14x8"     # the library's 2D default
 # DRAM bytes (read + write) per cell of one flux-kernel launch with 16x16 tiles, ncu
 # dram__bytes_{read,write}.sum on the 1024^2 vortex (records and state larger than L2) divided by the
 # cells; the 2048^2 bench grid moves the same bytes per cell: profiles/flux_kernels_ncu_vortex1024.md.

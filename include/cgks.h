@@ -139,7 +139,7 @@ cgks_status cgks_batch_step(cgks_solver* const* solvers, int n, int nsteps);
  * 0: 16x8, 1: 8x16, 2: 32x4, 3: 64x1, 4: 16x7, 5: 7x16, 6: 14x8, 7: 24x8,
  * 8: 16x14, 9: 20x11, 10: 15x15, 11: 22x10, 12: 18x12, 13: 20x12, 14: 15x16,
  * 15: 17x14, 16: 16x16, 17: 24x16, 18: 32x12; -1
- * restores the default (16x16 in 2D, 64x1 in 1D).  The shape changes only the
+ * restores the default (14x8 in 2D, 64x1 in 1D).  The shape changes only the
  * decomposition of the work, never the results.  Errors: CGKS_E_INVAL (1D
  * solvers take only 64x1; 2D solvers any other shape). */
 cgks_status cgks_set_tile_shape(cgks_solver* s, int shape);

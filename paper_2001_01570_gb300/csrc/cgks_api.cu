@@ -111,7 +111,7 @@ cgks_status read_ctrl(cgks_solver* s, Ctrl* c)
 
 int pick_shape(const cgks_problem& p)
 {
-    return p.dim == 1 ? TILE_64x1 : TILE_16x16;
+    return p.dim == 1 ? TILE_64x1 : TILE_14x8;
 }
 
 }  // namespace
@@ -325,7 +325,7 @@ cgks_status cgks_get_state(cgks_solver* s, double* planes, int on_device, double
 
 static cgks_status enqueue_steps(cgks_solver* s, int nsteps, long* launches)
 {
-    const int nblocks = s->ntiles < s->nsm ? s->ntiles : s->nsm;
+    const int nblocks = stage_blocks(s->ntiles, s->nsm);
     const int cv = s->prob.recon_vars;
     const int rblocks = record_blocks(s->nrchunks, s->nsm, cv);
     const int ublocks = update_blocks(s->ncchunks, s->nsm);
@@ -390,7 +390,7 @@ cgks_status cgks_step_profiled(cgks_solver* s, int nsteps, double stage_ms[8])
     constexpr int NK = 8;
     std::vector<cudaEvent_t> ev((size_t)nsteps * (NK + 1));
     for (auto& e : ev) CK(cudaEventCreate(&e));
-    const int nblocks = s->ntiles < s->nsm ? s->ntiles : s->nsm;
+    const int nblocks = stage_blocks(s->ntiles, s->nsm);
     const int cv = s->prob.recon_vars;
     const int rblocks = record_blocks(s->nrchunks, s->nsm, cv);
     const int ublocks = update_blocks(s->ncchunks, s->nsm);
@@ -460,7 +460,7 @@ void destroy_plan(BatchPlan* bp)
 static cudaError_t capture_graph(BatchPlan* bp, int shape)
 {
     const int n = (int)bp->solvers.size();
-    const int nblocks = bp->ntiles[shape] < bp->nsm ? bp->ntiles[shape] : bp->nsm;
+    const int nblocks = stage_blocks(bp->ntiles[shape], bp->nsm);
     // first calls configure the kernels' attributes outside the capture
     cudaError_t e = launch_stage(shape, 1, bp->d_grids, bp->d_tiles[shape], 0, 1, bp->stream);
     if (e == cudaSuccess) e = launch_stage(shape, 2, bp->d_grids, bp->d_tiles[shape], 0, 1, bp->stream);
@@ -546,7 +546,7 @@ cudaError_t make_plan(cgks_solver* const* solvers, int n, cudaStream_t stream, i
     }
     if (bp->dim == 1) { bp->candidates = {TILE_64x1}; }
     else if (forced_shape >= 0) { bp->candidates = {forced_shape}; }
-    else { bp->candidates = {TILE_16x16, TILE_15x16, TILE_32x12, TILE_16x8}; }
+    else { bp->candidates = {TILE_14x8, TILE_16x8, TILE_16x7, TILE_16x16}; }
     for (int shape : bp->candidates) {
         std::vector<TileRef> tiles;
         for (int g = 0; g < n; ++g) {

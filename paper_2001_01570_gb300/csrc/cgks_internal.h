@@ -84,6 +84,13 @@ cudaError_t launch_update(int stage, const GridDev* grids, const TileRef* chunks
                           cudaStream_t st);
 // persistent grid of the update kernel: up to 8 resident CTAs per SM
 inline int update_blocks(int nchunks, int nsm) { return nchunks < 8 * nsm ? nchunks : 8 * nsm; }
+// flux kernel: two resident CTAs of 128 threads per SM (one stages its tile
+// while the other computes)
+constexpr int kStageCtasPerSm = 2;
+inline int stage_blocks(int ntiles, int nsm)
+{
+    return ntiles < kStageCtasPerSm * nsm ? ntiles : kStageCtasPerSm * nsm;
+}
 
 // persistent grid of the record kernel: its resident CTAs (two per SM with
 // conservative variables, one with characteristic ones), at most one per chunk

@@ -194,7 +194,7 @@ cgks_status cgks_step_noalloc(const cgks_problem* prob, double* planes, int nste
     // control block starts from t, step 0, no error, state in the caller's buffer
     NCK(launch_set_ctrl(sym->ctrl, *t_inout, 0.0, -1, 1, stream));
     NCK(launch_cfl(sym->desc, 0, G, stream));
-    const int nblocks = nt < nsm ? nt : nsm;
+    const int nblocks = stage_blocks(nt, nsm);
     const int rblocks = record_blocks(nrc, nsm, cv);
     const int ublocks = update_blocks(ncc, nsm);
     for (int k = 0; k < nsteps; ++k) {

@@ -31,21 +31,41 @@
 
 namespace cgks {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 128;
 
 static __constant__ FluxFixed kFluxFixed = make_flux_fixed();
 
 template <int STAGE> struct FaceQ { static constexpr int n = (STAGE == 1) ? 16 : 8; };
 
+// Face-row records of one orientation in shared memory: T own rows of F faces.
+// Group A (RV, RN: 8 planes) on rows -2..T+1, group B (RL, RR, RLN, RRN: 16
+// planes) on rows -1..T, group C (RNN: 4 planes) on rows 0..T-1 -- the rows each
+// field is read on.
+template <int T, int F>
+struct RecGroups {
+    static constexpr int pa = (T + 4) * F, pb = (T + 2) * F, pc = T * F;
+    static constexpr int n = 8 * pa + 16 * pb + 4 * pc;
+};
+
+// field f, variable k, row `off` relative to the row of r0 = row * F + face
+__device__ __forceinline__ double rec_at(const double* rec, int pa, int pb, int pc, int r0, int F, int f, int k,
+                                         int off)
+{
+    if (f == RV || f == RN) return rec[(f * 4 + k) * pa + r0 + (off + 2) * F];
+    if (f == RNN) return rec[8 * pa + 16 * pb + k * pc + r0 + off * F];
+    return rec[8 * pa + ((f - RL) * 4 + k) * pb + r0 + (off + 1) * F];
+}
+
 template <int TX, int TY, int STAGE>
 struct StageLayout {
     static constexpr int NF = FaceQ<STAGE>::n;
-    static constexpr int n_rx = 4 * NREC * (TY + 4) * (TX + 1);
-    static constexpr int n_ry = 4 * NREC * (TX + 4) * (TY + 1);
+    static constexpr int n_rx = RecGroups<TY, TX + 1>::n;
+    static constexpr int n_ry = RecGroups<TX, TY + 1>::n;
     // where it fits, a per-thread slice of 32 doubles holds the Gauss-point-independent
     // parts of the tangential / normal derivatives of one segment (shared by its two points)
     static constexpr int n_dc_full = 32 * kThreads;
-    static constexpr bool share = sizeof(double) * (size_t)(n_rx + n_ry + n_dc_full) + 1024 <= 227 * 1024;
+    static constexpr bool share =
+        kStageCtasPerSm * (sizeof(double) * (size_t)(n_rx + n_ry + n_dc_full) + 2048) <= 228 * 1024;
     static constexpr int n_dc = share ? n_dc_full : 0;
     static constexpr size_t bytes = sizeof(double) * (size_t)(n_rx + n_ry + n_dc);
 };
@@ -60,12 +80,15 @@ template <bool SHARE>
 struct SegmentRows {
     RegK r;
     const double* rec;
-    int nrec, r0, rstride;
+    int pa, pb, pc, r0, rstride;
     double eta, iht;
     double W0[4], sL[4], sR[4];   // WENO-Z values at this point, non-equilibrium slopes
     const double* dc;             // SHARE: this thread's slice of the segment's derivative parts
 
-    __device__ __forceinline__ double at(int f, int k, int off) const { return rec[(f * 4 + k) * nrec + r0 + off * rstride]; }
+    __device__ __forceinline__ double at(int f, int k, int off) const
+    {
+        return rec_at(rec, pa, pb, pc, r0, rstride, f, k, off);
+    }
 
     __device__ __forceinline__ void eq_value(double W[4]) const
     {
@@ -161,14 +184,14 @@ struct SegmentRows {
 };
 
 template <int TX, int TY, int STAGE>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, kStageCtasPerSm)
 stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tiles, int ntiles)
 {
     using L = StageLayout<TX, TY, STAGE>;
     constexpr int NF = L::NF;
     extern __shared__ double smem[];
-    double* rx = smem;                  // [28][TY+4][TX+1]
-    double* ry = rx + L::n_rx;          // [28][TX+4][TY+1]
+    double* rx = smem;                  // x-face records, RecGroups<TY, TX+1>
+    double* ry = rx + L::n_rx;          // y-face records, RecGroups<TX, TY+1>
     double* dc = ry + L::n_ry + threadIdx.x;   // [32][kThreads] when L::share
     __shared__ double s_fk[FK_N];       // coefficient table (fixed part, then the tile's grid and dt)
     __shared__ int s_skip;
@@ -195,29 +218,40 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
 
         // ---------------- phase 1: the tile's face-row records (the record kernel
         // wrote them for every face row of the grid): x-faces x0..x0+TX on rows
-        // y0-2..y0+TY+1, y-faces y0..y0+TY on columns x0-2..x0+TX+1; rows beyond
-        // the grid's last ghost row are zero and unused
+        // y0-2..y0+TY+1, y-faces y0..y0+TY on columns x0-2..x0+TX+1, each field on
+        // the rows it is read on; rows beyond the grid's last ghost row are zero
+        // and unused.  Asynchronous 8-byte copies, zero-filled where invalid.
         {
-            constexpr int NRX = (TX + 1) * (TY + 4), NRY = (TY + 1) * (TX + 4);
             const size_t sx = (size_t)(ny + 4) * (nx + 1), sy = (size_t)(nx + 4) * (ny + 1);
-            // asynchronous 8-byte copies (zero-filled where the row lies outside the grid)
             const unsigned sbx = (unsigned)__cvta_generic_to_shared(rx), sby = (unsigned)__cvta_generic_to_shared(ry);
-            for (int idx = tid; idx < 4 * NREC * NRX; idx += kThreads) {
-                const int fk = idx / NRX, r = idx - fk * NRX;
-                const int fl = r % (TX + 1), rl = r / (TX + 1);
-                const bool valid = (x0 + fl <= nx) && (y0 - 2 + rl <= ny + 1);
-                const double* src = valid ? G.recx + fk * sx + (size_t)(y0 + rl) * (nx + 1) + x0 + fl : G.recx;
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(sbx + 8u * (unsigned)idx), "l"(src),
-                             "r"(valid ? 8 : 0) : "memory");
-            }
-            for (int idx = tid; idx < 4 * NREC * NRY; idx += kThreads) {
-                const int fk = idx / NRY, r = idx - fk * NRY;
-                const int gl = r % (TY + 1), rl = r / (TY + 1);
-                const bool valid = !dim1 && (y0 + gl <= ny) && (x0 - 2 + rl <= nx + 1);
-                const double* src = valid ? G.recy + fk * sy + (size_t)(x0 + rl) * (ny + 1) + y0 + gl : G.recx;
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(sby + 8u * (unsigned)idx), "l"(src),
-                             "r"(valid ? 8 : 0) : "memory");
-            }
+            // group g of one orientation: plane p of the group is global plane p0 + p, its
+            // local row q is record row base + q (records carry two ghost rows first)
+            auto stage = [&](unsigned sbase, int sofs, int np, int plane, int nrow, int F, int p0, const double* g,
+                             size_t gs, int gfaces, int row0, int face0, int nface_max, int row_max, bool on) {
+                const int n = np * plane;
+                for (int idx = tid; idx < n; idx += kThreads) {
+                    const int p = idx / plane, rem = idx - p * plane;
+                    const int q = rem / F, fc = rem - q * F;
+                    const bool valid = on && (face0 + fc <= nface_max) && (row0 + q <= row_max);
+                    const double* src = valid ? g + (size_t)(p0 + p) * gs + (size_t)(row0 + q) * gfaces + face0 + fc
+                                              : G.recx;
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(sbase + 8u * (unsigned)(sofs + idx)),
+                                 "l"(src), "r"(valid ? 8 : 0) : "memory");
+                }
+                (void)nrow;
+            };
+            using RX = RecGroups<TY, TX + 1>;
+            using RY = RecGroups<TX, TY + 1>;
+            // x-faces: record rows y0 + 2 + (own row); group A starts two rows earlier, B one
+            stage(sbx, 0, 8, RX::pa, TY + 4, TX + 1, 0, G.recx, sx, nx + 1, y0, x0, nx, ny + 3, true);
+            stage(sbx, 8 * RX::pa, 16, RX::pb, TY + 2, TX + 1, 4 * RL, G.recx, sx, nx + 1, y0 + 1, x0, nx, ny + 3, true);
+            stage(sbx, 8 * RX::pa + 16 * RX::pb, 4, RX::pc, TY, TX + 1, 4 * RNN, G.recx, sx, nx + 1, y0 + 2, x0, nx,
+                  ny + 3, true);
+            stage(sby, 0, 8, RY::pa, TX + 4, TY + 1, 0, G.recy, sy, ny + 1, x0, y0, ny, nx + 3, !dim1);
+            stage(sby, 8 * RY::pa, 16, RY::pb, TX + 2, TY + 1, 4 * RL, G.recy, sy, ny + 1, x0 + 1, y0, ny, nx + 3,
+                  !dim1);
+            stage(sby, 8 * RY::pa + 16 * RY::pb, 4, RY::pc, TX, TY + 1, 4 * RNN, G.recy, sy, ny + 1, x0 + 2, y0, ny,
+                  nx + 3, !dim1);
             asm volatile("cp.async.wait_all;" ::: "memory");
         }
         __syncthreads();
@@ -241,16 +275,18 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
                 else { xo = false; il = it - xe; gl = TY; }
             }
             const double* rec;
-            int nrec, r0, rstride;
+            int pa, pb, pc, r0, rstride;
             double* out;
             size_t ostride, oidx;
             if (xo) {
                 if (!((x0 + fl <= nx) && (y0 + jl < ny))) continue;
-                rec = rx; nrec = (TY + 4) * (TX + 1); r0 = (jl + 2) * (TX + 1) + fl; rstride = TX + 1;
+                rec = rx; pa = RecGroups<TY, TX + 1>::pa; pb = RecGroups<TY, TX + 1>::pb; pc = RecGroups<TY, TX + 1>::pc;
+                r0 = jl * (TX + 1) + fl; rstride = TX + 1;
                 out = G.facex; ostride = nfx; oidx = (size_t)(y0 + jl) * (nx + 1) + x0 + fl;
             } else {
                 if (!((y0 + gl <= ny) && (x0 + il < nx))) continue;
-                rec = ry; nrec = (TX + 4) * (TY + 1); r0 = (il + 2) * (TY + 1) + gl; rstride = TY + 1;
+                rec = ry; pa = RecGroups<TX, TY + 1>::pa; pb = RecGroups<TX, TY + 1>::pb; pc = RecGroups<TX, TY + 1>::pc;
+                r0 = il * (TY + 1) + gl; rstride = TY + 1;
                 out = G.facey; ostride = nfy; oidx = (size_t)(y0 + gl) * nx + x0 + il;
             }
             const double iht = r.k(xo ? FK_IDY : FK_IDX);
@@ -262,7 +298,7 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
             double W0m[4], W0p[4], sL[4], sR[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                auto R = [&](int f, int off) { return rec[(f * 4 + k) * nrec + r0 + off * rstride]; };
+                auto R = [&](int f, int off) { return rec_at(rec, pa, pb, pc, r0, rstride, f, k, off); };
                 const double m2m = R(RV, -2), mm = R(RV, -1), m0 = R(RV, 0), mp = R(RV, 1), m2p = R(RV, 2);
                 tang_weno5_pair(r, m2m, mm, m0, mp, m2p, weps, W0m[k], W0p[k]);
                 if constexpr (L::share)
@@ -274,7 +310,7 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
 #pragma unroll 1
             for (int gp = 0; gp < 2; ++gp) {
                 const double eta = gp ? gq : -gq;
-                const SegmentRows<L::share> src{r, rec, nrec, r0, rstride, eta, iht,
+                const SegmentRows<L::share> src{r, rec, pa, pb, pc, r0, rstride, eta, iht,
                                                 {gp ? W0p[0] : W0m[0], gp ? W0p[1] : W0m[1], gp ? W0p[2] : W0m[2],
                                                  gp ? W0p[3] : W0m[3]},
                                                 {sL[0], sL[1], sL[2], sL[3]}, {sR[0], sR[1], sR[2], sR[3]}, dc};
