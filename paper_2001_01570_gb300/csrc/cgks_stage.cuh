@@ -226,8 +226,8 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
             const unsigned sbx = (unsigned)__cvta_generic_to_shared(rx), sby = (unsigned)__cvta_generic_to_shared(ry);
             // group g of one orientation: plane p of the group is global plane p0 + p, its
             // local row q is record row base + q (records carry two ghost rows first)
-            auto stage = [&](unsigned sbase, int sofs, int np, int plane, int nrow, int F, int p0, const double* g,
-                             size_t gs, int gfaces, int row0, int face0, int nface_max, int row_max, bool on) {
+            auto stage = [&](unsigned sbase, int sofs, int np, int plane, int F, int p0, const double* g, size_t gs,
+                             int gfaces, int row0, int face0, int nface_max, int row_max, bool on) {
                 const int n = np * plane;
                 for (int idx = tid; idx < n; idx += kThreads) {
                     const int p = idx / plane, rem = idx - p * plane;
@@ -238,20 +238,18 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
                     asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(sbase + 8u * (unsigned)(sofs + idx)),
                                  "l"(src), "r"(valid ? 8 : 0) : "memory");
                 }
-                (void)nrow;
             };
             using RX = RecGroups<TY, TX + 1>;
             using RY = RecGroups<TX, TY + 1>;
             // x-faces: record rows y0 + 2 + (own row); group A starts two rows earlier, B one
-            stage(sbx, 0, 8, RX::pa, TY + 4, TX + 1, 0, G.recx, sx, nx + 1, y0, x0, nx, ny + 3, true);
-            stage(sbx, 8 * RX::pa, 16, RX::pb, TY + 2, TX + 1, 4 * RL, G.recx, sx, nx + 1, y0 + 1, x0, nx, ny + 3, true);
-            stage(sbx, 8 * RX::pa + 16 * RX::pb, 4, RX::pc, TY, TX + 1, 4 * RNN, G.recx, sx, nx + 1, y0 + 2, x0, nx,
-                  ny + 3, true);
-            stage(sby, 0, 8, RY::pa, TX + 4, TY + 1, 0, G.recy, sy, ny + 1, x0, y0, ny, nx + 3, !dim1);
-            stage(sby, 8 * RY::pa, 16, RY::pb, TX + 2, TY + 1, 4 * RL, G.recy, sy, ny + 1, x0 + 1, y0, ny, nx + 3,
+            stage(sbx, 0, 8, RX::pa, TX + 1, 0, G.recx, sx, nx + 1, y0, x0, nx, ny + 3, true);
+            stage(sbx, 8 * RX::pa, 16, RX::pb, TX + 1, 4 * RL, G.recx, sx, nx + 1, y0 + 1, x0, nx, ny + 3, true);
+            stage(sbx, 8 * RX::pa + 16 * RX::pb, 4, RX::pc, TX + 1, 4 * RNN, G.recx, sx, nx + 1, y0 + 2, x0, nx, ny + 3,
+                  true);
+            stage(sby, 0, 8, RY::pa, TY + 1, 0, G.recy, sy, ny + 1, x0, y0, ny, nx + 3, !dim1);
+            stage(sby, 8 * RY::pa, 16, RY::pb, TY + 1, 4 * RL, G.recy, sy, ny + 1, x0 + 1, y0, ny, nx + 3, !dim1);
+            stage(sby, 8 * RY::pa + 16 * RY::pb, 4, RY::pc, TY + 1, 4 * RNN, G.recy, sy, ny + 1, x0 + 2, y0, ny, nx + 3,
                   !dim1);
-            stage(sby, 8 * RY::pa + 16 * RY::pb, 4, RY::pc, TX, TY + 1, 4 * RNN, G.recy, sy, ny + 1, x0 + 2, y0, ny,
-                  nx + 3, !dim1);
             asm volatile("cp.async.wait_all;" ::: "memory");
         }
         __syncthreads();
