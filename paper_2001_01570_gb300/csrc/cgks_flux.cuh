@@ -459,9 +459,9 @@ __device__ __forceinline__ bool gks_point(const RegK& r, const Src& src, double 
     double Fh[4], Th[4], Wh[4] = {0, 0, 0, 0}, Wsl[4] = {0, 0, 0, 0};
     {
         Moments ml;
-        const double ithl = r.rcp(thl);
         const double th2 = r.add(thl, thl);
-        const double sq = rsqrt(th2);                     // sqrt(lambda_l)
+        const double sq = rsqrt(th2);                     // sqrt(lambda_l) = 1/sqrt(2 theta)
+        const double ithl = r.mul(r.add(sq, sq), sq);     // 1/theta = 2 lambda_l
         half_moments01<+1>(r, Ul, sq, r.mul(th2, sq), ml.u[0], ml.u[1]);
         moments_tail(r, ml, Ul, Vl, thl);
         SlopeCtx sl;
@@ -483,9 +483,9 @@ __device__ __forceinline__ bool gks_point(const RegK& r, const Src& src, double 
     }
     {
         Moments mr;
-        const double ithr = r.rcp(thr);
         const double th2 = r.add(thr, thr);
         const double sq = rsqrt(th2);
+        const double ithr = r.mul(r.add(sq, sq), sq);
         half_moments01<-1>(r, Ur, sq, r.mul(th2, sq), mr.u[0], mr.u[1]);
         moments_tail(r, mr, Ur, Vr, thr);
         SlopeCtx sr;
