@@ -54,7 +54,7 @@ DEFAULT_TILE = "14x8"     # the library's 2D default
 # DRAM bytes (read + write) per cell of one flux-kernel launch with 14x8 tiles, ncu
 # dram__bytes_{read,write}.sum on the 1024^2 vortex (records and state larger than L2) divided by the
 # cells; the 2048^2 bench grid moves the same bytes per cell: profiles/flux_kernels_ncu_vortex1024.md.
-FLUX_DRAM_BYTES_PER_CELL = {1: 731.95e6 / 1048576, 2: 597.78e6 / 1048576}
+FLUX_DRAM_BYTES_PER_CELL = {1: 730.99e6 / 1048576, 2: 597.07e6 / 1048576}
 # algorithmic bytes per cell of the flux kernel: the two face rows' records (2 x 28 doubles) read and
 # the two faces' results written (stage 1: 16 doubles each, stage 2: 8)
 FLUX_ALGO_BYTES_PER_CELL = {1: 448 + 256, 2: 448 + 128}
