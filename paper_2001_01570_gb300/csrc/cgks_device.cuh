@@ -194,13 +194,15 @@ __device__ __forceinline__ void weno_side_rk(const RegK& r, double base, double 
     const double Z = fabs(r.kfma(RK_Z + 0, e0, r.kfma(RK_Z + 1, e4, -e3)));
     const double p01 = r.mul(e0, e1), p012 = r.mul(p01, e2), p0123 = r.mul(p012, e3), p01234 = r.mul(p0123, e4);
     const double s56 = r.mul(e5, e6), s456 = r.mul(e4, s56), s3456 = r.mul(e3, s456), s23456 = r.mul(e2, s3456);
-    const double t0 = r.mul(r.add(e0, Z), r.mul(e1, s23456));
-    const double t1 = r.mul(r.add(e1, Z), r.mul(e0, s23456));
-    const double t2 = r.mul(r.add(e2, Z), r.mul(p01, s3456));
-    const double t3 = r.mul(r.add(e3, Z), r.mul(p012, s456));
-    const double t4 = r.mul(r.add(e4, Z), r.mul(p0123, s56));
-    const double t5 = r.mul(r.add(e5, Z), r.mul(p01234, e6));
-    const double t6 = r.mul(r.add(e6, Z), r.mul(p01234, e5));
+    // t_k = (e_k + Z) L_k = P + Z L_k with L_k the product of the other six and P of all seven
+    const double P = r.mul(p01234, s56);
+    const double t0 = fma(Z, r.mul(e1, s23456), P);
+    const double t1 = fma(Z, r.mul(e0, s23456), P);
+    const double t2 = fma(Z, r.mul(p01, s3456), P);
+    const double t3 = fma(Z, r.mul(p012, s456), P);
+    const double t4 = fma(Z, r.mul(p0123, s56), P);
+    const double t5 = fma(Z, r.mul(p01234, e6), P);
+    const double t6 = fma(Z, r.mul(p01234, e5), P);
     const double n13 = r.kfma(RK_W + 1, t1, r.kmul(RK_W + 3, t3)), n4 = r.kmul(RK_W + 4, t4);
     const double den = r.kfma(RK_W + 6, t6, r.kfma(RK_W + 5, t5, r.add(r.kfma(RK_W + 2, t2, r.kfma(RK_W + 0, t0, n13)), n4)));
     const double inv = r.rcp(den);

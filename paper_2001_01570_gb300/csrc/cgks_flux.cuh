@@ -132,9 +132,11 @@ __device__ __forceinline__ void tang_weno5_pair(const RegK& r, double vmm, doubl
     const double e1 = fma(r.kmul(FK_QUARTER, D1), D1, fma(r.kmul(FK_T13_12, s1), s1, eps));
     const double e2 = fma(r.kmul(FK_QUARTER, D2), D2, fma(r.kmul(FK_T13_12, s2), s2, eps));
     const double Z = fabs(r.sub(e0, e2));
-    const double P0 = r.mul(r.add(e0, Z), r.mul(e1, e2));
-    const double P1 = r.mul(r.kmul(FK_T11_18, r.add(e1, Z)), r.mul(e0, e2));
-    const double P2 = r.mul(r.add(e2, Z), r.mul(e0, e1));
+    // (e_k + Z) times the other two = E + Z times the other two, E = e0 e1 e2
+    const double e12 = r.mul(e1, e2), E = r.mul(e0, e12);
+    const double P0 = fma(Z, e12, E);
+    const double P1 = r.kmul(FK_T11_18, fma(Z, r.mul(e0, e2), E));
+    const double P2 = fma(Z, r.mul(e0, e1), E);
     const double Q0 = r.mul(P0, D0), Q1 = r.mul(P1, D1), Q2 = r.mul(P2, D2);
     const double np = r.kfma(FK_DHI, Q2, r.kfma(FK_DLO, Q0, Q1)), dp = r.kfma(FK_DHI, P2, r.kfma(FK_DLO, P0, P1));
     const double nm = r.kfma(FK_DLO, Q2, r.kfma(FK_DHI, Q0, Q1)), dm = r.kfma(FK_DLO, P2, r.kfma(FK_DHI, P0, P1));
@@ -152,7 +154,8 @@ __device__ __forceinline__ double tang_weno3_slope(const RegK& r, double vm, dou
     const double dm = r.sub(v0, vm), dp = r.sub(vp, v0);
     const double e0 = fma(dm, dm, eps), e1 = fma(dp, dp, eps);
     const double Z = fabs(r.sub(e0, e1));
-    const double n0 = r.mul(r.add(e0, Z), e1), n1 = r.mul(r.add(e1, Z), e0);
+    const double e01 = r.mul(e0, e1);
+    const double n0 = fma(Z, e1, e01), n1 = fma(Z, e0, e01);          // (e0 + Z) e1, (e1 + Z) e0
     return r.mul(fma(n1, dp, r.mul(n0, dm)), r.rcp(r.add(n0, n1)));
 }
 
