@@ -269,8 +269,14 @@ __device__ __forceinline__ void q_moments(const RegK& r, const Moments& m, const
     for (int s2 = 0; s2 < 3; ++s2) {
         Z0[s2] = r.mul(h1, m.u[A + 1 + s2]);
         Z1[s2] = r.mul(h2, m.u[A + s2]);
-        S0[s2] = fma(h1, m.u[A + 3 + s2], fma(a1[1], m.u[A + 2 + s2], r.mul(a1[0], m.u[A + 1 + s2])));
-        S1[s2] = fma(h2, m.u[A + 2 + s2], fma(c12, m.u[A + 1 + s2], r.mul(a2[0], m.u[A + s2])));
+    }
+#pragma unroll
+    for (int s2 = 0; s2 < 3; ++s2) {
+        // h1 u[A+3] = Z0[2] and h2 u[A+2] = Z1[2] for the first shift
+        const double t0 = (s2 == 0) ? Z0[2] : r.mul(h1, m.u[A + 3 + s2]);
+        const double t1 = (s2 == 0) ? Z1[2] : r.mul(h2, m.u[A + 2 + s2]);
+        S0[s2] = fma(a1[1], m.u[A + 2 + s2], fma(a1[0], m.u[A + 1 + s2], t0));
+        S1[s2] = fma(c12, m.u[A + 1 + s2], fma(a2[0], m.u[A + s2], t1));
         S2[s2] = fma(a2[2], m.u[A + s2], Z0[s2]);
     }
     const double x1 = m.x1, x2 = m.x2;
@@ -341,12 +347,13 @@ __device__ __forceinline__ void euler_time_derivs(const RegK& r, const double W[
     const double px = r.mul(r.k(FK_GM1), r.sub(Wx[3], KEx)), py = r.mul(r.k(FK_GM1), r.sub(Wy[3], KEy));
     // primitive second derivatives
     const double rxx = Wxx[0], rxy = Wxy[0], ryy = Wyy[0];
-    const double Uxx = r.mul(fma(-U, rxx, fma(-r.add(Ux, Ux), rx, Wxx[1])), ir);
+    const double rx2 = r.add(rx, rx), ry2 = r.add(ry, ry);
+    const double Uxx = r.mul(fma(-U, rxx, fma(-Ux, rx2, Wxx[1])), ir);
     const double Uxy = r.mul(fma(-U, rxy, fma(-Uy, rx, fma(-Ux, ry, Wxy[1]))), ir);
-    const double Uyy = r.mul(fma(-U, ryy, fma(-r.add(Uy, Uy), ry, Wyy[1])), ir);
-    const double Vxx = r.mul(fma(-V, rxx, fma(-r.add(Vx, Vx), rx, Wxx[2])), ir);
+    const double Uyy = r.mul(fma(-U, ryy, fma(-Uy, ry2, Wyy[1])), ir);
+    const double Vxx = r.mul(fma(-V, rxx, fma(-Vx, rx2, Wxx[2])), ir);
     const double Vxy = r.mul(fma(-V, rxy, fma(-Vy, rx, fma(-Vx, ry, Wxy[2]))), ir);
-    const double Vyy = r.mul(fma(-V, ryy, fma(-r.add(Vy, Vy), ry, Wyy[2])), ir);
+    const double Vyy = r.mul(fma(-V, ryy, fma(-Vy, ry2, Wyy[2])), ir);
     const double KExx = fma(-hq2, rxx, fma(V, Wxx[2], fma(U, Wxx[1], r.mul(rho, fma(Ux, Ux, r.mul(Vx, Vx))))));
     const double KExy = fma(-hq2, rxy, fma(V, Wxy[2], fma(U, Wxy[1], r.mul(rho, fma(Ux, Uy, r.mul(Vx, Vy))))));
     const double KEyy = fma(-hq2, ryy, fma(V, Wyy[2], fma(U, Wyy[1], r.mul(rho, fma(Uy, Uy, r.mul(Vy, Vy))))));
@@ -522,9 +529,10 @@ __device__ __forceinline__ bool gks_point(const RegK& r, const Src& src, double 
     const double thm = r.sub(r.k(FK_3), h);                  // 3 - h
     const double ta = r.mul(tau, omh);
     const double a = r.mul(r.mul(ta, thm), idt);
-    const double g = r.mul(r.mul(r.mul(r.kmul(FK_4, ta), omh), idt), idt);
+    const double q4 = r.mul(r.mul(r.kmul(FK_4, ta), idt), idt);    // 4 tau (1 - h) / dt^2
+    const double g = r.mul(q4, omh);
     const double b4 = r.mul(r.mul(tau, fma(-r.mul(dt, h), r.sub(r.k(FK_2), h), r.mul(r.mul(tau, omh), thm))), idt);
-    const double f4 = r.mul(r.mul(r.mul(r.kmul(FK_4, ta), fma(dt, h, -ta)), idt), idt);
+    const double f4 = r.mul(q4, fma(dt, h, -ta));
     for (int k = 0; k < 4; ++k) {
         const double dTh = (k == 0) ? -r.add(e.Ft[0], Th[0]) : r.sub(r.sub(e.TNS[k], e.Ft[k]), Th[k]);
         const double dFh = r.sub(Fh[k], e.F[k]);
