@@ -353,6 +353,10 @@ cudaError_t launch_stage_t(const GridDev* grids, const TileRef* tiles, int ntile
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(stage_kernel<TX, TY, STAGE>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
+        // the largest shared-memory carveout, so that two CTAs fit where the shape allows
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(stage_kernel<TX, TY, STAGE>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
         configured = true;
     }
