@@ -140,23 +140,38 @@ __device__ __forceinline__ void tang_weno5_pair(const RegK& r, double vmm, doubl
     const double Q0 = r.mul(P0, D0), Q1 = r.mul(P1, D1), Q2 = r.mul(P2, D2);
     const double np = r.kfma(FK_DHI, Q2, r.kfma(FK_DLO, Q0, Q1)), dp = r.kfma(FK_DHI, P2, r.kfma(FK_DLO, P0, P1));
     const double nm = r.kfma(FK_DLO, Q2, r.kfma(FK_DHI, Q0, Q1)), dm = r.kfma(FK_DLO, P2, r.kfma(FK_DHI, P0, P1));
-    at_plus = r.kfma(FK_HG, r.mul(np, r.rcp(dp)), v0);
-    at_minus = r.kfma(FK_MHG, r.mul(nm, r.rcp(dm)), v0);
+    const double inv = r.rcp(r.mul(dp, dm));             // one reciprocal for both points
+    at_plus = r.kfma(FK_HG, r.mul(np, r.mul(dm, inv)), v0);
+    at_minus = r.kfma(FK_MHG, r.mul(nm, r.mul(dp, inv)), v0);
 }
 
 // Three means v_{-1..1}: two linear candidates with slopes v_0 - v_-1 and
 // v_1 - v_0, linear weights 1/2 at both Gauss points (the quadratic through the
 // three means has no eta^2 - 1/12 term there), beta_k = slope_k^2, Z = |beta_0 -
-// beta_1|.  The weights do not depend on eta: returns the nonlinear slope per
-// unit eta; the point value is v_0 + eta * slope.
-__device__ __forceinline__ double tang_weno3_slope(const RegK& r, double vm, double v0, double vp, double eps)
+// beta_1|.  The weights do not depend on eta: the nonlinear slope per unit eta
+// is num / den; the point value is v_0 + eta * slope.
+__device__ __forceinline__ void tang_weno3_parts(const RegK& r, double vm, double v0, double vp, double eps,
+                                                 double& num, double& den)
 {
     const double dm = r.sub(v0, vm), dp = r.sub(vp, v0);
     const double e0 = fma(dm, dm, eps), e1 = fma(dp, dp, eps);
     const double Z = fabs(r.sub(e0, e1));
     const double e01 = r.mul(e0, e1);
     const double n0 = fma(Z, e1, e01), n1 = fma(Z, e0, e01);          // (e0 + Z) e1, (e1 + Z) e0
-    return r.mul(fma(n1, dp, r.mul(n0, dm)), r.rcp(r.add(n0, n1)));
+    num = fma(n1, dp, r.mul(n0, dm));
+    den = r.add(n0, n1);
+}
+
+// the slopes of the left and right states' rows, with one reciprocal for both
+__device__ __forceinline__ void tang_weno3_slopes(const RegK& r, double lm, double l0, double lp, double rm,
+                                                  double r0, double rp, double eps, double& sl, double& sr)
+{
+    double nl, dl, nr, dr;
+    tang_weno3_parts(r, lm, l0, lp, eps, nl, dl);
+    tang_weno3_parts(r, rm, r0, rp, eps, nr, dr);
+    const double inv = r.rcp(r.mul(dl, dr));
+    sl = r.mul(nl, r.mul(dr, inv));
+    sr = r.mul(nr, r.mul(dl, inv));
 }
 
 // ------------------------------------------------------------------------

@@ -302,8 +302,8 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
                 if constexpr (L::share)
                     SegmentRows<true>::seg_deriv_parts(r, dc + 8 * k * kThreads, m2m, mm, m0, mp, m2p, R(RN, -2),
                                                        R(RN, -1), R(RN, 0), R(RN, 1), R(RN, 2));
-                sL[k] = tang_weno3_slope(r, R(RL, -1), R(RL, 0), R(RL, 1), weps);
-                sR[k] = tang_weno3_slope(r, R(RR, -1), R(RR, 0), R(RR, 1), weps);
+                tang_weno3_slopes(r, R(RL, -1), R(RL, 0), R(RL, 1), R(RR, -1), R(RR, 0), R(RR, 1), weps, sL[k],
+                                  sR[k]);
             }
 #pragma unroll 1
             for (int gp = 0; gp < 2; ++gp) {
