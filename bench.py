@@ -38,22 +38,22 @@ UNIT = "cell-updates/s"
 
 # Algorithmic FP64 operations per cell and stage (FMA = 2) on the 256^2 vortex, where every kernel does
 # exactly the method's work (no halo recomputation, every face once): two face-row records (1,888
-# each: linear P7 + WENO-Z pair of 4 variables), two face segments (3,152.4 in stage 1, 2,931.2 in
+# each: linear P7 + WENO-Z pair of 4 variables), two face segments (3,112.4 in stage 1, 2,916.4 in
 # stage 2: two Gauss points each) and the update (80 / 121).  The kernels issue their adds and
 # multiplies as DFMAs, so the operations are counted by ncu on a build with plain adds and
 # multiplies; each per-unit figure is the smallest count of the formulations measured (the current
-# code spends 1,916 per record and 3,152.4 / 2,956.4 per segment): profiles/stage_kernels_flops_vortex256.md.
+# code spends 1,916 per record and 3,112.4 / 2,916.4 per segment): profiles/stage_kernels_flops_vortex256.md.
 # The compact 6th-order variant (--order 6) changes only the record kernel's linear reconstruction:
 # 1,840 per face row with WENO-Z.
 RECORD_FLOP_PER_CELL = {8: 3776.0, 6: 3680.0}
-FLUX_FLOP_PER_CELL = {1: 6304.8, 2: 5862.4}
+FLUX_FLOP_PER_CELL = {1: 6224.8, 2: 5832.8}
 UPDATE_FLOP_PER_CELL = {1: 80.0, 2: 121.0}
 FLOP_PER_CELL = {s: RECORD_FLOP_PER_CELL[8] + FLUX_FLOP_PER_CELL[s] + UPDATE_FLOP_PER_CELL[s] for s in (1, 2)}
 DEFAULT_TILE = "14x8"     # the library's 2D default
 # DRAM bytes (read + write) per cell of one flux-kernel launch with 14x8 tiles, ncu
 # dram__bytes_{read,write}.sum on the 1024^2 vortex (records and state larger than L2) divided by the
 # cells; the 2048^2 bench grid moves the same bytes per cell: profiles/flux_kernels_ncu_vortex1024.md.
-FLUX_DRAM_BYTES_PER_CELL = {1: 731.01e6 / 1048576, 2: 597.49e6 / 1048576}
+FLUX_DRAM_BYTES_PER_CELL = {1: 732.16e6 / 1048576, 2: 599.89e6 / 1048576}
 # algorithmic bytes per cell of the flux kernel: the two face rows' records (2 x 28 doubles) read and
 # the two faces' results written (stage 1: 16 doubles each, stage 2: 8)
 FLUX_ALGO_BYTES_PER_CELL = {1: 448 + 256, 2: 448 + 128}
