@@ -8,6 +8,7 @@ seeded sample of cells.
   python tests/golden/make_golden.py vortex512     # isentropic vortex 512^2, 200 steps
   python tests/golden/make_golden.py shockvortex   # shock-vortex 1024x512, 400 steps
   python tests/golden/make_golden.py pulses        # 8 smallest grids of the 256-grid batch, 100 steps
+  python tests/golden/make_golden.py vortex2048    # isentropic vortex 2048^2 (the bench grid), 2 steps
 """
 import os
 import sys
@@ -50,6 +51,9 @@ def main(which):
     elif which == "shockvortex":
         spec, W = wl.shock_vortex(1024, 512)
         write_case("shockvortex1024x512_400", spec, W, 400, seed=1024)
+    elif which == "vortex2048":
+        spec, W = wl.isentropic_vortex(2048)
+        write_case("vortex2048_2", spec, W, 2, seed=2048)
     elif which == "pulses":
         params = wl.batched_pulses()
         order = sorted(range(len(params)), key=lambda k: params[k]["N"])[:8]

@@ -53,6 +53,15 @@ def test_vortex_512_200_steps():
     _compare(out, g, spec)
 
 
+def test_vortex_2048_bench_grid_2_steps():
+    """The bench's own grid and launch configuration (default tile shape, plain steps)."""
+    g = _golden("vortex2048_2")
+    spec, W = wl.isentropic_vortex(2048)
+    out, t, steps = _run(spec, W, 2)
+    assert steps == int(g["steps"]) == 2 and abs(t - float(g["t"])) <= 1e-13 * float(g["t"])
+    _compare(out, g, spec)
+
+
 def test_shock_vortex_1024x512_400_steps():
     g = _golden("shockvortex1024x512_400")
     spec, W = wl.shock_vortex(1024, 512)
