@@ -9,6 +9,7 @@ seeded sample of cells.
   python tests/golden/make_golden.py shockvortex   # shock-vortex 1024x512, 400 steps
   python tests/golden/make_golden.py pulses        # 8 smallest grids of the 256-grid batch, 100 steps
   python tests/golden/make_golden.py vortex2048    # isentropic vortex 2048^2 (the bench grid), 2 steps
+  python tests/golden/make_golden.py vortex2048o6  # the same grid, compact 6th-order variant, 1 step
 """
 import os
 import sys
@@ -54,6 +55,10 @@ def main(which):
     elif which == "vortex2048":
         spec, W = wl.isentropic_vortex(2048)
         write_case("vortex2048_2", spec, W, 2, seed=2048)
+    elif which == "vortex2048o6":
+        spec, W = wl.isentropic_vortex(2048)
+        spec.order = 6
+        write_case("vortex2048o6_1", spec, W, 1, seed=2049)
     elif which == "pulses":
         params = wl.batched_pulses()
         order = sorted(range(len(params)), key=lambda k: params[k]["N"])[:8]

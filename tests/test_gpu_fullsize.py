@@ -62,6 +62,15 @@ def test_vortex_2048_bench_grid_2_steps():
     _compare(out, g, spec)
 
 
+def test_vortex_2048_sixth_order_variant_1_step():
+    g = _golden("vortex2048o6_1")
+    spec, W = wl.isentropic_vortex(2048)
+    spec.order = 6
+    out, t, steps = _run(spec, W, 1)
+    assert steps == int(g["steps"]) == 1 and abs(t - float(g["t"])) <= 1e-13 * float(g["t"])
+    _compare(out, g, spec)
+
+
 def test_shock_vortex_1024x512_400_steps():
     g = _golden("shockvortex1024x512_400")
     spec, W = wl.shock_vortex(1024, 512)
