@@ -1209,7 +1209,7 @@ int oc_step2d_halo(const oc_problem *P, double *W, double dt, oc_exchange_fn fn,
 }
 
 /* ------------------------------------------------------------------ */
-/* driver: advance nsteps (or until t_end when t_end > 0).  W holds the
+/* time loop: advance nsteps (or until t_end when t_end > 0).  W holds the
  * planes (1D: 6 x nx, 2D: 12 x ny x nx).  t and steps are updated.       */
 int oc_run(const oc_problem *P, double *W, int nsteps, double t_end, double *t, long *steps, double *last_dt)
 {

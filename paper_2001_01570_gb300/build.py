@@ -3,7 +3,7 @@
 Each .cu translation unit is compiled by its own nvcc process (the tile-shape
 instantiations of the stage kernel are the slow ones), then linked with
 ``nvcc -shared``.  CUDA runtime is linked statically so the library only
-needs the driver.
+needs the CUDA driver library (libcuda).
 """
 from __future__ import annotations
 
