@@ -224,3 +224,34 @@ def test_gks_point_mirror_symmetry():
     assert np.allclose(b["S1"], flux_sign * a["S1"], rtol=1e-12, atol=1e-14)
     assert np.allclose(b["S2"], flux_sign * a["S2"], rtol=1e-12, atol=1e-14)
     assert np.allclose(b["NEf"], m(a["NEf"]), rtol=1e-12, atol=1e-14)
+
+
+def test_collision_time_pressure_jump_limits():
+    """Sec. 4's collision time at an interface: equal left/right pressures leave only eps*dt (the
+    smooth-flow value); the enhancement is symmetric in the two sides, grows with |p_l - p_r| and
+    tends to (eps + C) dt as one pressure dominates; with mu > 0 the first part is mu/p of the
+    equilibrium state, whatever the jump."""
+    D, dt, eps, C = 1, 0.01, 0.01, 1.0
+    P = O.make_problem(dim=D, nx=4, ny=1, dx=1, dy=1, eps_tau=eps, c_tau=C)
+
+    def tau_of(pl, pr, problem=P, p0=None):
+        Wl = np.array([1.0, 0.0, pl / (GAMMA - 1.0)])
+        Wr = np.array([1.0, 0.0, pr / (GAMMA - 1.0)])
+        W0 = 0.5 * (Wl + Wr) if p0 is None else np.array([1.0, 0.0, p0 / (GAMMA - 1.0)])
+        return O.gks_point(problem, D, dt, W0=W0, Wl=Wl, Wr=Wr)["tau"]
+
+    assert tau_of(0.7, 0.7) == eps * dt
+    jumps = [tau_of(1.0, pr) for pr in (1.0, 0.9, 0.5, 0.1, 1e-3, 1e-9)]
+    assert all(b > a for a, b in zip(jumps, jumps[1:])), jumps
+    assert tau_of(1.0, 0.3) == tau_of(0.3, 1.0)
+    # p_r / p_l = 1e-9: the limit (eps + C) dt is approached as 2 C (p_r / p_l) dt
+    assert 0.0 < (eps + C) * dt - jumps[-1] < 2.5e-9 * C * dt
+    # without the jump term (C = 0) the pressure ratio is irrelevant
+    P0 = O.make_problem(dim=D, nx=4, ny=1, dx=1, dy=1, eps_tau=eps, c_tau=0.0)
+    assert tau_of(1.0, 1e-3, P0) == eps * dt
+    # viscous: mu / p of the equilibrium state, the jump term added on top
+    mu = 2e-3
+    Pv = O.make_problem(dim=D, nx=4, ny=1, dx=1, dy=1, eps_tau=eps, c_tau=0.0, mu=mu)
+    assert abs(tau_of(1.0, 1.0, Pv, p0=0.8) - mu / 0.8) < 1e-15
+    Pvc = O.make_problem(dim=D, nx=4, ny=1, dx=1, dy=1, eps_tau=eps, c_tau=C, mu=mu)
+    assert tau_of(1.0, 0.5, Pvc, p0=0.8) > tau_of(1.0, 0.5, Pv, p0=0.8)

@@ -1,0 +1,153 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case below plants one mistake (a wrong coefficient, sign or index, a dropped term, a transposed
+operand) in a copy of the oracle's C source, builds that copy with the oracle's own flags, and runs
+the pin tests named beside it against the planted library (``CGKS_ORACLE_LIB``): at least one of
+them must fail.  A control run of every named pin against an unplanted copy, through the same
+override, must pass, so a failure comes from the planted mistake and not from the harness.
+
+Everything here is CPU-only and touches only the oracle; the CUDA library is not involved.
+"""
+from __future__ import annotations
+
+import os
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+import pytest
+
+import oracle as O
+
+REPO = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+R = "tests/test_oracle_recon.py::"
+K = "tests/test_oracle_kinetic.py::"
+S = "tests/test_oracle_scheme.py::"
+V = "tests/test_oracle_viscous.py::"
+C = "tests/test_oracle_characteristic.py::"
+T = "tests/test_oracle_tangential.py::"
+X = "tests/test_oracle_sixth_order.py::"
+
+# (what the mistake is, text in the oracle source, its replacement, pins expected to catch it)
+MUTANTS = [
+    ("P7 value: one coefficient of Eq. (recons-8th-val)", "185.0 * Q[2]", "158.0 * Q[2]",
+     [R + "test_linear_recon_exact_up_to_degree_7"]),
+    ("P7 slope: one sign", "- 99.0 * hQp[2]", "+ 99.0 * hQp[2]",
+     [R + "test_linear_recon_exact_up_to_degree_7"]),
+    ("P7 second derivative: a dropped term", "- hQp[0] - 9.0 * hQp[1]", "- 9.0 * hQp[1]",
+     [R + "test_linear_recon_exact_up_to_degree_7"]),
+    ("candidate slope at the interface: the power factor dropped",
+     "sl += m * c[m] * ipow(0.5, m - 1)", "sl += c[m] * ipow(0.5, m - 1)",
+     [R + "test_indicators_slopes_match_symbolic_definition"]),
+    ("smoothness indicator: wrong integral of xi^e", "ipow(-0.5, e + 1)) / (e + 1)",
+     "ipow(-0.5, e + 1)) / (e + 2)", [R + "test_indicators_slopes_match_symbolic_definition"]),
+    ("beta_1 not taken from the cubic on the reduced stencil",
+     "beta[1] = poly_beta(POLY_DEFS[7].deg, c);", "(void)c;",
+     [R + "test_indicators_slopes_match_symbolic_definition"]),
+    ("global reference Z: wrong indicator index", "3.0 * (beta[0] - beta[4])", "3.0 * (beta[0] - beta[3])",
+     [X + "test_weno6_smooth_order", S + "test_shock_tube_vs_exact_riemann"]),
+    ("WENO-Z weight: the 1 dropped", "dlin[k] * (1.0 + Z / (beta[k] + eps))", "dlin[k] * (Z / (beta[k] + eps))",
+     [S + "test_uniform_flow_preserved_bitwise_2d", S + "test_2d_reproduces_1d_on_y_uniform_data"]),
+    ("linear weight d_2 of Sec. 3.3", "4.0 / 49.0, 7.0 / 98.0", "5.0 / 49.0, 7.0 / 98.0",
+     [R + "test_weno_smooth_limit_and_zref_order"]),
+    ("right state: slope not mirrored", "*val = v; *hslope = -sl;", "*val = v; *hslope = sl;",
+     [R + "test_right_state_is_mirror_of_left"]),
+    ("half-line first moment: sign of the Gaussian term", "out[1] = U * out[0] + e;", "out[1] = U * out[0] - e;",
+     [K + "test_half_line_moments_quadrature"]),
+    ("moment recurrence: off-by-one factor", "(n + 1) / (2.0 * lam) * out[n]", "n / (2.0 * lam) * out[n]",
+     [K + "test_whole_line_moments_gauss_hermite"]),
+    ("<xi^4> of the internal degrees of freedom", "(K * K + 2.0 * K)", "(K * K + K)",
+     [K + "test_psi_moment_assembly"]),
+    ("energy component of psi: factor 1/2 dropped (1D)",
+     "p->coef[0] = p->coef[1] = 0.5; p->a[0] = 2; p->c[1] = 1;",
+     "p->coef[0] = p->coef[1] = 1.0; p->a[0] = 2; p->c[1] = 1;", [K + "test_psi_moment_assembly"]),
+    ("internal degrees of freedom: the 1D value used in 2D", ": (4.0 - 2.0 * gamma) / (gamma - 1.0);",
+     ": (3.0 - gamma) / (gamma - 1.0);", [K + "test_gks_point_euler_limit", S + "test_2d_reproduces_1d_on_y_uniform_data"]),
+    ("time integral coefficient of (T2 + T1): sign", "double c3 = -tau * D_;", "double c3 = tau * D_;",
+     [V + "test_entropy_wave_decays_at_alpha_k2", C + "test_characteristic_shock_tubes"]),
+    ("time integral coefficient of (T2 - Th): sign inside", "tau * (D_ + tau) * e", "tau * (D_ - tau) * e",
+     [S + "test_shock_tube_vs_exact_riemann"]),
+    ("flux time slope F_t: factor 2 dropped", "4.0 * (o->S1[k] - 2.0 * o->S2[k])", "4.0 * (o->S1[k] - o->S2[k])",
+     [S + "test_table1_eighth_order_small_dt"]),
+    ("S2O4 second stage: weight dt^2/3 -> dt^2/6 (1D)", "W[k * nx + i] = R[k * nx + i] - dt * dt / 3.0 *",
+     "W[k * nx + i] = R[k * nx + i] - dt * dt / 6.0 *", [S + "test_table3_fourth_order_at_cfl_08"]),
+    ("Euler energy flux: pressure work dropped (1D)", "F[2] = jmul(U, jadd(E, p));", "F[2] = jmul(U, E);",
+     [K + "test_euler_time_derivatives_match_symbolic"]),
+    ("second time derivative: the tangential flux dropped",
+     "Wtt[k] = -F[k].h[0][2] - (D == 2 ? G[k].h[1][2] : 0.0);", "Wtt[k] = -F[k].h[0][2];",
+     [K + "test_euler_time_derivatives_match_symbolic"]),
+    ("viscous collision time: mu/rho for mu/p", "P->mu / p :", "P->mu / rho :",
+     [V + "test_entropy_wave_decays_at_alpha_k2"]),
+    ("collision time: pressure-jump term dropped", "P->c_tau * fabs((pl - pr) / (pl + pr)) * dt",
+     "0.0 * fabs((pl - pr) / (pl + pr)) * dt",
+     [K + "test_collision_time_pressure_jump_limits", S + "test_pressure_jump_collision_time_damps_shock_oscillations"]),
+    ("two-point Gauss rule along the face: wrong node", "const double g = 1.0 / (2.0 * sqrt(3.0));",
+     "const double g = 1.0 / (2.0 * sqrt(2.0));", [S + "test_isentropic_vortex_convergence"]),
+    ("tangential derivative not divided by the spacing", "in.W0t[k] = dp / ht;", "in.W0t[k] = dp;",
+     [S + "test_isentropic_vortex_convergence"]),
+    ("tangential WENO-Z reference: wrong candidate", "double Z = fabs(beta[0] - beta[nc - 1]);",
+     "double Z = fabs(beta[0] - beta[1]);", [T + "test_jump_value_stays_on_the_smooth_side_and_mirror_symmetry"]),
+    ("y-faces: momentum components not rotated", "return (k == 1) ? 2 : (k == 2) ? 1 : k;", "return k;",
+     [S + "test_transpose_symmetry"]),
+    ("y-faces: x-gradients used as the normal ones", "int gn = (o == 0) ? 1 : 2;", "int gn = 1;",
+     [S + "test_transpose_symmetry"]),
+    ("characteristic basis: U+c column energy entry", "R[(nv - 1) * nv + nv - 1] = H + U * c;",
+     "R[(nv - 1) * nv + nv - 1] = H - U * c;", [C + "test_eigenbasis_diagonalises_the_flux_jacobian"]),
+    ("6th-order variant: one linear weight", "8.0 / 70.0", "9.0 / 70.0",
+     [X + "test_weights_recombine_printed_candidates_into_the_degree5_fit"]),
+    ("viscous time-step bound: half the diffusion term (x)", "2.0 * nu / P->dx", "nu / P->dx",
+     [V + "test_viscous_cfl_term"]),
+    ("half-step interface state: dt^2/8 -> dt^2/4", "0.125 * dt * dt * o->Wtt[k]", "0.25 * dt * dt * o->Wtt[k]",
+     [S + "test_table3_fourth_order_at_cfl_08"]),
+    ("non-equilibrium interface part: -t W_t dropped", "- in->W0[k] - t * out->Wt[k]);", "- in->W0[k]);",
+     [K + "test_gks_point_equal_states"]),
+    ("2D first stage: sign of the y flux difference",
+     "- ((0.5 * dt * yr->Fb[k] + 0.125 * dt * dt * yr->Ft[k])",
+     "+ ((0.5 * dt * yr->Fb[k] + 0.125 * dt * dt * yr->Ft[k])", [S + "test_transpose_symmetry"]),
+]
+
+
+def _pytest(nodeids, lib, threads):
+    env = dict(os.environ, CGKS_ORACLE_LIB=lib, OMP_NUM_THREADS=str(threads))
+    r = subprocess.run([sys.executable, "-m", "pytest", *nodeids, "-x", "-q", "-p", "no:cacheprovider",
+                        "-m", "not gpu"], cwd=REPO, env=env, capture_output=True, text=True, timeout=1200)
+    return r.returncode, r.stdout[-3000:]
+
+
+@pytest.fixture(scope="module")
+def outcomes(tmp_path_factory):
+    d = tmp_path_factory.mktemp("planted")
+    with open(O._SRC) as f:
+        src = f.read()
+
+    def job(idx):
+        if idx < 0:
+            text, ids, threads = src, sorted({n for m in MUTANTS for n in m[3]}), 4
+        else:
+            _, old, new, ids = MUTANTS[idx]
+            assert src.count(old) == 1, f"planting site no longer unique in the oracle source: {old!r}"
+            text, threads = src.replace(old, new), 1
+        c = os.path.join(d, f"m{idx + 1}.c")
+        so = os.path.join(d, f"m{idx + 1}.so")
+        with open(c, "w") as f:
+            f.write(text)
+        O.compile_to(c, so)
+        return _pytest(ids, so, threads)
+
+    workers = max(2, min(8, os.cpu_count() or 2))
+    with ThreadPoolExecutor(workers) as ex:
+        res = list(ex.map(job, [-1] + list(range(len(MUTANTS)))))
+    return {"control": res[0], "mutants": res[1:]}
+
+
+def test_unplanted_copy_passes_every_named_pin(outcomes):
+    rc, out = outcomes["control"]
+    assert rc == 0, out
+
+
+@pytest.mark.parametrize("idx", range(len(MUTANTS)), ids=[m[0] for m in MUTANTS])
+def test_planted_mistake_is_caught(outcomes, idx):
+    rc, out = outcomes["mutants"][idx]
+    # exit status 1: tests ran and at least one failed (not a collection or usage error)
+    assert rc == 1 and " failed" in out, (MUTANTS[idx][0], rc, out)

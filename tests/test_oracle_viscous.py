@@ -47,3 +47,17 @@ def test_viscous_cfl_term():
     dt = O.cfl_dt(P, W)
     c = 1.0                     # rho = 1, p = 1/gamma; |v| <= 1e-4
     assert abs(dt / (0.5 / 64 / (c + 2 * 0.01 * 64)) - 1.0) < 2e-4
+    # each direction's diffusion term on its own spacing: with dy = 4 dx the x bound decides,
+    # with dx = 4 dy the y bound, and in 1D the x bound alone
+    h = 1.0 / 64
+    for dx, dy in ((h, 4 * h), (4 * h, h)):
+        kw = spec.as_kwargs()
+        kw.update(dx=dx, dy=dy)
+        want = 0.5 * min(dx / (c + 2 * 0.01 / dx), dy / (c + 2 * 0.01 / dy))
+        assert abs(O.cfl_dt(O.make_problem(**kw), W) / want - 1.0) < 2e-4
+    spec1, W1 = wl.density_wave_1d(32, eps=0.0)
+    spec1.mu = 0.01
+    P1 = O.make_problem(**spec1.as_kwargs())
+    u, a = W1[1, 0] / W1[0, 0], math.sqrt(1.4 * 1.0 / W1[0, 0])
+    want = P1.cfl * P1.dx / (abs(u) + a + 2 * 0.01 / P1.dx)
+    assert abs(O.cfl_dt(P1, W1) / want - 1.0) < 1e-12
