@@ -18,6 +18,9 @@ Parity status of each oracle function (pins in ``tests/test_oracle_*.py``):
   Maxwellian moments (Sec. 2.1)           pinned: Gauss-Hermite / adaptive quadrature
   Euler time derivatives (CK)             pinned: symbolic differentiation
   gas-kinetic flux (Sec. 2.1-2.2)         pinned: Euler limit, symmetry, 1D = 2D
+  boundaries, tangential profiles         pinned: walls = mirrored periodic domain, uniform
+                                          inflow on every side, polynomial exactness of the
+                                          segment profiles, x -> s x / t -> s t invariance
   collision time (Sec. 4)                 pinned: limits of the pressure-jump term, its damping
                                           of shock oscillations, viscous mu/p (decay rates)
   S2O4 step (Sec. 2.2)                    pinned: uniform flow, conservation, Table 1/3
@@ -123,6 +126,7 @@ def lib():
             L.oc_poly_coef_matrix.argtypes = [ctypes.c_int, dp]
             L.oc_char_basis.argtypes = [ctypes.c_int, ctypes.c_double, dp, dp, dp]
             L.oc_tang_weno.argtypes = [ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, dp, dp, dp]
+            L.oc_seg_profile.argtypes = [ctypes.c_int, dp, ctypes.c_double, dp]
             L.oc_moments_u.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int, dp]
             L.oc_mom_psi_poly.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp]
@@ -210,6 +214,16 @@ def tang_weno(v, eta, eps=1e-6):
     val, dval, om = np.zeros(1), np.zeros(1), np.zeros(3)
     lib().oc_tang_weno(int(v.size), _dp(v), float(eta), float(eps), _dp(val), _dp(dval), _dp(om))
     return val[0], dval[0], om[: v.size // 2 + 1].copy()
+
+
+def seg_profile(v, eta):
+    """2D reading: value, first and second derivative (per unit eta) at eta of the linear profile
+    (degree n - 1) through n = 5 or 3 means over unit segments centred at -(n // 2) .. n // 2."""
+    v = _f64(v)
+    assert v.size in (3, 5)
+    out = np.zeros(3)
+    lib().oc_seg_profile(int(v.size), _dp(v), float(eta), _dp(out))
+    return out
 
 
 def poly_coef_matrix(p):

@@ -1016,6 +1016,14 @@ static void seg_profile(int n, const double *v, double eta, double *p, double *d
     *p = a; *dp = b; *d2p = cc;
 }
 
+/* exported for the pin tests: out = (p, dp/deta, d2p/deta2) at eta of the
+ * profile through n = 5 or 3 segment means */
+void oc_seg_profile(int n, const double *v, double eta, double out[3])
+{
+    build_segfit();
+    seg_profile(n, v, eta, &out[0], &out[1], &out[2]);
+}
+
 /* Nonlinear point value along a face (2D reading).  WENO-Z in the form of
  * Sec. 3.3 over the n segment means v[0..n-1] (n = 5: rows j-2..j+2, three
  * quadratic candidates; n = 3: rows j-1..j+1, two linear candidates):

@@ -105,6 +105,59 @@ MUTANTS = [
     ("2D first stage: sign of the y flux difference",
      "- ((0.5 * dt * yr->Fb[k] + 0.125 * dt * dt * yr->Ft[k])",
      "+ ((0.5 * dt * yr->Fb[k] + 0.125 * dt * dt * yr->Ft[k])", [S + "test_transpose_symmetry"]),
+    # boundaries
+    ("2D x-walls: parity of the x-gradients dropped",
+     "int odd = (grp == 0 && var == 1) || (grp == 1 && var != 1) || (grp == 2 && var == 1);",
+     "int odd = (grp == 0 && var == 1) || (grp == 2 && var == 1);",
+     [S + "test_reflecting_walls_equal_the_mirrored_periodic_domain"]),
+    ("2D y-walls: parity of the y-gradients inverted", "(grp == 2 && var != 2);", "(grp == 2 && var == 2);",
+     [S + "test_reflecting_walls_equal_the_mirrored_periodic_domain"]),
+    ("1D walls: parity of the gradients dropped", "int odd = (grp == 0 && var == 1) || (grp == 1 && var != 1);\n",
+     "int odd = (grp == 0 && var == 1);\n", [S + "test_reflecting_walls_equal_the_mirrored_periodic_domain"]),
+    ("1D outflow: the normal gradient copied instead of zeroed",
+     "else v = (grp == 1) ? 0.0 : E[p * X + (side ? nx - 1 : 0) + NG];", "else v = E[p * X + (side ? nx - 1 : 0) + NG];",
+     [T + "test_strong_normal_shock_on_a_2d_grid"]),
+    ("2D periodic wrap in x: off by one", "side ? m % nx : ((nx - 1 - m) % nx + nx) % nx",
+     "side ? m % nx : ((nx - m) % nx + nx) % nx", [S + "test_2d_reproduces_1d_on_y_uniform_data"]),
+    ("2D inflow: the other side's state", "v = (grp == 0) ? inflow_cons[side][var] : 0.0;",
+     "v = (grp == 0) ? inflow_cons[1 - side][var] : 0.0;", [S + "test_supersonic_inflow_keeps_its_uniform_state"]),
+    # characteristic variables, tangential profiles, scalings
+    ("characteristic back-projection: R transposed", "vl[k] += R[k * nv + m] * cvl[m];",
+     "vl[k] += R[m * nv + k] * cvl[m];", [C + "test_characteristic_shock_tubes"]),
+    ("tangential profile: second-derivative factor", "cc += m * (m - 1) * c[m] * ipow(eta, m - 2);",
+     "cc += m * m * c[m] * ipow(eta, m - 2);", [T + "test_segment_profiles_exact_for_polynomials"]),
+    ("tangential second derivative divided by h once", "in.W0tt[k] = d2p / (ht * ht);", "in.W0tt[k] = d2p / ht;",
+     [S + "test_scale_invariance"]),
+    ("tangential slope of the left state not divided by h", "in.Wlt[k] = dw / ht;", "in.Wlt[k] = dw;",
+     [S + "test_scale_invariance"]),
+    ("mixed derivative not divided by h", "in.W0nt[k] = dp / ht;", "in.W0nt[k] = dp;", [S + "test_scale_invariance"]),
+    ("tangential linear weight: wrong candidate", "d[nc - 1] = wfl / wcl;", "d[nc - 1] = wfl / wc0;",
+     [S + "test_transpose_symmetry"]),
+    # time step, updates, fluxes, moments
+    ("2D time step: the y bound ignored", "if (dy < d) d = dy;", "(void)dy;", [V + "test_viscous_cfl_term"]),
+    ("time step: sound speed without gamma", "double a = sqrt(P->gamma * p / rho);", "double a = sqrt(p / rho);",
+     [S + "test_cfl_rule_reproduces_tam_webb_step_count"]),
+    ("1D gradient update: sign", "Ws[(3 + k) * nx + i] = (Rf->Wm[k] - L->Wm[k]) / dx;",
+     "Ws[(3 + k) * nx + i] = (L->Wm[k] - Rf->Wm[k]) / dx;", [S + "test_table1_eighth_order_small_dt"]),
+    ("2D second stage: sign of the y-gradient term", "W[(8 + k) * PL + c] = R[(8 + k) * PL + c] + dt * dt / 3.0 *",
+     "W[(8 + k) * PL + c] = R[(8 + k) * PL + c] - dt * dt / 3.0 *", [S + "test_transpose_symmetry"]),
+    ("Euler y-momentum flux: pressure dropped", "G[2] = jadd(jmul(n, V), p);", "G[2] = jmul(n, V);",
+     [K + "test_euler_time_derivatives_match_symbolic"]),
+    ("energy component of psi: v^2 dropped (2D)",
+     "p->coef[0] = p->coef[1] = p->coef[2] = 0.5; p->a[0] = 2; p->b[1] = 2; p->c[2] = 1;",
+     "p->coef[0] = p->coef[1] = p->coef[2] = 0.5; p->a[0] = 2; p->c[2] = 1;", [K + "test_psi_moment_assembly"]),
+    ("half-line zeroth moment: sign of the erfc argument", "out[0] = 0.5 * erfc(-s * U);",
+     "out[0] = 0.5 * erfc(s * U);", [K + "test_half_line_moments_quadrature"]),
+    ("time integral coefficient of F0", "double c1 = D_ - tau * (1.0 - e);", "double c1 = D_ - tau * e;",
+     [K + "test_gks_point_equal_states"]),
+    ("time integral coefficient of Fh", "double c5 = tau * (1.0 - e);", "double c5 = tau * e;",
+     [K + "test_gks_point_equal_states"]),
+    ("non-equilibrium interface part: sign of the slope term", "NE[k] = e * ((Wh[k] - t * Wsl[k])",
+     "NE[k] = e * ((Wh[k] + t * Wsl[k])", [K + "test_gks_point_equal_states"]),
+    ("end-of-step interface state: dt^2/6 -> dt^2/2", "dt * dt / 6.0 * o->Wtt[k]", "dt * dt / 2.0 * o->Wtt[k]",
+     [S + "test_table3_fourth_order_at_cfl_08"]),
+    ("mean flux of the step: factor 4 -> 2", "(4.0 * o->S2[k] - o->S1[k]) / dt", "(2.0 * o->S2[k] - o->S1[k]) / dt",
+     [S + "test_shock_tube_vs_exact_riemann"]),
 ]
 
 

@@ -206,3 +206,110 @@ def test_cfl_rule_reproduces_tam_webb_step_count():
     dt = O.cfl_dt(P, W)
     assert math.ceil(28.45 / dt) == 143
     assert abs(math.ceil(56.9 / dt) - 286) <= 1
+
+
+def _smooth_periodic_2d(Lx, Ly):
+    def fun(x, y):
+        a, b = 2 * math.pi * x / Lx, 2 * math.pi * y / Ly
+        return (1.0 + 0.2 * np.sin(a) * np.cos(b) + 0.1 * np.cos(2 * b), 0.4 + 0.3 * np.cos(a + b),
+                -0.2 + 0.25 * np.sin(b - a), 1.0 + 0.15 * np.sin(a + 2 * b))
+    return fun
+
+
+def test_reflecting_walls_equal_the_mirrored_periodic_domain():
+    """A reflecting wall is a mirror (Sec. 4's reflective boundaries): on a domain with walls at
+    both ends the solution equals the half of the periodic domain of twice the length whose other
+    half holds the mirror image.  Under x -> -x a field f maps to S f(-x) with S flipping the sign
+    of the x-momentum, so cell averages and y-gradients map by S and x-gradients by -S (and the
+    same with x and y exchanged, and in 1D)."""
+    g = 1.4
+    nst = 4
+    # 1D
+    spec, W = wl.density_wave_1d(10, eps=0.2)
+    S = np.array([1.0, -1.0, 1.0])
+    mirror = np.concatenate([(S[:, None] * W[:3])[:, ::-1], (-S[:, None] * W[3:])[:, ::-1]])
+    Wd = np.concatenate([mirror, W], axis=1)
+    kw = spec.as_kwargs()
+    dt = 0.02
+    Pw = O.make_problem(**dict(kw, bc=(O.BC_REFLECT, O.BC_REFLECT, 0, 0)))
+    Pp = O.make_problem(**dict(kw, nx=20))
+    a = O.run_fixed_dt(Pw, W, nst, dt)
+    b = O.run_fixed_dt(Pp, Wd, nst, dt)[:, 10:]
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max(), np.abs(a - b).max()
+    # 2D, walls on x (periodic in y) and walls on y (periodic in x)
+    nx, ny, Lx, Ly = 8, 6, 0.8, 0.6
+    W2 = wl.cell_state_2d(_smooth_periodic_2d(Lx, Ly), nx, ny, 0.0, Lx, 0.0, Ly, g)
+    for axis in (0, 1):
+        S = np.array([1.0, -1.0, 1.0, 1.0]) if axis == 0 else np.array([1.0, 1.0, -1.0, 1.0])
+        grad_sign = [1.0, -1.0, 1.0] if axis == 0 else [1.0, 1.0, -1.0]   # groups W, W_x, W_y
+        flip = (lambda A: A[:, :, ::-1]) if axis == 0 else (lambda A: A[:, ::-1, :])
+        mirror = np.concatenate([grad_sign[q] * S[:, None, None] * flip(W2[4 * q:4 * q + 4]) for q in range(3)])
+        Wd = np.concatenate([mirror, W2], axis=2 - axis)
+        base = dict(dim=2, nx=nx, ny=ny, dx=Lx / nx, dy=Ly / ny, gamma=g, eps_tau=0.01)
+        bcw = (O.BC_REFLECT, O.BC_REFLECT, 0, 0) if axis == 0 else (0, 0, O.BC_REFLECT, O.BC_REFLECT)
+        Pw = O.make_problem(**dict(base, bc=bcw))
+        Pp = O.make_problem(**dict(base, nx=2 * nx if axis == 0 else nx, ny=2 * ny if axis == 1 else ny))
+        a = O.run_fixed_dt(Pw, W2, nst, 0.01)
+        b = O.run_fixed_dt(Pp, Wd, nst, 0.01)
+        b = b[:, :, nx:] if axis == 0 else b[:, ny:, :]
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max(), (axis, np.abs(a - b).max())
+
+
+def test_supersonic_inflow_keeps_its_uniform_state():
+    """A uniform supersonic stream entering through an inflow side with the same state is an exact
+    steady solution, whatever states the other sides' inflow entries hold."""
+    g = 1.4
+    state = np.array([1.0, 2.5, 0.0, 1.0 / g])     # sound speed 1: Mach 2.5
+    other = [3.0, 0.3, -0.2, 2.0]
+    for side in range(4):
+        q = state.copy()
+        axis, sign = side // 2, (1.0 if side % 2 == 0 else -1.0)
+        q[1], q[2] = (sign * 2.5, 0.3) if axis == 0 else (0.3, sign * 2.5)
+        inflow = [other] * 4
+        inflow[side] = list(q)
+        bc = [0, 0, 0, 0]
+        bc[side], bc[side ^ 1] = O.BC_INFLOW, O.BC_OUTFLOW
+        P = O.make_problem(dim=2, nx=8, ny=7, dx=0.1, dy=0.1, gamma=g, bc=bc, inflow=inflow)
+        W = np.zeros((12, 7, 8))
+        W[0:4] = np.array([q[0], q[0] * q[1], q[0] * q[2], q[3] / (g - 1) + 0.5 * q[0] * (q[1] ** 2 + q[2] ** 2)])[:, None, None]
+        out = O.run_fixed_dt(P, W, 3, 0.01)
+        assert np.abs(out - W).max() <= 1e-13, (side, np.abs(out - W).max())
+    for side in range(2):
+        u = 2.5 if side == 0 else -2.5
+        inflow = [other] * 4
+        inflow[side] = [1.0, u, 0.0, 1.0 / g]
+        bc = [O.BC_INFLOW, O.BC_OUTFLOW, 0, 0] if side == 0 else [O.BC_OUTFLOW, O.BC_INFLOW, 0, 0]
+        P = O.make_problem(dim=1, nx=9, ny=1, dx=0.1, dy=0.1, gamma=g, bc=bc, inflow=inflow)
+        W = np.zeros((6, 9))
+        W[0:3] = np.array([1.0, u, 1.0 / (g * (g - 1)) + 0.5 * u * u])[:, None]
+        out = O.run_fixed_dt(P, W, 3, 0.01)
+        assert np.abs(out - W).max() <= 1e-13, (side, np.abs(out - W).max())
+
+
+@pytest.mark.parametrize("mu", [0.0, 2e-3])
+def test_scale_invariance(mu):
+    """The Euler (and Navier-Stokes) equations are unchanged by x -> s x, t -> s t (with mu -> s mu):
+    the same cell averages on a grid s times coarser, gradients divided by s, advanced with s dt,
+    give the same averages and gradients divided by s.  Every spacing enters the scheme only in such
+    ratios, so with s a power of two the results agree to rounding.  A large eps_tau keeps the
+    non-equilibrium terms of the interface state in play."""
+    s = 4.0
+    nx, ny, Lx, Ly = 8, 6, 0.8, 0.9
+    W2 = wl.cell_state_2d(_smooth_periodic_2d(Lx, Ly), nx, ny, 0.0, Lx, 0.0, Ly, 1.4)
+    Ws = W2.copy()
+    Ws[4:] /= s
+    base = dict(dim=2, nx=nx, ny=ny, gamma=1.4, eps_tau=0.3)
+    a = O.run_fixed_dt(O.make_problem(**base, dx=Lx / nx, dy=Ly / ny, mu=mu), W2, 3, 0.01)
+    b = O.run_fixed_dt(O.make_problem(**base, dx=s * Lx / nx, dy=s * Ly / ny, mu=s * mu), Ws, 3, s * 0.01)
+    b[4:] *= s
+    for q in range(3):
+        A, B = a[4 * q:4 * q + 4], b[4 * q:4 * q + 4]
+        assert np.abs(A - B).max() <= 1e-12 * np.abs(A).max(), (q, np.abs(A - B).max())
+    spec, W1 = wl.density_wave_1d(12, eps=0.2, eps_tau=0.3)
+    kw = dict(spec.as_kwargs(), mu=mu)
+    W1s = W1.copy()
+    W1s[3:] /= s
+    a = O.run_fixed_dt(O.make_problem(**kw), W1, 3, 0.02)
+    b = O.run_fixed_dt(O.make_problem(**dict(kw, dx=s * kw["dx"], mu=s * mu)), W1s, 3, s * 0.02)
+    b[3:] *= s
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()

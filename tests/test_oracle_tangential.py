@@ -108,3 +108,31 @@ def test_strong_normal_shock_on_a_2d_grid(recon_vars):
     assert rel[:3].max() < 1e-12
     assert np.abs(b[2]).max() <= 1e-15 * np.abs(b[1]).max()
     assert np.abs(b[8:]).max() <= 1e-15 * np.abs(b[4:8]).max()
+
+
+@pytest.mark.parametrize("n", [5, 3])
+def test_segment_profiles_exact_for_polynomials(n):
+    """The linear tangential profile through n unit-segment means is the degree-(n-1) polynomial
+    with those means: for every polynomial of degree <= n - 1 it returns the value and the first
+    and second derivatives exactly, at any eta on the central segment; degree n is not reproduced."""
+    rng = np.random.default_rng(70 + n)
+    offs = np.arange(n) - n // 2
+
+    def means(coef):
+        # exact mean of sum_m coef[m] eta^m over [o - 1/2, o + 1/2]
+        return np.array([sum(c * ((o + 0.5) ** (m + 1) - (o - 0.5) ** (m + 1)) / (m + 1)
+                             for m, c in enumerate(coef)) for o in offs])
+
+    for deg in range(n):
+        for _ in range(3):
+            coef = rng.normal(size=deg + 1)
+            for eta in (-0.5, -0.2886751345948129, 0.0, 0.31, 0.5):
+                got = O.seg_profile(means(coef), eta)
+                want = [sum(c * eta ** m for m, c in enumerate(coef)),
+                        sum(m * c * eta ** (m - 1) for m, c in enumerate(coef) if m >= 1),
+                        sum(m * (m - 1) * c * eta ** (m - 2) for m, c in enumerate(coef) if m >= 2)]
+                assert np.allclose(got, want, rtol=0, atol=1e-12), (n, deg, eta, got, want)
+    coef = np.zeros(n + 1)
+    coef[n] = 1.0
+    got = O.seg_profile(means(coef), 0.3)
+    assert abs(got[0] - 0.3 ** n) > 1e-4 or abs(got[2] - n * (n - 1) * 0.3 ** (n - 2)) > 1e-4
