@@ -76,3 +76,23 @@ def test_reflecting_walls_equal_mirrored_periodic_domain(nx, ny, axis):
     assert abs(ta - tb) <= 1e-14 * ta
     b = b[:, :, nx:] if axis == 0 else b[:, ny:, :]
     _assert_planes(a, b, 4)
+
+
+def _transpose_state(W):
+    """g(x, y) = P f(y, x), P swapping the two momenta: averages transpose with P; the x-gradients of
+    g are the transposed y-gradients of f with P, and the other way round."""
+    P = [0, 2, 1, 3]
+    T = lambda A: np.ascontiguousarray(A[P].transpose(0, 2, 1))
+    return np.concatenate([T(W[0:4]), T(W[8:12]), T(W[4:8])])
+
+
+@pytest.mark.parametrize("n", [40, 2048])
+def test_transpose_symmetry_vortex(n):
+    """x <-> y with the momenta swapped is a symmetry of the equations; the x and y faces run through
+    the same kernels with differently oriented tiles, so the transposed run must give the transposed
+    result (to rounding) over the whole field."""
+    spec, W = wl.isentropic_vortex(n)
+    a, ta, _ = run_gpu(spec, W, 2)
+    b, tb, _ = run_gpu(spec, _transpose_state(W), 2)
+    assert abs(ta - tb) <= 1e-14 * ta
+    _assert_planes(_transpose_state(b), a, 4)
