@@ -205,3 +205,15 @@ def test_acoustic_wave_1d_ten_lengths(n, eps_tau):
     o, to, so = run_oracle(spec, W, 10 ** 6, t_end=0.01)
     assert sg == so and tg == to == 0.01
     _check(g, o, spec=spec)
+
+
+@pytest.mark.parametrize("recon_vars,order", [(1, 8), (0, 6), (1, 6)])
+def test_viscous_with_other_options(recon_vars, order):
+    """Every option together: Navier-Stokes collision time with characteristic variables and/or the
+    6th-order variant, on the shock-vortex grid with all four boundary types and ragged tiles."""
+    spec, W = wl.shock_vortex(nx=58, ny=30, mach=1.2)
+    spec.mu, spec.recon_vars, spec.order = 1e-4, recon_vars, order
+    g, _, sg = run_gpu(spec, W, 6)
+    o, _, so = run_oracle(spec, W, 6)
+    assert sg == so == 6
+    _check(g, o, spec=spec)
