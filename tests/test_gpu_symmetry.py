@@ -96,3 +96,25 @@ def test_transpose_symmetry_vortex(n):
     b, tb, _ = run_gpu(spec, _transpose_state(W), 2)
     assert abs(ta - tb) <= 1e-14 * ta
     _assert_planes(_transpose_state(b), a, 4)
+
+
+def test_symmetries_1d():
+    """The 1D path: x -> 4x, t -> 4t, and walls at both ends = the mirrored periodic domain."""
+    spec, W = wl.density_wave_1d(100, eps=0.2, eps_tau=0.3)
+    big = dataclasses.replace(spec, x0=4 * spec.x0, x1=4 * spec.x1)
+    Wb = W.copy()
+    Wb[3:] /= 4.0
+    a, ta, _ = run_gpu(spec, W, 20)
+    b, tb, _ = run_gpu(big, Wb, 20)
+    assert tb == 4.0 * ta
+    b[3:] *= 4.0
+    _assert_planes(b, a, 3)
+    S = np.array([1.0, -1.0, 1.0])
+    mirror = np.concatenate([(S[:, None] * W[:3])[:, ::-1], (-S[:, None] * W[3:])[:, ::-1]])
+    Wd = np.ascontiguousarray(np.concatenate([mirror, W], axis=1))
+    walls = dataclasses.replace(spec, bc=(wl.BC_REFLECT, wl.BC_REFLECT, wl.BC_PERIODIC, wl.BC_PERIODIC))
+    doubled = dataclasses.replace(spec, nx=200, x0=spec.x0 - (spec.x1 - spec.x0))
+    a, ta, _ = run_gpu(walls, W, 20)
+    b, tb, _ = run_gpu(doubled, Wd, 20)
+    assert abs(ta - tb) <= 1e-14 * ta
+    _assert_planes(a, b[:, 100:], 3)
