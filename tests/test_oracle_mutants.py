@@ -158,6 +158,21 @@ MUTANTS = [
      [S + "test_table3_fourth_order_at_cfl_08"]),
     ("mean flux of the step: factor 4 -> 2", "(4.0 * o->S2[k] - o->S1[k]) / dt", "(2.0 * o->S2[k] - o->S1[k]) / dt",
      [S + "test_shock_tube_vs_exact_riemann"]),
+    ("2D y-outflow: the normal gradient copied instead of zeroed",
+     "else { int src = side ? ny - 1 : 0; v = (grp == 2) ? 0.0 : AT(p, src, i); }",
+     "else { int src = side ? ny - 1 : 0; v = AT(p, src, i); }", [T + "test_strong_normal_shock_along_y_on_a_2d_grid"]),
+    ("tangential spacing of x-faces and y-faces exchanged", "double ht = (o == 0) ? P->dy : P->dx;",
+     "double ht = (o == 0) ? P->dx : P->dy;", [S + "test_isentropic_vortex_convergence_on_tall_cells"]),
+    ("normal second derivative divided by h once", "out->NN[k] = lin[2] / (h * h);", "out->NN[k] = lin[2] / h;",
+     [S + "test_scale_invariance"]),
+    ("W0nn taken from the wrong row", "in.W0nn[k] = rr[2]->NN[k];", "in.W0nn[k] = rr[1]->NN[k];",
+     [S + "test_reflecting_walls_equal_the_mirrored_periodic_domain"]),
+    ("right normal slope taken from the left state", "out->Rn[k] = sr[k] / h;", "out->Rn[k] = sl[k] / h;",
+     [S + "test_2d_reproduces_1d_on_y_uniform_data"]),
+    ("time step: CFL number not applied", "return P->cfl * best;", "return best;",
+     [S + "test_table3_fourth_order_at_cfl_08"]),
+    ("last step not clipped to t_end", "if (t_end > 0.0 && *t + dt > t_end) dt = t_end - *t;", "(void)0;",
+     [S + "test_shock_tube_vs_exact_riemann"]),
 ]
 
 

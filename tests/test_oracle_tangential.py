@@ -136,3 +136,21 @@ def test_segment_profiles_exact_for_polynomials(n):
     coef[n] = 1.0
     got = O.seg_profile(means(coef), 0.3)
     assert abs(got[0] - 0.3 ** n) > 1e-4 or abs(got[2] - n * (n - 1) * 0.3 ** (n - 2)) > 1e-4
+
+
+def test_strong_normal_shock_along_y_on_a_2d_grid():
+    """Sod along y, uniform in x, outflow at both y ends: the 2D steps agree with the 1D scheme, the
+    y-outflow ghosts behaving as the 1D ones do."""
+    spec, W1 = wl.shock_tube_1d(40, wl.SOD, cfl=0.5)
+    a, _, _, _ = O.run(O.make_problem(**spec.as_kwargs()), W1, 12)
+    kw = spec.as_kwargs()
+    kw.update(dim=2, nx=4, ny=40, dx=1.0, dy=spec.dx, bc=(0, 0, spec.bc[0], spec.bc[1]))
+    W2 = np.zeros((12, 40, 4))
+    for k_1d, k_2d in ((0, 0), (1, 2), (2, 3)):
+        W2[k_2d] = W1[k_1d][:, None]
+        W2[8 + k_2d] = W1[3 + k_1d][:, None]
+    b, _, _, _ = O.run(O.make_problem(**kw), W2, 12)
+    assert np.all(b[:, :, 1:] == b[:, :, :1])                          # columns stay identical
+    b1 = np.array([b[0, :, 0], b[2, :, 0], b[3, :, 0], b[8, :, 0], b[10, :, 0], b[11, :, 0]])
+    rel = np.abs(a - b1).max(axis=1) / np.abs(a).max(axis=1)
+    assert rel[:3].max() < 1e-12 and rel[3:].max() < 1e-10
