@@ -217,3 +217,15 @@ def test_viscous_with_other_options(recon_vars, order):
     o, _, so = run_oracle(spec, W, 6)
     assert sg == so == 6
     _check(g, o, spec=spec)
+
+
+def test_vortex_on_tall_cells():
+    """dy = 2 dx (and ragged tiles): each direction's spacing in the derivatives along and across
+    every face, against the oracle."""
+    L = 10.0
+    spec = wl.ProblemSpec(dim=2, nx=46, ny=23, x0=0.0, x1=L, y0=0.0, y1=L)
+    W = wl.cell_state_2d(wl._vortex_fun(0.5 * L, 0.5 * L, L, 5.0, 1.4), 46, 23, 0.0, L, 0.0, L, 1.4)
+    g, tg, sg = run_gpu(spec, W, 8)
+    o, to, so = run_oracle(spec, W, 8)
+    assert sg == so == 8 and tg == pytest.approx(to, rel=1e-14)
+    _check(g, o, spec=spec)
