@@ -173,6 +173,26 @@ MUTANTS = [
      [S + "test_table3_fourth_order_at_cfl_08"]),
     ("last step not clipped to t_end", "if (t_end > 0.0 && *t + dt > t_end) dt = t_end - *t;", "(void)0;",
      [S + "test_shock_tube_vs_exact_riemann"]),
+    ("Taylor-jet product: one cross term of the Hessian", "a.g[i] * b.g[j] + a.g[j] * b.g[i] + a.h[i][j] * b.v;",
+     "a.g[i] * b.g[j] + a.h[i][j] * b.v;", [K + "test_euler_time_derivatives_match_symbolic"]),
+    ("Taylor-jet reciprocal: factor 2 of the Hessian", "+ 2.0 * q * q * q * a.g[i] * a.g[j];",
+     "+ q * q * q * a.g[i] * a.g[j];", [S + "test_shock_tube_vs_exact_riemann"]),
+    ("pressure: kinetic energy without 1/2", "double ke = 0.5 * (*rho) * ((*U) * (*U) + (*V) * (*V));",
+     "double ke = (*rho) * ((*U) * (*U) + (*V) * (*V));", [S + "test_transpose_symmetry"]),
+    ("1D normal second derivative divided by h once", "in.W0nn[k] = lin[2] / (h * h);", "in.W0nn[k] = lin[2] / h;",
+     [S + "test_shock_tube_vs_exact_riemann"]),
+    ("1D right normal slope not divided by h", "in.Wr[k] = vr[k]; in.Wrn[k] = sr[k] / h;",
+     "in.Wr[k] = vr[k]; in.Wrn[k] = sr[k];", [S + "test_scale_invariance"]),
+    ("y-momentum component of psi: u for v",
+     "else if (D == 2 && k == 2) { p->n = 1; p->coef[0] = 1.0; p->b[0] = 1; }",
+     "else if (D == 2 && k == 2) { p->n = 1; p->coef[0] = 1.0; p->a[0] = 1; }",
+     [S + "test_uniform_flow_preserved_bitwise_2d"]),
+    ("1D inflow: the other side's state", "else if (bc == BC_INFLOW) v = (grp == 0) ? ic[side][var] : 0.0;",
+     "else if (bc == BC_INFLOW) v = (grp == 0) ? ic[1 - side][var] : 0.0;",
+     [S + "test_supersonic_inflow_keeps_its_uniform_state"]),
+    ("right-state mirror: two slopes exchanged",
+     "double m[8] = {s[3], s[2], s[1], s[0], -s[7], -s[6], -s[5], -s[4]};",
+     "double m[8] = {s[3], s[2], s[1], s[0], -s[6], -s[7], -s[5], -s[4]};", [S + "test_density_wave_100_cells"]),
 ]
 
 
