@@ -117,6 +117,14 @@ cgks_status cgks_destroy(cgks_solver* s);
  * pointer.  Computes the CFL bound of the new state on the device. */
 cgks_status cgks_set_state(cgks_solver* s, const double* planes, int on_device, double t);
 
+/* Resume from a checkpoint: like cgks_set_state, but the step count starts at
+ * `steps` (>= 0), the count cgks_get_state returned with the saved planes and
+ * time.  The CFL bound of the restored state is computed with the same
+ * rounding as at the end of a step, so that N steps, a checkpoint, a restore
+ * into a new solver (same problem) and M more steps give the same bits as
+ * N + M steps without interruption.  Errors: CGKS_E_INVAL, CGKS_E_CUDA. */
+cgks_status cgks_restore_state(cgks_solver* s, const double* planes, int on_device, double t, long steps);
+
 /* Copy the current state out (synchronises the stream).  t and steps may be
  * NULL.  Returns the solve's sticky status (CGKS_OK or CGKS_E_NONPHYSICAL). */
 cgks_status cgks_get_state(cgks_solver* s, double* planes, int on_device, double* t, long* steps);
@@ -179,9 +187,8 @@ const char* cgks_last_error(void);
  * exists for callers of this library, not for the method.)
  *
  * Some callers cannot let a library call cudaMalloc: applications that manage
- * all device memory through their own pool or allocator, code that is inside a
- * region where the allocator must not be re-entered, or embeddings with a
- * fixed memory footprint.  cgks_step_noalloc advances a 2D problem whose state
+ * all device memory through their own pool or allocator, or embeddings with a
+ * fixed device footprint where the allocator must not be re-entered.  cgks_step_noalloc advances a 2D problem whose state
  * the caller already holds in device memory and allocates nothing: the second
  * state buffer, the intermediate state, the face-row records, the control
  * block and the work queues live in fixed-size device arrays of the library
@@ -198,11 +205,13 @@ const char* cgks_last_error(void);
  * nsteps:      S2O4 steps to take (dt from the CFL condition each step)
  * t_inout:     time of the state in, time after the steps out
  * cuda_stream: stream for all work (NULL: the legacy default stream); the
- *              call synchronises it before returning
+ *              call reads the control block back and synchronises the stream
+ *              before returning, so it must not be called while a stream
+ *              capture is active
  * Errors: CGKS_E_INVAL (3D/1D problem, grid larger than the maximum, bad
  * parameters), CGKS_E_NONPHYSICAL, CGKS_E_CUDA.
  * The first call on a device looks up the addresses of the fixed arrays and
- * sets kernel attributes; make that first call before any stream capture.
+ * sets kernel attributes.
  * All calls share the same arrays: calls whose work overlaps on the GPU (from
  * several threads or streams) race and must be serialised by the caller.
  * Each call re-initialises the control block and overwrites the scratch it

@@ -1,9 +1,11 @@
-"""Build libcgks.so (sm_103a) in-tree: paper_2001_01570_gb300/_build/libcgks.so.
+"""Build libcgks.so (sm_103a) in-tree: paper_2001_01570_gb300/_build/libcgks.so,
+and the diagnostics library libcgks_diag.so beside it (csrc/diag: checks of the
+kernels' math routines against CUDA's and the FP64 throughput probe).
 
 Each .cu translation unit is compiled by its own nvcc process (the tile-shape
 instantiations of the stage kernel are the slow ones), then linked with
-``nvcc -shared``.  CUDA runtime is linked statically so the library only
-needs the CUDA driver library (libcuda).
+``nvcc -shared``.  CUDA runtime is linked statically so the libraries only
+need the CUDA driver library (libcuda).
 """
 from __future__ import annotations
 
@@ -18,6 +20,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libcgks.so")
+DIAG_LIB = os.path.join(BUILD, "libcgks_diag.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr"]
@@ -34,15 +37,20 @@ def _sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
+def _diag_sources():
+    return sorted(glob.glob(os.path.join(CSRC, "diag", "*.cu")))
+
+
 def _deps():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu*")) + glob.glob(os.path.join(CSRC, "*.h"))
+                  + glob.glob(os.path.join(CSRC, "diag", "*.cu"))
                   + glob.glob(os.path.join(HERE, "..", "include", "*.h")) + [os.path.abspath(__file__)])
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not (os.path.exists(LIB) and os.path.exists(DIAG_LIB)):
         return False
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(DIAG_LIB))
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
@@ -51,8 +59,9 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
-    srcs = _sources()
+    srcs = _sources() + _diag_sources()
     objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    ndiag = len(_diag_sources())
     extra = ["-Xptxas", "-v"] if ptxas_info else []
 
     def compile_one(pair):
@@ -68,12 +77,13 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     if verbose or ptxas_info:
         for l in logs:
             sys.stderr.write(l)
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    for lib, parts in ((LIB, objs[:len(objs) - ndiag]), (DIAG_LIB, objs[len(objs) - ndiag:])):
+        tmp = lib + f".tmp{os.getpid()}"
+        cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *parts]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, lib)
     return LIB
 
 

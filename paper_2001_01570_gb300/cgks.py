@@ -74,12 +74,13 @@ def load():
     L.cgks_create.argtypes = [ctypes.POINTER(cgks_problem), vp, ctypes.POINTER(vp)]
     L.cgks_destroy.argtypes = [vp]
     L.cgks_set_state.argtypes = [vp, vp, ctypes.c_int, ctypes.c_double]
+    L.cgks_restore_state.argtypes = [vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_long]
     L.cgks_get_state.argtypes = [vp, vp, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_long)]
     L.cgks_step.argtypes = [vp, ctypes.c_int, ctypes.c_double, dp]
     L.cgks_batch_step.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int]
     L.cgks_step_profiled.argtypes = [vp, ctypes.c_int, dp]
-    for name in ("cgks_create", "cgks_destroy", "cgks_set_state", "cgks_get_state", "cgks_step", "cgks_batch_step",
-                 "cgks_step_profiled"):
+    for name in ("cgks_create", "cgks_destroy", "cgks_set_state", "cgks_restore_state", "cgks_get_state", "cgks_step",
+                 "cgks_batch_step", "cgks_step_profiled"):
         getattr(L, name).restype = ctypes.c_int
     L.cgks_set_tile_shape.argtypes = [vp, ctypes.c_int]
     L.cgks_set_tile_shape.restype = ctypes.c_int
@@ -175,6 +176,12 @@ def _ptr(buf):
 def cgks_set_state(solver, planes, t=0.0):
     p, dev = _ptr(planes)
     _check(load().cgks_set_state(solver, p, dev, float(t)))
+
+
+def cgks_restore_state(solver, planes, t, steps):
+    """Resume from a checkpoint (planes, t and the step count cgks_get_state returned)."""
+    p, dev = _ptr(planes)
+    _check(load().cgks_restore_state(solver, p, dev, float(t), int(steps)))
 
 
 def cgks_get_state(solver, planes=None):
@@ -274,6 +281,7 @@ def cgks_serve_stop(server):
 
 
 NOALLOC_MAX_CELLS = 65536
+NOALLOC_MAX_SIDE = 4096
 
 
 def cgks_step_noalloc(problem: cgks_problem, planes_device, nsteps, t=0.0, stream=None):
@@ -310,6 +318,9 @@ class Solver:
 
     def set_state(self, planes, t=0.0):
         cgks_set_state(self.handle, planes, t)
+
+    def restore(self, planes, t, steps):
+        cgks_restore_state(self.handle, planes, t, steps)
 
     def get_state(self):
         out = np.empty(self.shape, dtype=np.float64)

@@ -282,12 +282,13 @@ cgks_status cgks_destroy(cgks_solver* s)
     return CGKS_OK;
 }
 
-cgks_status cgks_set_state(cgks_solver* s, const double* planes, int on_device, double t)
+static cgks_status set_state_impl(cgks_solver* s, const double* planes, int on_device, double t, long long steps)
 {
     if (!s || !planes) return fail(CGKS_E_INVAL, "NULL argument");
+    if (steps < 0) return fail(CGKS_E_INVAL, "steps must be >= 0");
     const size_t PL = (size_t)s->nx * s->ny;
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    CK(launch_set_ctrl(s->d_ctrl, t, 0.0, -1, 1, s->stream));
+    CK(launch_set_ctrl(s->d_ctrl, t, 0.0, -1, 1, s->stream, steps));
     if (s->prob.dim == 1) {
         CK(cudaMemcpyAsync(s->d_stage1d, planes, 6 * PL * sizeof(double), kind, s->stream));
         CK(launch_expand1d(s->d_stage1d, s->host_desc.buf[0], s->nx, s->stream));
@@ -297,6 +298,16 @@ cgks_status cgks_set_state(cgks_solver* s, const double* planes, int on_device, 
     CK(launch_cfl(s->d_desc, 0, s->host_desc, s->stream));
     if (!on_device) CK(cudaStreamSynchronize(s->stream));
     return CGKS_OK;
+}
+
+cgks_status cgks_set_state(cgks_solver* s, const double* planes, int on_device, double t)
+{
+    return set_state_impl(s, planes, on_device, t, 0);
+}
+
+cgks_status cgks_restore_state(cgks_solver* s, const double* planes, int on_device, double t, long steps)
+{
+    return set_state_impl(s, planes, on_device, t, steps);
 }
 
 cgks_status cgks_get_state(cgks_solver* s, double* planes, int on_device, double* t, long* steps)

@@ -77,15 +77,8 @@ __global__ void cfl_kernel(const GridDev* grids, int gidx)
     double dmin = INFINITY;
     bool bad = false;
     for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < PL; c += (size_t)gridDim.x * blockDim.x) {
-        const double r = W[c], m = W[PL + c], n = W[2 * PL + c], E = W[3 * PL + c];
-        const double ir = 1.0 / r;
-        const double U = m * ir, V = n * ir;
-        const double p = (G.gamma - 1.0) * (E - 0.5 * (m * U + n * V));
-        if (!(r > 0.0) || !(p > 0.0)) { bad = true; continue; }
-        const double c0 = sqrt(G.gamma * p * ir);
-        const double nu = G.mu * ir;
-        double d = G.dx / (fabs(U) + c0 + 2.0 * nu * G.inv_dx);
-        if (G.dim == 2) d = fmin(d, G.dy / (fabs(V) + c0 + 2.0 * nu * G.inv_dy));
+        double d;
+        if (!cfl_cell_bound(G, W[c], W[PL + c], W[2 * PL + c], W[3 * PL + c], G.dim == 1, &d)) { bad = true; continue; }
         dmin = fmin(dmin, d);
     }
     if (bad) atomicOr(&G.ctrl->status, (int)CGKS_E_NONPHYSICAL);
@@ -94,11 +87,11 @@ __global__ void cfl_kernel(const GridDev* grids, int gidx)
         atomicMin(&G.ctrl->dtmin_bits, (unsigned long long)__double_as_longlong(dmin));
 }
 
-__global__ void set_ctrl_kernel(Ctrl* c, double t, double t_end, long long steps_target, int reset)
+__global__ void set_ctrl_kernel(Ctrl* c, double t, double t_end, long long steps_target, int reset, long long steps0)
 {
     if (reset) {
         c->t = t;
-        c->steps = 0;
+        c->steps = steps0;
         c->status = 0;
         c->done = 0;
         c->par = 0;
@@ -162,9 +155,10 @@ cudaError_t launch_cfl(const GridDev* grids, int gidx, const GridDev& host, cuda
     return cudaGetLastError();
 }
 
-cudaError_t launch_set_ctrl(Ctrl* c, double t, double t_end, long long steps_target, int reset, cudaStream_t st)
+cudaError_t launch_set_ctrl(Ctrl* c, double t, double t_end, long long steps_target, int reset, cudaStream_t st,
+                            long long steps0)
 {
-    set_ctrl_kernel<<<1, 1, 0, st>>>(c, t, t_end, steps_target, reset);
+    set_ctrl_kernel<<<1, 1, 0, st>>>(c, t, t_end, steps_target, reset, steps0);
     return cudaGetLastError();
 }
 

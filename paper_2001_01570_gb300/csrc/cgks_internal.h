@@ -7,6 +7,10 @@
 
 namespace cgks {
 
+// devices whose per-device state (kernel attributes, fixed-array addresses) the
+// library tracks
+constexpr int kMaxDevices = 64;
+
 // Per-grid control block in device memory.  Written only by the step-control
 // kernels and the stage kernels, so a sequence of steps (or a CUDA graph of
 // them) runs without any host round trip.
@@ -40,6 +44,29 @@ struct GridDev {
     double* facex;      // face results of the stage in flight: x-faces [16][ny][nx+1]
     double* facey;      // y-faces [16][ny+1][nx] (2D)
 };
+
+#ifdef __CUDACC__
+// CFL bound of one cell, dx/(|U|+c+2 nu/dx) and dy/(|V|+c+2 nu/dy) (Sec. 4; nu =
+// mu/rho), written with explicitly rounded operations so that every kernel that
+// evaluates it (the stage-2 update of a step, the bound of a state that was set
+// or restored) gets the same bits: a restored checkpoint continues exactly as
+// the uninterrupted run.  Returns false for rho <= 0 or p <= 0 (or NaN).
+__device__ __forceinline__ bool cfl_cell_bound(const GridDev& G, double r, double m, double n, double E, bool dim1,
+                                               double* d_out)
+{
+    const double ir = __ddiv_rn(1.0, r);
+    const double U = __dmul_rn(m, ir), V = __dmul_rn(n, ir);
+    const double ke = __dmul_rn(0.5, __dadd_rn(__dmul_rn(m, U), __dmul_rn(n, V)));
+    const double p = __dmul_rn(__dsub_rn(G.gamma, 1.0), __dsub_rn(E, ke));
+    if (!(r > 0.0) || !(p > 0.0)) return false;
+    const double c = __dsqrt_rn(__dmul_rn(__dmul_rn(G.gamma, p), ir));
+    const double two_nu = __dmul_rn(2.0, __dmul_rn(G.mu, ir));
+    double d = __ddiv_rn(G.dx, __dadd_rn(__dadd_rn(fabs(U), c), __dmul_rn(two_nu, G.inv_dx)));
+    if (!dim1) d = fmin(d, __ddiv_rn(G.dy, __dadd_rn(__dadd_rn(fabs(V), c), __dmul_rn(two_nu, G.inv_dy))));
+    *d_out = d;
+    return true;
+}
+#endif
 
 // face rows with a record: x-faces 0..nx on rows -2..ny+1, y-faces 0..ny on
 // columns -2..nx+1 (2D); each record holds 7 fields x 4 variables
@@ -111,7 +138,10 @@ cudaError_t launch_end_step(const GridDev* grids, int ngrids, cudaStream_t st);
 cudaError_t launch_cfl(const GridDev* grids, int gidx, const GridDev& host, cudaStream_t st);
 cudaError_t launch_expand1d(const double* src6, double* dst12, int nx, cudaStream_t st);
 cudaError_t launch_compress1d(const double* src12, double* dst6, int nx, cudaStream_t st);
-cudaError_t launch_set_ctrl(Ctrl* c, double t, double t_end, long long steps_target, int reset, cudaStream_t st);
+// reset != 0: the control block starts a solve at time t with `steps0` steps
+// already taken (0 for a new solve, the checkpoint's count on a restore)
+cudaError_t launch_set_ctrl(Ctrl* c, double t, double t_end, long long steps_target, int reset, cudaStream_t st,
+                            long long steps0 = 0);
 cudaError_t launch_batch_resume(const GridDev* grids, int n, cudaStream_t st);
 
 }  // namespace cgks

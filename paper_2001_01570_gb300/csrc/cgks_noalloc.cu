@@ -3,12 +3,14 @@
 //
 // Such callers exist when the library runs inside code that owns the device
 // memory itself: a host application with a fixed memory pool or a custom
-// allocator, code running while a CUDA graph is being recorded by someone else,
-// or an embedding where the allocator must not be re-entered.  They pass the
-// state planes they already own; everything else the step needs (the second
-// state buffer, the intermediate state W*, the control block, the descriptor
-// and the tile queue) lives in file-scope device arrays of fixed size that
-// every GPU loading this library keeps until the process exits.
+// allocator, or an embedding with a fixed device footprint where the allocator
+// must not be re-entered.  They pass the state planes they already own;
+// everything else the step needs (the second state buffer, the intermediate
+// state W*, the control block, the descriptor and the tile queue) lives in
+// file-scope device arrays of fixed size that every GPU loading this library
+// keeps until the process exits.  The call reads the control block back and
+// synchronises its stream before it returns, so it must not be called while a
+// stream capture is active on that stream.
 #include "cgks_internal.h"
 #include "../../include/cgks.h"
 
@@ -55,8 +57,7 @@ struct DeviceSymbols {
     double* faces = nullptr;
     cgks::TileRef* cchunks = nullptr;
 };
-constexpr int kMaxDevices = 64;
-DeviceSymbols g_syms[kMaxDevices];
+DeviceSymbols g_syms[cgks::kMaxDevices];
 std::mutex g_mu;
 thread_local std::string g_err;
 
@@ -68,7 +69,7 @@ cgks_status nfail(cgks_status st, const std::string& m)
 
 cgks_status setup_device(int dev, DeviceSymbols** out)
 {
-    if (dev < 0 || dev >= kMaxDevices) return nfail(CGKS_E_INVAL, "device index out of range");
+    if (dev < 0 || dev >= cgks::kMaxDevices) return nfail(CGKS_E_INVAL, "device index out of range");
     std::lock_guard<std::mutex> lk(g_mu);
     DeviceSymbols& s = g_syms[dev];
     if (!s.ready) {

@@ -29,6 +29,8 @@
 #include "cgks_internal.h"
 #include "../../include/cgks.h"
 
+#include <mutex>
+
 namespace cgks {
 
 constexpr int kThreads = 128;
@@ -345,21 +347,37 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
     }
 }
 
+// The kernel's attributes (more than 48 KB of dynamic shared memory, the
+// largest carveout) belong to one device's context: they are set once per
+// device, thread-safely, before the first launch on that device.
+template <int TX, int TY, int STAGE>
+cudaError_t configure_stage_t()
+{
+    using L = StageLayout<TX, TY, STAGE>;
+    static std::once_flag once[kMaxDevices];
+    static cudaError_t status[kMaxDevices];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::call_once(once[dev], [dev] {
+        cudaError_t r = cudaFuncSetAttribute(stage_kernel<TX, TY, STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)L::bytes);
+        // the largest shared-memory carveout, so that two CTAs fit where the shape allows
+        if (r == cudaSuccess)
+            r = cudaFuncSetAttribute(stage_kernel<TX, TY, STAGE>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared);
+        status[dev] = r;
+    });
+    return status[dev];
+}
+
 template <int TX, int TY, int STAGE>
 cudaError_t launch_stage_t(const GridDev* grids, const TileRef* tiles, int ntiles, int nblocks, cudaStream_t st)
 {
     using L = StageLayout<TX, TY, STAGE>;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(stage_kernel<TX, TY, STAGE>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
-        // the largest shared-memory carveout, so that two CTAs fit where the shape allows
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(stage_kernel<TX, TY, STAGE>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                     (int)cudaSharedmemCarveoutMaxShared);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    cudaError_t e = configure_stage_t<TX, TY, STAGE>();
+    if (e != cudaSuccess) return e;
     if (ntiles <= 0) return cudaSuccess;
     stage_kernel<TX, TY, STAGE><<<nblocks, kThreads, L::bytes, st>>>(grids, tiles, ntiles);
     return cudaGetLastError();

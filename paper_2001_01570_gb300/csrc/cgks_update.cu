@@ -62,15 +62,9 @@ __global__ void __launch_bounds__(256) update_kernel(const GridDev* __restrict__
                     rbuf[(8 + k) * PL + off] += (FY(4 + k, yt) - FY(4 + k, yb)) * idy_;
                 }
                 // CFL bound of the new state (Sec. 4)
-                const double ir = 1.0 / Wn[0];
-                const double U = Wn[1] * ir, V = Wn[2] * ir;
-                const double p = (G.gamma - 1.0) * (Wn[3] - 0.5 * (Wn[1] * U + Wn[2] * V));
-                const bool ok = (Wn[0] > 0.0) && (p > 0.0);
+                double d;
+                const bool ok = cfl_cell_bound(G, Wn[0], Wn[1], Wn[2], Wn[3], dim1, &d);
                 bad = !ok;
-                const double c = sqrt(G.gamma * p * ir);
-                const double nu = G.mu * ir;
-                double d = G.dx / (fabs(U) + c + 2.0 * nu * G.inv_dx);
-                if (!dim1) d = fmin(d, G.dy / (fabs(V) + c + 2.0 * nu * G.inv_dy));
                 if (ok) dtmin = d;
             }
         }

@@ -14,3 +14,19 @@ def pytest_configure(config):
 
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def pytest_sessionfinish(session, exitstatus):
+    """Write the parity errors of the session (both definitions, per case) where
+    $CGKS_PARITY_REPORT says."""
+    path = os.environ.get("CGKS_PARITY_REPORT")
+    if not path:
+        return
+    try:
+        import json
+        import parity_util
+    except Exception:
+        return
+    with open(path, "a") as f:
+        for r in parity_util.REPORT:
+            f.write(json.dumps(r) + "\n")

@@ -8,6 +8,11 @@ seeded sample of cells.
   python tests/golden/make_golden.py vortex512     # isentropic vortex 512^2, 200 steps
   python tests/golden/make_golden.py shockvortex   # shock-vortex 1024x512, 400 steps
   python tests/golden/make_golden.py pulses        # 8 smallest grids of the 256-grid batch, 100 steps
+  python tests/golden/make_golden.py pulses16      # 16 grids of the batch across its size quantiles
+                                                   # (smallest to largest, 65^2..501^2), 100 steps
+  python tests/golden/make_golden.py served        # sampled requests of the served stream at their
+                                                   # stated N and step count (every kind; Mach 1.07,
+                                                   # 1.48 and 1.50 shock-vortex)
   python tests/golden/make_golden.py vortex2048    # isentropic vortex 2048^2 (the bench grid), 2 steps
   python tests/golden/make_golden.py vortex2048o6  # the same grid, compact 6th-order variant, 1 step
 """
@@ -25,6 +30,17 @@ import oracle as O  # noqa: E402
 from paper_2001_01570_gb300 import workloads as wl  # noqa: E402
 
 NSAMPLE = 1500
+
+# the stratified sample of the 256 batched grids: sorted by N, 16 evenly spaced ranks
+def pulse_quantile_grids(params, count=16):
+    order = sorted(range(len(params)), key=lambda k: params[k]["N"])
+    ranks = np.linspace(0, len(params) - 1, count).round().astype(int)
+    return [order[r] for r in ranks]
+
+
+# requests of the served stream (seed 2001) that the oracle runs at their stated size and step
+# count: the cheapest of each kind plus weak pulses and the strongest shocks
+SERVED_SAMPLE = (1661, 1283, 1920, 1208, 10, 1356, 1919, 221)
 
 
 def sample_cells(ny, nx, seed):
@@ -66,6 +82,20 @@ def main(which):
             p = params[k]
             spec, W = wl.acoustic_pulse(p["N"], p["A"], p["b"], p["cx"], p["cy"])
             write_case(f"pulse{k:03d}_100", spec, W, 100, seed=k)
+    elif which == "pulses16":
+        params = wl.batched_pulses()
+        for k in pulse_quantile_grids(params):
+            p = params[k]
+            if os.path.exists(os.path.join(HERE, f"oracle_pulse{k:03d}_100.npz")):
+                continue
+            spec, W = wl.acoustic_pulse(p["N"], p["A"], p["b"], p["cx"], p["cy"])
+            write_case(f"pulse{k:03d}_100", spec, W, 100, seed=k)
+    elif which == "served":
+        reqs = {r["id"]: r for r in wl.served_requests()}
+        for rid in SERVED_SAMPLE:
+            r = reqs[rid]
+            spec, W = wl.request_problem(r)
+            write_case(f"request{rid:04d}_{r['steps']}", spec, W, r["steps"], seed=20010 + rid)
     else:
         raise SystemExit(__doc__)
 

@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 from conftest import GOLDEN
-from parity_util import plane_scales
+from parity_util import check
 from paper_2001_01570_gb300 import cgks, workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -27,13 +27,11 @@ def _golden(name):
     return np.load(path)
 
 
-def _compare(out, g, spec):
+def _compare(out, g, spec, name=None):
     planes = out.reshape(out.shape[0], -1)[:, g["idx"]]
-    scale = plane_scales(g["maxabs"], 2, spec.dx, spec.dy, spec.gamma)
-    err = np.abs(planes - g["values"]).max(axis=1) / np.where(scale > 0, scale, 1.0)
-    assert err[:4].max() <= TOL, err
-    assert err[4:].max() <= GRAD_TOL, err
-    return err
+    scaled, _ = check(name, planes, g["values"], dx=spec.dx, dy=spec.dy, gamma=spec.gamma, tol=TOL,
+                      grad_tol=GRAD_TOL, maxabs=g["maxabs"])
+    return scaled
 
 
 def _run(spec, W, nsteps):
