@@ -152,11 +152,18 @@ cgks_status cgks_batch_step(cgks_solver* const* solvers, int n, int nsteps);
  * solvers take only 64x1; 2D solvers any other shape). */
 cgks_status cgks_set_tile_shape(cgks_solver* s, int shape);
 
-/* Tile shape (numbered as for cgks_set_tile_shape) that the
- * autotuner of cgks_batch_step chose for this exact batch, or -1 while it is
- * still timing the candidates (it times each candidate shape on the first
- * steps of a new batch composition; the shape never changes the results). */
+/* Tile shape (numbered as for cgks_set_tile_shape) that the autotuner of
+ * cgks_batch_step chose for this exact batch, or -1 while it is still timing
+ * the candidates.  The tuner times, on the first steps of a new batch
+ * composition, the flux kernel's tile shapes 14x8, 16x8, 16x7 and 16x16 (with
+ * 1.75, 2, 1.75 and 4 face segments per thread), then the update kernel at 2
+ * and 4 cells per thread with the best shape (12 steps in all); neither choice
+ * changes a result. */
 int cgks_batch_tile_shape(cgks_solver* const* solvers, int n);
+
+/* Cells per thread of the update kernel (1, 2 or 4) that the autotuner chose
+ * for this exact batch, or -1 while it is still timing the candidates. */
+int cgks_batch_update_cpt(cgks_solver* const* solvers, int n);
 
 /* Same as cgks_step(s, nsteps, 0, NULL), but with CUDA events recorded on the
  * solver's stream around every kernel of every step; stage_ms[0..7] receive
@@ -228,12 +235,17 @@ const char* cgks_noalloc_last_error(void);
 /* ------------------------------------------------------------------------
  * Serving: a continuous-batching solve server.  Requests (2D problems with an
  * initial state and a step count) may be submitted from any thread at any
- * time.  A scheduler thread admits them in arrival order while the active set
- * has fewer than max_active solves and their device bytes
- * (cgks_problem_device_bytes) fit hbm_budget_bytes; all active solves advance together in
- * rounds of steps_per_round steps of the batched launch (each with its own dt
- * and step target); a finished solve is copied to host memory and its device
- * memory freed, so waiting requests can enter at the next round. */
+ * time.  The server admits them in arrival order while fewer than max_active
+ * solves are admitted and their device bytes (cgks_problem_device_bytes) fit
+ * hbm_budget_bytes; it copies an admitted request's state to the GPU while
+ * other solves run and adds it to the batched launch at the next round
+ * boundary; all active solves advance together in rounds of steps_per_round
+ * steps of that launch (each with its own dt and step target; the captured
+ * step graphs are kept across changes of the active set, whose work queues are
+ * rewritten in place); a finished solve is copied to host memory and its
+ * device memory returned to the server's pool while later rounds run, so
+ * waiting requests can enter.  A solve's result is the same whatever it
+ * shares the launch with. */
 typedef struct cgks_server cgks_server;
 
 typedef struct {
@@ -241,7 +253,8 @@ typedef struct {
     int max_active;            /* at most this many solves share a launch */
     int steps_per_round;       /* steps between admission / retirement points */
     int tile_shape;            /* -1: autotune on the first batch; else a fixed shape */
-    void* cuda_stream;         /* cudaStream_t for all server work (NULL: default stream) */
+    void* cuda_stream;         /* cudaStream_t of the rounds (NULL: a stream of the server's own);
+                                  the copies run on two further streams of the server */
 } cgks_serve_cfg;
 
 typedef struct {
@@ -254,11 +267,17 @@ typedef struct {
     long submitted, completed, rejected, failed, active, pending, rounds;
     double cell_updates;        /* completed solves: sum of cells x steps */
     double wall_s;              /* first arrival to last completion */
-    double busy_s;              /* time spent in rounds */
+    double busy_s;              /* time during which at least one solve was active on the GPU */
     double cell_updates_per_s;  /* cell_updates / wall_s */
     double p50_s, p99_s, mean_s;/* solve latency, arrival to result on the host */
     double hbm_in_use, hbm_peak;/* bytes of admitted solves */
-    int tile_shape;             /* shape in use (-1 before it is chosen) */
+    int tile_shape;             /* flux-kernel tile shape in use (-1 while the tuner runs) */
+    int update_cpt;             /* cells per thread of the update kernel (-1 while the tuner runs) */
+    double gpu_s;               /* device time of all rounds (CUDA events around each round) */
+    double round_overhead;      /* 1 - gpu_s / busy_s: share of the time with active solves in
+                                   which the GPU ran none of their steps */
+    long graph_captures;        /* step graphs captured so far (one per tuner candidate; changes
+                                   of the active set capture none) */
 } cgks_serve_stats_t;
 
 /* Start a server (spawns the scheduler thread).  Errors: CGKS_E_INVAL. */
@@ -279,11 +298,15 @@ cgks_status cgks_serve_poll(cgks_server* srv, long req_id, double* out_planes, i
  * Returns CGKS_E_TIMEOUT if it has not finished by then. */
 cgks_status cgks_serve_wait(cgks_server* srv, long req_id, double timeout_s, double* out_planes);
 
-/* Throughput and latency statistics so far. */
+/* Throughput and latency statistics so far (always CGKS_OK for a valid
+ * server: a failure of the server's scheduler is reported to new submissions,
+ * to the requests it could not finish and by cgks_serve_stop). */
 cgks_status cgks_serve_stats(cgks_server* srv, cgks_serve_stats_t* out);
 
 /* Stop accepting requests, finish the queued and active ones, join the
- * scheduler thread and free the server. */
+ * server's threads and free the server.  Returns CGKS_OK, or the CUDA error
+ * status that stopped the scheduler (its queued requests then completed with
+ * that status). */
 cgks_status cgks_serve_stop(cgks_server* srv);
 
 /* Detail of the last failing cgks_serve_* call on the calling thread. */

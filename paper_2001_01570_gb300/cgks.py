@@ -51,7 +51,8 @@ class cgks_serve_stats_t(ctypes.Structure):
                                               "rounds")] + \
                [(n, ctypes.c_double) for n in ("cell_updates", "wall_s", "busy_s", "cell_updates_per_s", "p50_s",
                                                 "p99_s", "mean_s", "hbm_in_use", "hbm_peak")] + \
-               [("tile_shape", ctypes.c_int)]
+               [("tile_shape", ctypes.c_int), ("update_cpt", ctypes.c_int), ("gpu_s", ctypes.c_double),
+                ("round_overhead", ctypes.c_double), ("graph_captures", ctypes.c_long)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -86,6 +87,8 @@ def load():
     L.cgks_set_tile_shape.restype = ctypes.c_int
     L.cgks_batch_tile_shape.argtypes = [ctypes.POINTER(vp), ctypes.c_int]
     L.cgks_batch_tile_shape.restype = ctypes.c_int
+    L.cgks_batch_update_cpt.argtypes = [ctypes.POINTER(vp), ctypes.c_int]
+    L.cgks_batch_update_cpt.restype = ctypes.c_int
     L.cgks_serve_start.argtypes = [ctypes.POINTER(cgks_serve_cfg), ctypes.POINTER(vp)]
     L.cgks_serve_submit.argtypes = [vp, ctypes.POINTER(cgks_request), ctypes.POINTER(ctypes.c_long)]
     L.cgks_serve_poll.argtypes = [vp, ctypes.c_long, dp, ctypes.POINTER(ctypes.c_int)]
@@ -234,6 +237,11 @@ def cgks_set_tile_shape(solver, shape):
 def cgks_batch_tile_shape(solvers) -> int:
     arr = (ctypes.c_void_p * len(solvers))(*[s.value if isinstance(s, ctypes.c_void_p) else s for s in solvers])
     return int(load().cgks_batch_tile_shape(arr, len(solvers)))
+
+
+def cgks_batch_update_cpt(solvers) -> int:
+    arr = (ctypes.c_void_p * len(solvers))(*[s.value if isinstance(s, ctypes.c_void_p) else s for s in solvers])
+    return int(load().cgks_batch_update_cpt(arr, len(solvers)))
 
 
 def _scheck(st):

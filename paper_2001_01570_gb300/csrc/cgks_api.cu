@@ -1,6 +1,7 @@
 // cgks_api.cu -- host runtime behind the C ABI of include/cgks.h: solver
-// objects (device planes, control block, tile queue), state transfer, the
-// plain step loop and the batched CUDA-graph step over many grids.
+// objects (device planes, control block, tile queue), state transfer and the
+// plain step loop (the batched step is in cgks_batch.cu, serving in
+// cgks_serve.cu).
 #include "cgks_internal.h"
 #include "../../include/cgks.h"
 
@@ -9,35 +10,10 @@
 #include <stdio.h>
 #include <string.h>
 
-#include <map>
-#include <mutex>
 #include <string>
 #include <vector>
 
 using namespace cgks;
-
-struct cgks_solver {
-    cgks_problem prob;
-    size_t device_bytes = 0;
-    int nx = 0, ny = 0;
-    int device = 0;
-    int nsm = 1;
-    cudaStream_t stream = nullptr;
-    double* d_planes = nullptr;   // 3 x 12 planes: buf0, buf1, ws
-    double* d_records = nullptr;  // face-row records of the stage in flight
-    TileRef* d_rchunks = nullptr; // record-kernel work queue
-    int nrchunks = 0;
-    double* d_faces = nullptr;    // face results of the stage in flight
-    TileRef* d_cchunks = nullptr; // update-kernel work queue
-    int ncchunks = 0;
-    double* d_stage1d = nullptr;  // 6-plane staging for dim 1
-    Ctrl* d_ctrl = nullptr;
-    GridDev host_desc;
-    GridDev* d_desc = nullptr;
-    TileRef* d_tiles = nullptr;
-    int ntiles = 0;
-    int shape = TILE_16x8;
-};
 
 namespace {
 
@@ -116,7 +92,66 @@ int pick_shape(const cgks_problem& p)
 
 }  // namespace
 
+namespace cgks {
+
+void fill_grid_desc(const cgks_problem& p, double* planes, double* records, double* faces, Ctrl* ctrl, GridDev& G)
+{
+    const int nx = p.nx, ny = p.dim == 1 ? 1 : p.ny;
+    const size_t PL = (size_t)nx * ny;
+    memset(&G, 0, sizeof(G));
+    G.buf[0] = planes;
+    G.buf[1] = planes + 12 * PL;
+    G.ws = planes + 24 * PL;
+    G.ctrl = ctrl;
+    G.recx = records;
+    G.recy = p.dim == 2 ? records + (size_t)28 * (nx + 1) * (ny + 4) : nullptr;
+    G.facex = faces;
+    G.facey = p.dim == 2 ? faces + (size_t)16 * (nx + 1) * ny : nullptr;
+    G.nx = nx;
+    G.ny = ny;
+    G.dim = p.dim;
+    for (int k = 0; k < 4; ++k) G.bc[k] = (p.dim == 1 && k >= 2) ? CGKS_BC_PERIODIC : p.bc[k];
+    G.dx = (p.x1 - p.x0) / nx;
+    G.dy = p.dim == 1 ? 1.0 : (p.y1 - p.y0) / ny;
+    G.inv_dx = 1.0 / G.dx;
+    G.inv_dy = 1.0 / G.dy;
+    G.gamma = p.gamma;
+    // internal degrees of freedom of the 2D Maxwellian; a 1D problem runs as a
+    // y-uniform 2D one, whose extra velocity direction plays the role of the
+    // additional internal degree of freedom of the 1D model
+    G.K = (4.0 - 2.0 * p.gamma) / (p.gamma - 1.0);
+    G.cfl = p.cfl;
+    G.eps_tau = p.eps_tau;
+    G.c_tau = p.c_tau;
+    G.weno_eps = p.weno_eps;
+    G.mu = p.mu;
+    G.recon_vars = p.recon_vars;
+    G.order = p.order == 6 ? 6 : 8;
+    for (int side = 0; side < 4; ++side) {
+        const double* q = p.inflow[side];
+        const double r = q[0], u = q[1], v = p.dim == 1 ? 0.0 : q[2], pr = q[3];
+        G.inflow[side][0] = r;
+        G.inflow[side][1] = r * u;
+        G.inflow[side][2] = r * v;
+        G.inflow[side][3] = pr / (p.gamma - 1.0) + 0.5 * r * (u * u + v * v);
+    }
+}
+
+size_t grid_device_bytes(const cgks_problem& p)
+{
+    const int ny = p.dim == 1 ? 1 : p.ny;
+    return (size_t)3 * 12 * p.nx * ny * sizeof(double)
+           + (record_doubles(p.nx, ny, p.dim) + face_doubles(p.nx, ny, p.dim)) * sizeof(double);
+}
+
+cgks_status validate_problem(const cgks_problem* p) { return validate(p); }
+
+}  // namespace cgks
+
 extern "C" {
+
+void cgks_set_batch_error(const char* m) { g_last_error = m; }
+void cgks_set_launch_count(long n) { g_last_launches = n; }
 
 const char* cgks_status_string(cgks_status st)
 {
@@ -187,43 +222,7 @@ cgks_status cgks_create(const cgks_problem* prob, void* cuda_stream, cgks_solver
                                               : cuda_fail(e, "cgks_create");
     }
     GridDev& G = s->host_desc;
-    memset(&G, 0, sizeof(G));
-    G.buf[0] = s->d_planes;
-    G.buf[1] = s->d_planes + 12 * PL;
-    G.ws = s->d_planes + 24 * PL;
-    G.ctrl = s->d_ctrl;
-    G.recx = s->d_records;
-    G.recy = prob->dim == 2 ? s->d_records + (size_t)28 * (s->nx + 1) * (s->ny + 4) : nullptr;
-    G.facex = s->d_faces;
-    G.facey = prob->dim == 2 ? s->d_faces + (size_t)16 * (s->nx + 1) * s->ny : nullptr;
-    G.nx = s->nx;
-    G.ny = s->ny;
-    G.dim = prob->dim;
-    for (int k = 0; k < 4; ++k) G.bc[k] = (prob->dim == 1 && k >= 2) ? CGKS_BC_PERIODIC : prob->bc[k];
-    G.dx = (prob->x1 - prob->x0) / prob->nx;
-    G.dy = prob->dim == 1 ? 1.0 : (prob->y1 - prob->y0) / prob->ny;
-    G.inv_dx = 1.0 / G.dx;
-    G.inv_dy = 1.0 / G.dy;
-    G.gamma = prob->gamma;
-    // internal degrees of freedom of the 2D Maxwellian; a 1D problem runs as a
-    // y-uniform 2D one, whose extra velocity direction plays the role of the
-    // additional internal degree of freedom of the 1D model
-    G.K = (4.0 - 2.0 * prob->gamma) / (prob->gamma - 1.0);
-    G.cfl = prob->cfl;
-    G.eps_tau = prob->eps_tau;
-    G.c_tau = prob->c_tau;
-    G.weno_eps = prob->weno_eps;
-    G.mu = prob->mu;
-    G.recon_vars = prob->recon_vars;
-    G.order = prob->order == 6 ? 6 : 8;
-    for (int side = 0; side < 4; ++side) {
-        const double* q = prob->inflow[side];
-        const double r = q[0], u = q[1], v = prob->dim == 1 ? 0.0 : q[2], p = q[3];
-        G.inflow[side][0] = r;
-        G.inflow[side][1] = r * u;
-        G.inflow[side][2] = r * v;
-        G.inflow[side][3] = p / (prob->gamma - 1.0) + 0.5 * r * (u * u + v * v);
-    }
+    fill_grid_desc(*prob, s->d_planes, s->d_records, s->d_faces, s->d_ctrl, G);
     e = cudaMemcpyAsync(s->d_desc, &G, sizeof(GridDev), cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(s->d_tiles, tiles.data(), tiles.size() * sizeof(TileRef), cudaMemcpyHostToDevice, s->stream);
@@ -384,13 +383,6 @@ cgks_status cgks_step(cgks_solver* s, int nsteps, double t_end, double* t_out)
 
 }  // extern "C"
 
-// internal (used by the server): stop the solve after `target` steps
-cgks_status cgks_set_step_target(cgks_solver* s, long long target)
-{
-    CK(launch_set_ctrl(s->d_ctrl, 0.0, 0.0, target, 0, s->stream));
-    return CGKS_OK;
-}
-
 extern "C" {
 
 cgks_status cgks_step_profiled(cgks_solver* s, int nsteps, double stage_ms[8])
@@ -438,238 +430,6 @@ cgks_status cgks_step_profiled(cgks_solver* s, int nsteps, double stage_ms[8])
     if (st != CGKS_OK) return st;
     if (c.status & CGKS_E_NONPHYSICAL) return fail(CGKS_E_NONPHYSICAL, "non-physical state met; last valid state kept");
     return CGKS_OK;
-}
-
-// ---------------------------------------------------------------------------
-// batched stepping: one persistent launch per stage over the tiles of all
-// grids, captured into a CUDA graph per batch composition and replayed.  The
-// tile shape of each plan is chosen by timing the candidate shapes on its first
-// steps (the shape changes only the work decomposition, never the arithmetic of
-// a face or a cell, so results are identical whichever shape runs).
-}  // extern "C"
-
-namespace {
-std::mutex g_batch_mu;
-std::map<std::vector<cgks_solver*>, cgks::BatchPlan*> g_batch_plans;
-}  // namespace
-
-namespace cgks {
-
-void destroy_plan(BatchPlan* bp)
-{
-    if (!bp) return;
-    for (int k = 0; k < TILE_COUNT; ++k) {
-        if (bp->exec[k]) cudaGraphExecDestroy(bp->exec[k]);
-        cudaFree(bp->d_tiles[k]);
-    }
-    for (int c = 0; c < 2; ++c) cudaFree(bp->d_rchunks[c]);
-    cudaFree(bp->d_cchunks);
-    cudaFree(bp->d_grids);
-    delete bp;
-}
-
-static cudaError_t capture_graph(BatchPlan* bp, int shape)
-{
-    const int n = (int)bp->solvers.size();
-    const int nblocks = stage_blocks(bp->ntiles[shape], bp->nsm);
-    // first calls configure the kernels' attributes outside the capture
-    cudaError_t e = launch_stage(shape, 1, bp->d_grids, bp->d_tiles[shape], 0, 1, bp->stream);
-    if (e == cudaSuccess) e = launch_stage(shape, 2, bp->d_grids, bp->d_tiles[shape], 0, 1, bp->stream);
-    if (e != cudaSuccess) return e;
-    auto records = [&](int stage, cudaStream_t st) {
-        cudaError_t r = cudaSuccess;
-        for (int c = 0; c < 2 && r == cudaSuccess; ++c)
-            r = launch_records(stage, c, bp->d_grids, bp->d_rchunks[c], bp->nrchunks[c],
-                               record_blocks(bp->nrchunks[c], bp->nsm, c), st);
-        return r;
-    };
-    cudaStream_t cap;
-    e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
-    if (e != cudaSuccess) return e;
-    cudaGraph_t graph;
-    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-        cudaError_t e1 = launch_begin_step(bp->d_grids, n, cap);
-        for (int stage = 1; stage <= 2; ++stage) {
-            if (e1 == cudaSuccess) e1 = records(stage, cap);
-            if (e1 == cudaSuccess)
-                e1 = launch_stage(shape, stage, bp->d_grids, bp->d_tiles[shape], bp->ntiles[shape], nblocks, cap);
-            if (e1 == cudaSuccess)
-                e1 = launch_update(stage, bp->d_grids, bp->d_cchunks, bp->ncchunks, update_blocks(bp->ncchunks, bp->nsm),
-                                   cap);
-        }
-        if (e1 == cudaSuccess) e1 = launch_end_step(bp->d_grids, n, cap);
-        e = cudaStreamEndCapture(cap, &graph);
-        if (e1 != cudaSuccess) e = e1;
-    }
-    cudaStreamDestroy(cap);
-    if (e != cudaSuccess) return e;
-    e = cudaGraphInstantiate(&bp->exec[shape], graph, 0);
-    cudaGraphDestroy(graph);
-    return e;
-}
-
-cudaError_t make_plan(cgks_solver* const* solvers, int n, cudaStream_t stream, int forced_shape, BatchPlan** out)
-{
-    BatchPlan* bp = new BatchPlan();
-    bp->solvers.assign(solvers, solvers + n);
-    bp->stream = stream;
-    bp->nsm = solvers[0]->nsm;
-    bp->dim = solvers[0]->prob.dim;
-    std::vector<GridDev> descs;
-    for (int g = 0; g < n; ++g) descs.push_back(solvers[g]->host_desc);
-    cudaError_t e = cudaMalloc(&bp->d_grids, descs.size() * sizeof(GridDev));
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(bp->d_grids, descs.data(), descs.size() * sizeof(GridDev), cudaMemcpyHostToDevice, stream);
-    long long cells = 0;
-    for (int g = 0; g < n; ++g) cells += (long long)solvers[g]->nx * solvers[g]->ny;
-    bp->cells = cells;
-    // update-kernel queue of all grids
-    {
-        std::vector<TileRef> q;
-        for (int g = 0; g < n; ++g) {
-            std::vector<TileRef> r = cell_chunks(solvers[g]->nx, solvers[g]->ny, g);
-            q.insert(q.end(), r.begin(), r.end());
-        }
-        bp->ncchunks = (int)q.size();
-        bp->launches_per_step += 2;
-        if (e == cudaSuccess) e = cudaMalloc(&bp->d_cchunks, q.size() * sizeof(TileRef));
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(bp->d_cchunks, q.data(), q.size() * sizeof(TileRef), cudaMemcpyHostToDevice, stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-    }
-    // record-kernel queues of the conservative and the characteristic grids
-    for (int c = 0; c < 2; ++c) {
-        std::vector<TileRef> q;
-        for (int g = 0; g < n; ++g) {
-            const cgks_problem& p = solvers[g]->prob;
-            if (p.recon_vars != c) continue;
-            std::vector<TileRef> r = record_chunks(solvers[g]->nx, solvers[g]->ny, p.dim, p.recon_vars, g);
-            q.insert(q.end(), r.begin(), r.end());
-        }
-        bp->nrchunks[c] = (int)q.size();
-        if (q.empty()) continue;
-        bp->launches_per_step += 2;
-        if (e == cudaSuccess) e = cudaMalloc(&bp->d_rchunks[c], q.size() * sizeof(TileRef));
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(bp->d_rchunks[c], q.data(), q.size() * sizeof(TileRef), cudaMemcpyHostToDevice, stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-    }
-    if (bp->dim == 1) { bp->candidates = {TILE_64x1}; }
-    else if (forced_shape >= 0) { bp->candidates = {forced_shape}; }
-    else { bp->candidates = {TILE_14x8, TILE_16x8, TILE_16x7, TILE_16x16}; }
-    for (int shape : bp->candidates) {
-        std::vector<TileRef> tiles;
-        for (int g = 0; g < n; ++g) {
-            const int tw = tile_w(shape), th = tile_h(shape);
-            for (int y0 = 0; y0 < solvers[g]->ny; y0 += th)
-                for (int x0 = 0; x0 < solvers[g]->nx; x0 += tw) tiles.push_back(TileRef{g, x0, y0, 0});
-        }
-        bp->ntiles[shape] = (int)tiles.size();
-        if (e == cudaSuccess) e = cudaMalloc(&bp->d_tiles[shape], tiles.size() * sizeof(TileRef));
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(bp->d_tiles[shape], tiles.data(), tiles.size() * sizeof(TileRef), cudaMemcpyHostToDevice,
-                                stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-        if (e == cudaSuccess) e = capture_graph(bp, shape);
-    }
-    if (e != cudaSuccess) { destroy_plan(bp); return e; }
-    bp->chosen = bp->candidates.size() == 1 ? bp->candidates[0] : -1;
-    *out = bp;
-    return cudaSuccess;
-}
-
-// run nsteps steps of the plan; while the shape is not yet chosen, each
-// candidate runs timed steps and the fastest is kept
-cudaError_t run_plan(BatchPlan* bp, int nsteps, long* launches)
-{
-    cudaError_t e = cudaSuccess;
-    int k = 0;
-    while (bp->chosen < 0 && k < nsteps) {
-        const int shape = bp->candidates[bp->trial_idx];
-        cudaEvent_t a, b;
-        cudaEventCreate(&a);
-        cudaEventCreate(&b);
-        cudaEventRecord(a, bp->stream);
-        e = cudaGraphLaunch(bp->exec[shape], bp->stream);
-        cudaEventRecord(b, bp->stream);
-        if (e == cudaSuccess) e = cudaEventSynchronize(b);
-        float ms = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
-        cudaEventDestroy(a);
-        cudaEventDestroy(b);
-        if (e != cudaSuccess) return e;
-        *launches += bp->launches_per_step;
-        ++k;
-        if (bp->trial_count[shape] > 0) bp->trial_ms[shape] += ms;   // the first run of a shape is a warm-up
-        bp->trial_count[shape] += 1;
-        if (bp->trial_count[shape] >= 2) {
-            bp->trial_idx += 1;
-            if (bp->trial_idx >= (int)bp->candidates.size()) {
-                int best = bp->candidates[0];
-                for (int s2 : bp->candidates)
-                    if (bp->trial_ms[s2] < bp->trial_ms[best]) best = s2;
-                bp->chosen = best;
-            }
-        }
-    }
-    for (; k < nsteps; ++k) {
-        e = cudaGraphLaunch(bp->exec[bp->chosen], bp->stream);
-        if (e != cudaSuccess) return e;
-        *launches += bp->launches_per_step;
-    }
-    return cudaSuccess;
-}
-
-}  // namespace cgks
-
-extern "C" {
-
-void cgks_forget_solver_plans(cgks_solver* s)
-{
-    std::lock_guard<std::mutex> lk(g_batch_mu);
-    for (auto it = g_batch_plans.begin(); it != g_batch_plans.end();) {
-        bool has = false;
-        for (cgks_solver* x : it->first) has |= (x == s);
-        if (has) { cgks::destroy_plan(it->second); it = g_batch_plans.erase(it); }
-        else ++it;
-    }
-}
-
-cgks_status cgks_batch_step(cgks_solver* const* solvers, int n, int nsteps)
-{
-    if (!solvers || n <= 0 || nsteps < 0) return fail(CGKS_E_INVAL, "bad arguments");
-    for (int g = 0; g < n; ++g) {
-        if (!solvers[g]) return fail(CGKS_E_INVAL, "NULL solver in batch");
-        if (solvers[g]->prob.dim != solvers[0]->prob.dim) return fail(CGKS_E_INVAL, "mixed dims in one batch");
-    }
-    std::lock_guard<std::mutex> lk(g_batch_mu);
-    g_last_launches = 0;
-    std::vector<cgks_solver*> key(solvers, solvers + n);
-    BatchPlan* bp = nullptr;
-    auto it = g_batch_plans.find(key);
-    if (it != g_batch_plans.end()) bp = it->second;
-    else {
-        cudaError_t e = make_plan(solvers, n, solvers[0]->stream, -1, &bp);
-        if (e != cudaSuccess) return cuda_fail(e, "batch plan");
-        g_batch_plans[key] = bp;
-    }
-    long launches = 0;
-    CK(launch_batch_resume(bp->d_grids, n, bp->stream));
-    launches += 1;
-    CK(run_plan(bp, nsteps, &launches));
-    CK(cudaStreamSynchronize(bp->stream));
-    g_last_launches = launches;
-    return CGKS_OK;
-}
-
-int cgks_batch_tile_shape(cgks_solver* const* solvers, int n)
-{
-    std::lock_guard<std::mutex> lk(g_batch_mu);
-    std::vector<cgks_solver*> key(solvers, solvers + n);
-    auto it = g_batch_plans.find(key);
-    if (it == g_batch_plans.end()) return -1;
-    return it->second->chosen;
 }
 
 }  // extern "C"

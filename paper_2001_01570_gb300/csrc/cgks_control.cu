@@ -7,17 +7,17 @@
 namespace cgks {
 
 #define CGKS_DECLARE_TILE(w, h)                                                                          \
-    cudaError_t launch_stage_##w##x##h(int, const GridDev*, const TileRef*, int, int, cudaStream_t);  \
+    cudaError_t launch_stage_##w##x##h(int, const GridDev*, const TileRef*, int, int, cudaStream_t, const int*); \
     size_t smem_##w##x##h(int);
 CGKS_FOR_EACH_TILE(CGKS_DECLARE_TILE)
 #undef CGKS_DECLARE_TILE
 
 cudaError_t launch_stage(int shape, int stage, const GridDev* grids, const TileRef* tiles, int ntiles, int nblocks,
-                         cudaStream_t st)
+                         cudaStream_t st, const int* dcount)
 {
     switch (shape) {
 #define CGKS_LAUNCH_CASE(w, h) \
-    case TILE_##w##x##h: return launch_stage_##w##x##h(stage, grids, tiles, ntiles, nblocks, st);
+    case TILE_##w##x##h: return launch_stage_##w##x##h(stage, grids, tiles, ntiles, nblocks, st, dcount);
     CGKS_FOR_EACH_TILE(CGKS_LAUNCH_CASE)
 #undef CGKS_LAUNCH_CASE
     default: return cudaErrorInvalidValue;

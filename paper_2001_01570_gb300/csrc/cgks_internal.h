@@ -3,7 +3,10 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <utility>
 #include <vector>
+
+#include "../../include/cgks.h"
 
 namespace cgks {
 
@@ -107,10 +110,16 @@ std::vector<TileRef> record_chunks(int nx, int ny, int dim, int recon_vars, int 
 // the update kernel's work queue: chunks of 256 cells of one grid (TileRef.x0
 // is the first cell)
 std::vector<TileRef> cell_chunks(int nx, int ny, int grid);
+// cpt: cells per thread of the update kernel (1, 2 or 4: CTAs of 256, 128 or 64
+// threads per chunk of 256 cells)
 cudaError_t launch_update(int stage, const GridDev* grids, const TileRef* chunks, int nchunks, int nblocks,
-                          cudaStream_t st);
+                          cudaStream_t st, const int* dcount = nullptr, int cpt = 1);
 // persistent grid of the update kernel: up to 8 resident CTAs per SM
-inline int update_blocks(int nchunks, int nsm) { return nchunks < 8 * nsm ? nchunks : 8 * nsm; }
+inline int update_blocks(int nchunks, int nsm, int cpt = 1)
+{
+    const int cap = 8 * cpt * nsm;
+    return nchunks < cap ? nchunks : cap;
+}
 // flux kernel: two resident CTAs of 128 threads per SM (one stages its tile
 // while the other computes)
 constexpr int kStageCtasPerSm = 2;
@@ -127,11 +136,15 @@ inline int record_blocks(int nchunks, int nsm, int char_vars)
     return nchunks < cap ? nchunks : cap;
 }
 
-// launchers (defined in the kernel translation units)
+// launchers (defined in the kernel translation units).  The persistent kernels
+// stride over a work queue of `n` entries; a non-NULL `dcount` points to an int
+// in device memory that holds the queue's current length instead (read when the
+// kernel starts), so that a captured graph keeps working while a server patches
+// its queues between replays.
 cudaError_t launch_records(int stage, int char_vars, const GridDev* grids, const TileRef* chunks, int nchunks,
-                           int nblocks, cudaStream_t st);
+                           int nblocks, cudaStream_t st, const int* dcount = nullptr);
 cudaError_t launch_stage(int shape, int stage, const GridDev* grids, const TileRef* tiles, int ntiles,
-                         int nblocks, cudaStream_t st);
+                         int nblocks, cudaStream_t st, const int* dcount = nullptr);
 size_t stage_smem_bytes(int shape, int stage);
 cudaError_t launch_begin_step(const GridDev* grids, int ngrids, cudaStream_t st);
 cudaError_t launch_end_step(const GridDev* grids, int ngrids, cudaStream_t st);
@@ -146,34 +159,114 @@ cudaError_t launch_batch_resume(const GridDev* grids, int n, cudaStream_t st);
 
 }  // namespace cgks
 
-struct cgks_solver;
+// A solver: one grid's device planes, control block, descriptor and queues
+// (the object behind the opaque cgks_solver of the C ABI).
+struct cgks_solver {
+    cgks_problem prob;
+    size_t device_bytes = 0;
+    int nx = 0, ny = 0;
+    int device = 0;
+    int nsm = 1;
+    cudaStream_t stream = nullptr;
+    double* d_planes = nullptr;   // 3 x 12 planes: buf0, buf1, ws
+    double* d_records = nullptr;  // face-row records of the stage in flight
+    cgks::TileRef* d_rchunks = nullptr; // record-kernel work queue
+    int nrchunks = 0;
+    double* d_faces = nullptr;    // face results of the stage in flight
+    cgks::TileRef* d_cchunks = nullptr; // update-kernel work queue
+    int ncchunks = 0;
+    double* d_stage1d = nullptr;  // 6-plane staging for dim 1
+    cgks::Ctrl* d_ctrl = nullptr;
+    cgks::GridDev host_desc;
+    cgks::GridDev* d_desc = nullptr;
+    cgks::TileRef* d_tiles = nullptr;
+    int ntiles = 0;
+    int shape = cgks::TILE_16x8;
+};
 
 namespace cgks {
 
-// A batch of solvers stepped together: device descriptor array, one tile
-// queue and one captured step graph per candidate tile shape.
-struct BatchPlan {
-    std::vector<cgks_solver*> solvers;
-    cudaStream_t stream = nullptr;
-    int nsm = 1, dim = 2;
-    long long cells = 0;
-    GridDev* d_grids = nullptr;
-    TileRef* d_tiles[TILE_COUNT] = {};
-    int ntiles[TILE_COUNT] = {};
-    TileRef* d_rchunks[2] = {};   // record-kernel queues: conservative / characteristic grids
-    int nrchunks[2] = {};
-    TileRef* d_cchunks = nullptr; // update-kernel queue
-    int ncchunks = 0;
-    int launches_per_step = 4;
-    cudaGraphExec_t exec[TILE_COUNT] = {};
-    std::vector<int> candidates;
-    int chosen = -1, trial_idx = 0;
-    float trial_ms[TILE_COUNT] = {};
-    int trial_count[TILE_COUNT] = {};
-};
+// the descriptor of a grid of problem p whose buffers start at the given
+// device addresses (planes: 3 x 12 planes of nx*ny)
+void fill_grid_desc(const cgks_problem& p, double* planes, double* records, double* faces, Ctrl* ctrl, GridDev& G);
+// device bytes of one grid's planes, records and face results
+size_t grid_device_bytes(const cgks_problem& p);
+// argument checks of a problem (CGKS_OK or CGKS_E_INVAL with the detail in
+// cgks_last_error)
+cgks_status validate_problem(const cgks_problem* p);
 
-cudaError_t make_plan(cgks_solver* const* solvers, int n, cudaStream_t stream, int forced_shape, BatchPlan** out);
-cudaError_t run_plan(BatchPlan* bp, int nsteps, long* launches);
-void destroy_plan(BatchPlan* bp);
+// ---------------------------------------------------------------------------
+// The batched engine: many grids of any size advance together, one persistent
+// launch per kernel and stage over flattened work queues of all of them,
+// replayed as a CUDA graph.  Grids sit in slots of a descriptor table; an
+// empty slot points to a control block marked done.  The queues and their
+// lengths live in device memory and may be rewritten between replays (on the
+// engine's stream), so one captured graph per candidate serves every
+// composition of the slots.  A candidate is a tile shape of the flux kernel
+// (the face segments per thread follow from it) and a cells-per-thread count
+// of the update kernel; the tuner times each candidate on the first steps
+// (shapes first, then cells per thread with the best shape) and keeps the
+// fastest; no candidate changes a result.
+struct BatchCand { int shape, cpt; };
+
+class BatchEngine {
+public:
+    // nslots: size of the descriptor table; forced_shape >= 0 fixes the tile
+    // shape (no tuning of the shape)
+    static cudaError_t create(int nslots, int dim, cudaStream_t stream, int forced_shape, BatchEngine** out);
+    ~BatchEngine();
+
+    // Set the grids of the slots (slot index, descriptor); the others become
+    // empty.  Rebuilds the queues and enqueues their upload on the stream, so
+    // the next replay sees the new composition.
+    cudaError_t set_members(const std::vector<std::pair<int, GridDev>>& members);
+    // Enqueue nsteps steps.  While the tuner runs it times candidates (one
+    // tuning step per call synchronises the stream).
+    cudaError_t run(int nsteps, long* launches, bool tune = true);
+    // Enqueue one replay of candidate `cand` for `nsteps` steps, bracketed by
+    // the events (either may be NULL): the server times its rounds with them.
+    cudaError_t replay(int cand, int nsteps, cudaEvent_t before, cudaEvent_t after, long* launches);
+    // Enqueue a copy of every slot's control block into dst (nslots entries).
+    cudaError_t snapshot(Ctrl* dst);
+    // The tuner's current choice, or -1 while candidates are still timed.
+    int chosen() const { return chosen_; }
+    // the candidate the next step runs, and the tuner's record of its time
+    int next_candidate() const;
+    void record_time(int cand, double ms_per_cell_step);
+    const BatchCand& candidate(int k) const { return cands_[k]; }
+    int ncandidates() const { return (int)cands_.size(); }
+    long long member_cells() const { return cells_; }
+    int launches_per_step() const { return launches_per_step_; }
+    long captures() const { return captures_; }
+    cudaStream_t stream() const { return stream_; }
+    const GridDev* device_table() const { return d_grids_; }
+
+private:
+    BatchEngine() = default;
+    cudaError_t ensure_capacity(int k, size_t n);
+    cudaError_t capture(int cand);
+    int nslots_ = 0, dim_ = 2, nsm_ = 1;
+    cudaStream_t stream_ = nullptr;
+    GridDev* d_grids_ = nullptr;
+    Ctrl* d_dummy_ = nullptr;
+    // device queues: [0, TILE_COUNT) tiles per shape, then records (2), cells
+    static constexpr int kQ = TILE_COUNT + 3;
+    TileRef* d_q_[kQ] = {};
+    size_t cap_[kQ] = {};
+    int* d_counts_ = nullptr;
+    // pinned staging of the uploads, reused once the previous upload finished
+    char* h_stage_ = nullptr;
+    size_t stage_cap_ = 0;
+    cudaEvent_t stage_done_ = nullptr;
+    std::vector<BatchCand> cands_;
+    std::vector<cudaGraphExec_t> exec_;
+    std::vector<double> trial_;
+    int chosen_ = -1, tune_phase_ = 0, trial_next_ = 0;
+    long long cells_ = 0;
+    int launches_per_step_ = 0;
+    bool has_char_ = false;
+    int member_count_ = 0;
+    long captures_ = 0;
+};
 
 }  // namespace cgks

@@ -236,8 +236,10 @@ __device__ __forceinline__ void char_row(const RegK& r, const GridDev& G, const 
 // The reconstruction order is per grid (a uniform branch per chunk).
 template <int STAGE, int CHAR>
 __global__ void __launch_bounds__(256, CHAR ? 1 : 2) records_kernel(const GridDev* __restrict__ grids,
-                                                                    const TileRef* __restrict__ chunks, int nchunks)
+                                                                    const TileRef* __restrict__ chunks, int nchunks,
+                                                                    const int* __restrict__ dcount)
 {
+    if (dcount) nchunks = *dcount;   // queue length in device memory (a server's patched queue)
     __shared__ double s_tab[2 * RK_N];
     for (int i = threadIdx.x; i < 2 * RK_N; i += blockDim.x) s_tab[i] = kReconTab.v[i / RK_N][i % RK_N];
     __syncthreads();
@@ -273,15 +275,15 @@ std::vector<TileRef> record_chunks(int nx, int ny, int dim, int recon_vars, int 
 }
 
 cudaError_t launch_records(int stage, int char_vars, const GridDev* grids, const TileRef* chunks, int nchunks,
-                           int nblocks, cudaStream_t st)
+                           int nblocks, cudaStream_t st, const int* dcount)
 {
-    if (nchunks <= 0) return cudaSuccess;
+    if (nchunks <= 0 || nblocks <= 0) return cudaSuccess;
     if (char_vars) {
-        if (stage == 1) records_kernel<1, 1><<<nblocks, 256, 0, st>>>(grids, chunks, nchunks);
-        else records_kernel<2, 1><<<nblocks, 256, 0, st>>>(grids, chunks, nchunks);
+        if (stage == 1) records_kernel<1, 1><<<nblocks, 256, 0, st>>>(grids, chunks, nchunks, dcount);
+        else records_kernel<2, 1><<<nblocks, 256, 0, st>>>(grids, chunks, nchunks, dcount);
     } else {
-        if (stage == 1) records_kernel<1, 0><<<nblocks, 256, 0, st>>>(grids, chunks, nchunks);
-        else records_kernel<2, 0><<<nblocks, 256, 0, st>>>(grids, chunks, nchunks);
+        if (stage == 1) records_kernel<1, 0><<<nblocks, 256, 0, st>>>(grids, chunks, nchunks, dcount);
+        else records_kernel<2, 0><<<nblocks, 256, 0, st>>>(grids, chunks, nchunks, dcount);
     }
     return cudaGetLastError();
 }

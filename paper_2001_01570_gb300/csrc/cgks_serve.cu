@@ -2,23 +2,30 @@
 // include/cgks.h.
 //
 // Requests (2D problems with an initial state and a step count) arrive on any
-// thread.  One scheduler thread owns all device work:
-//   admit    pending requests in arrival order while the active set is below
-//            max_active and their device planes fit the HBM budget; the state
-//            is uploaded and the solve joins the active set
-//   run      one round = steps_per_round steps of the batched persistent
-//            launch over the tiles of every active grid (a CUDA graph per
-//            active-set composition); every grid carries its own step target
-//            and dt, so grids of any size and step count share a launch
-//   retire   grids that reached their target (or failed) are copied back to
-//            host memory, their device memory is freed and their latency
-//            (arrival to result) is recorded
-// Requests that arrive while others run are admitted at the next round
-// boundary, as slots and memory free up.
+// thread.  Three threads of the server do the rest, each on its own stream:
+//   scheduler   admits pending requests in arrival order into free slots while
+//               their device bytes fit the HBM budget; launches rounds of
+//               steps_per_round steps of the batched engine (cgks_batch.cu) over
+//               every active grid; after each round copies all control blocks
+//               to pinned host memory and, one round later, retires the grids
+//               that reached their step count (or failed).  It keeps two
+//               rounds in flight, so its host work overlaps the GPU's.
+//   uploader    allocates an admitted request's device memory from a
+//               stream-ordered pool and copies its initial state in, while
+//               the rounds run; the scheduler adds the grid to the engine's
+//               queues (patched in place: the captured graphs stay) at the next
+//               round boundary after the copy has finished
+//   downloader  copies a retired grid's state to host memory once the rounds
+//               that could still touch it are done, frees its device memory and
+//               completes the request
+// Every grid carries its own step target and dt, so grids of any size and step
+// count share a launch, and a grid's results do not depend on what it shares
+// the launch with.
 #include "cgks_internal.h"
 #include "../../include/cgks.h"
 
 #include <cuda_runtime.h>
+#include <string.h>
 
 #include <algorithm>
 #include <chrono>
@@ -30,8 +37,7 @@
 #include <thread>
 #include <vector>
 
-extern "C" void cgks_forget_solver_plans(cgks_solver* s);
-cgks_status cgks_set_step_target(cgks_solver* s, long long target);
+using namespace cgks;
 
 namespace {
 
@@ -42,43 +48,85 @@ double now_s()
     return std::chrono::duration<double>(clock_t_::now().time_since_epoch()).count();
 }
 
+enum ReqState { R_PENDING, R_LOADING, R_READY, R_ACTIVE, R_RETIRING, R_DONE };
+
 struct Request {
     long id = 0;
     cgks_problem prob;
-    std::vector<double> init;      // host copy of the initial planes
+    std::vector<double> init;      // host copy of the initial planes (until uploaded)
     int nsteps = 0;
-    size_t bytes = 0;              // device bytes while active
+    size_t bytes = 0;              // device bytes while admitted
     long long cells = 0;
     double t_arrival = 0, t_admit = 0, t_done = 0;
-    cgks_solver* solver = nullptr;
     std::vector<double> result;    // host copy of the final planes
     int status = CGKS_OK;
     bool done = false;
-    bool taken = false;
+    ReqState state = R_PENDING;
+    // device side, between admission and completion
+    int slot = -1;
+    char* mem = nullptr;
+    GridDev desc;
+    cudaEvent_t ev = nullptr;      // upload finished / last round that touches the grid
+    long join_round = -1;          // first round that includes the grid
+    Ctrl final_ctrl;
+    int forced_status = CGKS_OK;   // set when the scheduler stopped before the grid finished
+};
+
+// one grid's device memory: 3 x 12 state planes, face-row records, face
+// results, control block, descriptor (the kernels of cgks_create's layout)
+struct GridLayout {
+    size_t planes, records, faces, ctrl, desc, total;
+};
+
+GridLayout grid_layout(const cgks_problem& p)
+{
+    GridLayout L;
+    const size_t PL = (size_t)p.nx * p.ny;
+    L.planes = 0;
+    L.records = L.planes + 36 * PL * sizeof(double);
+    L.faces = L.records + record_doubles(p.nx, p.ny, 2) * sizeof(double);
+    L.ctrl = (L.faces + face_doubles(p.nx, p.ny, 2) * sizeof(double) + 255) & ~(size_t)255;
+    L.desc = L.ctrl + 256;
+    L.total = L.desc + ((sizeof(GridDev) + 255) & ~(size_t)255);
+    return L;
+}
+
+struct InFlight {
+    long round;
+    int cand;
+    int buf;
+    long long cells;
 };
 
 }  // namespace
 
 struct cgks_server {
     cgks_serve_cfg cfg;
-    cudaStream_t stream = nullptr;
-    std::thread worker;
+    int device = 0;
+    cudaStream_t S = nullptr, Cu = nullptr, Cd = nullptr;
+    bool own_S = false;
+    cudaMemPool_t pool = nullptr;
+    std::thread sched, uploader, downloader;
     std::mutex mu;
-    std::condition_variable cv_work, cv_done;
-    std::deque<Request*> pending;
-    std::vector<Request*> active;
+    std::condition_variable cv_sched, cv_done, cv_up, cv_down;
+    std::deque<Request*> pending, up_jobs, down_jobs;
+    std::vector<Request*> ready;
+    std::vector<Request*> slots;          // max_active entries, NULL = free
     std::map<long, Request*> requests;
-    bool stopping = false;
+    bool stopping = false, workers_exit = false, worker_stopped = false;
     long next_id = 1;
     size_t bytes_in_use = 0, bytes_peak = 0;
+    long inflight_requests = 0;           // admitted and not yet completed
     // statistics
     long submitted = 0, completed = 0, rejected = 0, failed = 0, rounds = 0;
     double cell_updates = 0.0;
-    double t_first_arrival = -1.0, t_last_done = -1.0, busy_s = 0.0;
+    double t_first_arrival = -1.0, t_last_done = -1.0;
+    double gpu_s = 0.0, active_s = 0.0;
     std::vector<double> latencies;
     std::string worker_error;
     int worker_status = CGKS_OK;
-    int tile_shape = -1;
+    int tile_shape = -1, update_cpt = -1;
+    long graph_captures = 0;
 };
 
 namespace {
@@ -91,131 +139,323 @@ cgks_status sfail(cgks_status st, const std::string& m)
     return st;
 }
 
-size_t request_bytes(const cgks_problem& p)
+// complete a request (lock held)
+void finish(cgks_server* S, Request* r, int status, double t)
 {
-    return (size_t)cgks_problem_device_bytes(&p);
+    r->status = status;
+    r->done = true;
+    r->state = R_DONE;
+    r->t_done = t;
+    if (status == CGKS_OK) {
+        S->completed += 1;
+        S->cell_updates += (double)r->cells * r->nsteps;
+        S->latencies.push_back(r->t_done - r->t_arrival);
+    } else {
+        S->failed += 1;
+    }
+    S->t_last_done = t;
+    S->cv_done.notify_all();
+}
+
+void upload_loop(cgks_server* S)
+{
+    cudaSetDevice(S->device);
+    for (;;) {
+        Request* r = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv_up.wait(lk, [&] { return S->workers_exit || !S->up_jobs.empty(); });
+            if (S->up_jobs.empty()) return;
+            r = S->up_jobs.front();
+            S->up_jobs.pop_front();
+        }
+        const GridLayout L = grid_layout(r->prob);
+        cudaError_t e = cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&r->mem, L.total, S->pool, S->Cu);
+        if (e == cudaSuccess) {
+            fill_grid_desc(r->prob, (double*)(r->mem + L.planes), (double*)(r->mem + L.records),
+                           (double*)(r->mem + L.faces), (Ctrl*)(r->mem + L.ctrl), r->desc);
+            GridDev* d_desc = (GridDev*)(r->mem + L.desc);
+            e = cudaMemcpyAsync(r->desc.buf[0], r->init.data(), 12 * (size_t)r->cells * sizeof(double),
+                                cudaMemcpyHostToDevice, S->Cu);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(d_desc, &r->desc, sizeof(GridDev), cudaMemcpyHostToDevice, S->Cu);
+            if (e == cudaSuccess) e = launch_set_ctrl(r->desc.ctrl, 0.0, 0.0, r->nsteps, 1, S->Cu);
+            if (e == cudaSuccess) e = launch_cfl(d_desc, 0, r->desc, S->Cu);
+            if (e == cudaSuccess) e = cudaEventRecord(r->ev, S->Cu);
+            // the host copy of the initial state may go once the copy has run
+            if (e == cudaSuccess) e = cudaEventSynchronize(r->ev);
+        }
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (e != cudaSuccess) {
+            if (r->mem) cudaFreeAsync(r->mem, S->Cu);
+            r->mem = nullptr;
+            if (r->ev) cudaEventDestroy(r->ev);
+            r->ev = nullptr;
+            S->slots[r->slot] = nullptr;
+            S->bytes_in_use -= r->bytes;
+            S->inflight_requests -= 1;
+            finish(S, r, e == cudaErrorMemoryAllocation ? CGKS_E_NOMEM : CGKS_E_CUDA, now_s());
+            S->cv_sched.notify_all();
+            continue;
+        }
+        r->init.clear();
+        r->init.shrink_to_fit();
+        if (S->worker_stopped) {
+            // the scheduler is gone: the downloader frees the grid and reports the failure
+            r->forced_status = S->worker_status ? S->worker_status : CGKS_E_CUDA;
+            memset(&r->final_ctrl, 0, sizeof(Ctrl));
+            r->state = R_RETIRING;
+            S->slots[r->slot] = nullptr;
+            S->down_jobs.push_back(r);
+            S->cv_down.notify_one();
+            continue;
+        }
+        r->state = R_READY;
+        S->ready.push_back(r);
+        S->cv_sched.notify_all();
+    }
+}
+
+void download_loop(cgks_server* S)
+{
+    cudaSetDevice(S->device);
+    for (;;) {
+        Request* r = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv_down.wait(lk, [&] { return S->workers_exit || !S->down_jobs.empty(); });
+            if (S->down_jobs.empty()) return;
+            r = S->down_jobs.front();
+            S->down_jobs.pop_front();
+        }
+        const Ctrl& c = r->final_ctrl;
+        cudaError_t e = cudaStreamWaitEvent(S->Cd, r->ev, 0);
+        r->result.resize((size_t)12 * r->cells);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(r->result.data(), r->desc.buf[c.par & 1], 12 * (size_t)r->cells * sizeof(double),
+                                cudaMemcpyDeviceToHost, S->Cd);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(S->Cd);
+        cudaFreeAsync(r->mem, S->Cd);
+        r->mem = nullptr;
+        const double t = now_s();
+        std::lock_guard<std::mutex> lk(S->mu);
+        cudaEventDestroy(r->ev);
+        r->ev = nullptr;
+        S->bytes_in_use -= r->bytes;
+        S->inflight_requests -= 1;
+        int st = CGKS_OK;
+        if (r->forced_status != CGKS_OK) st = r->forced_status;
+        else if (e != cudaSuccess) st = CGKS_E_CUDA;
+        else if (c.status & CGKS_E_NONPHYSICAL) st = CGKS_E_NONPHYSICAL;
+        else if (c.steps < r->nsteps) st = CGKS_E_CUDA;
+        finish(S, r, st, t);
+        S->cv_sched.notify_all();
+    }
 }
 
 // scheduler thread body
-void serve_loop(cgks_server* S)
+// the server's streams and its stream-ordered pool (freed grids stay reserved
+// for the next ones), created by the scheduler before it admits anything
+cudaError_t setup_device(cgks_server* S)
 {
-    cgks::BatchPlan* plan = nullptr;
-    bool membership_changed = true;
-    for (;;) {
-        // ---- admit
-        std::vector<Request*> admitted;
+    cudaError_t e = cudaSetDevice(S->device);
+    if (e == cudaSuccess && !S->S) {
+        e = cudaStreamCreateWithFlags(&S->S, cudaStreamNonBlocking);
+        S->own_S = (e == cudaSuccess);
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->Cu, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->Cd, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = S->device;
+        e = cudaMemPoolCreate(&S->pool, &props);
+        if (e == cudaSuccess) {
+            unsigned long long keep = (unsigned long long)S->cfg.hbm_budget_bytes;
+            e = cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+    }
+    return e;
+}
+
+void sched_loop(cgks_server* S)
+{
+    const int nslots = S->cfg.max_active;
+    BatchEngine* E = nullptr;
+    Ctrl* d_snap = nullptr;
+    Ctrl* h_snap = nullptr;
+    cudaEvent_t ev_snap[2] = {}, ev_r0[2] = {}, ev_r1[2] = {};
+    cudaError_t e = setup_device(S);
+    if (e == cudaSuccess) e = BatchEngine::create(nslots, 2, S->S, S->cfg.tile_shape, &E);
+    if (e == cudaSuccess) e = cudaMalloc(&d_snap, 2 * (size_t)nslots * sizeof(Ctrl));
+    if (e == cudaSuccess) e = cudaHostAlloc(&h_snap, 2 * (size_t)nslots * sizeof(Ctrl), cudaHostAllocDefault);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+        e = cudaEventCreateWithFlags(&ev_snap[b], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreate(&ev_r0[b]);
+        if (e == cudaSuccess) e = cudaEventCreate(&ev_r1[b]);
+    }
+    std::deque<InFlight> inflight;
+    long round = 0;
+    bool patch = false;
+    double t_active0 = -1.0;   // start of the current stretch with active grids
+    while (e == cudaSuccess) {
+        std::vector<Request*> joined;
+        int nactive = 0;
         {
             std::unique_lock<std::mutex> lk(S->mu);
-            while (S->pending.empty() && S->active.empty() && !S->stopping) S->cv_work.wait(lk);
-            if (S->pending.empty() && S->active.empty() && S->stopping) break;
-            while (!S->pending.empty() && (int)S->active.size() < S->cfg.max_active &&
-                   S->bytes_in_use + S->pending.front()->bytes <= (size_t)S->cfg.hbm_budget_bytes) {
+            for (Request* r : S->slots) nactive += (r && r->state == R_ACTIVE);
+            const bool idle = nactive == 0 && inflight.empty() && S->ready.empty();
+            if (idle && S->stopping && S->pending.empty() && S->inflight_requests == 0) break;
+            // admission in arrival order: a free slot and room in the budget
+            while (!S->pending.empty()) {
                 Request* r = S->pending.front();
+                if (S->bytes_in_use + r->bytes > (size_t)S->cfg.hbm_budget_bytes) break;
+                int slot = -1;
+                for (int k = 0; k < nslots && slot < 0; ++k)
+                    if (!S->slots[k]) slot = k;
+                if (slot < 0) break;
                 S->pending.pop_front();
+                S->slots[slot] = r;
+                r->slot = slot;
+                r->state = R_LOADING;
+                r->t_admit = now_s();
                 S->bytes_in_use += r->bytes;
                 S->bytes_peak = std::max(S->bytes_peak, S->bytes_in_use);
-                admitted.push_back(r);
+                S->inflight_requests += 1;
+                S->up_jobs.push_back(r);
+                S->cv_up.notify_one();
             }
-        }
-        for (Request* r : admitted) {
-            cgks_status st = cgks_create(&r->prob, S->stream, &r->solver);
-            if (st == CGKS_OK) st = cgks_set_state(r->solver, r->init.data(), 0, 0.0);
-            if (st == CGKS_OK) st = cgks_set_step_target(r->solver, r->nsteps);
-            r->t_admit = now_s();
-            std::lock_guard<std::mutex> lk(S->mu);
-            if (st != CGKS_OK) {
-                r->status = st;
-                r->done = true;
-                S->failed += 1;
-                S->bytes_in_use -= r->bytes;
-                if (r->solver) { cgks_destroy(r->solver); r->solver = nullptr; }
-                S->cv_done.notify_all();
+            joined.swap(S->ready);
+            if (idle && joined.empty()) {
+                // nothing to run: wait for an upload, a completion (room in the budget), a request or stop
+                S->cv_sched.wait_for(lk, std::chrono::milliseconds(50));
                 continue;
             }
-            r->init.clear();
-            r->init.shrink_to_fit();
-            S->active.push_back(r);
-            membership_changed = true;
         }
-        std::vector<Request*> act;
+        // grids whose upload finished join at this round boundary
+        for (Request* r : joined) {
+            e = cudaStreamWaitEvent(S->S, r->ev, 0);
+            if (e != cudaSuccess) break;
+            std::lock_guard<std::mutex> lk(S->mu);
+            r->state = R_ACTIVE;
+            r->join_round = round;
+            patch = true;
+        }
+        if (e != cudaSuccess) break;
+        std::vector<std::pair<int, GridDev>> members;
         {
             std::lock_guard<std::mutex> lk(S->mu);
-            act = S->active;
-        }
-        if (act.empty()) continue;
-
-        // ---- run one round of the batched launch
-        const double t0 = now_s();
-        if (membership_changed) {
-            if (plan) cgks::destroy_plan(plan);
-            plan = nullptr;
-            std::vector<cgks_solver*> sol;
-            for (Request* r : act) sol.push_back(r->solver);
-            cudaError_t e = cgks::make_plan(sol.data(), (int)sol.size(), S->stream, S->tile_shape, &plan);
-            if (e != cudaSuccess) {
-                std::lock_guard<std::mutex> lk(S->mu);
-                S->worker_error = std::string("batch plan: ") + cudaGetErrorString(e);
-                S->worker_status = CGKS_E_CUDA;
-                break;
+            for (int k = 0; k < nslots; ++k) {
+                Request* r = S->slots[k];
+                if (r && r->state == R_ACTIVE) members.emplace_back(k, r->desc);
             }
-            membership_changed = false;
         }
-        long launches = 0;
-        cudaError_t e = cgks::run_plan(plan, S->cfg.steps_per_round, &launches);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
-        if (plan->chosen >= 0) S->tile_shape = plan->chosen;
-        if (e != cudaSuccess) {
+        if (patch) {
+            e = E->set_members(members);
+            if (e != cudaSuccess) break;
+            patch = false;
+        }
+        if (!members.empty()) {
+            if (t_active0 < 0.0) t_active0 = now_s();
+            const int buf = (int)(round & 1);
+            const int cand = E->next_candidate();
+            long launches = 0;
+            e = E->replay(cand, S->cfg.steps_per_round, ev_r0[buf], ev_r1[buf], &launches);
+            if (e == cudaSuccess) e = E->snapshot(d_snap + (size_t)buf * nslots);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(h_snap + (size_t)buf * nslots, d_snap + (size_t)buf * nslots,
+                                    (size_t)nslots * sizeof(Ctrl), cudaMemcpyDeviceToHost, S->S);
+            if (e == cudaSuccess) e = cudaEventRecord(ev_snap[buf], S->S);
+            if (e != cudaSuccess) break;
+            inflight.push_back(InFlight{round, cand, buf, E->member_cells()});
+            round += 1;
+        }
+        // with two rounds in flight (or nothing more to launch), retire from the older one
+        if (inflight.size() >= 2 || (members.empty() && !inflight.empty())) {
+            const InFlight F = inflight.front();
+            inflight.pop_front();
+            e = cudaEventSynchronize(ev_snap[F.buf]);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev_r0[F.buf], ev_r1[F.buf]);
+            if (e != cudaSuccess) break;
+            if (E->chosen() < 0 && F.cells > 0) E->record_time(F.cand, ms / ((double)F.cells * S->cfg.steps_per_round));
+            const Ctrl* snap = h_snap + (size_t)F.buf * nslots;
             std::lock_guard<std::mutex> lk(S->mu);
-            S->worker_error = std::string("batched round: ") + cudaGetErrorString(e);
-            S->worker_status = CGKS_E_CUDA;
-            break;
-        }
-        // ---- retire finished grids
-        std::vector<Request*> finished;
-        for (Request* r : act) {
-            double t = 0.0;
-            long steps = 0;
-            cgks_status st = cgks_get_state(r->solver, nullptr, 0, &t, &steps);
-            if (st != CGKS_OK || steps >= r->nsteps) {
-                r->status = st;
-                r->result.resize((size_t)12 * r->cells);
-                cgks_get_state(r->solver, r->result.data(), 0, nullptr, nullptr);
-                finished.push_back(r);
+            S->rounds += 1;
+            S->gpu_s += 1e-3 * ms;
+            S->graph_captures = E->captures();
+            if (E->chosen() >= 0) {
+                S->tile_shape = E->candidate(E->chosen()).shape;
+                S->update_cpt = E->candidate(E->chosen()).cpt;
+            }
+            for (int k = 0; k < nslots; ++k) {
+                Request* r = S->slots[k];
+                if (!r || r->state != R_ACTIVE || r->join_round > F.round || !snap[k].done) continue;
+                // finished (step target reached) or failed: no later round computes it; the
+                // download waits for the rounds already enqueued
+                r->final_ctrl = snap[k];
+                r->state = R_RETIRING;
+                e = cudaEventRecord(r->ev, S->S);
+                if (e != cudaSuccess) break;
+                S->slots[k] = nullptr;
+                S->down_jobs.push_back(r);
+                S->cv_down.notify_one();
+                patch = true;
+            }
+            bool any_active = false;
+            for (Request* r : S->slots) any_active |= (r && r->state == R_ACTIVE);
+            if (!any_active && inflight.empty() && t_active0 >= 0.0) {
+                S->active_s += now_s() - t_active0;
+                t_active0 = -1.0;
             }
         }
-        const double t1 = now_s();
-        std::lock_guard<std::mutex> lk(S->mu);
-        S->rounds += 1;
-        S->busy_s += t1 - t0;
-        for (Request* r : finished) {
-            cgks_destroy(r->solver);
-            r->solver = nullptr;
-            r->t_done = t1;
-            r->done = true;
-            S->bytes_in_use -= r->bytes;
-            if (r->status == CGKS_OK) {
-                S->completed += 1;
-                S->cell_updates += (double)r->cells * r->nsteps;
-                S->latencies.push_back(r->t_done - r->t_arrival);
-            } else {
-                S->failed += 1;
-            }
-            S->t_last_done = t1;
-            S->active.erase(std::find(S->active.begin(), S->active.end(), r));
-            membership_changed = true;
-        }
-        if (!finished.empty()) S->cv_done.notify_all();
     }
-    if (plan) cgks::destroy_plan(plan);
     std::lock_guard<std::mutex> lk(S->mu);
-    for (Request* r : S->active) {
-        if (r->solver) cgks_destroy(r->solver);
-        r->solver = nullptr;
-        r->done = true;
-        r->status = S->worker_status ? S->worker_status : CGKS_E_CUDA;
+    if (e != cudaSuccess) {
+        S->worker_error = std::string("scheduler: ") + cudaGetErrorString(e);
+        S->worker_status = CGKS_E_CUDA;
     }
-    S->active.clear();
+    S->worker_stopped = true;
+    // fail what can no longer run: pending, uploaded and active requests (the
+    // workers finish the uploads and downloads already handed to them)
+    const double t = now_s();
+    for (Request* r : S->pending) {
+        if (!r->done) finish(S, r, S->worker_status ? S->worker_status : CGKS_E_CUDA, t);
+    }
+    S->pending.clear();
+    for (Request* r : S->ready) {
+        S->slots[r->slot] = nullptr;
+        r->state = R_RETIRING;
+        r->forced_status = S->worker_status ? S->worker_status : CGKS_E_CUDA;
+        memset(&r->final_ctrl, 0, sizeof(Ctrl));
+        S->down_jobs.push_back(r);
+        S->cv_down.notify_one();
+    }
+    S->ready.clear();
+    for (int k = 0; k < nslots; ++k) {
+        Request* r = S->slots[k];
+        if (r && (r->state == R_ACTIVE || r->state == R_READY)) {
+            S->slots[k] = nullptr;
+            r->state = R_RETIRING;
+            r->forced_status = S->worker_status ? S->worker_status : CGKS_E_CUDA;
+            memset(&r->final_ctrl, 0, sizeof(Ctrl));
+            cudaEventRecord(r->ev, S->S);
+            S->down_jobs.push_back(r);   // the downloader frees its memory and reports its status
+            S->cv_down.notify_one();
+        }
+    }
     S->cv_done.notify_all();
+    cudaStreamSynchronize(S->S);
+    delete E;
+    cudaFree(d_snap);
+    if (h_snap) cudaFreeHost(h_snap);
+    for (int b = 0; b < 2; ++b) {
+        if (ev_snap[b]) cudaEventDestroy(ev_snap[b]);
+        if (ev_r0[b]) cudaEventDestroy(ev_r0[b]);
+        if (ev_r1[b]) cudaEventDestroy(ev_r1[b]);
+    }
 }
 
 double percentile(std::vector<double> v, double q)
@@ -226,6 +466,16 @@ double percentile(std::vector<double> v, double q)
     const size_t lo = (size_t)pos;
     const size_t hi = std::min(lo + 1, v.size() - 1);
     return v[lo] + (pos - lo) * (v[hi] - v[lo]);
+}
+
+void destroy_server(cgks_server* S)
+{
+    if (S->Cu) cudaStreamDestroy(S->Cu);
+    if (S->Cd) cudaStreamDestroy(S->Cd);
+    if (S->own_S && S->S) cudaStreamDestroy(S->S);
+    if (S->pool) cudaMemPoolDestroy(S->pool);
+    for (auto& kv : S->requests) delete kv.second;
+    delete S;
 }
 
 }  // namespace
@@ -239,11 +489,18 @@ cgks_status cgks_serve_start(const cgks_serve_cfg* cfg, cgks_server** out)
     if (!cfg || !out) return sfail(CGKS_E_INVAL, "NULL argument");
     if (!(cfg->hbm_budget_bytes > 0) || cfg->max_active < 1 || cfg->steps_per_round < 1)
         return sfail(CGKS_E_INVAL, "budget, max_active and steps_per_round must be positive");
+    if (cfg->tile_shape >= TILE_COUNT || cfg->tile_shape == TILE_64x1)
+        return sfail(CGKS_E_INVAL, "unknown or 1D tile shape");
     cgks_server* S = new cgks_server();
     S->cfg = *cfg;
-    S->stream = (cudaStream_t)cfg->cuda_stream;
-    S->tile_shape = cfg->tile_shape;
-    S->worker = std::thread(serve_loop, S);
+    S->slots.assign((size_t)cfg->max_active, nullptr);
+    // the current device; the scheduler thread creates the streams and the pool
+    // on it (a failure there stops the server: submissions then return its status)
+    if (cudaGetDevice(&S->device) != cudaSuccess) S->device = 0;
+    S->S = (cudaStream_t)cfg->cuda_stream;
+    S->uploader = std::thread(upload_loop, S);
+    S->downloader = std::thread(download_loop, S);
+    S->sched = std::thread(sched_loop, S);
     *out = S;
     return CGKS_OK;
 }
@@ -253,14 +510,19 @@ cgks_status cgks_serve_submit(cgks_server* S, const cgks_request* req, long* req
     if (!S || !req || !req->init_planes || !req_id) return sfail(CGKS_E_INVAL, "NULL argument");
     if (req->prob.dim != 2) return sfail(CGKS_E_INVAL, "served solves are 2D");
     if (req->nsteps < 0) return sfail(CGKS_E_INVAL, "nsteps must be >= 0");
-    if (req->prob.nx < 1 || req->prob.ny < 1) return sfail(CGKS_E_INVAL, "bad grid");
-    const size_t bytes = request_bytes(req->prob);
+    if (validate_problem(&req->prob) != CGKS_OK)
+        return sfail(CGKS_E_INVAL, std::string("bad problem: ") + cgks_last_error());
+    // the budget counts what cgks_problem_device_bytes reports (an upper bound of the allocation)
+    const size_t bytes = (size_t)cgks_problem_device_bytes(&req->prob);
     std::lock_guard<std::mutex> lk(S->mu);
-    if (S->stopping) return sfail(CGKS_E_BUSY, "server is stopping");
     if (bytes > (size_t)S->cfg.hbm_budget_bytes) {
         S->rejected += 1;
         return sfail(CGKS_E_BUDGET, "request can never fit the HBM budget");
     }
+    if (S->worker_stopped)
+        return sfail(S->worker_status ? (cgks_status)S->worker_status : CGKS_E_BUSY,
+                     "the server's scheduler has stopped: " + S->worker_error);
+    if (S->stopping) return sfail(CGKS_E_BUSY, "server is stopping");
     Request* r = new Request();
     r->id = S->next_id++;
     r->prob = req->prob;
@@ -274,7 +536,7 @@ cgks_status cgks_serve_submit(cgks_server* S, const cgks_request* req, long* req
     S->pending.push_back(r);
     S->submitted += 1;
     *req_id = r->id;
-    S->cv_work.notify_one();
+    S->cv_sched.notify_all();
     return CGKS_OK;
 }
 
@@ -308,8 +570,9 @@ cgks_status cgks_serve_wait(cgks_server* S, long req_id, double timeout_s, doubl
             if (it == S->requests.end()) return sfail(CGKS_E_NOTFOUND, "unknown request id");
             if (it->second->done) break;
             if (S->cv_done.wait_until(lk, deadline) == std::cv_status::timeout) {
-                if (!S->requests.count(req_id) || !S->requests[req_id]->done)
-                    return sfail(CGKS_E_TIMEOUT, "request not finished within the timeout");
+                auto jt = S->requests.find(req_id);
+                if (jt == S->requests.end()) return sfail(CGKS_E_NOTFOUND, "unknown request id");
+                if (!jt->second->done) return sfail(CGKS_E_TIMEOUT, "request not finished within the timeout");
             }
         }
     }
@@ -325,11 +588,13 @@ cgks_status cgks_serve_stats(cgks_server* S, cgks_serve_stats_t* out)
     out->completed = S->completed;
     out->rejected = S->rejected;
     out->failed = S->failed;
-    out->active = (long)S->active.size();
+    long active = 0;
+    for (Request* r : S->slots) active += (r != nullptr);
+    out->active = active;
     out->pending = (long)S->pending.size();
     out->rounds = S->rounds;
     out->cell_updates = S->cell_updates;
-    out->busy_s = S->busy_s;
+    out->busy_s = S->active_s;
     out->wall_s = (S->t_first_arrival >= 0 && S->t_last_done >= 0) ? S->t_last_done - S->t_first_arrival : 0.0;
     out->cell_updates_per_s = out->wall_s > 0 ? S->cell_updates / out->wall_s : 0.0;
     out->p50_s = percentile(S->latencies, 0.50);
@@ -340,7 +605,11 @@ cgks_status cgks_serve_stats(cgks_server* S, cgks_serve_stats_t* out)
     out->hbm_in_use = (double)S->bytes_in_use;
     out->hbm_peak = (double)S->bytes_peak;
     out->tile_shape = S->tile_shape;
-    return (cgks_status)S->worker_status;
+    out->update_cpt = S->update_cpt;
+    out->gpu_s = S->gpu_s;
+    out->round_overhead = S->active_s > 0 ? 1.0 - S->gpu_s / S->active_s : 0.0;
+    out->graph_captures = S->graph_captures;
+    return CGKS_OK;
 }
 
 cgks_status cgks_serve_stop(cgks_server* S)
@@ -349,13 +618,22 @@ cgks_status cgks_serve_stop(cgks_server* S)
     {
         std::lock_guard<std::mutex> lk(S->mu);
         S->stopping = true;
-        S->cv_work.notify_all();
+        S->cv_sched.notify_all();
     }
-    if (S->worker.joinable()) S->worker.join();
-    cgks_status st = (cgks_status)S->worker_status;
-    for (auto& kv : S->requests) delete kv.second;
-    for (Request* r : S->pending) (void)r;   // owned by `requests`
-    delete S;
+    if (S->sched.joinable()) S->sched.join();
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->workers_exit = true;
+        S->cv_up.notify_all();
+        S->cv_down.notify_all();
+    }
+    if (S->uploader.joinable()) S->uploader.join();
+    if (S->downloader.joinable()) S->downloader.join();
+    cudaStreamSynchronize(S->Cu);
+    cudaStreamSynchronize(S->Cd);
+    const cgks_status st = (cgks_status)S->worker_status;
+    if (st != CGKS_OK) s_err = S->worker_error;
+    destroy_server(S);
     return st;
 }
 

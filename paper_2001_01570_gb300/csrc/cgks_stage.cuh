@@ -187,8 +187,10 @@ struct SegmentRows {
 
 template <int TX, int TY, int STAGE>
 __global__ void __launch_bounds__(kThreads, kStageCtasPerSm)
-stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tiles, int ntiles)
+stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tiles, int ntiles,
+             const int* __restrict__ dcount)
 {
+    if (dcount) ntiles = *dcount;   // queue length in device memory (a server's patched queue)
     using L = StageLayout<TX, TY, STAGE>;
     constexpr int NF = L::NF;
     extern __shared__ double smem[];
@@ -373,13 +375,14 @@ cudaError_t configure_stage_t()
 }
 
 template <int TX, int TY, int STAGE>
-cudaError_t launch_stage_t(const GridDev* grids, const TileRef* tiles, int ntiles, int nblocks, cudaStream_t st)
+cudaError_t launch_stage_t(const GridDev* grids, const TileRef* tiles, int ntiles, int nblocks, cudaStream_t st,
+                           const int* dcount)
 {
     using L = StageLayout<TX, TY, STAGE>;
     cudaError_t e = configure_stage_t<TX, TY, STAGE>();
     if (e != cudaSuccess) return e;
-    if (ntiles <= 0) return cudaSuccess;
-    stage_kernel<TX, TY, STAGE><<<nblocks, kThreads, L::bytes, st>>>(grids, tiles, ntiles);
+    if (ntiles <= 0 || nblocks <= 0) return cudaSuccess;
+    stage_kernel<TX, TY, STAGE><<<nblocks, kThreads, L::bytes, st>>>(grids, tiles, ntiles, dcount);
     return cudaGetLastError();
 }
 
@@ -388,10 +391,10 @@ cudaError_t launch_stage_t(const GridDev* grids, const TileRef* tiles, int ntile
 #define CGKS_STAGE_INSTANCE(TX, TY)                                                                         \
     static_assert(StageLayout<TX, TY, 1>::bytes + 64 <= 227 * 1024, "stage-1 tile exceeds shared memory");  \
     cudaError_t launch_stage_##TX##x##TY(int stage, const GridDev* grids, const TileRef* tiles, int ntiles,  \
-                                         int nblocks, cudaStream_t st)                                      \
+                                         int nblocks, cudaStream_t st, const int* dcount)                   \
     {                                                                                                       \
-        return stage == 1 ? launch_stage_t<TX, TY, 1>(grids, tiles, ntiles, nblocks, st)                    \
-                          : launch_stage_t<TX, TY, 2>(grids, tiles, ntiles, nblocks, st);                   \
+        return stage == 1 ? launch_stage_t<TX, TY, 1>(grids, tiles, ntiles, nblocks, st, dcount)            \
+                          : launch_stage_t<TX, TY, 2>(grids, tiles, ntiles, nblocks, st, dcount);           \
     }                                                                                                       \
     size_t smem_##TX##x##TY(int stage)                                                                      \
     {                                                                                                       \

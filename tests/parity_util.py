@@ -86,20 +86,26 @@ def _current_test():
     return os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0]
 
 
-def record(name, strict, scaled, nv):
+def record(name, strict, scaled, nv, maxabs=None):
     name = name or _current_test()
     REPORT.append({"case": name, "nvars": int(nv),
-                   "strict": [float(x) for x in strict], "scaled": [float(x) for x in scaled]})
+                   "strict": [float(x) for x in strict], "scaled": [float(x) for x in scaled],
+                   "maxabs": None if maxabs is None else [float(x) for x in maxabs[:nv]]})
     print(f"parity {name}: strict conserved {np.array2string(np.asarray(strict[:nv]), precision=2)} "
           f"scaled {np.array2string(np.asarray(scaled[:nv]), precision=2)}")
 
 
 # A conserved variable must meet TOL under both definitions, except momentum, which must meet TOL
-# against its rounding scale (plane_scales) and MOMENTUM_STRICT_TOL against its own maximum: in
-# a near-quiescent flow (an acoustic pulse of amplitude 1e-5 on a fluid at rest) the momentum is
-# the small difference of O(rho c^2) pressure fluxes, and two correct FP64 evaluations of the
-# scheme that round in different orders differ in it by ~1e-16 rho c per step.
+# against its rounding scale (plane_scales) and, where it carries a resolved signal (max |m| of at
+# least RESOLVED_MOMENTUM rho c: an acoustic pulse of amplitude 1e-5 has ~2e-6 rho c),
+# MOMENTUM_STRICT_TOL against its own maximum.  In a near-quiescent flow the momentum is the
+# small difference of O(rho c^2) pressure fluxes, and two correct FP64 evaluations of the scheme
+# that round in different orders differ in it by ~1e-15 rho c (tests/test_oracle_rounding_floor.py:
+# the oracle against itself transposed, ~1e-9 of max |m| on a 1e-5 pulse).  A momentum component
+# whose maximum is below that (zero by symmetry, or a second-order effect such as the ~3e-9 rho c
+# x-motion that viscous heating drives in a shear wave) is checked on the rounding scale only.
 MOMENTUM_STRICT_TOL = 1e-8
+RESOLVED_MOMENTUM = 1e-6
 
 
 def check(name, gpu, ora, dx=1.0, dy=1.0, gamma=1.4, tol=TOL, grad_tol=1e-9, maxabs=None, idx=None):
@@ -113,11 +119,14 @@ def check(name, gpu, ora, dx=1.0, dy=1.0, gamma=1.4, tol=TOL, grad_tol=1e-9, max
     diff = np.abs(gpu.reshape(nplanes, -1) - ora.reshape(nplanes, -1)).max(axis=1)
     scaled = np.where(scale > 0, diff / np.where(scale > 0, scale, 1.0), diff)
     strict = np.where(m > 0, diff / np.where(m > 0, m, 1.0), diff)
-    record(name, strict, scaled, nv)
+    record(name, strict, scaled, nv, m)
     assert scaled[:nv].max() <= tol, f"{name}: conserved-variable errors (rounding scale) {scaled[:nv]}"
     dens_energy = [0, nv - 1]
     assert strict[dens_energy].max() <= tol, f"{name}: density/energy errors {strict[:nv]}"
-    assert strict[1:nv - 1].max() <= MOMENTUM_STRICT_TOL, f"{name}: momentum errors vs own maximum {strict[:nv]}"
+    rho_c = np.sqrt(gamma * (gamma - 1.0) * m[0] * m[nv - 1])
+    for k in range(1, nv - 1):
+        if m[k] >= RESOLVED_MOMENTUM * rho_c:
+            assert strict[k] <= MOMENTUM_STRICT_TOL, f"{name}: momentum errors vs own maximum {strict[:nv]}"
     assert scaled[nv:].max() <= grad_tol, f"{name}: gradient errors {scaled[nv:]}"
     return scaled, strict
 

@@ -131,3 +131,35 @@ def test_batched_mixed_options_equal_alone_bitwise():
         assert sb == steps == 5 and tb == t
         assert np.array_equal(out, ref)
         s.close()
+
+
+def test_autotuner_picks_a_shape_and_cells_per_thread_without_changing_results():
+    """The batched autotuner times four tile shapes and then the update kernel at 2 and 4 cells per
+    thread (12 steps); its choice is reported, and the results equal the solves alone whichever
+    candidate ran which step."""
+    cases = [wl.acoustic_pulse(70, 1e-3, 5.0, 20.0, 40.0), wl.isentropic_vortex(45),
+             wl.shock_vortex(nx=52, ny=26, mach=1.45)]
+    nsteps = 15
+    alone = []
+    for spec, W in cases:
+        s = cgks.Solver(cgks.problem_from_spec(spec))
+        s.set_state(W)
+        s.step(nsteps)
+        alone.append(s.get_state())
+        s.close()
+    solvers = []
+    for spec, W in cases:
+        s = cgks.Solver(cgks.problem_from_spec(spec))
+        s.set_state(W)
+        solvers.append(s)
+    handles = [s.handle for s in solvers]
+    cgks.cgks_batch_step(handles, 5)
+    assert cgks.cgks_batch_tile_shape(handles) == -1           # still timing candidates
+    cgks.cgks_batch_step(handles, nsteps - 5)
+    assert cgks.TILE_SHAPES[cgks.cgks_batch_tile_shape(handles)] in ("14x8", "16x8", "16x7", "16x16")
+    assert cgks.cgks_batch_update_cpt(handles) in (1, 2, 4)
+    for s, (ref, t, steps) in zip(solvers, alone):
+        out, tb, sb = s.get_state()
+        assert sb == steps == nsteps and tb == t
+        assert np.array_equal(out, ref)
+        s.close()

@@ -81,9 +81,21 @@ def _pulse_ic(p):
     return wl.acoustic_pulse(p["N"], p["A"], p["b"], p["cx"], p["cy"])
 
 
+def _pulse_sample(params):
+    """The grids of the 256-grid batch with stored oracle values: the 8 smallest and 16 across the
+    size quantiles (65^2 .. 501^2), tests/golden/make_golden.py pulses / pulses16."""
+    smallest = sorted(range(len(params)), key=lambda k: params[k]["N"])[:8]
+    order = sorted(range(len(params)), key=lambda k: params[k]["N"])
+    ranks = np.linspace(0, len(params) - 1, 16).round().astype(int)
+    return sorted(set(smallest) | {order[r] for r in ranks})
+
+
 def test_batched_256_grids_100_steps():
+    """All 256 grids of the batched workload (seed 1570) in one cgks_batch_step call of 100 steps;
+    the sampled grids are compared with the oracle (the smallest eight and sixteen across the size
+    quantiles up to the largest), every grid's step count and time checked."""
     params = wl.batched_pulses()
-    order = sorted(range(len(params)), key=lambda k: params[k]["N"])[:8]
+    order = _pulse_sample(params)
     goldens = {k: _golden(f"pulse{k:03d}_100") for k in order}
     with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 4)) as pool:
         ics = pool.map(_pulse_ic, params)
@@ -97,7 +109,11 @@ def test_batched_256_grids_100_steps():
         for k in order:
             out, t, steps = solvers[k].get_state()
             assert steps == int(goldens[k]["steps"]) == 100
-            _compare(out, goldens[k], ics[k][0])
+            assert abs(t - float(goldens[k]["t"])) <= 1e-13 * float(goldens[k]["t"])
+            _compare(out, goldens[k], ics[k][0], name=f"batched256 grid {k} ({params[k]['N']}^2, "
+                                                      f"A={params[k]['A']:.1e})")
+        for s in solvers:
+            assert s.get_state()[2] == 100
     finally:
         for s in solvers:
             s.close()

@@ -80,3 +80,70 @@ def test_budget_limits_concurrency():
         cgks.cgks_serve_stop(srv)
     assert stats["hbm_peak"] <= one * 1.5 and stats["completed"] == 3
     assert np.array_equal(out, _alone(spec, W, 3))
+
+
+def test_composition_changes_keep_the_captured_graphs():
+    """Twelve requests through four slots: the active set changes at almost every round, the queues
+    are rewritten in place and no graph is captured beyond one per tuner candidate; the results
+    equal the solves alone."""
+    cases = [(wl.acoustic_pulse(24 + 4 * k, 1e-4, 3.0, 5.0 + k, 9.0), 3 + (k % 4)) for k in range(12)]
+    srv = cgks.cgks_serve_start(hbm_budget_bytes=1e9, max_active=4, steps_per_round=2)
+    try:
+        ids = [cgks.cgks_serve_submit(srv, cgks.problem_from_spec(spec), W, n) for (spec, W), n in cases]
+        outs = []
+        for rid, ((spec, W), n) in zip(ids, cases):
+            out = np.empty_like(W)
+            cgks.cgks_serve_wait(srv, rid, 120.0, out)
+            outs.append(out)
+        stats = cgks.cgks_serve_stats(srv)
+    finally:
+        cgks.cgks_serve_stop(srv)
+    assert stats["completed"] == 12
+    assert 1 <= stats["graph_captures"] <= 6
+    assert stats["gpu_s"] > 0.0
+    for out, ((spec, W), n) in zip(outs, cases):
+        assert np.array_equal(out, _alone(spec, W, n))
+
+
+def test_server_and_batch_step_from_another_thread():
+    """cgks_batch_step on one thread while the server runs requests on its own threads: both give
+    the results of the solves alone."""
+    serve_cases = [(wl.isentropic_vortex(40), 6), (wl.shock_vortex(nx=44, ny=22, mach=1.4), 5),
+                   (wl.acoustic_pulse(48, 1e-5, 5.0, 12.0, 30.0), 7)]
+    batch_cases = [wl.acoustic_pulse(36, 1e-3, 4.0, 9.0, 9.0), wl.isentropic_vortex(28)]
+    batch_refs = [_alone(spec, W, 6) for spec, W in batch_cases]
+    serve_refs = [_alone(spec, W, n) for (spec, W), n in serve_cases]
+    errors = []
+
+    def batch_thread():
+        try:
+            for _ in range(3):
+                solvers = []
+                for spec, W in batch_cases:
+                    s = cgks.Solver(cgks.problem_from_spec(spec))
+                    s.set_state(W)
+                    solvers.append(s)
+                cgks.cgks_batch_step([s.handle for s in solvers], 6)
+                for s, ref in zip(solvers, batch_refs):
+                    out, _, steps = s.get_state()
+                    if steps != 6 or not np.array_equal(out, ref):
+                        errors.append("batched result differs")
+                    s.close()
+        except Exception as e:  # noqa: BLE001
+            errors.append(repr(e))
+
+    srv = cgks.cgks_serve_start(hbm_budget_bytes=1e9, max_active=2, steps_per_round=2)
+    th = threading.Thread(target=batch_thread)
+    try:
+        th.start()
+        for _ in range(2):
+            ids = [cgks.cgks_serve_submit(srv, cgks.problem_from_spec(spec), W, n) for (spec, W), n in serve_cases]
+            for rid, ((spec, W), n), ref in zip(ids, serve_cases, serve_refs):
+                out = np.empty_like(W)
+                cgks.cgks_serve_wait(srv, rid, 120.0, out)
+                assert np.array_equal(out, ref)
+        th.join(timeout=300)
+    finally:
+        cgks.cgks_serve_stop(srv)
+    assert not th.is_alive()
+    assert not errors, errors

@@ -1,0 +1,54 @@
+"""Served requests of the config-5 stream against the oracle.
+
+Sampled requests of the seeded request stream (seed 2001) at their stated grid size and step count
+-- pulses (one of amplitude 2.4e-5), vortices and shock-vortex interactions at Mach 1.07, 1.48 and
+1.50 -- are submitted to the continuous-batching server mixed with three larger requests of the
+same stream, and each sampled result is compared element by element with the oracle's values
+stored by tests/golden/make_golden.py served (which calls only oracle/), at 1500 seeded cells."""
+import os
+
+import numpy as np
+import pytest
+
+from conftest import GOLDEN
+from parity_util import check
+from paper_2001_01570_gb300 import cgks, workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+SAMPLE = (1661, 1283, 1920, 1208, 10, 1356, 1919, 221)   # tests/golden/make_golden.py SERVED_SAMPLE
+LARGER = (2, 6, 12)                                         # 533^2 vortex, 483^2 pulse, 177^2 pulse
+
+
+def test_served_sample_matches_oracle():
+    reqs = {r["id"]: r for r in wl.served_requests()}
+    goldens = {}
+    for rid in SAMPLE:
+        path = os.path.join(GOLDEN, f"oracle_request{rid:04d}_{reqs[rid]['steps']}.npz")
+        if not os.path.exists(path):
+            pytest.skip(f"golden file {path} not generated")
+        goldens[rid] = np.load(path)
+    order = [LARGER[0], SAMPLE[0], SAMPLE[1], LARGER[1], *SAMPLE[2:5], LARGER[2], *SAMPLE[5:]]
+    ics = {rid: wl.request_problem(reqs[rid]) for rid in order}
+    srv = cgks.cgks_serve_start(hbm_budget_bytes=8e9, max_active=6, steps_per_round=8)
+    ids, outs = {}, {}
+    try:
+        for rid in order:
+            spec, W = ics[rid]
+            ids[rid] = cgks.cgks_serve_submit(srv, cgks.problem_from_spec(spec), W, reqs[rid]["steps"])
+        for rid in order:
+            out = np.empty_like(ics[rid][1])
+            cgks.cgks_serve_wait(srv, ids[rid], 600.0, out)
+            outs[rid] = out
+        stats = cgks.cgks_serve_stats(srv)
+    finally:
+        cgks.cgks_serve_stop(srv)
+    assert stats["completed"] == len(order) and stats["failed"] == 0
+    for rid in SAMPLE:
+        spec = ics[rid][0]
+        g = goldens[rid]
+        planes = outs[rid].reshape(12, -1)[:, g["idx"]]
+        r = reqs[rid]
+        check(f"served request {rid} ({r['kind']}, {spec.nx}x{spec.ny}, {r['steps']} steps"
+              + (f", Mach {r['mach']:.2f}" if "mach" in r else "") + (f", A={r['A']:.1e}" if "A" in r else "") + ")",
+              planes, g["values"], dx=spec.dx, dy=spec.dy, gamma=spec.gamma, maxabs=g["maxabs"])
