@@ -1,17 +1,28 @@
 """Throughput benchmark of the compact 8th-order GKS on GB300 (FP64 cell-updates/s).
 
 A step is one full two-stage fourth-order time step of the whole grid (CFL time step, both
-stages of reconstruction + gas-kinetic flux + Gauss-theorem update).  Default workload: the 2D
-isentropic vortex on a 2048^2 periodic grid (vortex strength 5 on free stream (1,1,1,1), [0,10]^2,
-CFL 0.5), synthetic initial data, state (3 x 12 planes, 1.2 GB) resident in HBM and larger than L2.
+stages of reconstruction + gas-kinetic flux + Gauss-theorem update).  The default run prints one
+JSON line with three measurements:
+
+  value    the plain sweep of the 2D isentropic vortex on a 2048^2 periodic grid (vortex strength 5
+           on free stream (1,1,1,1), [0,10]^2, CFL 0.5), K steps, state (3 x 12 planes, 1.2 GB)
+           resident in HBM and larger than L2; with its roofline, per-kernel times, e2e through the
+           C ABI from pinned host buffers and the oracle's CPU rate
+  batched  256 uneven periodic grids (acoustic pulses, N log-uniform in [64, 512], seed 1570): K
+           steps of the batched persistent launch (cgks_batch_step, autotuned) against one grid per
+           launch, overall and per size class
+  served   a prefix of the seeded Poisson request stream (seed 2001, grids 128^2..2048^2,
+           100..2000 steps, pulse / vortex / Mach 1.05..1.5 shock-vortex) at the stated grid sizes
+           and step counts through the continuous-batching server, saturated (all requests at once)
+           and capacity-matched (arrivals time-scaled to ~70 % of the saturated capacity), against
+           the same requests solved one after another; p50/p99 latency
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cgks|reference] [--workload NAME]
 
-Other workloads: vortex256/512/1024, shockvortex1024x512 (plain sweep; --order 6 runs the compact
-6th-order variant of the reconstruction instead), batched256 (256 uneven 2D
-grids, batched persistent launch vs one grid per launch), acoustic1d (2048 copies of the 1D
-acoustic-wave test, 12-48 cells each, batched vs plain), served (the Poisson request stream
-through the continuous-batching server).
+--no-batched / --no-served drop those records.  Other workloads (plain sweeps unless noted):
+vortex256/512/1024, shockvortex1024x512 (--order 6 runs the compact 6th-order variant of the
+reconstruction), batched256 and acoustic1d (2048 copies of the 1D acoustic-wave test, 12-48 cells
+each) as batched-vs-plain lines, served (the served record alone).
 
 --impl reference times the CPU oracle (test infrastructure, plain FP64 C) on a bounded sample of
 the same workload on the host cores.  Prints one JSON line (rank 0).
@@ -43,7 +54,7 @@ UNIT = "cell-updates/s"
 # stage 2: two Gauss points each) and the update (80 / 121).  The kernels issue their adds and
 # multiplies as DFMAs, so the operations are counted by ncu on a build with plain adds and
 # multiplies; each per-unit figure is the smallest count of the formulations measured (the current
-# code spends 1,916 per record and 3,112.4 / 2,916.4 per segment): profiles/stage_kernels_flops_vortex256.md.
+# code spends 1,916 per record and 3,112.4 / 2,916.4 per segment).
 # The compact 6th-order variant (--order 6) changes only the record kernel's linear reconstruction:
 # 1,840 per face row with WENO-Z.
 RECORD_FLOP_PER_CELL = {8: 3776.0, 6: 3680.0}
@@ -53,14 +64,15 @@ FLOP_PER_CELL = {s: RECORD_FLOP_PER_CELL[8] + FLUX_FLOP_PER_CELL[s] + UPDATE_FLO
 DEFAULT_TILE = "14x8"     # the library's 2D default
 # DRAM bytes (read + write) per cell of one flux-kernel launch with 14x8 tiles, ncu
 # dram__bytes_{read,write}.sum on the 1024^2 vortex (records and state larger than L2) divided by the
-# cells; the 2048^2 bench grid moves the same bytes per cell: profiles/flux_kernels_ncu_vortex1024.md.
+# cells; the 2048^2 bench grid moves the same bytes per cell.
 FLUX_DRAM_BYTES_PER_CELL = {1: 732.16e6 / 1048576, 2: 599.89e6 / 1048576}
 # algorithmic bytes per cell of the flux kernel: the two face rows' records (2 x 28 doubles) read and
 # the two faces' results written (stage 1: 16 doubles each, stage 2: 8)
 FLUX_ALGO_BYTES_PER_CELL = {1: 448 + 256, 2: 448 + 128}
-# measured FP64 peak of this GB300: DFMA with register operands issues 1.99 per SM and cycle
-# (throughput loop, FMA = 2 flops): profiles/fp64_peak_gb300.md.  The peak is taken at the median
-# SM clock sampled during the timed region (1.252 TFLOP/s at 2070 MHz).
+# FP64 peak of this GB300: DFMA with register operands issues 1.99 per SM and cycle (measured by
+# paper_2001_01570_gb300.diag, FMA = 2 flops; the nominal 1.25 TFLOP/s at 2070 MHz on 152 SMs is
+# 1.99 too).  The peak is taken at the median SM clock sampled during the timed region
+# (1.252 TFLOP/s at 2070 MHz).
 FP64_DFMA_PER_SM_CYCLE = 1.99
 DEFAULT_SM_MHZ = 2070.0
 
@@ -278,7 +290,7 @@ def run_cgks(args, world, rank, local):
 
     solver.close()
     if rank != 0:
-        return
+        return None
     cpu = None if args.no_cpu_baseline or world > 1 else oracle_sample(order=args.order)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -301,7 +313,7 @@ def run_cgks(args, world, rank, local):
         "clocks": clocks,
         "cpu_baseline": cpu,
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def _pulse_ic(p):
@@ -321,33 +333,23 @@ def _request_ic(req):
 
 
 def _parallel_ics(fn, items):
-    """Initial conditions in a spawn pool (started before any CUDA call of this process)."""
+    """Initial conditions in a spawn pool (fresh interpreters: safe after the first CUDA call)."""
     import multiprocessing as mp
     with mp.get_context("spawn").Pool(min(len(items), os.cpu_count() or 4)) as pool:
         return pool.map(fn, items)
 
 
-def run_batched(args, world, rank, local):
-    """Many independent grids of uneven size: one grid per launch (cgks_step per grid) against one
-    persistent launch over all grids' tiles per stage (cgks_batch_step, CUDA graph, autotuned)."""
-    from paper_2001_01570_gb300 import workloads as wl
-    if args.workload == "acoustic1d":
-        count = args.grids if args.grids_set else 2048
-        params = wl.batched_acoustic_1d(seed=618, count=count)
-        ics = _parallel_ics(_acoustic_ic, params)
-        what = (f"FP64 cell-updates/s, {count} 1D acoustic-wave grids: batched persistent launch vs one grid "
-                "per launch")
-        sizes = "N log-uniform in [12, 48], seed 618; eps_tau = 0"
-    else:
-        count = args.grids
-        params = wl.batched_pulses(seed=1570, count=count)
-        ics = _parallel_ics(_pulse_ic, params)
-        what = f"FP64 cell-updates/s, {count} uneven grids: batched persistent launch vs one grid per launch"
-        sizes = "N log-uniform in [64, 512], seed 1570"
+TUNE_STEPS = 12   # steps the batched autotuner times its candidates on (4 tile shapes, then 2 more
+                  # cells-per-thread counts of the update kernel, one untimed and one timed step each)
+
+
+def measure_batched(args, local, ics, steps, classes=None):
+    """One grid per launch (cgks_step per grid, each timed with CUDA events) against the batched
+    persistent launch over all grids (cgks_batch_step, warmed up through the autotuner), both for
+    `steps` steps from the same state; `classes` maps a label to the indices of a size class, each
+    also batched on its own."""
     import torch
-    from paper_2001_01570_gb300 import build as libbuild
     from paper_2001_01570_gb300 import cgks
-    libbuild.build()
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
     solvers = []
@@ -355,111 +357,192 @@ def run_batched(args, world, rank, local):
         s = cgks.Solver(cgks.problem_from_spec(spec), stream=stream.cuda_stream)
         s.set_state(W)
         solvers.append(s)
-    cells = sum(spec.cells for spec, _ in ics)
+    cells = [spec.cells for spec, _ in ics]
     handles = [s.handle for s in solvers]
-    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    # plain: each grid stepped by its own launches
     for s in solvers:
         s.step(args.warmup)
     torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in solvers]
     launches_plain = 0
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk_plain:
         start.record(stream)
-        for s in solvers:
-            cgks.cgks_step(s.handle, args.steps)
+        for s, (a, b) in zip(solvers, ev):
+            a.record(stream)
+            cgks.cgks_step(s.handle, steps)
+            b.record(stream)
             launches_plain += cgks.cgks_last_launch_count()
         stop.record(stream)
         torch.cuda.synchronize()
     ms_plain = start.elapsed_time(stop)
-    # batched: warm-up covers the tile-shape autotuning (4 candidate shapes x 2 steps)
-    cgks.cgks_batch_step(handles, max(args.warmup, 8))
-    torch.cuda.synchronize()
-    shape = cgks.cgks_batch_tile_shape(handles)
-    with ClockSampler(local) as clk:
-        start.record(stream)
-        cgks.cgks_batch_step(handles, args.steps)
-        stop.record(stream)
+    per_grid_ms = [a.elapsed_time(b) for a, b in ev]
+
+    def batched(idx):
+        hs = [handles[k] for k in idx]
+        cgks.cgks_batch_step(hs, max(args.warmup, TUNE_STEPS))
         torch.cuda.synchronize()
-    launches = cgks.cgks_last_launch_count()
-    ms_batch = start.elapsed_time(stop)
+        with ClockSampler(local) as clk:
+            start.record(stream)
+            cgks.cgks_batch_step(hs, steps)
+            stop.record(stream)
+            torch.cuda.synchronize()
+        shape, cpt = cgks.cgks_batch_tile_shape(hs), cgks.cgks_batch_update_cpt(hs)
+        return (start.elapsed_time(stop), cgks.cgks_last_launch_count(), clk.summary(),
+                cgks.TILE_SHAPES[shape] if shape >= 0 else None, cpt)
+
+    ms_batch, launches, clocks, shape, cpt = batched(list(range(len(solvers))))
+    total = sum(cells) * steps
+    rec = {"grids": len(solvers), "cells": sum(cells), "steps": steps,
+           "value": total / (ms_batch * 1e-3), "ms_per_step": ms_batch / steps, "gpu_launches": launches,
+           "tile_shape": shape, "update_cells_per_thread": cpt, "clocks": clocks,
+           "plain": {"value": total / (ms_plain * 1e-3), "ms_per_step": ms_plain / steps,
+                     "gpu_launches": launches_plain, "clocks": clk_plain.summary()}}
+    rec["batched_vs_plain"] = rec["value"] / rec["plain"]["value"]
+    if classes:
+        rec["size_classes"] = {}
+        for label, idx in classes.items():
+            if not idx:
+                continue
+            work = sum(cells[k] for k in idx) * steps
+            ms_p = sum(per_grid_ms[k] for k in idx)
+            ms_b, _, _, shp, cp = batched(idx)
+            rec["size_classes"][label] = {"grids": len(idx), "plain": work / (ms_p * 1e-3),
+                                          "batched": work / (ms_b * 1e-3), "batched_vs_plain": ms_p / ms_b,
+                                          "tile_shape": shp, "update_cells_per_thread": cp}
     for s in solvers:
         s.close()
-    plain = cells * args.steps / (ms_plain * 1e-3)
-    batched = cells * args.steps / (ms_batch * 1e-3)
-    if rank == 0:
-        print(json.dumps({
-            "metric": what,
-            "value": batched, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms_batch / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload if args.workload == "acoustic1d" else f"batched{count}",
-                       "grids": count, "cells": cells, "sizes": sizes,
-                       "tile_shape": cgks.TILE_SHAPES[shape] if shape >= 0 else None},
-            "plain": {"value": plain, "ms_per_step": ms_plain / args.steps, "gpu_launches": launches_plain,
-                      "clocks": clk_plain.summary()},
-            "batched_vs_plain": batched / plain, "gpu_launches": launches, "clocks": clk.summary()}), flush=True)
+    return rec
 
 
-def run_served(args, world, rank, local):
-    """A documented prefix / scaled copy of the seeded Poisson request stream through the
-    continuous-batching server, against the same requests solved one after another."""
+def batched_record(args, local):
+    """Config 4: the 256 uneven grids, seed 1570, `--steps` steps."""
     from paper_2001_01570_gb300 import workloads as wl
-    reqs = wl.served_requests(seed=2001)[: args.requests]
-    sc = args.served_scale
-    for r in reqs:
-        r["N"] = max(16, int(round(r["N"] / sc)))
-        r["steps"] = max(1, int(round(r["steps"] / sc)))
-        if "cx" in r:
-            r["cx"] /= sc
-            r["cy"] /= sc
-            r["b"] = max(1.5, r["b"] / sc)
-    ics = _parallel_ics(_request_ic, reqs)
-    import torch
-    from paper_2001_01570_gb300 import build as libbuild
-    from paper_2001_01570_gb300 import cgks
-    libbuild.build()
-    torch.cuda.set_device(local)
-    work = sum(spec.cells * r["steps"] for r, (spec, _) in zip(reqs, ics))
-    # plain: one request after another, each on its own solver
-    t0 = time.perf_counter()
-    for r, (spec, W) in zip(reqs, ics):
-        s = cgks.Solver(cgks.problem_from_spec(spec))
-        s.set_state(W)
-        s.step(r["steps"])
-        out, _, _ = s.get_state()
-        s.close()
-    plain_s = time.perf_counter() - t0
-    # served: submissions at the stream's arrival times (scaled by --arrival-scale)
+    params = wl.batched_pulses(seed=1570, count=args.grids)
+    ics = _parallel_ics(_pulse_ic, params)
+    N = [p["N"] for p in params]
+    classes = {"64-128": [k for k, n in enumerate(N) if n < 128],
+               "128-256": [k for k, n in enumerate(N) if 128 <= n < 256],
+               "256-512": [k for k, n in enumerate(N) if n >= 256]}
+    rec = measure_batched(args, local, ics, args.batched_steps or args.steps, classes)
+    rec["workload"] = (f"batched{args.grids}: periodic acoustic pulses, N log-uniform in [64, 512], A log-uniform "
+                       "in [1e-5, 1e-3], half-width 3..10 cells, seed 1570")
+    rec["l2"] = "state of all grids (%.2f GB) larger than L2" % (36 * rec["cells"] * 8 / 1e9)
+    return rec
+
+
+def _serve_pass(cgks, local, reqs, ics, arrival_scale, args):
+    """Submit the requests at their stream arrival times x arrival_scale (0: all at once) and wait
+    for every result; the server's statistics."""
     srv = cgks.cgks_serve_start(hbm_budget_bytes=120e9, max_active=args.max_active,
                                 steps_per_round=args.steps_per_round,
                                 tile_shape=cgks.TILE_SHAPES.index(args.tile) if args.tile else -1)
     ids = []
-    t_start = time.perf_counter()
-    with ClockSampler(local) as clk:
+    t0 = time.perf_counter()
+    try:
+        with ClockSampler(local) as clk:
+            for r, (spec, W) in zip(reqs, ics):
+                delay = (r["arrival"] - reqs[0]["arrival"]) * arrival_scale - (time.perf_counter() - t0)
+                if delay > 0:
+                    time.sleep(delay)
+                ids.append(cgks.cgks_serve_submit(srv, cgks.problem_from_spec(spec), W, r["steps"]))
+            for rid, (spec, W) in zip(ids, ics):
+                out = np.empty_like(W)
+                cgks.cgks_serve_wait(srv, rid, 3600.0, out)
+            stats = cgks.cgks_serve_stats(srv)
+    finally:
+        cgks.cgks_serve_stop(srv)
+    keep = ("cell_updates_per_s", "p50_s", "p99_s", "mean_s", "wall_s", "busy_s", "gpu_s", "round_overhead",
+            "rounds", "completed", "failed", "hbm_peak", "tile_shape", "update_cpt", "graph_captures")
+    out = {k: stats[k] for k in keep}
+    out["value"] = out.pop("cell_updates_per_s")
+    out["tile_shape"] = cgks.TILE_SHAPES[out["tile_shape"]] if out["tile_shape"] >= 0 else None
+    out["clocks"] = clk.summary()
+    return out
+
+
+def served_record(args, local):
+    """Config 5: a prefix of the seeded request stream at the stated sizes and step counts."""
+    import torch
+    from paper_2001_01570_gb300 import cgks
+    from paper_2001_01570_gb300 import workloads as wl
+    reqs = wl.served_requests(seed=2001)[: args.requests]
+    ics = _parallel_ics(_request_ic, reqs)
+    torch.cuda.set_device(local)
+    work = sum(spec.cells * r["steps"] for r, (spec, _) in zip(reqs, ics))
+    # one request after another, each on its own solver: allocation and copies timed apart from the steps
+    alloc_copy = steps_s = 0.0
+    t0 = time.perf_counter()
+    with ClockSampler(local) as clk_plain:
         for r, (spec, W) in zip(reqs, ics):
-            delay = r["arrival"] * args.arrival_scale - (time.perf_counter() - t_start)
-            if delay > 0:
-                time.sleep(delay)
-            ids.append(cgks.cgks_serve_submit(srv, cgks.problem_from_spec(spec), W, r["steps"]))
-        for rid, (spec, W) in zip(ids, ics):
-            out = np.empty_like(W)
-            cgks.cgks_serve_wait(srv, rid, 3600.0, out)
-        stats = cgks.cgks_serve_stats(srv)
-    cgks.cgks_serve_stop(srv)
+            ta = time.perf_counter()
+            s = cgks.Solver(cgks.problem_from_spec(spec))
+            s.set_state(W)
+            tb = time.perf_counter()
+            s.step(r["steps"])
+            tc = time.perf_counter()
+            s.get_state()
+            s.close()
+            td = time.perf_counter()
+            alloc_copy += (tb - ta) + (td - tc)
+            steps_s += tc - tb
+    plain_s = time.perf_counter() - t0
+    plain = {"value": work / plain_s, "wall_s": plain_s, "steps_s": steps_s, "alloc_copy_s": alloc_copy,
+             "steps_only_value": work / steps_s, "clocks": clk_plain.summary()}
+    saturated = _serve_pass(cgks, local, reqs, ics, 0.0, args)
+    span = reqs[-1]["arrival"] - reqs[0]["arrival"]
+    # arrivals stretched so that the offered load is 70 % of the saturated capacity
+    scale = saturated["wall_s"] / (0.7 * span) if span > 0 else 1.0
+    matched = _serve_pass(cgks, local, reqs, ics, scale, args)
+    matched["arrival_scale"] = scale
+    matched["offered_load_vs_capacity"] = 0.7
+    kinds = {}
+    for r in reqs:
+        kinds[r["kind"]] = kinds.get(r["kind"], 0) + 1
+    return {"workload": f"served: the first {len(reqs)} requests of the seeded stream (seed 2001, Poisson 50 req/s, "
+                        "N log-uniform 128..2048, steps log-uniform 100..2000, pulse/vortex/shock-vortex, "
+                        "Mach 1.05..1.5) at their stated N and step counts, 120 GB budget",
+            "requests": len(reqs), "kinds": kinds, "cell_updates": work,
+            "grids": [[spec.nx, spec.ny, r["steps"]] for r, (spec, _) in zip(reqs, ics)],
+            "max_active": args.max_active, "steps_per_round": args.steps_per_round,
+            "plain": plain, "saturated": saturated, "capacity_matched": matched,
+            "served_vs_plain": saturated["value"] / plain["value"],
+            "served_vs_plain_steps_only": saturated["value"] / plain["steps_only_value"]}
+
+
+def run_batched_line(args, world, rank, local):
+    """--workload batched256 / acoustic1d: the batched record as a line of its own."""
+    from paper_2001_01570_gb300 import build as libbuild
+    from paper_2001_01570_gb300 import workloads as wl
+    libbuild.build()
+    if args.workload == "acoustic1d":
+        count = args.grids if args.grids_set else 2048
+        params = wl.batched_acoustic_1d(seed=618, count=count)
+        ics = _parallel_ics(_acoustic_ic, params)
+        rec = measure_batched(args, local, ics, args.steps)
+        rec["workload"] = f"acoustic1d: {count} 1D acoustic-wave grids, N log-uniform in [12, 48], seed 618; eps_tau = 0"
+    else:
+        rec = batched_record(args, local)
     if rank == 0:
-        print(json.dumps({
-            "metric": "FP64 cell-updates/s, served continuous batching vs one request after another; p50/p99 latency",
-            "value": stats["cell_updates_per_s"], "unit": UNIT, "n_gpus": world, "steps": None, "warmup": 0,
-            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": "served", "requests": len(reqs), "scale": sc, "arrival_scale": args.arrival_scale,
-                       "stream": "seed 2001, Poisson 50 req/s, N log-uniform 128..2048, steps 100..2000, "
-                                 "kinds pulse/vortex/shock-vortex, Mach 1.05..1.5; N and steps divided by scale",
-                       "max_active": args.max_active, "steps_per_round": args.steps_per_round,
-                       "tile_shape": args.tile or "autotuned",
-                       "cell_updates": work},
-            "served": stats, "plain": {"value": work / plain_s, "wall_s": plain_s},
-            "served_vs_plain": stats["cell_updates_per_s"] / (work / plain_s), "clocks": clk.summary()}), flush=True)
+        line = {"metric": "FP64 cell-updates/s, batched persistent launch vs one grid per launch",
+                "value": rec["value"], "unit": UNIT, "n_gpus": world, "steps": rec["steps"], "warmup": args.warmup,
+                "ms_per_step": rec["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": rec["workload"]}, "batched": rec,
+                "gpu_launches": rec["gpu_launches"], "clocks": rec["clocks"]}
+        print(json.dumps(line), flush=True)
+
+
+def run_served_line(args, world, rank, local):
+    from paper_2001_01570_gb300 import build as libbuild
+    libbuild.build()
+    rec = served_record(args, local)
+    if rank == 0:
+        line = {"metric": "FP64 cell-updates/s, served continuous batching vs one request after another; p50/p99",
+                "value": rec["saturated"]["value"], "unit": UNIT, "n_gpus": world, "steps": None, "warmup": 0,
+                "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic", "config": {"workload": rec["workload"]}, "served": rec,
+                "clocks": rec["saturated"]["clocks"]}
+        print(json.dumps(line), flush=True)
 
 
 def main():
@@ -470,13 +553,14 @@ def main():
     ap.add_argument("--impl", default="cgks", choices=["cgks", "reference"])
     ap.add_argument("--workload", default="vortex2048")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="default run: leave out the batched record")
+    ap.add_argument("--no-served", action="store_true", help="default run: leave out the served record")
     ap.add_argument("--tile", default=None, help="tile shape of the plain path (e.g. 16x7, 24x8)")
     ap.add_argument("--order", type=int, default=8, choices=[8, 6],
                     help="plain sweeps: 8 = the paper's scheme, 6 = its compact 6th-order variant")
     ap.add_argument("--grids", type=int, default=None)
-    ap.add_argument("--requests", type=int, default=200)
-    ap.add_argument("--served-scale", type=float, default=8.0)
-    ap.add_argument("--arrival-scale", type=float, default=1.0)
+    ap.add_argument("--batched-steps", type=int, default=None, help="steps of the batched record (default --steps)")
+    ap.add_argument("--requests", type=int, default=12, help="served record: requests of the stream's prefix")
     ap.add_argument("--max-active", type=int, default=64)
     ap.add_argument("--steps-per-round", type=int, default=8)
     args = ap.parse_args()
@@ -487,11 +571,22 @@ def main():
     if args.impl == "reference":
         run_reference(args, world, rank)
     elif args.workload.startswith("batched") or args.workload == "acoustic1d":
-        run_batched(args, world, rank, local)
+        run_batched_line(args, world, rank, local)
     elif args.workload == "served":
-        run_served(args, world, rank, local)
+        run_served_line(args, world, rank, local)
     else:
-        run_cgks(args, world, rank, local)
+        line = run_cgks(args, world, rank, local)
+        # the batched and served records are single-GPU measurements (under torchrun every rank
+        # would run its own copy): the default run adds them at N = 1
+        default = args.workload == "vortex2048" and args.order == 8 and not args.tile and world == 1
+        batched = None if (args.no_batched or not default) else batched_record(args, local)
+        served = None if (args.no_served or not default) else served_record(args, local)
+        if rank == 0:
+            if batched is not None:
+                line["batched"] = batched
+            if served is not None:
+                line["served"] = served
+            print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

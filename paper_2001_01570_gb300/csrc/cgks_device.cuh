@@ -65,6 +65,15 @@ struct RegK {
     const double* tab;   // shared-memory coefficient table (read through volatile loads)
     double one, nzero;   // 1.0 and -0.0 in registers
     __device__ __forceinline__ double k(int i) const { return ((volatile const double*)tab)[i]; }
+#ifdef CGKS_OPCOUNT_HOST
+    // the host operation count (csrc/opcount): each method is the operation it stands for
+    double add(double x, double y) const { return x + y; }
+    double sub(double x, double y) const { return x - y; }
+    double mul(double x, double y) const { return x * y; }
+    double kfma(int i, double x, double y) const { return fma(k(i), x, y); }
+    double kmul(int i, double x) const { return k(i) * x; }
+    double rcp(double x) const { return cgks_opcount_rcp(x); }
+#else
     __device__ __forceinline__ double add(double x, double y) const { return fma(x, one, y); }
     __device__ __forceinline__ double sub(double x, double y) const { return fma(x, one, -y); }
     __device__ __forceinline__ double mul(double x, double y) const { return fma(x, y, nzero); }
@@ -83,6 +92,7 @@ struct RegK {
         e = fma(-x, y, one);
         return fma(y, e, y);
     }
+#endif
 };
 
 // Layout of the reconstruction coefficient table: one block per order (8, 6),

@@ -181,6 +181,9 @@ __device__ __forceinline__ void tang_weno3_slopes(const RegK& r, double lm, doub
 // table, 2^m added to the exponent field.  Below -700 (e^x < 1e-304) it returns 0.
 __device__ __forceinline__ double exp_neg(const RegK& r, double x)
 {
+#ifdef CGKS_OPCOUNT_HOST
+    return cgks_opcount_exp(x);   // one exponential in the host operation count
+#endif
     if (x < -700.0) return 0.0;
     const double t = r.kfma(FK_X32LN2, x, r.k(FK_SHIFT));
     const double n = r.sub(t, r.k(FK_SHIFT));             // round(32 x / ln 2), exactly
@@ -203,6 +206,9 @@ __device__ __forceinline__ double exp_neg(const RegK& r, double x)
 // t = 27.3 e underflows to 0; a NaN t selects the last piece and stays NaN.
 __device__ __forceinline__ double erfc_scaled(const RegK& r, double t, double e)
 {
+#ifdef CGKS_OPCOUNT_HOST
+    return cgks_opcount_erfc(t);   // one erfc in the host operation count
+#endif
     const int k = (int)r.kmul(FK_4, fmin(t, r.k(FK_ERFC_TMAX)));
     const double* c = cgks_erfcx_coef[k];
     const double z = r.sub(t, r.kfma(FK_QUARTER, (double)k, r.k(FK_EIGHTH)));

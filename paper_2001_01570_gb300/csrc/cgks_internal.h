@@ -48,7 +48,7 @@ struct GridDev {
     double* facey;      // y-faces [16][ny+1][nx] (2D)
 };
 
-#ifdef __CUDACC__
+#if defined(__CUDACC__) || defined(CGKS_OPCOUNT_HOST)
 // CFL bound of one cell, dx/(|U|+c+2 nu/dx) and dy/(|V|+c+2 nu/dy) (Sec. 4; nu =
 // mu/rho), written with explicitly rounded operations so that every kernel that
 // evaluates it (the stage-2 update of a step, the bound of a state that was set

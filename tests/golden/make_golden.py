@@ -12,7 +12,8 @@ seeded sample of cells.
                                                    # (smallest to largest, 65^2..501^2), 100 steps
   python tests/golden/make_golden.py served        # sampled requests of the served stream at their
                                                    # stated N and step count (every kind; Mach 1.07,
-                                                   # 1.48 and 1.50 shock-vortex)
+                                                   # 1.48 and 1.50 shock-vortex), with the oracle's
+                                                   # own rounding floor (y-mirrored run)
   python tests/golden/make_golden.py vortex2048    # isentropic vortex 2048^2 (the bench grid), 2 steps
   python tests/golden/make_golden.py vortex2048o6  # the same grid, compact 6th-order variant, 1 step
 """
@@ -50,15 +51,34 @@ def sample_cells(ny, nx, seed):
     return np.sort(flat)
 
 
-def write_case(name, spec, W, nsteps, seed):
+def mirror_y(W):
+    """The state mirrored in y (rows reversed): the y-momentum, its x-gradient and the y-gradients
+    of the other variables change sign."""
+    W = W[:, ::-1, :].copy()
+    for p in (2, 6, 8, 9, 11):
+        W[p] *= -1.0
+    return W
+
+
+def write_case(name, spec, W, nsteps, seed, floor=False):
+    """The oracle's result after nsteps steps at NSAMPLE seeded cells.  floor=True also stores the
+    oracle's own rounding floor for this run: the oracle on the y-mirrored problem, mirrored back,
+    against the oracle (the same arithmetic on the same values, rounded in another order), per
+    plane relative to the plane's maximum."""
     t0 = time.time()
-    Wn, t, steps, last_dt = O.run(O.make_problem(**spec.as_kwargs()), W, nsteps)
+    P = O.make_problem(**spec.as_kwargs())
+    Wn, t, steps, last_dt = O.run(P, W, nsteps)
     idx = sample_cells(spec.ny, spec.nx, seed)
     planes = Wn.reshape(Wn.shape[0], -1)
+    maxabs = np.abs(planes).max(axis=1)
+    extra = {}
+    if floor:
+        Wm = mirror_y(O.run(P, mirror_y(W), nsteps)[0]).reshape(Wn.shape[0], -1)
+        extra["floor"] = np.abs(Wm - planes).max(axis=1) / np.where(maxabs > 0, maxabs, 1.0)
     np.savez_compressed(os.path.join(HERE, f"oracle_{name}.npz"), idx=idx, values=planes[:, idx],
-                        maxabs=np.abs(planes).max(axis=1), t=t, steps=steps, last_dt=last_dt,
-                        nx=spec.nx, ny=spec.ny)
-    print(f"{name}: {steps} steps to t={t:.6f} in {time.time() - t0:.0f} s", flush=True)
+                        maxabs=maxabs, t=t, steps=steps, last_dt=last_dt, nx=spec.nx, ny=spec.ny, **extra)
+    msg = "" if not floor else "; rounding floor " + " ".join(f"{x:.1e}" for x in extra["floor"][:4])
+    print(f"{name}: {steps} steps to t={t:.6f} in {time.time() - t0:.0f} s{msg}", flush=True)
 
 
 def main(which):
@@ -95,7 +115,11 @@ def main(which):
         for rid in SERVED_SAMPLE:
             r = reqs[rid]
             spec, W = wl.request_problem(r)
-            write_case(f"request{rid:04d}_{r['steps']}", spec, W, r["steps"], seed=20010 + rid)
+            write_case(f"request{rid:04d}_{r['steps']}", spec, W, r["steps"], seed=20010 + rid, floor=True)
+        # the Mach 1.48 request before its vortex reaches the shock (the rounding floor of the
+        # full run is set by that interaction)
+        spec, W = wl.request_problem(reqs[1919])
+        write_case("request1919_150", spec, W, 150, seed=21919, floor=True)
     else:
         raise SystemExit(__doc__)
 

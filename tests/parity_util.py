@@ -108,7 +108,15 @@ MOMENTUM_STRICT_TOL = 1e-8
 RESOLVED_MOMENTUM = 1e-6
 
 
-def check(name, gpu, ora, dx=1.0, dy=1.0, gamma=1.4, tol=TOL, grad_tol=1e-9, maxabs=None, idx=None):
+# Where a run amplifies rounding differences (a strong shock that a vortex crosses: the oracle and
+# the oracle on the mirrored problem, mirrored back, then differ by up to ~1e-9 of the variables'
+# maxima), two correct FP64 evaluations cannot agree to TOL.  Such a case carries that measured
+# floor (per plane, relative to the plane's maximum; tests/golden/make_golden.py), and each bar
+# below becomes the larger of itself and FLOOR_FACTOR times the floor.
+FLOOR_FACTOR = 10.0
+
+
+def check(name, gpu, ora, dx=1.0, dy=1.0, gamma=1.4, tol=TOL, grad_tol=1e-9, maxabs=None, floor=None):
     """Assert parity of `gpu` against `ora` (both full planes, or the planes at sampled cells with
     the full-grid maxima in `maxabs`) and record both error definitions."""
     nplanes = gpu.shape[0]
@@ -120,14 +128,19 @@ def check(name, gpu, ora, dx=1.0, dy=1.0, gamma=1.4, tol=TOL, grad_tol=1e-9, max
     scaled = np.where(scale > 0, diff / np.where(scale > 0, scale, 1.0), diff)
     strict = np.where(m > 0, diff / np.where(m > 0, m, 1.0), diff)
     record(name, strict, scaled, nv, m)
-    assert scaled[:nv].max() <= tol, f"{name}: conserved-variable errors (rounding scale) {scaled[:nv]}"
-    dens_energy = [0, nv - 1]
-    assert strict[dens_energy].max() <= tol, f"{name}: density/energy errors {strict[:nv]}"
+    fl = np.zeros(nplanes) if floor is None else FLOOR_FACTOR * np.asarray(floor, dtype=float)
+    if floor is not None:
+        REPORT[-1]["floor"] = [float(x) for x in np.asarray(floor)[:nv]]
+    fl_scaled = fl * m / np.where(scale > 0, scale, 1.0)
+    bar = np.maximum(tol, fl_scaled[:nv])
+    assert np.all(scaled[:nv] <= bar), f"{name}: conserved-variable errors (rounding scale) {scaled[:nv]}"
+    for k in (0, nv - 1):
+        assert strict[k] <= max(tol, fl[k]), f"{name}: density/energy errors {strict[:nv]}"
     rho_c = np.sqrt(gamma * (gamma - 1.0) * m[0] * m[nv - 1])
     for k in range(1, nv - 1):
         if m[k] >= RESOLVED_MOMENTUM * rho_c:
-            assert strict[k] <= MOMENTUM_STRICT_TOL, f"{name}: momentum errors vs own maximum {strict[:nv]}"
-    assert scaled[nv:].max() <= grad_tol, f"{name}: gradient errors {scaled[nv:]}"
+            assert strict[k] <= max(MOMENTUM_STRICT_TOL, fl[k]), f"{name}: momentum errors vs own maximum {strict[:nv]}"
+    assert np.all(scaled[nv:] <= np.maximum(grad_tol, fl_scaled[nv:])), f"{name}: gradient errors {scaled[nv:]}"
     return scaled, strict
 
 

@@ -4,7 +4,13 @@ Sampled requests of the seeded request stream (seed 2001) at their stated grid s
 -- pulses (one of amplitude 2.4e-5), vortices and shock-vortex interactions at Mach 1.07, 1.48 and
 1.50 -- are submitted to the continuous-batching server mixed with three larger requests of the
 same stream, and each sampled result is compared element by element with the oracle's values
-stored by tests/golden/make_golden.py served (which calls only oracle/), at 1500 seeded cells."""
+stored by tests/golden/make_golden.py served (which calls only oracle/), at 1500 seeded cells.
+
+The bar is 1e-11 relative (tests/parity_util.check), or ten times the oracle's own rounding floor
+for that request where that is larger: the Mach 1.48 request's vortex reaches the shock after ~175
+steps, and from there the oracle against the oracle on the mirrored problem differs by up to
+~5e-10 of the variables' maxima at step 205.  The same request is also compared at 150 steps, before
+that interaction, on the plain path at the 1e-11 bar."""
 import os
 
 import numpy as np
@@ -51,4 +57,24 @@ def test_served_sample_matches_oracle():
         r = reqs[rid]
         check(f"served request {rid} ({r['kind']}, {spec.nx}x{spec.ny}, {r['steps']} steps"
               + (f", Mach {r['mach']:.2f}" if "mach" in r else "") + (f", A={r['A']:.1e}" if "A" in r else "") + ")",
-              planes, g["values"], dx=spec.dx, dy=spec.dy, gamma=spec.gamma, maxabs=g["maxabs"])
+              planes, g["values"], dx=spec.dx, dy=spec.dy, gamma=spec.gamma, maxabs=g["maxabs"],
+              floor=g["floor"] if "floor" in g.files else None)
+
+
+def test_mach_1p48_request_before_the_vortex_reaches_the_shock():
+    """Request 1919 (132 x 66, Mach 1.48) on the plain path for 150 of its 205 steps: 1e-11."""
+    reqs = {r["id"]: r for r in wl.served_requests()}
+    path = os.path.join(GOLDEN, "oracle_request1919_150.npz")
+    if not os.path.exists(path):
+        pytest.skip(f"golden file {path} not generated")
+    g = np.load(path)
+    spec, W = wl.request_problem(reqs[1919])
+    s = cgks.Solver(cgks.problem_from_spec(spec))
+    s.set_state(W)
+    s.step(150)
+    out, t, steps = s.get_state()
+    s.close()
+    assert steps == int(g["steps"]) == 150
+    planes = out.reshape(12, -1)[:, g["idx"]]
+    check("request 1919 (shock-vortex, Mach 1.48, 132x66), 150 steps", planes, g["values"], dx=spec.dx,
+          dy=spec.dy, gamma=spec.gamma, maxabs=g["maxabs"])

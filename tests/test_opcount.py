@@ -1,0 +1,42 @@
+"""The host operation count of the kernels' formulas (paper_2001_01570_gb300/opcount.py), which
+gives the roofline's algorithmic FP64 count in the convention add/sub/mul 1, fma 2, divide,
+square root, reciprocal, exponential, erfc 1 each.  Pinned against hand counts of the update
+formulas (Sec. 2.2, Eq. step-hyper-1; Sec. 3.1, Eq. compact-deriv-1; the CFL bound of Sec. 4) and
+checked for the special functions a smooth inviscid flux evaluation calls."""
+import pytest
+
+from paper_2001_01570_gb300 import opcount, workloads as wl
+
+
+@pytest.fixture(scope="module")
+def vortex64():
+    spec, W = wl.isentropic_vortex(64)
+    return spec, opcount.count_step(spec, W)
+
+
+def test_update_counts_match_the_formulas(vortex64):
+    spec, res = vortex64
+    # stage 1, per variable: W* and R (3 subtractions, 2 multiplications each) and the four
+    # gradient differences (1 subtraction, 1 multiplication each): 20
+    assert res["update1"]["flop_per_cell"] == 4 * 20
+    # stage 2, per variable: W^{n+1} (3 sub, 2 mul) and two gradient increments (sub, mul, add);
+    # CFL bound: 1/rho, U, V, the kinetic energy (2 mul, add, mul), gamma-1, E-KE, p, c (2 mul, sqrt),
+    # 2 nu (2 mul), both directions' signal speed (add, mul, add) and dx / speed
+    assert res["update2"]["flop_per_cell"] == 4 * 12 + 23
+
+
+def test_flux_special_functions_per_segment(vortex64):
+    spec, res = vortex64
+    n = spec.nx
+    segments = 2 * n * n + 2 * n            # every face once (periodic: the last faces too)
+    c = res["flux1"]["counts"]
+    # per Gauss point: the two half-line moment sets (one exp and one erfc each), two 1/sqrt(2 theta),
+    # reciprocals of the three densities and of p_l + p_r; per segment also one reciprocal per
+    # variable for the WENO-Z weights along the face and one for the two slopes: 16
+    # (the collision-time exponential is skipped where dt > 80 tau, as for eps_tau = 0.01)
+    assert c["exp"] == 4 * segments and c["erfc"] == 4 * segments
+    assert c["sqrt"] == 4 * segments
+    assert c["rcp"] == 16 * segments
+    assert c["div"] == 0
+    # the record kernel: one reciprocal per (face row, variable) with WENO-Z
+    assert res["records1"]["counts"]["exp"] == 0 and res["records1"]["counts"]["rcp"] > 0
