@@ -61,6 +61,11 @@ RECORD_FLOP_PER_CELL = {8: 3776.0, 6: 3680.0}
 FLUX_FLOP_PER_CELL = {1: 6224.8, 2: 5832.8}
 UPDATE_FLOP_PER_CELL = {1: 80.0, 2: 121.0}
 FLOP_PER_CELL = {s: RECORD_FLOP_PER_CELL[8] + FLUX_FLOP_PER_CELL[s] + UPDATE_FLOP_PER_CELL[s] for s in (1, 2)}
+# The same per-cell counts taken from the kernels' formulas rather than from an instruction stream:
+# a host build of the kernels' device arithmetic with a counting FP64 type, run over one step of the
+# 2048^2 bench grid (python -m paper_2001_01570_gb300.opcount 2048), counting add/sub/mul 1, fma 2 and
+# every divide, square root, reciprocal, exponential and erfc as 1 however the GPU expands it.
+OPCOUNT_FLOP_PER_CELL = {"records": 3733.73, "flux": {1: 5502.69, 2: 5154.52}, "update": {1: 80.0, 2: 71.0}}
 DEFAULT_TILE = "14x8"     # the library's 2D default
 # DRAM bytes (read + write) per cell of one flux-kernel launch with 14x8 tiles, ncu
 # dram__bytes_{read,write}.sum on the 1024^2 vortex (records and state larger than L2) divided by the
@@ -272,6 +277,18 @@ def run_cgks(args, world, rank, local):
                 "peak_source": "measured FP64 DFMA rate (register operands, FMA = 2): %.2f per SM and cycle x %d SMs "
                                "x %.0f MHz (median SM clock in the timed region), of measured"
                                % (FP64_DFMA_PER_SM_CYCLE, nsm, peak_mhz)}
+    # the same kernels against the operation count of their formulas (exp, erfc, reciprocal,
+    # divide, square root one operation each): the convention of the algorithmic FP64 count
+    oc_flux = OPCOUNT_FLOP_PER_CELL["flux"][1]
+    oc_stage1 = OPCOUNT_FLOP_PER_CELL["records"] + oc_flux + OPCOUNT_FLOP_PER_CELL["update"][1]
+    oc_ach = oc_flux * cells / (flux_ms * 1e-3) / 1e12
+    oc_stage1_ach = oc_stage1 * cells / ((flux_ms + rec_ms + upd_ms) * 1e-3) / 1e12
+    roofline["formula_count"] = {
+        "convention": "add/sub/mul 1, fma 2, div/sqrt/rcp/exp/erfc 1 each (host count of the kernels' formulas, "
+                      "python -m paper_2001_01570_gb300.opcount 2048)",
+        "algorithmic_flop_per_cell": oc_flux, "achieved": oc_ach, "frac": oc_ach / peak,
+        "stage1_algorithmic_flop_per_cell": oc_stage1, "stage1_achieved": oc_stage1_ach,
+        "stage1_frac": oc_stage1_ach / peak}
 
     # ---------------- end to end through the C ABI with host buffers
     host_in = torch.from_numpy(np.ascontiguousarray(W)).pin_memory()

@@ -38,7 +38,6 @@ __global__ void __launch_bounds__(kThreads, kStageCtasPerSm)
 stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tiles, int ntiles,
              const int* __restrict__ dcount)
 {
-    if (dcount) ntiles = *dcount;   // queue length in device memory (a server's patched queue)
     using L = StageLayout<TX, TY, STAGE>;
     constexpr int NF = L::NF;
     extern __shared__ double smem[];
@@ -47,13 +46,19 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
     double* dc = ry + L::n_ry + threadIdx.x;   // [32][kThreads] when L::share
     __shared__ double s_fk[FK_N];       // coefficient table (fixed part, then the tile's grid and dt)
     __shared__ int s_skip;
+    // the queue length (a kernel argument, or in device memory for a server's patched queue) is
+    // kept in shared memory: at 255 registers a loop bound in a register costs spills
     const int tid = threadIdx.x;
+
     for (int i = tid; i < FK_NFIX; i += kThreads) s_fk[i] = kFluxFixed.v[i];
     if (tid < 32) s_fk[FK_EXP2 + tid] = exp2((double)tid * (1.0 / 32.0));
     __syncthreads();
     const RegK r{s_fk, ((volatile const double*)s_fk)[FK_ONE], ((volatile const double*)s_fk)[FK_NZERO]};
 
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    // the queue length: the kernel argument, or the int in device memory behind dcount (a server's
+    // queue, patched between replays), read at each tile -- at 255 registers a bound kept in a
+    // register through the loop costs spills (5 % of the stage-1 kernel's time)
+    for (int tile = blockIdx.x; tile < (dcount ? *(volatile const int*)dcount : ntiles); tile += gridDim.x) {
         __syncthreads();
         const TileRef tr = tiles[tile];
         const GridDev& G = grids[tr.grid];

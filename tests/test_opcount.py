@@ -40,3 +40,40 @@ def test_flux_special_functions_per_segment(vortex64):
     assert c["div"] == 0
     # the record kernel: one reciprocal per (face row, variable) with WENO-Z
     assert res["records1"]["counts"]["exp"] == 0 and res["records1"]["counts"]["rcp"] > 0
+
+
+def test_bench_constants_are_the_count_on_the_bench_grid():
+    """bench.py's per-cell formula counts for the 2048^2 vortex follow from the per-unit counts
+    (record item with and without the WENO-Z pair, face segment, cell) measured on 64^2 and 128^2:
+    the smooth vortex takes no data-dependent branch, so each unit's count is the same on every
+    grid."""
+    import importlib.util
+    import os
+
+    import numpy as np
+    from conftest import ROOT
+
+    spec_b = importlib.util.spec_from_file_location("bench", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec_b)
+    spec_b.loader.exec_module(bench)
+    per = {}
+    for n in (64, 128):
+        spec, W = wl.isentropic_vortex(n)
+        per[n] = opcount.count_step(spec, W)
+
+    def units(n):
+        inner, outer = 2 * (n + 1) * (n + 2), 2 * (n + 1) * 2     # record rows with / without WENO-Z
+        return 4 * inner, 4 * outer, 2 * n * n + 2 * n, n * n      # record items, segments, cells
+
+    # records: two unknown per-item counts from two grids
+    A = np.array([units(n)[:2] for n in (64, 128)], dtype=float)
+    b = np.array([per[n]["records1"]["flop"] for n in (64, 128)], dtype=float)
+    item_in, item_out = np.linalg.solve(A, b)
+    n = 2048
+    ii, io, seg, cells = units(n)
+    assert (item_in * ii + item_out * io) / cells == pytest.approx(bench.OPCOUNT_FLOP_PER_CELL["records"], rel=2e-6)
+    for stage in (1, 2):
+        per_seg = per[128][f"flux{stage}"]["flop"] / units(128)[2]
+        assert per[64][f"flux{stage}"]["flop"] / units(64)[2] == pytest.approx(per_seg, rel=1e-12)
+        assert per_seg * seg / cells == pytest.approx(bench.OPCOUNT_FLOP_PER_CELL["flux"][stage], rel=2e-6)
+        assert per[128][f"update{stage}"]["flop_per_cell"] == bench.OPCOUNT_FLOP_PER_CELL["update"][stage]
