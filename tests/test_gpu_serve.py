@@ -147,3 +147,31 @@ def test_server_and_batch_step_from_another_thread():
         cgks.cgks_serve_stop(srv)
     assert not th.is_alive()
     assert not errors, errors
+
+
+def test_nonphysical_request_fails_alone():
+    """A request whose state turns non-physical (a cell with negative pressure) completes with
+    CGKS_E_NONPHYSICAL and its last valid state, while the requests sharing its rounds finish with
+    the results they have alone."""
+    good = [(wl.isentropic_vortex(36), 6), (wl.acoustic_pulse(44, 1e-4, 4.0, 11.0, 30.0), 5)]
+    spec_b, W_b = wl.acoustic_pulse(40, 1e-3, 4.0, 16.0, 16.0)
+    bad = W_b.copy()
+    bad[3, 5, 7] = 0.1 * bad[3, 5, 7] - 10.0
+    refs = [_alone(spec, W, n) for (spec, W), n in good]
+    srv = cgks.cgks_serve_start(hbm_budget_bytes=1e9, max_active=3, steps_per_round=2)
+    try:
+        ids = [cgks.cgks_serve_submit(srv, cgks.problem_from_spec(good[0][0][0]), good[0][0][1], good[0][1]),
+               cgks.cgks_serve_submit(srv, cgks.problem_from_spec(spec_b), bad, 4),
+               cgks.cgks_serve_submit(srv, cgks.problem_from_spec(good[1][0][0]), good[1][0][1], good[1][1])]
+        out_bad = np.empty_like(bad)
+        with pytest.raises(cgks.CgksError) as ei:
+            cgks.cgks_serve_wait(srv, ids[1], 120.0, out_bad)
+        assert ei.value.status == cgks.CGKS_E_NONPHYSICAL
+        for rid, ((spec, W), n), ref in zip((ids[0], ids[2]), good, refs):
+            out = np.empty_like(W)
+            cgks.cgks_serve_wait(srv, rid, 120.0, out)
+            assert np.array_equal(out, ref)
+        stats = cgks.cgks_serve_stats(srv)
+    finally:
+        cgks.cgks_serve_stop(srv)
+    assert stats["completed"] == 2 and stats["failed"] == 1
