@@ -69,3 +69,37 @@ def test_ctypes_structs_match_the_c_layout(tmp_path):
         assert got[(name, "size")] == ctypes.sizeof(py), name
         for fname, _ in py._fields_:
             assert got[(name, fname)] == getattr(py, fname).offset, (name, fname)
+
+
+def test_invalid_problems_are_rejected_before_any_device_work():
+    """Argument checks of cgks_create run on the host: every one returns CGKS_E_INVAL with a
+    message, on a machine with or without a GPU."""
+    from paper_2001_01570_gb300 import cgks
+
+    def bad(**kw):
+        args = dict(dim=2, nx=8, ny=8, x0=0.0, x1=1.0)
+        args.update(kw)
+        p = cgks.make_problem(**args)
+        for k, v in kw.items():
+            if k in ("mu", "recon_vars", "order", "eps_tau", "weno_eps", "gamma", "cfl"):
+                setattr(p, k, v)
+        with __import__("pytest").raises(cgks.CgksError) as ei:
+            cgks.cgks_create(p)
+        assert ei.value.status == cgks.CGKS_E_INVAL
+        assert lib.cgks_last_error()
+
+    lib = cgks.load()
+    lib.cgks_last_error.restype = ctypes.c_char_p
+    bad(nx=0)
+    bad(ny=0)
+    bad(dim=3)
+    bad(x1=0.0)
+    bad(gamma=1.0)
+    bad(cfl=0.0)
+    bad(weno_eps=0.0)
+    bad(mu=-1.0)
+    bad(recon_vars=2)
+    bad(order=7)
+    bad(bc=(0, 1, 0, 0))                      # periodic on one x side only
+    bad(bc=(1, 1, 0, 0), nx=1)                # a reflecting side needs two cells
+    bad(bc=(2, 3, 0, 0), inflow=(0.0, 1.0, 0.0, 1.0))   # inflow density must be positive
