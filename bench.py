@@ -67,10 +67,11 @@ FLOP_PER_CELL = {s: RECORD_FLOP_PER_CELL[8] + FLUX_FLOP_PER_CELL[s] + UPDATE_FLO
 # every divide, square root, reciprocal, exponential and erfc as 1 however the GPU expands it.
 OPCOUNT_FLOP_PER_CELL = {"records": 3733.73, "flux": {1: 5502.69, 2: 5154.52}, "update": {1: 80.0, 2: 71.0}}
 DEFAULT_TILE = "14x8"     # the library's 2D default
-# DRAM bytes (read + write) per cell of one flux-kernel launch with 14x8 tiles, ncu
-# dram__bytes_{read,write}.sum on the 1024^2 vortex (records and state larger than L2) divided by the
-# cells; the 2048^2 bench grid moves the same bytes per cell.
-FLUX_DRAM_BYTES_PER_CELL = {1: 732.16e6 / 1048576, 2: 599.89e6 / 1048576}
+# DRAM bytes (read + write) per cell of one stage-1 flux-kernel launch with 14x8 tiles: ncu
+# dram__bytes_{read,write}.sum of the current kernel on the 1024^2 vortex (records and state larger
+# than L2), 476.55 + 254.91 MB, divided by the cells; the 2048^2 bench grid moves the same bytes per
+# cell (its launch is too large to capture under the profiling size rule).
+FLUX_DRAM_BYTES_PER_CELL = {1: (476.547072e6 + 254.909184e6) / 1048576}
 # algorithmic bytes per cell of the flux kernel: the two face rows' records (2 x 28 doubles) read and
 # the two faces' results written (stage 1: 16 doubles each, stage 2: 8)
 FLUX_ALGO_BYTES_PER_CELL = {1: 448 + 256, 2: 448 + 128}

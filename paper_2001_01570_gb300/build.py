@@ -21,6 +21,10 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libcgks.so")
 DIAG_LIB = os.path.join(BUILD, "libcgks_diag.so")
+# the same library compiled with CGKS_CHECK_BOUNDS: every kernel index checked against its buffer
+# (a violation is recorded in the grid's status and the access skipped); for tests only
+CHECK_BUILD = os.path.join(BUILD, "check")
+CHECK_LIB = os.path.join(CHECK_BUILD, "libcgks.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr"]
@@ -54,15 +58,23 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    if not force and up_to_date():
+def build_check() -> str:
+    """The bounds-checked build of libcgks (CHECK_LIB)."""
+    if os.path.exists(CHECK_LIB) and all(os.path.getmtime(d) <= os.path.getmtime(CHECK_LIB) for d in _deps()):
+        return CHECK_LIB
+    return build(force=True, check_bounds=True)
+
+
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, check_bounds: bool = False) -> str:
+    if not force and not check_bounds and up_to_date():
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
+    out_dir = CHECK_BUILD if check_bounds else BUILD
+    os.makedirs(out_dir, exist_ok=True)
     nvcc = _nvcc()
-    srcs = _sources() + _diag_sources()
-    objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in srcs]
-    ndiag = len(_diag_sources())
-    extra = ["-Xptxas", "-v"] if ptxas_info else []
+    srcs = _sources() + ([] if check_bounds else _diag_sources())
+    objs = [os.path.join(out_dir, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    ndiag = 0 if check_bounds else len(_diag_sources())
+    extra = (["-Xptxas", "-v"] if ptxas_info else []) + (["-DCGKS_CHECK_BOUNDS"] if check_bounds else [])
 
     def compile_one(pair):
         src, obj = pair
@@ -77,14 +89,16 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     if verbose or ptxas_info:
         for l in logs:
             sys.stderr.write(l)
-    for lib, parts in ((LIB, objs[:len(objs) - ndiag]), (DIAG_LIB, objs[len(objs) - ndiag:])):
+    targets = [(CHECK_LIB, objs)] if check_bounds else [(LIB, objs[:len(objs) - ndiag]),
+                                                         (DIAG_LIB, objs[len(objs) - ndiag:])]
+    for lib, parts in targets:
         tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *parts]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
         os.replace(tmp, lib)
-    return LIB
+    return CHECK_LIB if check_bounds else LIB
 
 
 if __name__ == "__main__":

@@ -63,11 +63,12 @@ def library_path() -> str:
 
 
 def load():
-    """Load libcgks.so (built by paper_2001_01570_gb300.build / __graft_entry__.build)."""
+    """Load libcgks.so (built by paper_2001_01570_gb300.build / __graft_entry__.build).
+    $CGKS_LIBRARY names another build of the same library (the bounds-checked one of the tests)."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
+    path = os.environ.get("CGKS_LIBRARY") or _build.LIB
     if not os.path.exists(path):
         raise RuntimeError(f"libcgks is not built ({path} missing): run __graft_entry__.build()")
     L = ctypes.CDLL(path)

@@ -329,6 +329,7 @@ cgks_status cgks_get_state(cgks_solver* s, double* planes, int on_device, double
         }
         CK(cudaStreamSynchronize(s->stream));
     }
+    if (c.status & kStatusBounds) return fail(CGKS_E_CUDA, "a kernel index left its buffer (bounds-checked build)");
     if (c.status & CGKS_E_NONPHYSICAL) return fail(CGKS_E_NONPHYSICAL, "non-physical state met; last valid state kept");
     return CGKS_OK;
 }
@@ -377,6 +378,7 @@ cgks_status cgks_step(cgks_solver* s, int nsteps, double t_end, double* t_out)
     cgks_status st = read_ctrl(s, &c);
     if (st != CGKS_OK) return st;
     if (t_out) *t_out = c.t;
+    if (c.status & kStatusBounds) return fail(CGKS_E_CUDA, "a kernel index left its buffer (bounds-checked build)");
     if (c.status & CGKS_E_NONPHYSICAL) return fail(CGKS_E_NONPHYSICAL, "non-physical state met; last valid state kept");
     return CGKS_OK;
 }
@@ -428,6 +430,7 @@ cgks_status cgks_step_profiled(cgks_solver* s, int nsteps, double stage_ms[8])
     Ctrl c;
     cgks_status st = read_ctrl(s, &c);
     if (st != CGKS_OK) return st;
+    if (c.status & kStatusBounds) return fail(CGKS_E_CUDA, "a kernel index left its buffer (bounds-checked build)");
     if (c.status & CGKS_E_NONPHYSICAL) return fail(CGKS_E_NONPHYSICAL, "non-physical state met; last valid state kept");
     return CGKS_OK;
 }

@@ -30,6 +30,11 @@ struct Ctrl {
     long long steps_target;           // < 0: unlimited
 };
 
+// Ctrl.status bit raised by a build with CGKS_CHECK_BOUNDS when a kernel index
+// falls outside its buffer (the access is skipped); the host reports it as a
+// CUDA error.  Other builds never set it.
+constexpr int kStatusBounds = 1 << 8;
+
 // Per-grid descriptor (read-only for kernels).
 struct GridDev {
     double* buf[2];     // current state / next state ping-pong, 12 planes each
@@ -49,6 +54,19 @@ struct GridDev {
 };
 
 #if defined(__CUDACC__) || defined(CGKS_OPCOUNT_HOST)
+// Bounds check of the CGKS_CHECK_BOUNDS build: true if ok; otherwise the grid's
+// status records it.  In other builds it is true and the condition is not evaluated.
+#if defined(CGKS_CHECK_BOUNDS) && defined(__CUDACC__)
+__device__ __forceinline__ bool in_bounds(bool ok, Ctrl* c)
+{
+    if (!ok) atomicOr(&c->status, kStatusBounds);
+    return ok;
+}
+#define CGKS_IN_BOUNDS(cond, ctrl) ::cgks::in_bounds((cond), (ctrl))
+#else
+#define CGKS_IN_BOUNDS(cond, ctrl) true
+#endif
+
 // CFL bound of one cell, dx/(|U|+c+2 nu/dx) and dy/(|V|+c+2 nu/dy) (Sec. 4; nu =
 // mu/rho), written with explicitly rounded operations so that every kernel that
 // evaluates it (the stage-2 update of a step, the bound of a state that was set

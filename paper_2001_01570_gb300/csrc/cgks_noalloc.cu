@@ -216,6 +216,8 @@ cgks_status cgks_step_noalloc(const cgks_problem* prob, double* planes, int nste
         NCK(cudaStreamSynchronize(stream));
     }
     *t_inout = c.t;
+    if (c.status & kStatusBounds)
+        return nfail(CGKS_E_CUDA, "a kernel index left its buffer (bounds-checked build)");
     if (c.status & CGKS_E_NONPHYSICAL)
         return nfail(CGKS_E_NONPHYSICAL, "non-physical state met; the planes hold the last valid state");
     return CGKS_OK;

@@ -18,6 +18,7 @@ __device__ __forceinline__ double cell_value(const GridDev& G, const double* __r
     int kx, ky;
     const int si = map_axis(i, G.nx, G.bc[0], G.bc[1], kx);
     const int sj = map_axis(j, G.ny, G.bc[2], G.bc[3], ky);
+    if (!CGKS_IN_BOUNDS(si >= 0 && si < G.nx && sj >= 0 && sj < G.ny && p >= 0 && p < 12, G.ctrl)) return 0.0;
     double v = __ldg(src + (size_t)p * PL + (size_t)sj * G.nx + si);
     if (kx == 1) { if (p == 1 || p == 4 || p == 6 || p == 7 || p == 9) v = -v; }
     else if (kx == 2) v = p < 4 ? G.inflow[i < 0 ? 0 : 1][p] : 0.0;
@@ -129,6 +130,7 @@ __device__ __forceinline__ void cons_row(const RegK& r, const GridDev& G, const 
                                          int row, int k)
 {
     const RowRef q = row_ref(G, row);
+    if (!CGKS_IN_BOUNDS(q.idx < q.stride, G.ctrl)) return;
     const int pv = q.xo ? k : ((k == 1) ? 2 : (k == 2) ? 1 : k);   // face frame: normal momentum first
     double Q[4], S[4];
     const int i3 = q.i0 + 3 * q.di, j3 = q.j0 + 3 * q.dj;
@@ -169,6 +171,7 @@ __device__ __forceinline__ void char_row(const RegK& r, const GridDev& G, const 
                                          int row)
 {
     const RowRef q = row_ref(G, row);
+    if (!CGKS_IN_BOUNDS(q.idx < q.stride, G.ctrl)) return;
     double Qa[4][4], Sa[4][4], Wref[4];
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk) {

@@ -246,6 +246,7 @@ void download_loop(cgks_server* S)
         int st = CGKS_OK;
         if (r->forced_status != CGKS_OK) st = r->forced_status;
         else if (e != cudaSuccess) st = CGKS_E_CUDA;
+        else if (c.status & kStatusBounds) st = CGKS_E_CUDA;
         else if (c.status & CGKS_E_NONPHYSICAL) st = CGKS_E_NONPHYSICAL;
         else if (c.steps < r->nsteps) st = CGKS_E_CUDA;
         finish(S, r, st, t);

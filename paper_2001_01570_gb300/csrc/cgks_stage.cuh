@@ -83,12 +83,18 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
             // group g of one orientation: plane p of the group is global plane p0 + p, its
             // local row q is record row base + q (records carry two ghost rows first)
             auto stage = [&](unsigned sbase, int sofs, int np, int plane, int F, int p0, const double* g, size_t gs,
-                             int gfaces, int row0, int face0, int nface_max, int row_max, bool on) {
+                             int gfaces, int row0, int face0, int nface_max, int row_max, bool on, int nsmem) {
                 const int n = np * plane;
                 for (int idx = tid; idx < n; idx += kThreads) {
                     const int p = idx / plane, rem = idx - p * plane;
                     const int q = rem / F, fc = rem - q * F;
-                    const bool valid = on && (face0 + fc <= nface_max) && (row0 + q <= row_max);
+                    bool valid = on && (face0 + fc <= nface_max) && (row0 + q <= row_max);
+                    if (!CGKS_IN_BOUNDS(sofs + idx < nsmem, G.ctrl)) continue;
+                    if (valid)
+                        valid = CGKS_IN_BOUNDS(row0 + q >= 0 && face0 + fc >= 0 &&
+                                                   (size_t)(p0 + p) * gs + (size_t)(row0 + q) * gfaces + face0 + fc <
+                                                       28 * gs,
+                                               G.ctrl);
                     const double* src = valid ? g + (size_t)(p0 + p) * gs + (size_t)(row0 + q) * gfaces + face0 + fc
                                               : G.recx;
                     asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(sbase + 8u * (unsigned)(sofs + idx)),
@@ -98,14 +104,15 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
             using RX = RecGroups<TY, TX + 1>;
             using RY = RecGroups<TX, TY + 1>;
             // x-faces: record rows y0 + 2 + (own row); group A starts two rows earlier, B one
-            stage(sbx, 0, 8, RX::pa, TX + 1, 0, G.recx, sx, nx + 1, y0, x0, nx, ny + 3, true);
-            stage(sbx, 8 * RX::pa, 16, RX::pb, TX + 1, 4 * RL, G.recx, sx, nx + 1, y0 + 1, x0, nx, ny + 3, true);
+            stage(sbx, 0, 8, RX::pa, TX + 1, 0, G.recx, sx, nx + 1, y0, x0, nx, ny + 3, true, RX::n);
+            stage(sbx, 8 * RX::pa, 16, RX::pb, TX + 1, 4 * RL, G.recx, sx, nx + 1, y0 + 1, x0, nx, ny + 3, true, RX::n);
             stage(sbx, 8 * RX::pa + 16 * RX::pb, 4, RX::pc, TX + 1, 4 * RNN, G.recx, sx, nx + 1, y0 + 2, x0, nx, ny + 3,
-                  true);
-            stage(sby, 0, 8, RY::pa, TY + 1, 0, G.recy, sy, ny + 1, x0, y0, ny, nx + 3, !dim1);
-            stage(sby, 8 * RY::pa, 16, RY::pb, TY + 1, 4 * RL, G.recy, sy, ny + 1, x0 + 1, y0, ny, nx + 3, !dim1);
+                  true, RX::n);
+            stage(sby, 0, 8, RY::pa, TY + 1, 0, G.recy, sy, ny + 1, x0, y0, ny, nx + 3, !dim1, RY::n);
+            stage(sby, 8 * RY::pa, 16, RY::pb, TY + 1, 4 * RL, G.recy, sy, ny + 1, x0 + 1, y0, ny, nx + 3, !dim1,
+                  RY::n);
             stage(sby, 8 * RY::pa + 16 * RY::pb, 4, RY::pc, TY + 1, 4 * RNN, G.recy, sy, ny + 1, x0 + 2, y0, ny, nx + 3,
-                  !dim1);
+                  !dim1, RY::n);
             asm volatile("cp.async.wait_all;" ::: "memory");
         }
         __syncthreads();
@@ -143,6 +150,12 @@ stage_kernel(const GridDev* __restrict__ grids, const TileRef* __restrict__ tile
                 r0 = il * (TY + 1) + gl; rstride = TY + 1;
                 out = G.facey; ostride = nfy; oidx = (size_t)(y0 + gl) * nx + x0 + il;
             }
+            // the segment's record window (rows -2..2 of group A, -1..1 of group B, 0 of group C)
+            // and its output index
+            if (!CGKS_IN_BOUNDS(r0 >= 0 && r0 + 4 * rstride < pa && r0 + 2 * rstride < pb && r0 < pc &&
+                                    oidx < ostride,
+                                G.ctrl))
+                continue;
             const double iht = r.k(xo ? FK_IDY : FK_IDX);
             double acc[NF];
             bad |= !segment_results<STAGE, L::share>(r, rec, pa, pb, pc, r0, rstride, iht, dc, acc);

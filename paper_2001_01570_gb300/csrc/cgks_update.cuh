@@ -23,6 +23,7 @@ __device__ __forceinline__ void update_cell(const GridDev& G, int par, long long
     const size_t off = (size_t)cell;
     const size_t xl = (size_t)j * (nx + 1) + i, xr = xl + 1;
     const size_t yb = (size_t)j * nx + i, yt = yb + nx;
+    if (!CGKS_IN_BOUNDS(cell >= 0 && cell < (long long)PL && xr < nfx && (dim1 || yt < nfy), G.ctrl)) return;
     auto FX = [&](int q, size_t at) { return __ldg(G.facex + q * nfx + at); };
     auto FY = [&](int q, size_t at) { return dim1 ? 0.0 : __ldg(G.facey + q * nfy + at); };
     if (STAGE == 1) {
