@@ -255,6 +255,9 @@ typedef struct {
     int tile_shape;            /* -1: autotune on the first batch; else a fixed shape */
     void* cuda_stream;         /* cudaStream_t of the rounds (NULL: a stream of the server's own);
                                   the copies run on two further streams of the server */
+    const char* log_path;      /* NULL, or a file to which the server appends one JSON line per
+                                  finished request: id, grid, steps, status, and the times (s since
+                                  cgks_serve_start) of arrival, admission, first round and result */
 } cgks_serve_cfg;
 
 typedef struct {

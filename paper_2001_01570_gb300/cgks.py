@@ -39,7 +39,8 @@ class cgks_problem(ctypes.Structure):
 
 class cgks_serve_cfg(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_double), ("max_active", ctypes.c_int),
-                ("steps_per_round", ctypes.c_int), ("tile_shape", ctypes.c_int), ("cuda_stream", ctypes.c_void_p)]
+                ("steps_per_round", ctypes.c_int), ("tile_shape", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
+                ("log_path", ctypes.c_char_p)]
 
 
 class cgks_request(ctypes.Structure):
@@ -250,9 +251,9 @@ def _scheck(st):
         raise CgksError(st, load().cgks_serve_last_error().decode())
 
 
-def cgks_serve_start(hbm_budget_bytes, max_active=64, steps_per_round=8, tile_shape=-1, stream=None):
+def cgks_serve_start(hbm_budget_bytes, max_active=64, steps_per_round=8, tile_shape=-1, stream=None, log_path=None):
     cfg = cgks_serve_cfg(float(hbm_budget_bytes), int(max_active), int(steps_per_round), int(tile_shape),
-                         ctypes.c_void_p(stream or 0))
+                         ctypes.c_void_p(stream or 0), None if log_path is None else str(log_path).encode())
     out = ctypes.c_void_p()
     _scheck(load().cgks_serve_start(ctypes.byref(cfg), ctypes.byref(out)))
     return out

@@ -6,6 +6,7 @@
 #include "../../include/cgks.h"
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -353,9 +354,16 @@ static cgks_status enqueue_steps(cgks_solver* s, int nsteps, long* launches)
     return CGKS_OK;
 }
 
+// NVTX range around a call (visible to profilers that record NVTX; no cost otherwise)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 cgks_status cgks_step(cgks_solver* s, int nsteps, double t_end, double* t_out)
 {
     if (!s || nsteps < 0) return fail(CGKS_E_INVAL, "bad arguments");
+    NvtxRange range("cgks_step");
     g_last_launches = 0;
     long launches = 0;
     CK(launch_set_ctrl(s->d_ctrl, 0.0, t_end > 0.0 ? t_end : 0.0, -1, 0, s->stream));

@@ -12,6 +12,7 @@
 #include "../../include/cgks.h"
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <string.h>
 
 #include <algorithm>
@@ -371,6 +372,8 @@ cgks_status cgks_batch_step(cgks_solver* const* solvers, int n, int nsteps)
         }
     }
     std::lock_guard<std::mutex> lk(g_batch_mu);
+    nvtxRangePushA("cgks_batch_step");
+    struct Pop { ~Pop() { nvtxRangePop(); } } pop;
     std::vector<cgks_solver*> key(solvers, solvers + n);
     auto it = std::find_if(g_plans.begin(), g_plans.end(), [&](const Plan& p) { return p.key == key; });
     BatchEngine* E = nullptr;

@@ -25,6 +25,8 @@
 #include "../../include/cgks.h"
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -68,6 +70,7 @@ struct Request {
     GridDev desc;
     cudaEvent_t ev = nullptr;      // upload finished / last round that touches the grid
     long join_round = -1;          // first round that includes the grid
+    double t_join = 0;             // when the grid joined the rounds
     Ctrl final_ctrl;
     int forced_status = CGKS_OK;   // set when the scheduler stopped before the grid finished
 };
@@ -127,6 +130,8 @@ struct cgks_server {
     int worker_status = CGKS_OK;
     int tile_shape = -1, update_cpt = -1;
     long graph_captures = 0;
+    double t_start = 0.0;                 // cgks_serve_start
+    FILE* log = nullptr;                  // one JSON line per finished request (cfg.log_path)
 };
 
 namespace {
@@ -154,6 +159,17 @@ void finish(cgks_server* S, Request* r, int status, double t)
         S->failed += 1;
     }
     S->t_last_done = t;
+    if (S->log) {
+        const double t0 = S->t_start;
+        fprintf(S->log,
+                "{\"id\": %ld, \"nx\": %d, \"ny\": %d, \"steps\": %d, \"cells\": %lld, \"status\": %d, "
+                "\"arrival_s\": %.6f, \"admit_s\": %.6f, \"first_round_s\": %.6f, \"done_s\": %.6f, "
+                "\"latency_s\": %.6f}\n",
+                r->id, r->prob.nx, r->prob.ny, r->nsteps, r->cells, status, r->t_arrival - t0,
+                r->t_admit > 0 ? r->t_admit - t0 : -1.0, r->t_join > 0 ? r->t_join - t0 : -1.0, t - t0,
+                t - r->t_arrival);
+        fflush(S->log);
+    }
     S->cv_done.notify_all();
 }
 
@@ -169,6 +185,7 @@ void upload_loop(cgks_server* S)
             r = S->up_jobs.front();
             S->up_jobs.pop_front();
         }
+        nvtxRangePushA("serve upload");
         const GridLayout L = grid_layout(r->prob);
         cudaError_t e = cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&r->mem, L.total, S->pool, S->Cu);
@@ -185,6 +202,7 @@ void upload_loop(cgks_server* S)
             // the host copy of the initial state may go once the copy has run
             if (e == cudaSuccess) e = cudaEventSynchronize(r->ev);
         }
+        nvtxRangePop();
         std::lock_guard<std::mutex> lk(S->mu);
         if (e != cudaSuccess) {
             if (r->mem) cudaFreeAsync(r->mem, S->Cu);
@@ -228,6 +246,7 @@ void download_loop(cgks_server* S)
             r = S->down_jobs.front();
             S->down_jobs.pop_front();
         }
+        nvtxRangePushA("serve download");
         const Ctrl& c = r->final_ctrl;
         cudaError_t e = cudaStreamWaitEvent(S->Cd, r->ev, 0);
         r->result.resize((size_t)12 * r->cells);
@@ -237,6 +256,7 @@ void download_loop(cgks_server* S)
         if (e == cudaSuccess) e = cudaStreamSynchronize(S->Cd);
         cudaFreeAsync(r->mem, S->Cd);
         r->mem = nullptr;
+        nvtxRangePop();
         const double t = now_s();
         std::lock_guard<std::mutex> lk(S->mu);
         cudaEventDestroy(r->ev);
@@ -342,6 +362,7 @@ void sched_loop(cgks_server* S)
             std::lock_guard<std::mutex> lk(S->mu);
             r->state = R_ACTIVE;
             r->join_round = round;
+            r->t_join = now_s();
             patch = true;
         }
         if (e != cudaSuccess) break;
@@ -362,6 +383,7 @@ void sched_loop(cgks_server* S)
             if (t_active0 < 0.0) t_active0 = now_s();
             const int buf = (int)(round & 1);
             const int cand = E->next_candidate();
+            nvtxRangePushA("serve round");
             long launches = 0;
             e = E->replay(cand, S->cfg.steps_per_round, ev_r0[buf], ev_r1[buf], &launches);
             if (e == cudaSuccess) e = E->snapshot(d_snap + (size_t)buf * nslots);
@@ -369,6 +391,7 @@ void sched_loop(cgks_server* S)
                 e = cudaMemcpyAsync(h_snap + (size_t)buf * nslots, d_snap + (size_t)buf * nslots,
                                     (size_t)nslots * sizeof(Ctrl), cudaMemcpyDeviceToHost, S->S);
             if (e == cudaSuccess) e = cudaEventRecord(ev_snap[buf], S->S);
+            nvtxRangePop();
             if (e != cudaSuccess) break;
             inflight.push_back(InFlight{round, cand, buf, E->member_cells()});
             round += 1;
@@ -475,6 +498,7 @@ void destroy_server(cgks_server* S)
     if (S->Cd) cudaStreamDestroy(S->Cd);
     if (S->own_S && S->S) cudaStreamDestroy(S->S);
     if (S->pool) cudaMemPoolDestroy(S->pool);
+    if (S->log) fclose(S->log);
     for (auto& kv : S->requests) delete kv.second;
     delete S;
 }
@@ -499,6 +523,15 @@ cgks_status cgks_serve_start(const cgks_serve_cfg* cfg, cgks_server** out)
     // on it (a failure there stops the server: submissions then return its status)
     if (cudaGetDevice(&S->device) != cudaSuccess) S->device = 0;
     S->S = (cudaStream_t)cfg->cuda_stream;
+    S->t_start = now_s();
+    if (cfg->log_path) {
+        S->log = fopen(cfg->log_path, "a");
+        if (!S->log) {
+            destroy_server(S);
+            return sfail(CGKS_E_INVAL, std::string("cannot open the request log ") + cfg->log_path);
+        }
+    }
+    S->cfg.log_path = nullptr;   // the caller's string is not kept
     S->uploader = std::thread(upload_loop, S);
     S->downloader = std::thread(download_loop, S);
     S->sched = std::thread(sched_loop, S);

@@ -175,3 +175,27 @@ def test_nonphysical_request_fails_alone():
     finally:
         cgks.cgks_serve_stop(srv)
     assert stats["completed"] == 2 and stats["failed"] == 1
+
+
+def test_request_log(tmp_path):
+    """With a log path the server appends one JSON line per finished request, with its grid, steps,
+    status and the times of arrival, admission, first round and result (seconds since start)."""
+    import json
+
+    log = tmp_path / "serve.jsonl"
+    cases = [(wl.isentropic_vortex(24), 4), (wl.acoustic_pulse(32, 1e-4, 3.0, 9.0, 20.0), 6),
+             (wl.shock_vortex(nx=30, ny=16, mach=1.2), 3)]
+    srv = cgks.cgks_serve_start(hbm_budget_bytes=1e9, max_active=2, steps_per_round=2, log_path=log)
+    try:
+        ids = [cgks.cgks_serve_submit(srv, cgks.problem_from_spec(spec), W, n) for (spec, W), n in cases]
+        for rid, ((spec, W), n) in zip(ids, cases):
+            cgks.cgks_serve_wait(srv, rid, 120.0, np.empty_like(W))
+    finally:
+        cgks.cgks_serve_stop(srv)
+    lines = [json.loads(l) for l in log.read_text().splitlines()]
+    assert sorted(l["id"] for l in lines) == sorted(ids)
+    for l in lines:
+        (spec, W), n = cases[ids.index(l["id"])]
+        assert (l["nx"], l["ny"], l["steps"], l["status"]) == (spec.nx, spec.ny, n, cgks.CGKS_OK)
+        assert 0.0 <= l["arrival_s"] <= l["admit_s"] <= l["first_round_s"] <= l["done_s"]
+        assert l["latency_s"] == pytest.approx(l["done_s"] - l["arrival_s"], abs=1e-5)
