@@ -14,8 +14,9 @@ JSON line with three measurements:
   served   a prefix of the seeded Poisson request stream (seed 2001, grids 128^2..2048^2,
            100..2000 steps, pulse / vortex / Mach 1.05..1.5 shock-vortex) at the stated grid sizes
            and step counts through the continuous-batching server, saturated (all requests at once)
-           and capacity-matched (arrivals time-scaled to ~70 % of the saturated capacity), against
-           the same requests solved one after another; p50/p99 latency
+           (least remaining work first, and every solve in every round) and capacity-matched
+           (arrivals time-scaled to ~70 % of the saturated capacity), against the same requests
+           solved one after another; p50/p99 latency
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cgks|reference] [--workload NAME]
 
@@ -448,12 +449,13 @@ def batched_record(args, local):
     return rec
 
 
-def _serve_pass(cgks, local, reqs, ics, arrival_scale, args):
+def _serve_pass(cgks, local, reqs, ics, arrival_scale, args, order=None):
     """Submit the requests at their stream arrival times x arrival_scale (0: all at once) and wait
     for every result; the server's statistics."""
+    order = cgks.CGKS_SERVE_LEAST_WORK_FIRST if order is None else order
     srv = cgks.cgks_serve_start(hbm_budget_bytes=120e9, max_active=args.max_active,
                                 steps_per_round=args.steps_per_round,
-                                tile_shape=cgks.TILE_SHAPES.index(args.tile) if args.tile else -1)
+                                tile_shape=cgks.TILE_SHAPES.index(args.tile) if args.tile else -1, order=order)
     ids = []
     t0 = time.perf_counter()
     try:
@@ -474,6 +476,8 @@ def _serve_pass(cgks, local, reqs, ics, arrival_scale, args):
     out = {k: stats[k] for k in keep}
     out["value"] = out.pop("cell_updates_per_s")
     out["tile_shape"] = cgks.TILE_SHAPES[out["tile_shape"]] if out["tile_shape"] >= 0 else None
+    out["order"] = "least remaining work first (4e6 cells per round)" if order == cgks.CGKS_SERVE_LEAST_WORK_FIRST \
+        else "every admitted solve in every round"
     out["clocks"] = clk.summary()
     return out
 
@@ -507,6 +511,7 @@ def served_record(args, local):
     plain = {"value": work / plain_s, "wall_s": plain_s, "steps_s": steps_s, "alloc_copy_s": alloc_copy,
              "steps_only_value": work / steps_s, "clocks": clk_plain.summary()}
     saturated = _serve_pass(cgks, local, reqs, ics, 0.0, args)
+    saturated_all = _serve_pass(cgks, local, reqs, ics, 0.0, args, order=cgks.CGKS_SERVE_ALL_ACTIVE)
     span = reqs[-1]["arrival"] - reqs[0]["arrival"]
     # arrivals stretched so that the offered load is 70 % of the saturated capacity
     scale = saturated["wall_s"] / (0.7 * span) if span > 0 else 1.0
@@ -522,7 +527,8 @@ def served_record(args, local):
             "requests": len(reqs), "kinds": kinds, "cell_updates": work,
             "grids": [[spec.nx, spec.ny, r["steps"]] for r, (spec, _) in zip(reqs, ics)],
             "max_active": args.max_active, "steps_per_round": args.steps_per_round,
-            "plain": plain, "saturated": saturated, "capacity_matched": matched,
+            "plain": plain, "saturated": saturated, "saturated_every_solve_every_round": saturated_all,
+            "capacity_matched": matched,
             "served_vs_plain": saturated["value"] / plain["value"],
             "served_vs_plain_steps_only": saturated["value"] / plain["steps_only_value"]}
 

@@ -258,7 +258,18 @@ typedef struct {
     const char* log_path;      /* NULL, or a file to which the server appends one JSON line per
                                   finished request: id, grid, steps, status, and the times (s since
                                   cgks_serve_start) of arrival, admission, first round and result */
+    int order;                 /* which admitted solves a round computes:
+                                  CGKS_SERVE_ALL_ACTIVE: every one (all advance at the same step rate);
+                                  CGKS_SERVE_LEAST_WORK_FIRST: those with the fewest remaining
+                                  cell-updates, as many as it takes to reach fill_cells cells (at least
+                                  one); the others wait, state untouched, until they are among them.
+                                  The order changes latencies, never a result. */
+    double fill_cells;         /* cells a least-work-first round aims for (enough to fill the GPU:
+                                  4e6 is the 2048^2 grid) */
 } cgks_serve_cfg;
+
+#define CGKS_SERVE_ALL_ACTIVE 0
+#define CGKS_SERVE_LEAST_WORK_FIRST 1
 
 typedef struct {
     cgks_problem prob;         /* dim must be 2 */
@@ -283,7 +294,10 @@ typedef struct {
                                    of the active set capture none) */
 } cgks_serve_stats_t;
 
-/* Start a server (spawns the scheduler thread).  Errors: CGKS_E_INVAL. */
+/* Start a server (spawns its scheduler, upload and download threads).  Errors:
+ * CGKS_E_INVAL (non-positive budget, slots or steps per round, an unknown tile
+ * shape or order, fill_cells <= 0 with CGKS_SERVE_LEAST_WORK_FIRST, a log file
+ * that cannot be opened). */
 cgks_status cgks_serve_start(const cgks_serve_cfg* cfg, cgks_server** out);
 
 /* Queue a request; *req_id receives its id.  The initial planes are copied.

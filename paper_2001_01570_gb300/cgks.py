@@ -40,7 +40,10 @@ class cgks_problem(ctypes.Structure):
 class cgks_serve_cfg(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_double), ("max_active", ctypes.c_int),
                 ("steps_per_round", ctypes.c_int), ("tile_shape", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
-                ("log_path", ctypes.c_char_p)]
+                ("log_path", ctypes.c_char_p), ("order", ctypes.c_int), ("fill_cells", ctypes.c_double)]
+
+
+CGKS_SERVE_ALL_ACTIVE, CGKS_SERVE_LEAST_WORK_FIRST = 0, 1
 
 
 class cgks_request(ctypes.Structure):
@@ -251,9 +254,11 @@ def _scheck(st):
         raise CgksError(st, load().cgks_serve_last_error().decode())
 
 
-def cgks_serve_start(hbm_budget_bytes, max_active=64, steps_per_round=8, tile_shape=-1, stream=None, log_path=None):
+def cgks_serve_start(hbm_budget_bytes, max_active=64, steps_per_round=8, tile_shape=-1, stream=None, log_path=None,
+                     order=CGKS_SERVE_LEAST_WORK_FIRST, fill_cells=4.0e6):
     cfg = cgks_serve_cfg(float(hbm_budget_bytes), int(max_active), int(steps_per_round), int(tile_shape),
-                         ctypes.c_void_p(stream or 0), None if log_path is None else str(log_path).encode())
+                         ctypes.c_void_p(stream or 0), None if log_path is None else str(log_path).encode(),
+                         int(order), float(fill_cells))
     out = ctypes.c_void_p()
     _scheck(load().cgks_serve_start(ctypes.byref(cfg), ctypes.byref(out)))
     return out

@@ -6,7 +6,8 @@
 //   scheduler   admits pending requests in arrival order into free slots while
 //               their device bytes fit the HBM budget; launches rounds of
 //               steps_per_round steps of the batched engine (cgks_batch.cu) over
-//               every active grid; after each round copies all control blocks
+//               the active grids (all of them, or those with the least remaining
+//               work up to fill_cells cells); after each round copies all control blocks
 //               to pinned host memory and, one round later, retires the grids
 //               that reached their step count (or failed).  It keeps two
 //               rounds in flight, so its host work overlaps the GPU's.
@@ -69,8 +70,8 @@ struct Request {
     char* mem = nullptr;
     GridDev desc;
     cudaEvent_t ev = nullptr;      // upload finished / last round that touches the grid
-    long join_round = -1;          // first round that includes the grid
-    double t_join = 0;             // when the grid joined the rounds
+    double t_join = 0;             // when the grid's first round was launched
+    long long steps_seen = 0;      // steps done at the latest snapshot read
     Ctrl final_ctrl;
     int forced_status = CGKS_OK;   // set when the scheduler stopped before the grid finished
 };
@@ -99,6 +100,7 @@ struct InFlight {
     int cand;
     int buf;
     long long cells;
+    std::vector<Request*> members;   // the grids this round computed
 };
 
 }  // namespace
@@ -319,7 +321,7 @@ void sched_loop(cgks_server* S)
     }
     std::deque<InFlight> inflight;
     long round = 0;
-    bool patch = false;
+    std::vector<std::pair<int, long>> last_run;
     double t_active0 = -1.0;   // start of the current stretch with active grids
     while (e == cudaSuccess) {
         std::vector<Request*> joined;
@@ -361,26 +363,45 @@ void sched_loop(cgks_server* S)
             if (e != cudaSuccess) break;
             std::lock_guard<std::mutex> lk(S->mu);
             r->state = R_ACTIVE;
-            r->join_round = round;
-            r->t_join = now_s();
-            patch = true;
         }
         if (e != cudaSuccess) break;
-        std::vector<std::pair<int, GridDev>> members;
+        // the round's grids: every active one, or (least-remaining-work order) the active grids
+        // sorted by remaining cell-updates, as many as fill fill_cells; the others wait with their
+        // state untouched (they are not in the descriptor table while they wait)
+        std::vector<Request*> run;
         {
             std::lock_guard<std::mutex> lk(S->mu);
             for (int k = 0; k < nslots; ++k) {
                 Request* r = S->slots[k];
-                if (r && r->state == R_ACTIVE) members.emplace_back(k, r->desc);
+                if (r && r->state == R_ACTIVE) run.push_back(r);
             }
         }
-        if (patch) {
+        if (S->cfg.order == CGKS_SERVE_LEAST_WORK_FIRST && !run.empty()) {
+            auto rem = [](const Request* r) { return (double)r->cells * (double)(r->nsteps - r->steps_seen); };
+            std::stable_sort(run.begin(), run.end(), [&](const Request* a, const Request* b) { return rem(a) < rem(b); });
+            double cells = 0.0;
+            size_t n = 0;
+            while (n < run.size() && (n == 0 || cells < S->cfg.fill_cells)) cells += (double)run[n++]->cells;
+            run.resize(n);
+            std::sort(run.begin(), run.end(), [](const Request* a, const Request* b) { return a->slot < b->slot; });
+        }
+        // the composition by request id (ids are never reused; a freed request's address may be)
+        std::vector<std::pair<int, long>> key;
+        for (Request* r : run) key.emplace_back(r->slot, r->id);
+        if (key != last_run) {
+            std::vector<std::pair<int, GridDev>> members;
+            for (Request* r : run) members.emplace_back(r->slot, r->desc);
             e = E->set_members(members);
             if (e != cudaSuccess) break;
-            patch = false;
+            last_run = key;
         }
-        if (!members.empty()) {
+        if (!run.empty()) {
             if (t_active0 < 0.0) t_active0 = now_s();
+            {
+                std::lock_guard<std::mutex> lk(S->mu);
+                for (Request* r : run)
+                    if (r->t_join <= 0.0) r->t_join = now_s();
+            }
             const int buf = (int)(round & 1);
             const int cand = E->next_candidate();
             nvtxRangePushA("serve round");
@@ -393,11 +414,11 @@ void sched_loop(cgks_server* S)
             if (e == cudaSuccess) e = cudaEventRecord(ev_snap[buf], S->S);
             nvtxRangePop();
             if (e != cudaSuccess) break;
-            inflight.push_back(InFlight{round, cand, buf, E->member_cells()});
+            inflight.push_back(InFlight{round, cand, buf, E->member_cells(), run});
             round += 1;
         }
         // with two rounds in flight (or nothing more to launch), retire from the older one
-        if (inflight.size() >= 2 || (members.empty() && !inflight.empty())) {
+        if (inflight.size() >= 2 || (run.empty() && !inflight.empty())) {
             const InFlight F = inflight.front();
             inflight.pop_front();
             e = cudaEventSynchronize(ev_snap[F.buf]);
@@ -414,19 +435,20 @@ void sched_loop(cgks_server* S)
                 S->tile_shape = E->candidate(E->chosen()).shape;
                 S->update_cpt = E->candidate(E->chosen()).cpt;
             }
-            for (int k = 0; k < nslots; ++k) {
-                Request* r = S->slots[k];
-                if (!r || r->state != R_ACTIVE || r->join_round > F.round || !snap[k].done) continue;
+            for (Request* r : F.members) {
+                if (r->state != R_ACTIVE) continue;
+                const Ctrl& c = snap[r->slot];
+                r->steps_seen = c.steps;
+                if (!c.done) continue;
                 // finished (step target reached) or failed: no later round computes it; the
                 // download waits for the rounds already enqueued
-                r->final_ctrl = snap[k];
+                r->final_ctrl = c;
                 r->state = R_RETIRING;
                 e = cudaEventRecord(r->ev, S->S);
                 if (e != cudaSuccess) break;
-                S->slots[k] = nullptr;
+                S->slots[r->slot] = nullptr;
                 S->down_jobs.push_back(r);
                 S->cv_down.notify_one();
-                patch = true;
             }
             bool any_active = false;
             for (Request* r : S->slots) any_active |= (r && r->state == R_ACTIVE);
@@ -516,6 +538,10 @@ cgks_status cgks_serve_start(const cgks_serve_cfg* cfg, cgks_server** out)
         return sfail(CGKS_E_INVAL, "budget, max_active and steps_per_round must be positive");
     if (cfg->tile_shape >= TILE_COUNT || cfg->tile_shape == TILE_64x1)
         return sfail(CGKS_E_INVAL, "unknown or 1D tile shape");
+    if (cfg->order != CGKS_SERVE_ALL_ACTIVE && cfg->order != CGKS_SERVE_LEAST_WORK_FIRST)
+        return sfail(CGKS_E_INVAL, "unknown round order");
+    if (cfg->order == CGKS_SERVE_LEAST_WORK_FIRST && !(cfg->fill_cells > 0))
+        return sfail(CGKS_E_INVAL, "fill_cells must be positive");
     cgks_server* S = new cgks_server();
     S->cfg = *cfg;
     S->slots.assign((size_t)cfg->max_active, nullptr);

@@ -10,9 +10,9 @@ seeded sample of cells.
   python tests/golden/make_golden.py pulses        # 8 smallest grids of the 256-grid batch, 100 steps
   python tests/golden/make_golden.py pulses16      # 16 grids of the batch across its size quantiles
                                                    # (smallest to largest, 65^2..501^2), 100 steps
-  python tests/golden/make_golden.py served        # sampled requests of the served stream at their
-                                                   # stated N and step count (every kind; Mach 1.07,
-                                                   # 1.48 and 1.50 shock-vortex), with the oracle's
+  python tests/golden/make_golden.py served        # 20 sampled requests of the served stream at
+                                                   # their stated N and step count (every kind; shock-
+                                                   # vortex from Mach 1.07 to 1.50), with the oracle's
                                                    # own rounding floor (y-mirrored run)
   python tests/golden/make_golden.py vortex2048    # isentropic vortex 2048^2 (the bench grid), 2 steps
   python tests/golden/make_golden.py vortex2048o6  # the same grid, compact 6th-order variant, 1 step
@@ -41,7 +41,8 @@ def pulse_quantile_grids(params, count=16):
 
 # requests of the served stream (seed 2001) that the oracle runs at their stated size and step
 # count: the cheapest of each kind plus weak pulses and the strongest shocks
-SERVED_SAMPLE = (1661, 1283, 1920, 1208, 10, 1356, 1919, 221)
+SERVED_SAMPLE = (1661, 1283, 1920, 1208, 10, 1356, 1919, 221,
+                 1126, 432, 1679, 205, 565, 1250, 669, 646, 1732, 1063, 776, 1014)
 
 
 def sample_cells(ny, nx, seed):
@@ -114,12 +115,15 @@ def main(which):
         reqs = {r["id"]: r for r in wl.served_requests()}
         for rid in SERVED_SAMPLE:
             r = reqs[rid]
+            if os.path.exists(os.path.join(HERE, f"oracle_request{rid:04d}_{r['steps']}.npz")):
+                continue
             spec, W = wl.request_problem(r)
             write_case(f"request{rid:04d}_{r['steps']}", spec, W, r["steps"], seed=20010 + rid, floor=True)
         # the Mach 1.48 request before its vortex reaches the shock (the rounding floor of the
         # full run is set by that interaction)
-        spec, W = wl.request_problem(reqs[1919])
-        write_case("request1919_150", spec, W, 150, seed=21919, floor=True)
+        if not os.path.exists(os.path.join(HERE, "oracle_request1919_150.npz")):
+            spec, W = wl.request_problem(reqs[1919])
+            write_case("request1919_150", spec, W, 150, seed=21919, floor=True)
     else:
         raise SystemExit(__doc__)
 

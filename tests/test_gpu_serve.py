@@ -199,3 +199,33 @@ def test_request_log(tmp_path):
         assert (l["nx"], l["ny"], l["steps"], l["status"]) == (spec.nx, spec.ny, n, cgks.CGKS_OK)
         assert 0.0 <= l["arrival_s"] <= l["admit_s"] <= l["first_round_s"] <= l["done_s"]
         assert l["latency_s"] == pytest.approx(l["done_s"] - l["arrival_s"], abs=1e-5)
+
+
+@pytest.mark.parametrize("order", [cgks.CGKS_SERVE_LEAST_WORK_FIRST, cgks.CGKS_SERVE_ALL_ACTIVE])
+def test_round_order(tmp_path, order):
+    """Least remaining work first with a fill of 500 cells: the small solve runs alone first and
+    the large one starts after it; every solve in every round: both start together.  The results
+    are the solves alone in both orders."""
+    import json
+
+    log = tmp_path / "order.jsonl"
+    small, big = (wl.isentropic_vortex(24), 40), (wl.acoustic_pulse(96, 1e-4, 5.0, 40.0, 50.0), 40)
+    srv = cgks.cgks_serve_start(hbm_budget_bytes=1e9, max_active=4, steps_per_round=4, log_path=log, order=order,
+                                fill_cells=500.0)
+    try:
+        ids = [cgks.cgks_serve_submit(srv, cgks.problem_from_spec(spec), W, n) for (spec, W), n in (big, small)]
+        outs = []
+        for rid, ((spec, W), n) in zip(ids, (big, small)):
+            out = np.empty_like(W)
+            cgks.cgks_serve_wait(srv, rid, 120.0, out)
+            outs.append(out)
+    finally:
+        cgks.cgks_serve_stop(srv)
+    for out, ((spec, W), n) in zip(outs, (big, small)):
+        assert np.array_equal(out, _alone(spec, W, n))
+    rec = {l["id"]: l for l in map(json.loads, log.read_text().splitlines())}
+    b, s = rec[ids[0]], rec[ids[1]]
+    if order == cgks.CGKS_SERVE_LEAST_WORK_FIRST:
+        assert b["first_round_s"] > s["first_round_s"] and s["done_s"] < b["done_s"]
+    else:
+        assert abs(b["first_round_s"] - s["first_round_s"]) < 0.05
