@@ -203,9 +203,9 @@ def test_request_log(tmp_path):
 
 @pytest.mark.parametrize("order", [cgks.CGKS_SERVE_LEAST_WORK_FIRST, cgks.CGKS_SERVE_ALL_ACTIVE])
 def test_round_order(tmp_path, order):
-    """Least remaining work first with a fill of 500 cells: the small solve runs alone first and
-    the large one starts after it; every solve in every round: both start together.  The results
-    are the solves alone in both orders."""
+    """Least remaining work first with a fill of 500 cells: the small solve (submitted first) runs
+    alone, and the large one, admitted meanwhile, starts only after it; every solve in every round:
+    both start together.  The results are the solves alone in both orders."""
     import json
 
     log = tmp_path / "order.jsonl"
@@ -213,7 +213,7 @@ def test_round_order(tmp_path, order):
     srv = cgks.cgks_serve_start(hbm_budget_bytes=1e9, max_active=4, steps_per_round=4, log_path=log, order=order,
                                 fill_cells=500.0)
     try:
-        ids = [cgks.cgks_serve_submit(srv, cgks.problem_from_spec(spec), W, n) for (spec, W), n in (big, small)]
+        ids = [cgks.cgks_serve_submit(srv, cgks.problem_from_spec(spec), W, n) for (spec, W), n in (small, big)][::-1]
         outs = []
         for rid, ((spec, W), n) in zip(ids, (big, small)):
             out = np.empty_like(W)
