@@ -100,7 +100,8 @@ struct InFlight {
     int cand;
     int buf;
     long long cells;
-    std::vector<Request*> members;   // the grids this round computed
+    std::vector<long> members;       // ids of the grids this round computed (a finished request
+                                     // may be freed by its caller before the round is read)
 };
 
 }  // namespace
@@ -414,7 +415,9 @@ void sched_loop(cgks_server* S)
             if (e == cudaSuccess) e = cudaEventRecord(ev_snap[buf], S->S);
             nvtxRangePop();
             if (e != cudaSuccess) break;
-            inflight.push_back(InFlight{round, cand, buf, E->member_cells(), run});
+            std::vector<long> ids;
+            for (Request* r : run) ids.push_back(r->id);
+            inflight.push_back(InFlight{round, cand, buf, E->member_cells(), ids});
             round += 1;
         }
         // with two rounds in flight (or nothing more to launch), retire from the older one
@@ -435,7 +438,10 @@ void sched_loop(cgks_server* S)
                 S->tile_shape = E->candidate(E->chosen()).shape;
                 S->update_cpt = E->candidate(E->chosen()).cpt;
             }
-            for (Request* r : F.members) {
+            for (long id : F.members) {
+                auto it = S->requests.find(id);
+                if (it == S->requests.end()) continue;
+                Request* r = it->second;
                 if (r->state != R_ACTIVE) continue;
                 const Ctrl& c = snap[r->slot];
                 r->steps_seen = c.steps;
