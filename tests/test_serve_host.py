@@ -62,3 +62,13 @@ def test_failed_scheduler_fails_requests_instead_of_hanging():
         with pytest.raises(cgks.CgksError) as ei:
             cgks.cgks_serve_stop(srv)
         assert ei.value.status == cgks.CGKS_E_CUDA
+
+
+def test_serve_config_checks():
+    """An unknown round order, a non-positive fill for least-work-first rounds, a 1D tile shape and
+    a request log that cannot be opened are rejected at start."""
+    for kw in (dict(order=2), dict(order=cgks.CGKS_SERVE_LEAST_WORK_FIRST, fill_cells=0.0),
+               dict(tile_shape=cgks.TILE_SHAPES.index("64x1")), dict(log_path="/nonexistent-dir/serve.log")):
+        with pytest.raises(cgks.CgksError) as ei:
+            cgks.cgks_serve_start(hbm_budget_bytes=1e9, max_active=2, steps_per_round=2, **kw)
+        assert ei.value.status == cgks.CGKS_E_INVAL
