@@ -8,7 +8,7 @@
 // multiply-add 2, and a divide, square root, reciprocal, exponential or erfc
 // 1 each, however the GPU expands them (the kernels' Tang exponential, table
 // erfc and Newton reciprocal count as one operation).  RegK's register forms
-// count as the operation they stand for.  The driver below runs one step of a
+// count as the operation they stand for.  The code below runs one step of a
 // 2D grid the way the kernels do -- every face row's record, every face
 // segment of every 14x8 tile (each face once), every cell's update, both
 // stages -- and reports the tally of each of the six launches.
@@ -202,7 +202,7 @@ extern "C" {
 // include/cgks.h), counted.  out receives 6 x 8 numbers: for the launches
 // records<1>, flux<1>, update<1>, records<2>, flux<2>, update<2> the counts of
 // add/sub, mul, fma, div, sqrt/rsqrt, reciprocal, exp, erfc.  Returns 0, or -1
-// for a problem this driver does not run (1D, characteristic variables) and
+// for a problem this count does not cover (1D, characteristic variables) and
 // -2 if a state met was non-physical.
 int cgks_opcount_step(const cgks_problem* prob, const double* planes, unsigned long long* out)
 {
