@@ -127,8 +127,6 @@ cudaError_t BatchEngine::set_members(const std::vector<std::pair<int, GridDev>>&
     }
     std::vector<TileRef> q[kQ];
     cells_ = 0;
-    has_char_ = false;
-    member_count_ = (int)members.size();
     // the tile shapes whose queues the next replays may need
     std::vector<int> shapes;
     if (chosen_ >= 0) shapes.push_back(cands_[chosen_].shape);
@@ -147,7 +145,6 @@ cudaError_t BatchEngine::set_members(const std::vector<std::pair<int, GridDev>>&
         }
         std::vector<TileRef> r = record_chunks(G.nx, G.ny, G.dim, G.recon_vars, slot);
         q[TILE_COUNT + G.recon_vars].insert(q[TILE_COUNT + G.recon_vars].end(), r.begin(), r.end());
-        has_char_ |= (G.recon_vars != 0);
         std::vector<TileRef> c = cell_chunks(G.nx, G.ny, slot);
         q[TILE_COUNT + 2].insert(q[TILE_COUNT + 2].end(), c.begin(), c.end());
     }

@@ -282,8 +282,6 @@ private:
     int chosen_ = -1, tune_phase_ = 0, trial_next_ = 0;
     long long cells_ = 0;
     int launches_per_step_ = 0;
-    bool has_char_ = false;
-    int member_count_ = 0;
     long captures_ = 0;
 };
 

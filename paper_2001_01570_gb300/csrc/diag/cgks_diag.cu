@@ -97,7 +97,7 @@ __device__ __forceinline__ unsigned long long global_ns()
 //   2 x * a (DMUL)                                 3 fma(x, 0.99999, b), immediate multiplicand
 //   4 x + b written as fma(x, one, b)              5 x * a written as fma(x, a, nzero)
 //   6 a / x + 1 (divide)                           7 -exp(x) - b (CUDA's exp)
-//   8 erfc(x) * a (CUDA's erfc)
+//   8 erfc(x) * a (CUDA's erfc)                    9 rsqrt(x) + b (CUDA's rsqrt)
 // with one = 1.0 and nzero = -0.0 read from shared memory through volatile loads
 // (the register forms of RegK)
 template <int OP>
@@ -126,6 +126,7 @@ __global__ void fp64_kernel(double* out, unsigned long long* clk, double a, doub
             if (OP == 6) x[c] = ar / x[c] + 1.0;
             if (OP == 7) x[c] = -exp(x[c]) - br;
             if (OP == 8) x[c] = erfc(x[c]) * ar;
+            if (OP == 9) x[c] = rsqrt(x[c]) + br;
         }
     }
     double s = 0.0;
@@ -151,7 +152,8 @@ void launch_fp64(int op, int blocks, int threads, double* d, unsigned long long*
     case 5: fp64_kernel<5><<<blocks, threads>>>(d, clk, a, b, iters); break;
     case 6: fp64_kernel<6><<<blocks, threads>>>(d, clk, a, b, iters); break;
     case 7: fp64_kernel<7><<<blocks, threads>>>(d, clk, a, b, iters); break;
-    default: fp64_kernel<8><<<blocks, threads>>>(d, clk, a, b, iters); break;
+    case 8: fp64_kernel<8><<<blocks, threads>>>(d, clk, a, b, iters); break;
+    default: fp64_kernel<9><<<blocks, threads>>>(d, clk, a, b, iters); break;
     }
 }
 
@@ -201,7 +203,7 @@ int cgks_diag_erfc_maxrel(int n, double* maxrel)
 // threads per SM).
 int cgks_diag_fp64_rate(int op, int iters, double out[3])
 {
-    if (op < 0 || op > 8 || iters <= 0 || !out) return (int)cudaErrorInvalidValue;
+    if (op < 0 || op > 9 || iters <= 0 || !out) return (int)cudaErrorInvalidValue;
     int dev = 0, nsm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);

@@ -15,7 +15,7 @@ _lib = None
 
 # operations of cgks_diag_fp64_rate, in its numbering
 FP64_OPS = ("dfma, register operands", "dadd", "dmul", "dfma, immediate multiplicand",
-            "add as fma(x, one, b)", "mul as fma(x, a, nzero)", "divide", "exp", "erfc")
+            "add as fma(x, one, b)", "mul as fma(x, a, nzero)", "divide", "exp", "erfc", "rsqrt")
 
 
 def load():
