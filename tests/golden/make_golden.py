@@ -14,6 +14,10 @@ seeded sample of cells.
                                                    # their stated N and step count (every kind; shock-
                                                    # vortex from Mach 1.07 to 1.50), with the oracle's
                                                    # own rounding floor (y-mirrored run)
+  python tests/golden/make_golden.py batched256 [workers]
+                                                   # every grid of the 256-grid batch, 100 steps, smallest
+                                                   # first, 128 cells each, into one file that is rewritten
+                                                   # after each grid (a rerun skips the grids it holds)
   python tests/golden/make_golden.py vortex2048    # isentropic vortex 2048^2 (the bench grid), 2 steps
   python tests/golden/make_golden.py vortex2048o6  # the same grid, compact 6th-order variant, 1 step
 """
@@ -82,6 +86,45 @@ def write_case(name, spec, W, nsteps, seed, floor=False):
     print(f"{name}: {steps} steps to t={t:.6f} in {time.time() - t0:.0f} s{msg}", flush=True)
 
 
+BATCHED_FILE = os.path.join(HERE, "oracle_batched256_100.npz")
+BATCHED_NSAMPLE = 128
+
+
+def _batched_grid(k):
+    """One grid of the batch on one oracle thread: its sampled cells after 100 steps."""
+    p = wl.batched_pulses()[k]
+    spec, W = wl.acoustic_pulse(p["N"], p["A"], p["b"], p["cx"], p["cy"])
+    Wn, t, steps, _ = O.run(O.make_problem(**spec.as_kwargs()), W, 100, threads=1)
+    rng = np.random.default_rng(25600 + k)
+    idx = np.sort(rng.choice(spec.nx * spec.ny, size=BATCHED_NSAMPLE, replace=False))
+    planes = Wn.reshape(Wn.shape[0], -1)
+    return k, idx, planes[:, idx], np.abs(planes).max(axis=1), t, steps
+
+
+def batched256(workers):
+    import multiprocessing as mp
+    params = wl.batched_pulses()
+    done = {}
+    if os.path.exists(BATCHED_FILE):
+        g = np.load(BATCHED_FILE)
+        for j, k in enumerate(g["grid"]):
+            done[int(k)] = (g["idx"][j], g["values"][j], g["maxabs"][j], float(g["t"][j]), int(g["steps"][j]))
+    todo = [k for k in sorted(range(len(params)), key=lambda k: (params[k]["N"], k)) if k not in done]
+    t0 = time.time()
+    with mp.get_context("spawn").Pool(workers) as pool:
+        for k, idx, values, maxabs, t, steps in pool.imap(_batched_grid, todo):
+            done[k] = (idx, values, maxabs, t, steps)
+            ks = sorted(done)
+            tmp = BATCHED_FILE + ".tmp.npz"
+            np.savez_compressed(tmp, grid=np.array(ks), idx=np.stack([done[j][0] for j in ks]),
+                                values=np.stack([done[j][1] for j in ks]),
+                                maxabs=np.stack([done[j][2] for j in ks]),
+                                t=np.array([done[j][3] for j in ks]), steps=np.array([done[j][4] for j in ks]))
+            os.replace(tmp, BATCHED_FILE)
+            print(f"grid {k} ({params[k]['N']}^2): {steps} steps to t={t:.6f}; {len(done)} of {len(params)} "
+                  f"grids after {time.time() - t0:.0f} s", flush=True)
+
+
 def main(which):
     if which == "vortex512":
         spec, W = wl.isentropic_vortex(512)
@@ -111,6 +154,8 @@ def main(which):
                 continue
             spec, W = wl.acoustic_pulse(p["N"], p["A"], p["b"], p["cx"], p["cy"])
             write_case(f"pulse{k:03d}_100", spec, W, 100, seed=k)
+    elif which == "batched256":
+        batched256(int(sys.argv[2]) if len(sys.argv) > 2 else max(1, (os.cpu_count() or 2) - 1))
     elif which == "served":
         reqs = {r["id"]: r for r in wl.served_requests()}
         for rid in SERVED_SAMPLE:

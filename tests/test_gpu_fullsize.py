@@ -90,13 +90,37 @@ def _pulse_sample(params):
     return sorted(set(smallest) | {order[r] for r in ranks})
 
 
+def _batched_all():
+    """tests/golden/make_golden.py batched256: 128 seeded cells of every grid of the batch that the
+    oracle has run (smallest first), one file."""
+    path = os.path.join(GOLDEN, "oracle_batched256_100.npz")
+    if not os.path.exists(path):
+        return {}
+    g = np.load(path)
+    return {int(k): {"idx": g["idx"][j], "values": g["values"][j], "maxabs": g["maxabs"][j], "t": g["t"][j],
+                     "steps": g["steps"][j]} for j, k in enumerate(g["grid"])}
+
+
+def test_batched_golden_covers_the_batch():
+    """The one-file golden of the batch holds whole size classes: every grid up to its largest N."""
+    params = wl.batched_pulses()
+    held = _batched_all()
+    if not held:
+        pytest.skip("oracle_batched256_100.npz not generated")
+    nmax = max(params[k]["N"] for k in held)
+    assert set(held) >= {k for k, p in enumerate(params) if p["N"] < nmax}
+    assert all(int(g["steps"]) == 100 for g in held.values())
+
+
 def test_batched_256_grids_100_steps():
     """All 256 grids of the batched workload (seed 1570) in one cgks_batch_step call of 100 steps;
-    the sampled grids are compared with the oracle (the smallest eight and sixteen across the size
-    quantiles up to the largest), every grid's step count and time checked."""
+    compared with the oracle: 1500 cells of the smallest eight and of sixteen across the size
+    quantiles up to the largest, 128 cells of every grid of the one-file golden; every grid's
+    step count and time checked."""
     params = wl.batched_pulses()
     order = _pulse_sample(params)
     goldens = {k: _golden(f"pulse{k:03d}_100") for k in order}
+    every = _batched_all()
     with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 4)) as pool:
         ics = pool.map(_pulse_ic, params)
     solvers = []
@@ -112,6 +136,12 @@ def test_batched_256_grids_100_steps():
             assert abs(t - float(goldens[k]["t"])) <= 1e-13 * float(goldens[k]["t"])
             _compare(out, goldens[k], ics[k][0], name=f"batched256 grid {k} ({params[k]['N']}^2, "
                                                       f"A={params[k]['A']:.1e})")
+        for k, g in every.items():
+            out, t, steps = solvers[k].get_state()
+            assert steps == int(g["steps"]) == 100
+            assert abs(t - float(g["t"])) <= 1e-13 * float(g["t"])
+            _compare(out, g, ics[k][0], name=f"batched256 grid {k} ({params[k]['N']}^2, A={params[k]['A']:.1e}, "
+                                             "128 cells)")
         for s in solvers:
             assert s.get_state()[2] == 100
     finally:
