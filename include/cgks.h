@@ -135,6 +135,15 @@ cgks_status cgks_get_state(cgks_solver* s, double* planes, int on_device, double
  * Errors: CGKS_E_NONPHYSICAL (state kept at the last valid step), CGKS_E_CUDA. */
 cgks_status cgks_step(cgks_solver* s, int nsteps, double t_end, double* t_out);
 
+/* cgks_step with both stages of each step in one kernel launch (the temporal
+ * fusion of the two-stage fourth-order step, Sec. 2.2, Eq. step-hyper-1): per
+ * 16 x 8 tile, stage 1 runs on the tile widened by two cells and W* stays in
+ * shared memory.  Same arguments, results (the same bits as cgks_step),
+ * errors and step count; 2D only (CGKS_E_INVAL for 1D).  Every tile recomputes
+ * the stage-1 work of its widened region, so on this FP64-bound path it is
+ * slower than cgks_step. */
+cgks_status cgks_step_fused(cgks_solver* s, int nsteps, double t_end, double* t_out);
+
 /* Advance `n` independent solvers (any sizes and boundary types) by `nsteps`
  * steps each, each with its own dt, through one persistent launch per stage
  * over a flattened tile queue, replayed as a CUDA graph.  All solvers must live

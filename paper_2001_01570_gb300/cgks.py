@@ -83,10 +83,11 @@ def load():
     L.cgks_restore_state.argtypes = [vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_long]
     L.cgks_get_state.argtypes = [vp, vp, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_long)]
     L.cgks_step.argtypes = [vp, ctypes.c_int, ctypes.c_double, dp]
+    L.cgks_step_fused.argtypes = [vp, ctypes.c_int, ctypes.c_double, dp]
     L.cgks_batch_step.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int]
     L.cgks_step_profiled.argtypes = [vp, ctypes.c_int, dp]
     for name in ("cgks_create", "cgks_destroy", "cgks_set_state", "cgks_restore_state", "cgks_get_state", "cgks_step",
-                 "cgks_batch_step", "cgks_step_profiled"):
+                 "cgks_step_fused", "cgks_batch_step", "cgks_step_profiled"):
         getattr(L, name).restype = ctypes.c_int
     L.cgks_set_tile_shape.argtypes = [vp, ctypes.c_int]
     L.cgks_set_tile_shape.restype = ctypes.c_int
@@ -207,6 +208,13 @@ def cgks_get_state(solver, planes=None):
 def cgks_step(solver, nsteps, t_end=0.0):
     t = ctypes.c_double()
     _check(load().cgks_step(solver, int(nsteps), float(t_end), ctypes.byref(t)))
+    return t.value
+
+
+def cgks_step_fused(solver, nsteps, t_end=0.0):
+    """cgks_step with both stages of each step in one kernel launch (2D; the same results)."""
+    t = ctypes.c_double()
+    _check(load().cgks_step_fused(solver, int(nsteps), float(t_end), ctypes.byref(t)))
     return t.value
 
 
@@ -342,8 +350,8 @@ class Solver:
         t, steps = cgks_get_state(self.handle, out)
         return out, t, steps
 
-    def step(self, nsteps, t_end=0.0):
-        return cgks_step(self.handle, nsteps, t_end)
+    def step(self, nsteps, t_end=0.0, fused=False):
+        return (cgks_step_fused if fused else cgks_step)(self.handle, nsteps, t_end)
 
     def close(self):
         if self.handle is not None:

@@ -278,6 +278,7 @@ cgks_status cgks_destroy(cgks_solver* s)
     cudaFree(s->d_ctrl);
     cudaFree(s->d_desc);
     cudaFree(s->d_tiles);
+    cudaFree(s->d_ftiles);
     delete s;
     return CGKS_OK;
 }
@@ -335,14 +336,21 @@ cgks_status cgks_get_state(cgks_solver* s, double* planes, int on_device, double
     return CGKS_OK;
 }
 
-static cgks_status enqueue_steps(cgks_solver* s, int nsteps, long* launches)
+static cgks_status enqueue_steps(cgks_solver* s, int nsteps, long* launches, bool fused)
 {
     const int nblocks = stage_blocks(s->ntiles, s->nsm);
     const int cv = s->prob.recon_vars;
     const int rblocks = record_blocks(s->nrchunks, s->nsm, cv);
     const int ublocks = update_blocks(s->ncchunks, s->nsm);
+    const int fblocks = s->nftiles < s->nsm ? s->nftiles : s->nsm;
     for (int k = 0; k < nsteps; ++k) {
         CK(launch_begin_step(s->d_desc, 1, s->stream));
+        if (fused) {
+            CK(launch_fused_step(s->d_desc, s->d_ftiles, s->nftiles, fblocks, s->stream));
+            CK(launch_end_step(s->d_desc, 1, s->stream));
+            *launches += 3;
+            continue;
+        }
         for (int stage = 1; stage <= 2; ++stage) {
             CK(launch_records(stage, cv, s->d_desc, s->d_rchunks, s->nrchunks, rblocks, s->stream));
             CK(launch_stage(s->shape, stage, s->d_desc, s->d_tiles, s->ntiles, nblocks, s->stream));
@@ -360,10 +368,22 @@ struct NvtxRange {
     ~NvtxRange() { nvtxRangePop(); }
 };
 
-cgks_status cgks_step(cgks_solver* s, int nsteps, double t_end, double* t_out)
+static cgks_status step_impl(cgks_solver* s, int nsteps, double t_end, double* t_out, bool fused)
 {
     if (!s || nsteps < 0) return fail(CGKS_E_INVAL, "bad arguments");
-    NvtxRange range("cgks_step");
+    if (fused && s->prob.dim != 2) return fail(CGKS_E_INVAL, "the fused step is 2D only");
+    if (fused && !s->d_ftiles) {
+        const std::vector<TileRef> tiles = make_tiles(s->nx, s->ny, TILE_16x8, 0);
+        TileRef* d = nullptr;
+        CK(cudaMalloc(&d, tiles.size() * sizeof(TileRef)));
+        cudaError_t e = cudaMemcpyAsync(d, tiles.data(), tiles.size() * sizeof(TileRef), cudaMemcpyHostToDevice,
+                                        s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) { cudaFree(d); return cuda_fail(e, "cgks_step_fused"); }
+        s->d_ftiles = d;
+        s->nftiles = (int)tiles.size();
+    }
+    NvtxRange range(fused ? "cgks_step_fused" : "cgks_step");
     g_last_launches = 0;
     long launches = 0;
     CK(launch_set_ctrl(s->d_ctrl, 0.0, t_end > 0.0 ? t_end : 0.0, -1, 0, s->stream));
@@ -373,7 +393,7 @@ cgks_status cgks_step(cgks_solver* s, int nsteps, double t_end, double* t_out)
     Ctrl c;
     while (done_steps < nsteps) {
         const int k = (nsteps - done_steps) < chunk ? (nsteps - done_steps) : chunk;
-        cgks_status st = enqueue_steps(s, k, &launches);
+        cgks_status st = enqueue_steps(s, k, &launches, fused);
         if (st != CGKS_OK) return st;
         done_steps += k;
         if (t_end > 0.0 && done_steps < nsteps) {
@@ -389,6 +409,16 @@ cgks_status cgks_step(cgks_solver* s, int nsteps, double t_end, double* t_out)
     if (c.status & kStatusBounds) return fail(CGKS_E_CUDA, "a kernel index left its buffer (bounds-checked build)");
     if (c.status & CGKS_E_NONPHYSICAL) return fail(CGKS_E_NONPHYSICAL, "non-physical state met; last valid state kept");
     return CGKS_OK;
+}
+
+cgks_status cgks_step(cgks_solver* s, int nsteps, double t_end, double* t_out)
+{
+    return step_impl(s, nsteps, t_end, t_out, false);
+}
+
+cgks_status cgks_step_fused(cgks_solver* s, int nsteps, double t_end, double* t_out)
+{
+    return step_impl(s, nsteps, t_end, t_out, true);
 }
 
 }  // extern "C"

@@ -326,13 +326,6 @@ struct Plan {
 
 std::mutex g_batch_mu;
 std::list<Plan> g_plans;   // most recently used first
-thread_local std::string g_batch_err;
-
-cgks_status bfail(cgks_status st, const std::string& m)
-{
-    g_batch_err = m;
-    return st;
-}
 
 }  // namespace
 

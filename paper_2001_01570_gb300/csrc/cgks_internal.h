@@ -164,6 +164,9 @@ cudaError_t launch_records(int stage, int char_vars, const GridDev* grids, const
 cudaError_t launch_stage(int shape, int stage, const GridDev* grids, const TileRef* tiles, int ntiles,
                          int nblocks, cudaStream_t st, const int* dcount = nullptr);
 size_t stage_smem_bytes(int shape, int stage);
+// the fused step (cgks_fused.cu): both stages of a step in one launch over 16 x 8
+// tiles (make_tiles with TILE_16x8), one CTA of 256 threads per SM
+cudaError_t launch_fused_step(const GridDev* grids, const TileRef* tiles, int ntiles, int nblocks, cudaStream_t st);
 cudaError_t launch_begin_step(const GridDev* grids, int ngrids, cudaStream_t st);
 cudaError_t launch_end_step(const GridDev* grids, int ngrids, cudaStream_t st);
 cudaError_t launch_cfl(const GridDev* grids, int gidx, const GridDev& host, cudaStream_t st);
@@ -200,6 +203,8 @@ struct cgks_solver {
     cgks::TileRef* d_tiles = nullptr;
     int ntiles = 0;
     int shape = cgks::TILE_16x8;
+    cgks::TileRef* d_ftiles = nullptr;  // 16 x 8 tiles of the fused step (made at its first call)
+    int nftiles = 0;
 };
 
 namespace cgks {

@@ -11,6 +11,19 @@
 
 namespace cgks {
 
+// plane p of ghost cell (i, j) from the value v of its source cell: kx, ky are
+// map_axis's transform kinds along x and y (x first, then y)
+__device__ __forceinline__ double bc_value(const GridDev& G, double v, int i, int j, int kx, int ky, int p)
+{
+    if (kx == 1) { if (p == 1 || p == 4 || p == 6 || p == 7 || p == 9) v = -v; }
+    else if (kx == 2) v = p < 4 ? G.inflow[i < 0 ? 0 : 1][p] : 0.0;
+    else if (kx == 3) { if (p >= 4 && p < 8) v = 0.0; }
+    if (ky == 1) { if (p == 2 || p == 6 || p == 8 || p == 9 || p == 11) v = -v; }
+    else if (ky == 2) v = p < 4 ? G.inflow[j < 0 ? 2 : 3][p] : 0.0;
+    else if (ky == 3) { if (p >= 8) v = 0.0; }
+    return v;
+}
+
 // plane p of cell (i, j) with the boundary conditions applied outside the grid
 __device__ __forceinline__ double cell_value(const GridDev& G, const double* __restrict__ src, size_t PL, int i, int j,
                                              int p)
@@ -19,14 +32,7 @@ __device__ __forceinline__ double cell_value(const GridDev& G, const double* __r
     const int si = map_axis(i, G.nx, G.bc[0], G.bc[1], kx);
     const int sj = map_axis(j, G.ny, G.bc[2], G.bc[3], ky);
     if (!CGKS_IN_BOUNDS(si >= 0 && si < G.nx && sj >= 0 && sj < G.ny && p >= 0 && p < 12, G.ctrl)) return 0.0;
-    double v = __ldg(src + (size_t)p * PL + (size_t)sj * G.nx + si);
-    if (kx == 1) { if (p == 1 || p == 4 || p == 6 || p == 7 || p == 9) v = -v; }
-    else if (kx == 2) v = p < 4 ? G.inflow[i < 0 ? 0 : 1][p] : 0.0;
-    else if (kx == 3) { if (p >= 4 && p < 8) v = 0.0; }
-    if (ky == 1) { if (p == 2 || p == 6 || p == 8 || p == 9 || p == 11) v = -v; }
-    else if (ky == 2) v = p < 4 ? G.inflow[j < 0 ? 2 : 3][p] : 0.0;
-    else if (ky == 3) { if (p >= 8) v = 0.0; }
-    return v;
+    return bc_value(G, __ldg(src + (size_t)p * PL + (size_t)sj * G.nx + si), i, j, kx, ky, p);
 }
 
 // geometry of record r of a grid: orientation, stencil start cell and step,
@@ -124,6 +130,82 @@ constexpr ReconTab make_recon_tab()
 }
 
 
+// The arithmetic of one record in conservative variables: variable k from its
+// four stencil cells (values Q, h times the normal gradients S), written through
+// out(field, k, value); the WENO-Z fields only where `inner` (the rows the
+// non-equilibrium states are needed on).
+template <int ORDER, class Out>
+__device__ __forceinline__ void cons_record(const RegK& r, const double Q[4], const double S[4], double ih,
+                                            double weno_eps, bool inner, int k, Out out)
+{
+    double v, hvx, h2vxx;
+    linear_recon_rk<ORDER>(r, Q[0], Q[1], Q[2], Q[3], S[0], S[1], S[2], S[3], v, hvx, h2vxx);
+    out(RV, k, v);
+    out(RN, k, r.mul(hvx, ih));
+    out(RNN, k, r.mul(r.mul(h2vxx, ih), ih));
+    if (inner) {
+        double vl, sl, vr, sr;
+        weno_pair_rk(r, Q[0], Q[1], Q[2], Q[3], S[0], S[1], S[2], S[3], weno_eps, vl, sl, vr, sr);
+        out(RL, k, vl);
+        out(RR, k, vr);
+        out(RLN, k, r.mul(sl, ih));
+        out(RRN, k, r.mul(sr, ih));
+    }
+}
+
+// The arithmetic of one record in characteristic variables: all four variables
+// from the stencil cells' values Qa[var][cell] and h times normal gradients
+// Sa[var][cell] (face frame), written through out(field, k, value).
+template <int ORDER, class Out>
+__device__ __forceinline__ void char_record(const RegK& r, double gamma, const double Qa[4][4], const double Sa[4][4],
+                                            double ih, double weno_eps, bool inner, Out out)
+{
+    double Wref[4];
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) Wref[kk] = 0.5 * (Qa[kk][1] + Qa[kk][2]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        double v, hvx, h2vxx;
+        linear_recon_rk<ORDER>(r, Qa[k][0], Qa[k][1], Qa[k][2], Qa[k][3], Sa[k][0], Sa[k][1], Sa[k][2], Sa[k][3], v,
+                               hvx, h2vxx);
+        out(RV, k, v);
+        out(RN, k, r.mul(hvx, ih));
+        out(RNN, k, r.mul(r.mul(h2vxx, ih), ih));
+    }
+    if (!inner) return;
+    // project on the left eigenvectors of the normal flux Jacobian at the
+    // mean of the two cells sharing the face, WENO-Z per field, map back
+    CharState cs;
+    char_state(Wref, gamma, cs);
+    double cvl[4], csl[4], cvr[4], csr[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        double l[4], Q[4], S[4];
+        char_left_row(cs, m, l);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            Q[c] = l[0] * Qa[0][c] + l[1] * Qa[1][c] + l[2] * Qa[2][c] + l[3] * Qa[3][c];
+            S[c] = l[0] * Sa[0][c] + l[1] * Sa[1][c] + l[2] * Sa[2][c] + l[3] * Sa[3][c];
+        }
+        weno_pair_rk(r, Q[0], Q[1], Q[2], Q[3], S[0], S[1], S[2], S[3], weno_eps, cvl[m], csl[m], cvr[m], csr[m]);
+        csl[m] = r.mul(csl[m], ih);
+        csr[m] = r.mul(csr[m], ih);
+    }
+    double o4[4];
+    char_to_cons(cs, cvl, o4);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) out(RL, k, o4[k]);
+    char_to_cons(cs, cvr, o4);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) out(RR, k, o4[k]);
+    char_to_cons(cs, csl, o4);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) out(RLN, k, o4[k]);
+    char_to_cons(cs, csr, o4);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) out(RRN, k, o4[k]);
+}
+
 // Conservative variables: variable k of face row `row`.
 template <int ORDER>
 __device__ __forceinline__ void cons_row(const RegK& r, const GridDev& G, const double* __restrict__ src, size_t PL,
@@ -149,20 +231,10 @@ __device__ __forceinline__ void cons_row(const RegK& r, const GridDev& G, const 
             S[c] = r.mul(q.h, cell_value(G, src, PL, i, j, q.gn + pv));
         }
     }
-    double v, hvx, h2vxx;
-    linear_recon_rk<ORDER>(r, Q[0], Q[1], Q[2], Q[3], S[0], S[1], S[2], S[3], v, hvx, h2vxx);
     double* o = q.base + q.idx;
-    o[(RV * 4 + k) * q.stride] = v;
-    o[(RN * 4 + k) * q.stride] = r.mul(hvx, q.ih);
-    o[(RNN * 4 + k) * q.stride] = r.mul(r.mul(h2vxx, q.ih), q.ih);
-    if (q.inner) {
-        double vl, sl, vr, sr;
-        weno_pair_rk(r, Q[0], Q[1], Q[2], Q[3], S[0], S[1], S[2], S[3], G.weno_eps, vl, sl, vr, sr);
-        o[(RL * 4 + k) * q.stride] = vl;
-        o[(RR * 4 + k) * q.stride] = vr;
-        o[(RLN * 4 + k) * q.stride] = r.mul(sl, q.ih);
-        o[(RRN * 4 + k) * q.stride] = r.mul(sr, q.ih);
-    }
+    const size_t st = q.stride;
+    cons_record<ORDER>(r, Q, S, q.ih, G.weno_eps, q.inner, k,
+                       [&](int f, int kk, double x) { o[(f * 4 + kk) * st] = x; });
 }
 
 // Characteristic variables: all four variables of face row `row`.
@@ -172,7 +244,7 @@ __device__ __forceinline__ void char_row(const RegK& r, const GridDev& G, const 
 {
     const RowRef q = row_ref(G, row);
     if (!CGKS_IN_BOUNDS(q.idx < q.stride, G.ctrl)) return;
-    double Qa[4][4], Sa[4][4], Wref[4];
+    double Qa[4][4], Sa[4][4];
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk) {
         const int pk = q.xo ? kk : ((kk == 1) ? 2 : (kk == 2) ? 1 : kk);
@@ -182,50 +254,11 @@ __device__ __forceinline__ void char_row(const RegK& r, const GridDev& G, const 
             Qa[kk][c] = cell_value(G, src, PL, i, j, pk);
             Sa[kk][c] = r.mul(q.h, cell_value(G, src, PL, i, j, q.gn + pk));
         }
-        Wref[kk] = 0.5 * (Qa[kk][1] + Qa[kk][2]);
     }
     double* o = q.base + q.idx;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        double v, hvx, h2vxx;
-        linear_recon_rk<ORDER>(r, Qa[k][0], Qa[k][1], Qa[k][2], Qa[k][3], Sa[k][0], Sa[k][1], Sa[k][2], Sa[k][3], v,
-                               hvx, h2vxx);
-        o[(RV * 4 + k) * q.stride] = v;
-        o[(RN * 4 + k) * q.stride] = r.mul(hvx, q.ih);
-        o[(RNN * 4 + k) * q.stride] = r.mul(r.mul(h2vxx, q.ih), q.ih);
-    }
-    if (!q.inner) return;
-    // project on the left eigenvectors of the normal flux Jacobian at the
-    // mean of the two cells sharing the face, WENO-Z per field, map back
-    CharState cs;
-    char_state(Wref, G.gamma, cs);
-    double cvl[4], csl[4], cvr[4], csr[4];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-        double l[4], Q[4], S[4];
-        char_left_row(cs, m, l);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            Q[c] = l[0] * Qa[0][c] + l[1] * Qa[1][c] + l[2] * Qa[2][c] + l[3] * Qa[3][c];
-            S[c] = l[0] * Sa[0][c] + l[1] * Sa[1][c] + l[2] * Sa[2][c] + l[3] * Sa[3][c];
-        }
-        weno_pair_rk(r, Q[0], Q[1], Q[2], Q[3], S[0], S[1], S[2], S[3], G.weno_eps, cvl[m], csl[m], cvr[m], csr[m]);
-        csl[m] = r.mul(csl[m], q.ih);
-        csr[m] = r.mul(csr[m], q.ih);
-    }
-    double out[4];
-    char_to_cons(cs, cvl, out);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) o[(RL * 4 + k) * q.stride] = out[k];
-    char_to_cons(cs, cvr, out);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) o[(RR * 4 + k) * q.stride] = out[k];
-    char_to_cons(cs, csl, out);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) o[(RLN * 4 + k) * q.stride] = out[k];
-    char_to_cons(cs, csr, out);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) o[(RRN * 4 + k) * q.stride] = out[k];
+    const size_t st = q.stride;
+    char_record<ORDER>(r, G.gamma, Qa, Sa, q.ih, G.weno_eps, q.inner,
+                       [&](int f, int kk, double x) { o[(f * 4 + kk) * st] = x; });
 }
 
 

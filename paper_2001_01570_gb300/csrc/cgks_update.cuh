@@ -8,8 +8,50 @@
 
 namespace cgks {
 
-// the update of one cell (its four faces' results); stage 2 also folds the
-// cell's CFL bound into dtmin and flags a non-physical state in bad
+// The arithmetic of one cell's update from the results of its four faces:
+// FX(q, side) and FY(q, side) give result q of its low (side 0) and high (side
+// 1) x- and y-faces.  Stage 1 reads W from buf[par] at `off` and writes W* and
+// its gradients through ws_out(plane, value) and R through r_out(plane, value);
+// stage 2 reads R from buf[par^1] at `off`, writes W^{n+1} there, folds the
+// cell's CFL bound into dtmin and flags a non-physical state in bad.
+template <int STAGE, class FXs, class FYs, class WSo, class Ro>
+__device__ __forceinline__ void update_cell_core(const GridDev& G, int par, size_t off, FXs FX, FYs FY, WSo ws_out,
+                                                 Ro r_out, double& dtmin, bool& bad)
+{
+    const bool dim1 = (G.dim == 1);
+    const size_t PL = (size_t)G.nx * G.ny;
+    double* __restrict__ rbuf = G.buf[par ^ 1];
+    const double idx_ = G.inv_dx, idy_ = G.inv_dy;
+    if (STAGE == 1) {
+        const double* __restrict__ src = G.buf[par];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const double W = __ldg(src + k * PL + off);
+            ws_out(k, W - (FX(k, 1) - FX(k, 0)) * idx_ - (FY(k, 1) - FY(k, 0)) * idy_);
+            ws_out(4 + k, (FX(8 + k, 1) - FX(8 + k, 0)) * idx_);
+            ws_out(8 + k, (FY(8 + k, 1) - FY(8 + k, 0)) * idy_);
+            r_out(k, W - (FX(4 + k, 1) - FX(4 + k, 0)) * idx_ - (FY(4 + k, 1) - FY(4 + k, 0)) * idy_);
+            r_out(4 + k, (FX(12 + k, 1) - FX(12 + k, 0)) * idx_);
+            r_out(8 + k, (FY(12 + k, 1) - FY(12 + k, 0)) * idy_);
+        }
+    } else {
+        double Wn[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const double R = rbuf[k * PL + off];
+            Wn[k] = R - (FX(k, 1) - FX(k, 0)) * idx_ - (FY(k, 1) - FY(k, 0)) * idy_;
+            rbuf[k * PL + off] = Wn[k];
+            rbuf[(4 + k) * PL + off] += (FX(4 + k, 1) - FX(4 + k, 0)) * idx_;
+            rbuf[(8 + k) * PL + off] += (FY(4 + k, 1) - FY(4 + k, 0)) * idy_;
+        }
+        // CFL bound of the new state (Sec. 4)
+        double d;
+        if (cfl_cell_bound(G, Wn[0], Wn[1], Wn[2], Wn[3], dim1, &d)) dtmin = fmin(dtmin, d);
+        else bad = true;
+    }
+}
+
+// the update of one cell of the grid from the face results in global memory
 template <int STAGE>
 __device__ __forceinline__ void update_cell(const GridDev& G, int par, long long cell, double& dtmin, bool& bad)
 {
@@ -17,42 +59,17 @@ __device__ __forceinline__ void update_cell(const GridDev& G, int par, long long
     const bool dim1 = (G.dim == 1);
     const size_t PL = (size_t)nx * ny;
     const size_t nfx = (size_t)ny * (nx + 1), nfy = (size_t)(ny + 1) * nx;
-    double* __restrict__ rbuf = G.buf[par ^ 1];
-    const double idx_ = G.inv_dx, idy_ = G.inv_dy;
     const int i = (int)(cell % nx), j = (int)(cell / nx);
     const size_t off = (size_t)cell;
     const size_t xl = (size_t)j * (nx + 1) + i, xr = xl + 1;
     const size_t yb = (size_t)j * nx + i, yt = yb + nx;
     if (!CGKS_IN_BOUNDS(cell >= 0 && cell < (long long)PL && xr < nfx && (dim1 || yt < nfy), G.ctrl)) return;
-    auto FX = [&](int q, size_t at) { return __ldg(G.facex + q * nfx + at); };
-    auto FY = [&](int q, size_t at) { return dim1 ? 0.0 : __ldg(G.facey + q * nfy + at); };
-    if (STAGE == 1) {
-        const double* __restrict__ src = G.buf[par];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const double W = __ldg(src + k * PL + off);
-            G.ws[k * PL + off] = W - (FX(k, xr) - FX(k, xl)) * idx_ - (FY(k, yt) - FY(k, yb)) * idy_;
-            G.ws[(4 + k) * PL + off] = (FX(8 + k, xr) - FX(8 + k, xl)) * idx_;
-            G.ws[(8 + k) * PL + off] = (FY(8 + k, yt) - FY(8 + k, yb)) * idy_;
-            rbuf[k * PL + off] = W - (FX(4 + k, xr) - FX(4 + k, xl)) * idx_ - (FY(4 + k, yt) - FY(4 + k, yb)) * idy_;
-            rbuf[(4 + k) * PL + off] = (FX(12 + k, xr) - FX(12 + k, xl)) * idx_;
-            rbuf[(8 + k) * PL + off] = (FY(12 + k, yt) - FY(12 + k, yb)) * idy_;
-        }
-    } else {
-        double Wn[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const double R = rbuf[k * PL + off];
-            Wn[k] = R - (FX(k, xr) - FX(k, xl)) * idx_ - (FY(k, yt) - FY(k, yb)) * idy_;
-            rbuf[k * PL + off] = Wn[k];
-            rbuf[(4 + k) * PL + off] += (FX(4 + k, xr) - FX(4 + k, xl)) * idx_;
-            rbuf[(8 + k) * PL + off] += (FY(4 + k, yt) - FY(4 + k, yb)) * idy_;
-        }
-        // CFL bound of the new state (Sec. 4)
-        double d;
-        if (cfl_cell_bound(G, Wn[0], Wn[1], Wn[2], Wn[3], dim1, &d)) dtmin = fmin(dtmin, d);
-        else bad = true;
-    }
+    double* __restrict__ rbuf = G.buf[par ^ 1];
+    update_cell_core<STAGE>(
+        G, par, off, [&](int q, int side) { return __ldg(G.facex + q * nfx + (side ? xr : xl)); },
+        [&](int q, int side) { return dim1 ? 0.0 : __ldg(G.facey + q * nfy + (side ? yt : yb)); },
+        [&](int p, double v) { G.ws[p * PL + off] = v; }, [&](int p, double v) { rbuf[p * PL + off] = v; }, dtmin,
+        bad);
 }
 
 }  // namespace cgks

@@ -1,5 +1,7 @@
 // cgks_opcount.cpp -- host count of the FP64 operations of one time step of
-// the CUDA kernels' own formulas (libcgks_opcount; not part of the solver).
+// the CUDA kernels' own formulas, and host runs of one step of those formulas
+// in the three-kernel and the fused arrangement (libcgks_opcount; not part of
+// the solver).
 //
 // The device arithmetic of the record, flux and update kernels
 // (cgks_records.cuh, cgks_segment.cuh / cgks_flux.cuh, cgks_update.cuh) is
@@ -99,6 +101,7 @@ inline int max(int a, int b) { return a > b ? a : b; }
 #include "../cgks_records.cuh"
 #include "../cgks_segment.cuh"
 #include "../cgks_update.cuh"
+#include "../cgks_fused.cuh"
 #undef double
 
 namespace {
@@ -194,6 +197,163 @@ void snapshot(unsigned long long* dst)
     for (int k = 0; k < cgks_oc::K_N; ++k) dst[k] = cgks_oc::g_tally[k];
 }
 
+// One step of a 2D grid on the host: the grid's buffers, dt from the CFL bound
+// of the state, the coefficient tables as the kernels build them.
+struct HostStep {
+    Grid g;
+    size_t PL = 0;
+    ReconTab rt;
+    std::vector<Real> fk;
+    RegK rrec{}, rflux{};
+
+    // 0, or -1 for a problem not covered (1D), -2 for a non-physical initial state
+    int setup(const cgks_problem* prob, const double* planes)
+    {
+        if (!prob || prob->dim != 2) return -1;
+        const int nx = prob->nx, ny = prob->ny;
+        PL = (size_t)nx * ny;
+        g.planes.assign(36 * PL, Real(0.0));
+        for (size_t i = 0; i < 12 * PL; ++i) g.planes[i] = Real(planes[i]);
+        g.records.assign(record_doubles(nx, ny, 2), Real(0.0));
+        g.faces.assign(face_doubles(nx, ny, 2), Real(0.0));
+        GridDev& G = g.G;
+        memset((void*)&G, 0, sizeof(G));
+        memset((void*)&g.ctrl, 0, sizeof(g.ctrl));
+        G.buf[0] = g.planes.data();
+        G.buf[1] = g.planes.data() + 12 * PL;
+        G.ws = g.planes.data() + 24 * PL;
+        G.ctrl = &g.ctrl;
+        G.recx = g.records.data();
+        G.recy = g.records.data() + (size_t)28 * (nx + 1) * (ny + 4);
+        G.facex = g.faces.data();
+        G.facey = g.faces.data() + (size_t)16 * (nx + 1) * ny;
+        G.nx = nx;
+        G.ny = ny;
+        G.dim = 2;
+        for (int k = 0; k < 4; ++k) G.bc[k] = prob->bc[k];
+        G.dx = Real((prob->x1 - prob->x0) / nx);
+        G.dy = Real((prob->y1 - prob->y0) / ny);
+        G.inv_dx = Real(1.0 / G.dx.v);
+        G.inv_dy = Real(1.0 / G.dy.v);
+        G.gamma = Real(prob->gamma);
+        G.K = Real((4.0 - 2.0 * prob->gamma) / (prob->gamma - 1.0));
+        G.cfl = Real(prob->cfl);
+        G.eps_tau = Real(prob->eps_tau);
+        G.c_tau = Real(prob->c_tau);
+        G.weno_eps = Real(prob->weno_eps);
+        G.mu = Real(prob->mu);
+        G.recon_vars = prob->recon_vars ? 1 : 0;
+        G.order = prob->order == 6 ? 6 : 8;
+        for (int side = 0; side < 4; ++side) {
+            const double* q = prob->inflow[side];
+            G.inflow[side][0] = Real(q[0]);
+            G.inflow[side][1] = Real(q[0] * q[1]);
+            G.inflow[side][2] = Real(q[0] * q[2]);
+            G.inflow[side][3] = Real(q[3] / (prob->gamma - 1.0) + 0.5 * q[0] * (q[1] * q[1] + q[2] * q[2]));
+        }
+        // dt from the CFL bound of the state (not part of the counted launches)
+        double dmin = INFINITY;
+        for (size_t c = 0; c < PL; ++c) {
+            Real d;
+            if (!cfl_cell_bound(G, G.buf[0][c], G.buf[0][PL + c], G.buf[0][2 * PL + c], G.buf[0][3 * PL + c], false,
+                                &d))
+                return -2;
+            dmin = std::min(dmin, d.v);
+        }
+        const Real dt = Real(prob->cfl * dmin);
+        rt = make_recon_tab();
+        const int ob = G.order == 6 ? 1 : 0;
+        rrec = RegK{rt.v[ob], rt.v[ob][RK_ONE], rt.v[ob][RK_NZERO]};
+        fk.assign(FK_N, Real(0.0));
+        const FluxFixed ff = make_flux_fixed();
+        for (int i = 0; i < FK_NFIX; ++i) fk[i] = ff.v[i];
+        for (int j = 0; j < 32; ++j) fk[FK_EXP2 + j] = Real(std::exp2(j / 32.0));
+        flux_table_tile(fk.data(), G, dt);
+        rflux = RegK{fk.data(), fk[FK_ONE], fk[FK_NZERO]};
+        return 0;
+    }
+
+    // the three-kernel step (records, flux over 14 x 8 tiles, update per stage);
+    // out (may be NULL): the counts of the six launches
+    bool unfused(unsigned long long* out)
+    {
+        GridDev& G = g.G;
+        const int nx = G.nx, ny = G.ny;
+        std::vector<Real> rx, ry, dc(32 * kThreads, Real(0.0));
+        const int nrec = record_rows(nx, ny, 2);
+        bool ok = true;
+        unsigned long long scratch[3 * cgks_oc::K_N];
+        for (int stage = 1; stage <= 2; ++stage) {
+            unsigned long long* o = out ? out + (size_t)(stage - 1) * 3 * cgks_oc::K_N : scratch;
+            const Real* src = stage == 1 ? G.buf[0] : G.ws;
+            // records
+            memset(cgks_oc::g_tally, 0, sizeof(cgks_oc::g_tally));
+            if (G.recon_vars) {
+                for (int item = 0; item < nrec; ++item) {
+                    if (G.order == 6) char_row<6>(rrec, G, src, PL, item);
+                    else char_row<8>(rrec, G, src, PL, item);
+                }
+            } else {
+                for (int item = 0; item < 4 * nrec; ++item) {
+                    const int k = item / nrec;
+                    if (G.order == 6) cons_row<6>(rrec, G, src, PL, item - k * nrec, k);
+                    else cons_row<8>(rrec, G, src, PL, item - k * nrec, k);
+                }
+            }
+            snapshot(o);
+            // face segments, 14 x 8 tiles
+            unsigned long long before[cgks_oc::K_N];
+            memset(cgks_oc::g_tally, 0, sizeof(cgks_oc::g_tally));
+            for (int y0 = 0; y0 < ny; y0 += 8)
+                for (int x0 = 0; x0 < nx; x0 += 14) {
+                    snapshot(before);
+                    stage_tile<14, 8>(G, x0, y0, rx, ry);   // copies, not counted
+                    for (int k = 0; k < cgks_oc::K_N; ++k) cgks_oc::g_tally[k] = before[k];
+                    ok &= stage == 1 ? tile_segments<14, 8, 1>(rflux, G, x0, y0, rx, ry, dc)
+                                     : tile_segments<14, 8, 2>(rflux, G, x0, y0, rx, ry, dc);
+                }
+            snapshot(o + cgks_oc::K_N);
+            // cell updates
+            memset(cgks_oc::g_tally, 0, sizeof(cgks_oc::g_tally));
+            Real dtmin = Real(INFINITY);
+            bool bad = false;
+            for (long long cell = 0; cell < (long long)PL; ++cell) {
+                if (stage == 1) update_cell<1>(G, 0, cell, dtmin, bad);
+                else update_cell<2>(G, 0, cell, dtmin, bad);
+            }
+            snapshot(o + 2 * cgks_oc::K_N);
+            ok &= !bad;
+        }
+        return ok;
+    }
+
+    // the fused step (cgks_fused.cuh): per 16 x 8 tile its six phases, each run by
+    // one caller thread over all of the phase's items
+    bool fused()
+    {
+        GridDev& G = g.G;
+        using L = FusedLayout<kFusedTX, kFusedTY>;
+        std::vector<Real> P(L::nP, Real(0.0)), Q(L::nQ, Real(0.0));
+        const RegK rr = rrec;
+        bool ok = true;
+        Real dtmin = Real(INFINITY);
+        for (int y0 = 0; y0 < G.ny; y0 += kFusedTY)
+            for (int x0 = 0; x0 < G.nx; x0 += kFusedTX) {
+                const FusedTile<kFusedTX, kFusedTY> T{G, P.data(), Q.data(), rflux, rr, x0, y0, 0,
+                                                       G.bc[0] == CGKS_BC_PERIODIC, G.bc[2] == CGKS_BC_PERIODIC};
+                bool bad = false;
+                T.records1(0, 1);
+                bad |= !T.flux1(0, 1);
+                T.update1(0, 1);
+                T.records2(0, 1);
+                bad |= !T.flux2(0, 1);
+                T.update2(0, 1, dtmin, bad);
+                ok &= !bad;
+            }
+        return ok;
+    }
+};
+
 }  // namespace
 
 extern "C" {
@@ -207,104 +367,23 @@ extern "C" {
 int cgks_opcount_step(const cgks_problem* prob, const double* planes, unsigned long long* out)
 {
     if (!prob || prob->dim != 2 || prob->recon_vars != 0) return -1;
-    const int nx = prob->nx, ny = prob->ny;
-    const size_t PL = (size_t)nx * ny;
-    Grid g;
-    g.planes.assign(36 * PL, Real(0.0));
-    for (size_t i = 0; i < 12 * PL; ++i) g.planes[i] = Real(planes[i]);
-    g.records.assign(record_doubles(nx, ny, 2), Real(0.0));
-    g.faces.assign(face_doubles(nx, ny, 2), Real(0.0));
-    GridDev& G = g.G;
-    memset((void*)&G, 0, sizeof(G));
-    G.buf[0] = g.planes.data();
-    G.buf[1] = g.planes.data() + 12 * PL;
-    G.ws = g.planes.data() + 24 * PL;
-    G.ctrl = &g.ctrl;
-    G.recx = g.records.data();
-    G.recy = g.records.data() + (size_t)28 * (nx + 1) * (ny + 4);
-    G.facex = g.faces.data();
-    G.facey = g.faces.data() + (size_t)16 * (nx + 1) * ny;
-    G.nx = nx;
-    G.ny = ny;
-    G.dim = 2;
-    for (int k = 0; k < 4; ++k) G.bc[k] = prob->bc[k];
-    G.dx = Real((prob->x1 - prob->x0) / nx);
-    G.dy = Real((prob->y1 - prob->y0) / ny);
-    G.inv_dx = Real(1.0 / G.dx.v);
-    G.inv_dy = Real(1.0 / G.dy.v);
-    G.gamma = Real(prob->gamma);
-    G.K = Real((4.0 - 2.0 * prob->gamma) / (prob->gamma - 1.0));
-    G.cfl = Real(prob->cfl);
-    G.eps_tau = Real(prob->eps_tau);
-    G.c_tau = Real(prob->c_tau);
-    G.weno_eps = Real(prob->weno_eps);
-    G.mu = Real(prob->mu);
-    G.recon_vars = 0;
-    G.order = prob->order == 6 ? 6 : 8;
-    for (int side = 0; side < 4; ++side) {
-        const double* q = prob->inflow[side];
-        G.inflow[side][0] = Real(q[0]);
-        G.inflow[side][1] = Real(q[0] * q[1]);
-        G.inflow[side][2] = Real(q[0] * q[2]);
-        G.inflow[side][3] = Real(q[3] / (prob->gamma - 1.0) + 0.5 * q[0] * (q[1] * q[1] + q[2] * q[2]));
-    }
-    // dt from the CFL bound of the state (not part of the counted launches)
-    double dmin = INFINITY;
-    for (size_t c = 0; c < PL; ++c) {
-        Real d;
-        if (!cfl_cell_bound(G, G.buf[0][c], G.buf[0][PL + c], G.buf[0][2 * PL + c], G.buf[0][3 * PL + c], false, &d))
-            return -2;
-        dmin = std::min(dmin, d.v);
-    }
-    const Real dt = Real(prob->cfl * dmin);
-    // coefficient tables as the kernels build them
-    const ReconTab rt = make_recon_tab();
-    const int ob = G.order == 6 ? 1 : 0;
-    const RegK rrec{rt.v[ob], rt.v[ob][RK_ONE], rt.v[ob][RK_NZERO]};
-    std::vector<Real> fk(FK_N, Real(0.0));
-    const FluxFixed ff = make_flux_fixed();
-    for (int i = 0; i < FK_NFIX; ++i) fk[i] = ff.v[i];
-    for (int j = 0; j < 32; ++j) fk[FK_EXP2 + j] = Real(std::exp2(j / 32.0));
-    flux_table_tile(fk.data(), G, dt);
-    const RegK rflux{fk.data(), fk[FK_ONE], fk[FK_NZERO]};
-    std::vector<Real> rx, ry, dc(32 * kThreads, Real(0.0));
-    const int nrec = record_rows(nx, ny, 2);
-    bool ok = true;
-    for (int stage = 1; stage <= 2; ++stage) {
-        unsigned long long* o = out + (size_t)(stage - 1) * 3 * cgks_oc::K_N;
-        const Real* src = stage == 1 ? G.buf[0] : G.ws;
-        // records
-        memset(cgks_oc::g_tally, 0, sizeof(cgks_oc::g_tally));
-        for (int item = 0; item < 4 * nrec; ++item) {
-            const int k = item / nrec;
-            if (G.order == 6) cons_row<6>(rrec, G, src, PL, item - k * nrec, k);
-            else cons_row<8>(rrec, G, src, PL, item - k * nrec, k);
-        }
-        snapshot(o);
-        // face segments, 14 x 8 tiles
-        std::vector<Real> dummy;
-        unsigned long long before[cgks_oc::K_N];
-        memset(cgks_oc::g_tally, 0, sizeof(cgks_oc::g_tally));
-        for (int y0 = 0; y0 < ny; y0 += 8)
-            for (int x0 = 0; x0 < nx; x0 += 14) {
-                snapshot(before);
-                stage_tile<14, 8>(G, x0, y0, rx, ry);   // copies, not counted
-                for (int k = 0; k < cgks_oc::K_N; ++k) cgks_oc::g_tally[k] = before[k];
-                ok &= stage == 1 ? tile_segments<14, 8, 1>(rflux, G, x0, y0, rx, ry, dc)
-                                 : tile_segments<14, 8, 2>(rflux, G, x0, y0, rx, ry, dc);
-            }
-        snapshot(o + cgks_oc::K_N);
-        // cell updates
-        memset(cgks_oc::g_tally, 0, sizeof(cgks_oc::g_tally));
-        Real dtmin = Real(INFINITY);
-        bool bad = false;
-        for (long long cell = 0; cell < (long long)PL; ++cell) {
-            if (stage == 1) update_cell<1>(G, 0, cell, dtmin, bad);
-            else update_cell<2>(G, 0, cell, dtmin, bad);
-        }
-        snapshot(o + 2 * cgks_oc::K_N);
-        ok &= !bad;
-    }
+    HostStep h;
+    const int st = h.setup(prob, planes);
+    if (st != 0) return st;
+    return h.unfused(out) ? 0 : -2;
+}
+
+// One step of the kernels' arithmetic on the host, three-kernel (fused = 0) or
+// fused (fused = 1), from `planes` to `out` (12 planes each; dt from the CFL
+// bound of `planes`).  Returns 0, -1 for 1D, -2 if a state met was non-physical.
+int cgks_host_step(const cgks_problem* prob, const double* planes, int fused, double* out)
+{
+    HostStep h;
+    const int st = h.setup(prob, planes);
+    if (st != 0) return st;
+    const bool ok = fused ? h.fused() : h.unfused(nullptr);
+    const Real* res = h.g.G.buf[1];
+    for (size_t i = 0; i < 12 * h.PL; ++i) out[i] = res[i].v;
     return ok ? 0 : -2;
 }
 

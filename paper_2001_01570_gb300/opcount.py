@@ -37,7 +37,8 @@ def build(force=False) -> str:
     os.makedirs(os.path.dirname(LIB), exist_ok=True)
     cuda_inc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
     tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.run(["g++", "-O2", "-std=c++20", "-fPIC", "-shared", "-Wno-unknown-pragmas", "-I", cuda_inc,
+    subprocess.run(["g++", "-O2", "-ffp-contract=off", "-std=c++20", "-fPIC", "-shared", "-Wno-unknown-pragmas",
+                    "-I", cuda_inc,
                     "-o", tmp, SRC], check=True)
     os.replace(tmp, LIB)
     return LIB
@@ -50,6 +51,9 @@ def load():
         L.cgks_opcount_step.argtypes = [ctypes.POINTER(cgks.cgks_problem), ctypes.c_void_p,
                                         ctypes.POINTER(ctypes.c_ulonglong)]
         L.cgks_opcount_step.restype = ctypes.c_int
+        L.cgks_host_step.argtypes = [ctypes.POINTER(cgks.cgks_problem), ctypes.c_void_p, ctypes.c_int,
+                                     ctypes.c_void_p]
+        L.cgks_host_step.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -72,6 +76,18 @@ def count_step(spec, W) -> dict:
         c = {k: int(out[i * len(KINDS) + j]) for j, k in enumerate(KINDS)}
         res[name] = {"counts": c, "flop": flops(c), "flop_per_cell": flops(c) / cells}
     return res
+
+
+def host_step(spec, W, fused: bool) -> np.ndarray:
+    """One step of the kernels' arithmetic on the host (dt from the CFL bound of W): the
+    three-kernel arrangement, or the fused one (cgks_fused.cuh).  2D."""
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    out = np.empty_like(W)
+    rc = load().cgks_host_step(ctypes.byref(cgks.problem_from_spec(spec)), W.ctypes.data, int(bool(fused)),
+                               out.ctypes.data)
+    if rc != 0:
+        raise RuntimeError(f"cgks_host_step returned {rc}")
+    return out
 
 
 def main():
