@@ -292,6 +292,26 @@ def run_cgks(args, world, rank, local):
         "stage1_algorithmic_flop_per_cell": oc_stage1, "stage1_achieved": oc_stage1_ach,
         "stage1_frac": oc_stage1_ach / peak}
 
+    # ---------------- the fused step (both stages of a step in one launch, W* in shared memory)
+    # on the same grid from the same initial state
+    fused = None
+    if spec.dim == 2:
+        fsteps = max(2, min(args.steps, 10))
+        solver.set_state(W)
+        cgks.cgks_step_fused(solver.handle, 2)
+        torch.cuda.synchronize()
+        with ClockSampler(local) as fclk:
+            start.record(stream)
+            cgks.cgks_step_fused(solver.handle, fsteps)
+            stop.record(stream)
+            torch.cuda.synchronize()
+        flaunch = cgks.cgks_last_launch_count()
+        fms = barrier_max(world, start.elapsed_time(stop))
+        fused = {"kernel": "fused_step_kernel<16,8> (one launch per step between the step-control kernels)",
+                 "steps": fsteps, "ms_per_step": fms / fsteps, "value": world * cells * fsteps / (fms * 1e-3),
+                 "vs_three_kernel_step": (ms / args.steps) / (fms / fsteps), "gpu_launches": flaunch,
+                 "clocks": fclk.summary()}
+
     # ---------------- end to end through the C ABI with host buffers
     host_in = torch.from_numpy(np.ascontiguousarray(W)).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
@@ -331,6 +351,7 @@ def run_cgks(args, world, rank, local):
         "gpu_launches": launches,
         "clocks": clocks,
         "cpu_baseline": cpu,
+        "fused_step": fused,
     }
     return line
 

@@ -13,7 +13,10 @@ namespace cgks {
 // 1) x- and y-faces.  Stage 1 reads W from buf[par] at `off` and writes W* and
 // its gradients through ws_out(plane, value) and R through r_out(plane, value);
 // stage 2 reads R from buf[par^1] at `off`, writes W^{n+1} there, folds the
-// cell's CFL bound into dtmin and flags a non-physical state in bad.
+// cell's CFL bound into dtmin and flags a non-physical state in bad.  The
+// operations are written out as explicitly rounded differences and products
+// and explicit FMAs (no contraction left to the compiler), so that each kernel
+// that inlines it -- the update kernel, the fused step -- gets the same bits.
 template <int STAGE, class FXs, class FYs, class WSo, class Ro>
 __device__ __forceinline__ void update_cell_core(const GridDev& G, int par, size_t off, FXs FX, FYs FY, WSo ws_out,
                                                  Ro r_out, double& dtmin, bool& bad)
@@ -22,27 +25,32 @@ __device__ __forceinline__ void update_cell_core(const GridDev& G, int par, size
     const size_t PL = (size_t)G.nx * G.ny;
     double* __restrict__ rbuf = G.buf[par ^ 1];
     const double idx_ = G.inv_dx, idy_ = G.inv_dy;
+    // high - low of face result q along x and y
+    auto dX = [&](int q) { return __dsub_rn(FX(q, 1), FX(q, 0)); };
+    auto dY = [&](int q) { return __dsub_rn(FY(q, 1), FY(q, 0)); };
+    // a - dX/h_x - dY/h_y
+    auto div = [&](double a, int q) { return fma(-dY(q), idy_, fma(-dX(q), idx_, a)); };
     if (STAGE == 1) {
         const double* __restrict__ src = G.buf[par];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const double W = __ldg(src + k * PL + off);
-            ws_out(k, W - (FX(k, 1) - FX(k, 0)) * idx_ - (FY(k, 1) - FY(k, 0)) * idy_);
-            ws_out(4 + k, (FX(8 + k, 1) - FX(8 + k, 0)) * idx_);
-            ws_out(8 + k, (FY(8 + k, 1) - FY(8 + k, 0)) * idy_);
-            r_out(k, W - (FX(4 + k, 1) - FX(4 + k, 0)) * idx_ - (FY(4 + k, 1) - FY(4 + k, 0)) * idy_);
-            r_out(4 + k, (FX(12 + k, 1) - FX(12 + k, 0)) * idx_);
-            r_out(8 + k, (FY(12 + k, 1) - FY(12 + k, 0)) * idy_);
+            ws_out(k, div(W, k));
+            ws_out(4 + k, __dmul_rn(dX(8 + k), idx_));
+            ws_out(8 + k, __dmul_rn(dY(8 + k), idy_));
+            r_out(k, div(W, 4 + k));
+            r_out(4 + k, __dmul_rn(dX(12 + k), idx_));
+            r_out(8 + k, __dmul_rn(dY(12 + k), idy_));
         }
     } else {
         double Wn[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const double R = rbuf[k * PL + off];
-            Wn[k] = R - (FX(k, 1) - FX(k, 0)) * idx_ - (FY(k, 1) - FY(k, 0)) * idy_;
+            Wn[k] = div(R, k);
             rbuf[k * PL + off] = Wn[k];
-            rbuf[(4 + k) * PL + off] += (FX(4 + k, 1) - FX(4 + k, 0)) * idx_;
-            rbuf[(8 + k) * PL + off] += (FY(4 + k, 1) - FY(4 + k, 0)) * idy_;
+            rbuf[(4 + k) * PL + off] = fma(dX(4 + k), idx_, rbuf[(4 + k) * PL + off]);
+            rbuf[(8 + k) * PL + off] = fma(dY(4 + k), idy_, rbuf[(8 + k) * PL + off]);
         }
         // CFL bound of the new state (Sec. 4)
         double d;
