@@ -20,7 +20,7 @@ namespace cgks {
 enum FluxK {
     FK_ONE = 0, FK_NZERO, FK_HALF, FK_MHALF, FK_2, FK_M2, FK_3, FK_4, FK_5, FK_M3, FK_M4, FK_QUARTER, FK_EIGHTH,
     FK_ERFC_TMAX,                          // last table piece of erfcx
-    FK_T13_12, FK_T11_18, FK_DLO, FK_DHI,  // tangential WENO-Z: beta weight, linear weights at the Gauss points
+    FK_T13_3, FK_DLO, FK_DHI,              // tangential WENO-Z: 4 x beta weight, linear weights at the Gauss points
     FK_HG, FK_MHG,                         // +-eta/2 at the Gauss point eta = 1/(2 sqrt 3)
     FK_A1T, FK_A2T, FK_S1T, FK_S2T, FK_M0T,         // quartic: d/deta coefficients
     FK_S1TT, FK_S2TT, FK_M0TT,                      // quartic: d^2/deta^2 coefficients
@@ -32,10 +32,10 @@ enum FluxK {
     FK_EXP2 = FK_NFIX,                               // 2^(j/32), j = 0..31 (computed per CTA)
     FK_NFIX2 = FK_EXP2 + 32,
     // per grid and tile
-    FK_DT = FK_NFIX2, FK_IDT, FK_HDT, FK_MHDT, FK_EPSDT, FK_CTAUDT, FK_C8, FK_C6,
+    FK_DT = FK_NFIX2, FK_IDT, FK_4IDT2, FK_HDT, FK_MHDT, FK_EPSDT, FK_CTAUDT, FK_C8, FK_C6,
     FK_W1A, FK_W1B, FK_W2A, FK_W2B, FK_W3,          // Gauss-average weights of the face results
-    FK_GAMMA, FK_GM1, FK_INVGM1, FK_K, FK_K2, FK_KK2, FK_INVK2, FK_K2INV2, FK_KHEAT, FK_MU,
-    FK_IDX, FK_IDY, FK_WEPS,
+    FK_GAMMA, FK_GM1, FK_K, FK_K2, FK_KK2, FK_INVK2, FK_K2INV2, FK_KHEAT, FK_MU,
+    FK_IDX, FK_IDY, FK_WEPS, FK_WEPS4,
     FK_N
 };
 
@@ -49,9 +49,11 @@ constexpr FluxFixed make_flux_fixed()
     k[FK_3] = 3.0; k[FK_4] = 4.0; k[FK_5] = 5.0; k[FK_M3] = -3.0; k[FK_M4] = -4.0; k[FK_QUARTER] = 0.25;
     k[FK_EIGHTH] = 0.125; k[FK_ERFC_TMAX] = 27.9;
     const double gq = 0.28867513459481287;               // 1/(2 sqrt 3)
-    k[FK_T13_12] = 13.0 / 12.0; k[FK_T11_18] = 11.0 / 18.0;
-    k[FK_DLO] = 7.0 / 36.0 - 1.7320508075688772 / 1080.0;
-    k[FK_DHI] = 7.0 / 36.0 + 1.7320508075688772 / 1080.0;
+    // the linear weights (d_lo, 11/18, d_hi) divided by 11/18 (the weights' normalisation
+    // cancels the common factor)
+    k[FK_T13_3] = 13.0 / 3.0;
+    k[FK_DLO] = (7.0 / 36.0 - 1.7320508075688772 / 1080.0) * (18.0 / 11.0);
+    k[FK_DHI] = (7.0 / 36.0 + 1.7320508075688772 / 1080.0) * (18.0 / 11.0);
     k[FK_HG] = 0.5 * gq; k[FK_MHG] = -0.5 * gq;
     // the quartic p(eta) through the five segment means (see SegmentRows::eq_derivs)
     k[FK_A1T] = 8.0 / 12.0; k[FK_A2T] = -1.0 / 12.0; k[FK_S1T] = 13.0 / 9.0; k[FK_S2T] = -1.0 / 9.0;
@@ -74,6 +76,7 @@ __device__ __forceinline__ void flux_table_tile(double* t, const GridDev& G, dou
 {
     t[FK_DT] = dt;
     t[FK_IDT] = __drcp_rn(dt);
+    t[FK_4IDT2] = 4.0 * __drcp_rn(dt * dt);
     t[FK_HDT] = 0.5 * dt;
     t[FK_MHDT] = -0.5 * dt;
     t[FK_EPSDT] = G.eps_tau * dt;
@@ -88,7 +91,6 @@ __device__ __forceinline__ void flux_table_tile(double* t, const GridDev& G, dou
     t[FK_W3] = dt * dt * (1.0 / 6.0);
     t[FK_GAMMA] = G.gamma;
     t[FK_GM1] = G.gamma - 1.0;
-    t[FK_INVGM1] = __drcp_rn(G.gamma - 1.0);
     t[FK_K] = G.K;
     t[FK_K2] = G.K + 2.0;
     t[FK_KK2] = G.K * (G.K + 2.0);
@@ -99,6 +101,7 @@ __device__ __forceinline__ void flux_table_tile(double* t, const GridDev& G, dou
     t[FK_IDX] = G.inv_dx;
     t[FK_IDY] = G.inv_dy;
     t[FK_WEPS] = G.weno_eps;
+    t[FK_WEPS4] = 4.0 * G.weno_eps;
 }
 
 // ------------------------------------------------------------------------
@@ -118,24 +121,29 @@ __device__ __forceinline__ void flux_table_tile(double* t, const GridDev& G, dou
 // reciprocal through the common denominator e_0 e_1 e_2.
 // Both Gauss points are evaluated at once (eta = -g and +g): the indicators
 // and the unnormalised weights are shared, only the linear weights and the
-// final normalisation differ.
+// final normalisation differ.  The weights are homogeneous in (e_k, Z) and in
+// (d_k), so the code carries 4 e_k = D_k^2 + 13/3 (second difference)^2 + 4 eps
+// (eps4 = 4 eps) and the linear weights divided by 11/18.
+// The caller passes A1 = v_1 - v_-1 and S1 = v_1 + v_-1, which the tangential
+// derivatives use too.
 __device__ __forceinline__ void tang_weno5_pair(const RegK& r, double vmm, double vm, double v0, double vp,
-                                                double vpp, double eps, double& at_minus, double& at_plus)
+                                                double vpp, double A1, double S1, double eps4, double& at_minus,
+                                                double& at_plus)
 {
     const double D0 = r.kfma(FK_3, v0, r.kfma(FK_M4, vm, vmm));
-    const double D1 = r.sub(vp, vm);
+    const double D1 = A1;
     const double D2 = r.kfma(FK_4, vp, r.kfma(FK_M3, v0, -vpp));
     const double s0 = r.kfma(FK_M2, vm, r.add(vmm, v0));
-    const double s1 = r.kfma(FK_M2, v0, r.add(vm, vp));
+    const double s1 = r.kfma(FK_M2, v0, S1);
     const double s2 = r.kfma(FK_M2, vp, r.add(v0, vpp));
-    const double e0 = fma(r.kmul(FK_QUARTER, D0), D0, fma(r.kmul(FK_T13_12, s0), s0, eps));
-    const double e1 = fma(r.kmul(FK_QUARTER, D1), D1, fma(r.kmul(FK_T13_12, s1), s1, eps));
-    const double e2 = fma(r.kmul(FK_QUARTER, D2), D2, fma(r.kmul(FK_T13_12, s2), s2, eps));
+    const double e0 = fma(D0, D0, fma(r.kmul(FK_T13_3, s0), s0, eps4));
+    const double e1 = fma(D1, D1, fma(r.kmul(FK_T13_3, s1), s1, eps4));
+    const double e2 = fma(D2, D2, fma(r.kmul(FK_T13_3, s2), s2, eps4));
     const double Z = fabs(r.sub(e0, e2));
     // (e_k + Z) times the other two = E + Z times the other two, E = e0 e1 e2
     const double e12 = r.mul(e1, e2), E = r.mul(e0, e12);
     const double P0 = fma(Z, e12, E);
-    const double P1 = r.kmul(FK_T11_18, fma(Z, r.mul(e0, e2), E));
+    const double P1 = fma(Z, r.mul(e0, e2), E);
     const double P2 = fma(Z, r.mul(e0, e1), E);
     const double Q0 = r.mul(P0, D0), Q1 = r.mul(P1, D1), Q2 = r.mul(P2, D2);
     const double np = r.kfma(FK_DHI, Q2, r.kfma(FK_DLO, Q0, Q1)), dp = r.kfma(FK_DHI, P2, r.kfma(FK_DLO, P0, P1));
@@ -342,8 +350,11 @@ __device__ __forceinline__ void micro_slope(const RegK& r, const SlopeCtx& s, co
 // ------------------------------------------------------------------------
 // Euler time derivatives by Cauchy-Kowalevski in primitive variables.
 // Inputs: conservative W and its x (normal), y (tangential) derivatives up to
-// second order.  Outputs conservative W_t, W_tt and the flux time derivative
-// F_t of the normal Euler flux.
+// second order, 1/rho, the velocity, the pressure p and the internal energy per
+// volume e = p / (gamma - 1).  The pressure's derivatives are carried as those
+// of e (p_x = (gamma - 1) e_x, ...), which are differences of the energy's and
+// the kinetic energy's.  Outputs conservative W_t, W_tt and the flux time
+// derivative F_t of the normal Euler flux.
 // TNS is rho <(a_n u + a_t v + A) u psi> of the equilibrium state, i.e. the
 // Chapman-Enskog Navier-Stokes flux of the BGK model per unit collision time
 // (mu = tau p, bulk part 2/(K+2), heat conduction (K+4)/2 tau p grad(p/rho)).
@@ -352,7 +363,7 @@ struct EulerTD { double Wt[4], Wtt[4], Ft[4], F[4], TNS[4]; };
 __device__ __forceinline__ void euler_time_derivs(const RegK& r, const double W[4], const double Wx[4],
                                                   const double Wy[4], const double Wxx[4], const double Wxy[4],
                                                   const double Wyy[4], double ir, double U, double V, double p,
-                                                  EulerTD& o)
+                                                  double e, EulerTD& o)
 {
     const double rho = W[0], m = W[1], E = W[3];
     // primitive first derivatives
@@ -365,7 +376,7 @@ __device__ __forceinline__ void euler_time_derivs(const RegK& r, const double W[
     const double hq2 = r.kmul(FK_HALF, q2);
     const double KEx = fma(-hq2, rx, fma(V, Wx[2], r.mul(U, Wx[1])));
     const double KEy = fma(-hq2, ry, fma(V, Wy[2], r.mul(U, Wy[1])));
-    const double px = r.mul(r.k(FK_GM1), r.sub(Wx[3], KEx)), py = r.mul(r.k(FK_GM1), r.sub(Wy[3], KEy));
+    const double ex = r.sub(Wx[3], KEx), ey = r.sub(Wy[3], KEy);
     // primitive second derivatives
     const double rxx = Wxx[0], rxy = Wxy[0], ryy = Wyy[0];
     const double rx2 = r.add(rx, rx), ry2 = r.add(ry, ry);
@@ -378,47 +389,45 @@ __device__ __forceinline__ void euler_time_derivs(const RegK& r, const double W[
     const double KExx = fma(-hq2, rxx, fma(V, Wxx[2], fma(U, Wxx[1], r.mul(rho, fma(Ux, Ux, r.mul(Vx, Vx))))));
     const double KExy = fma(-hq2, rxy, fma(V, Wxy[2], fma(U, Wxy[1], r.mul(rho, fma(Ux, Uy, r.mul(Vx, Vy))))));
     const double KEyy = fma(-hq2, ryy, fma(V, Wyy[2], fma(U, Wyy[1], r.mul(rho, fma(Uy, Uy, r.mul(Vy, Vy))))));
-    const double pxx = r.mul(r.k(FK_GM1), r.sub(Wxx[3], KExx));
-    const double pxy = r.mul(r.k(FK_GM1), r.sub(Wxy[3], KExy));
-    const double pyy = r.mul(r.k(FK_GM1), r.sub(Wyy[3], KEyy));
-    // first time derivatives
+    const double exx = r.sub(Wxx[3], KExx), exy = r.sub(Wxy[3], KExy), eyy = r.sub(Wyy[3], KEyy);
+    // first time derivatives (p_x / rho = e_x gir)
     const double gamma = r.k(FK_GAMMA);
+    const double gir = r.mul(r.k(FK_GM1), ir);
     const double Dv = r.add(Ux, Vy);
     const double rt = -fma(rho, Dv, fma(V, ry, r.mul(U, rx)));
-    const double Ut = -fma(px, ir, fma(V, Uy, r.mul(U, Ux)));
-    const double Vt = -fma(py, ir, fma(V, Vy, r.mul(U, Vx)));
-    const double pt = -fma(r.mul(gamma, p), Dv, fma(V, py, r.mul(U, px)));
+    const double Ut = -fma(ex, gir, fma(V, Uy, r.mul(U, Ux)));
+    const double Vt = -fma(ey, gir, fma(V, Vy, r.mul(U, Vx)));
+    const double et = -fma(r.mul(gamma, e), Dv, fma(V, ey, r.mul(U, ex)));
     // mixed derivatives d/dx, d/dy of the first time derivatives
     const double Dx = r.add(Uxx, Vxy), Dy = r.add(Uxy, Vyy);
     const double rxt = -fma(rho, Dx, fma(rx, Dv, fma(V, rxy, fma(Vx, ry, fma(U, rxx, r.mul(Ux, rx))))));
     const double ryt = -fma(rho, Dy, fma(ry, Dv, fma(V, ryy, fma(Vy, ry, fma(U, rxy, r.mul(Uy, rx))))));
-    const double Uxt = -fma(fma(-r.mul(px, rx), ir, pxx), ir, fma(V, Uxy, fma(Vx, Uy, fma(U, Uxx, r.mul(Ux, Ux)))));
-    const double Vyt = -fma(fma(-r.mul(py, ry), ir, pyy), ir, fma(V, Vyy, fma(Vy, Vy, fma(U, Vxy, r.mul(Uy, Vx)))));
-    const double Uyt = -fma(fma(-r.mul(px, ry), ir, pxy), ir, fma(V, Uyy, fma(Vy, Uy, fma(U, Uxy, r.mul(Uy, Ux)))));
-    const double Vxt = -fma(fma(-r.mul(py, rx), ir, pxy), ir, fma(V, Vxy, fma(Vx, Vy, fma(U, Vxx, r.mul(Ux, Vx)))));
-    const double pxt = -fma(gamma, fma(p, Dx, r.mul(px, Dv)), fma(V, pxy, fma(Vx, py, fma(U, pxx, r.mul(Ux, px)))));
-    const double pyt = -fma(gamma, fma(p, Dy, r.mul(py, Dv)), fma(V, pyy, fma(Vy, py, fma(U, pxy, r.mul(Uy, px)))));
+    const double Uxt = -fma(fma(-r.mul(ex, rx), ir, exx), gir, fma(V, Uxy, fma(Vx, Uy, fma(U, Uxx, r.mul(Ux, Ux)))));
+    const double Vyt = -fma(fma(-r.mul(ey, ry), ir, eyy), gir, fma(V, Vyy, fma(Vy, Vy, fma(U, Vxy, r.mul(Uy, Vx)))));
+    const double Uyt = -fma(fma(-r.mul(ex, ry), ir, exy), gir, fma(V, Uyy, fma(Vy, Uy, fma(U, Uxy, r.mul(Uy, Ux)))));
+    const double Vxt = -fma(fma(-r.mul(ey, rx), ir, exy), gir, fma(V, Vxy, fma(Vx, Vy, fma(U, Vxx, r.mul(Ux, Vx)))));
+    const double ext = -fma(gamma, fma(e, Dx, r.mul(ex, Dv)), fma(V, exy, fma(Vx, ey, fma(U, exx, r.mul(Ux, ex)))));
+    const double eyt = -fma(gamma, fma(e, Dy, r.mul(ey, Dv)), fma(V, eyy, fma(Vy, ey, fma(U, exy, r.mul(Uy, ex)))));
     // second time derivatives
     const double Dt = r.add(Uxt, Vyt);
     const double rtt = -fma(rho, Dt, fma(rt, Dv, fma(V, ryt, fma(Vt, ry, fma(U, rxt, r.mul(Ut, rx))))));
-    const double Utt = -fma(fma(-r.mul(px, rt), ir, pxt), ir, fma(V, Uyt, fma(Vt, Uy, fma(U, Uxt, r.mul(Ut, Ux)))));
-    const double Vtt = -fma(fma(-r.mul(py, rt), ir, pyt), ir, fma(V, Vyt, fma(Vt, Vy, fma(U, Vxt, r.mul(Ut, Vx)))));
-    const double ptt = -fma(gamma, fma(p, Dt, r.mul(pt, Dv)), fma(V, pyt, fma(Vt, py, fma(U, pxt, r.mul(Ut, px)))));
-    // back to conservative variables
+    const double Utt = -fma(fma(-r.mul(ex, rt), ir, ext), gir, fma(V, Uyt, fma(Vt, Uy, fma(U, Uxt, r.mul(Ut, Ux)))));
+    const double Vtt = -fma(fma(-r.mul(ey, rt), ir, eyt), gir, fma(V, Vyt, fma(Vt, Vy, fma(U, Vxt, r.mul(Ut, Vx)))));
+    const double ett = -fma(gamma, fma(e, Dt, r.mul(et, Dv)), fma(V, eyt, fma(Vt, ey, fma(U, ext, r.mul(Ut, ex)))));
+    // back to conservative variables (E = e + KE)
     const double uut = fma(V, Vt, r.mul(U, Ut));
-    const double inv_gm1 = r.k(FK_INVGM1);
     o.Wt[0] = rt;
     o.Wt[1] = fma(rho, Ut, r.mul(rt, U));
     o.Wt[2] = fma(rho, Vt, r.mul(rt, V));
-    o.Wt[3] = fma(rho, uut, fma(rt, hq2, r.mul(pt, inv_gm1)));
+    o.Wt[3] = fma(rho, uut, fma(rt, hq2, et));
     const double rt2 = r.add(rt, rt);
     o.Wtt[0] = rtt;
     o.Wtt[1] = fma(rho, Utt, fma(rt2, Ut, r.mul(rtt, U)));
     o.Wtt[2] = fma(rho, Vtt, fma(rt2, Vt, r.mul(rtt, V)));
-    o.Wtt[3] = fma(rho, fma(V, Vtt, fma(Vt, Vt, fma(U, Utt, r.mul(Ut, Ut)))),
-                   fma(rt2, uut, fma(rtt, hq2, r.mul(ptt, inv_gm1))));
+    o.Wtt[3] = fma(rho, fma(V, Vtt, fma(Vt, Vt, fma(U, Utt, r.mul(Ut, Ut)))), fma(rt2, uut, fma(rtt, hq2, ett)));
     // normal Euler flux and its time derivative
     const double Ep = r.add(E, p);
+    const double pt = r.mul(r.k(FK_GM1), et);
     o.F[0] = m;
     o.F[1] = fma(m, U, p);
     o.F[2] = r.mul(m, V);
@@ -431,7 +440,7 @@ __device__ __forceinline__ void euler_time_derivs(const RegK& r, const double W[
     // BGK Navier-Stokes flux per unit tau in the face-normal direction
     const double sxx = r.mul(p, fma(-r.k(FK_K2INV2), Dv, r.add(Ux, Ux)));
     const double sxy = r.mul(p, r.add(Uy, Vx));
-    const double thx = r.mul(fma(-r.mul(p, ir), rx, px), ir);            // d/dx (p / rho)
+    const double thx = r.mul(fma(-r.mul(e, ir), rx, ex), gir);            // d/dx (p / rho)
     o.TNS[0] = 0.0;
     o.TNS[1] = sxx;
     o.TNS[2] = sxy;
@@ -457,7 +466,8 @@ __device__ __forceinline__ bool gks_point(const RegK& r, const Src& src, double 
     src.eq_value(W0);
     const double ir0 = r.rcp(W0[0]);
     const double U0 = r.mul(W0[1], ir0), V0 = r.mul(W0[2], ir0);
-    const double p0 = r.mul(r.k(FK_GM1), r.kfma(FK_MHALF, fma(W0[2], V0, r.mul(W0[1], U0)), W0[3]));
+    const double e0 = r.kfma(FK_MHALF, fma(W0[2], V0, r.mul(W0[1], U0)), W0[3]);   // p0 / (gamma - 1)
+    const double p0 = r.mul(r.k(FK_GM1), e0);
     // non-equilibrium states
     double Wl[4], Wlt[4], Wr[4], Wrt[4];
     src.ne_value(0, Wl, Wlt);
@@ -541,19 +551,20 @@ __device__ __forceinline__ bool gks_point(const RegK& r, const Src& src, double 
     {
         double W0n[4], W0t[4], W0nn[4], W0nt[4], W0tt[4];
         src.eq_derivs(W0n, W0t, W0nn, W0nt, W0tt);
-        euler_time_derivs(r, W0, W0n, W0t, W0nn, W0nt, W0tt, ir0, U0, V0, p0, e);
+        euler_time_derivs(r, W0, W0n, W0t, W0nn, W0nt, W0tt, ir0, U0, V0, p0, e0, e);
     }
 
     // tau-terms of g0: rho <(a_n u + a_t v) u psi> = TNS - F_t (the time part is the Euler F_t)
     const double idt = r.k(FK_IDT);
     const double omh = r.sub(r.one, h);
-    const double thm = r.sub(r.k(FK_3), h);                  // 3 - h
-    const double ta = r.mul(tau, omh);
-    const double a = r.mul(r.mul(ta, thm), idt);
-    const double q4 = r.mul(r.mul(r.kmul(FK_4, ta), idt), idt);    // 4 tau (1 - h) / dt^2
+    const double ta = r.mul(tau, omh);                       // tau (1 - h)
+    const double q4 = r.mul(ta, r.k(FK_4IDT2));              // 4 tau (1 - h) / dt^2
     const double g = r.mul(q4, omh);
-    const double b4 = r.mul(r.mul(tau, fma(-r.mul(dt, h), r.sub(r.k(FK_2), h), r.mul(r.mul(tau, omh), thm))), idt);
-    const double f4 = r.mul(q4, fma(dt, h, -ta));
+    const double dh = r.mul(dt, h);
+    const double f4 = r.mul(q4, r.sub(dh, ta));
+    const double tat = r.mul(ta, r.sub(r.k(FK_3), h));       // tau (1 - h) (3 - h)
+    const double a = r.mul(tat, idt);
+    const double b4 = r.mul(r.mul(tau, fma(-dh, r.sub(r.k(FK_2), h), tat)), idt);
     for (int k = 0; k < 4; ++k) {
         const double dTh = (k == 0) ? -r.add(e.Ft[0], Th[0]) : r.sub(r.sub(e.TNS[k], e.Ft[k]), Th[k]);
         const double dFh = r.sub(Fh[k], e.F[k]);

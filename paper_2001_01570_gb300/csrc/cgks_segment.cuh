@@ -123,11 +123,12 @@ struct SegmentRows {
 
     // the eta-independent parts of the quartic's derivatives above for variable k
     // (rows m_{-2..2} of the values and of the normal derivatives), stored at dc
-    __device__ __forceinline__ static void seg_deriv_parts(const RegK& r, double* dc, double m2m, double mm, double m0,
-                                                           double mp, double m2p, double n2m, double nm, double n0,
+    // (S1 = mp + mm and A1 = mp - mm come from the caller, which shares them with the WENO-Z values)
+    __device__ __forceinline__ static void seg_deriv_parts(const RegK& r, double* dc, double m2m, double S1, double A1,
+                                                           double m0, double m2p, double n2m, double nm, double n0,
                                                            double np, double n2p)
     {
-        const double S1 = r.add(mp, mm), S2 = r.add(m2p, m2m), A1 = r.sub(mp, mm), A2 = r.sub(m2p, m2m);
+        const double S2 = r.add(m2p, m2m), A2 = r.sub(m2p, m2m);
         dc[0 * kThreads] = r.kfma(FK_A1T, A1, r.kmul(FK_A2T, A2));
         dc[1 * kThreads] = r.kfma(FK_S1T, S1, r.kfma(FK_S2T, S2, r.kmul(FK_M0T, m0)));
         dc[2 * kThreads] = r.kfma(FK_S1TT, S1, r.kfma(FK_S2TT, S2, r.kmul(FK_M0TT, m0)));
@@ -173,7 +174,7 @@ __device__ __forceinline__ bool segment_results(const RegK& r, const double* rec
 {
     constexpr int NF = FaceQ<STAGE>::n;
     constexpr double gq = 0.28867513459481287;   // 1/(2 sqrt 3): Gauss points at +-gq
-    const double weps = r.k(FK_WEPS);
+    const double weps = r.k(FK_WEPS), weps4 = r.k(FK_WEPS4);
     bool bad = false;
 #pragma unroll
     for (int q = 0; q < NF; ++q) acc[q] = 0.0;
@@ -183,9 +184,10 @@ __device__ __forceinline__ bool segment_results(const RegK& r, const double* rec
     for (int k = 0; k < 4; ++k) {
         auto R = [&](int f, int off) { return rec_at(rec, pa, pb, pc, r0, rstride, f, k, off); };
         const double m2m = R(RV, -2), mm = R(RV, -1), m0 = R(RV, 0), mp = R(RV, 1), m2p = R(RV, 2);
-        tang_weno5_pair(r, m2m, mm, m0, mp, m2p, weps, W0m[k], W0p[k]);
+        const double S1 = r.add(mp, mm), A1 = r.sub(mp, mm);
+        tang_weno5_pair(r, m2m, mm, m0, mp, m2p, A1, S1, weps4, W0m[k], W0p[k]);
         if constexpr (SHARE)
-            SegmentRows<true>::seg_deriv_parts(r, dc + 8 * k * kThreads, m2m, mm, m0, mp, m2p, R(RN, -2), R(RN, -1),
+            SegmentRows<true>::seg_deriv_parts(r, dc + 8 * k * kThreads, m2m, S1, A1, m0, m2p, R(RN, -2), R(RN, -1),
                                                R(RN, 0), R(RN, 1), R(RN, 2));
         tang_weno3_slopes(r, R(RL, -1), R(RL, 0), R(RL, 1), R(RR, -1), R(RR, 0), R(RR, 1), weps, sL[k], sR[k]);
     }
