@@ -287,11 +287,12 @@ __device__ __forceinline__ void psi_u(const RegK& r, const Moments& m, double o[
 //   v^2: a2_2 + h1 u,                v^3: h2,
 // (h = a_3/2, c12 = a1_2 + a2_1), so each psi component is a short sum of
 // products of the factorised u-, v- and xi-moments.
+// (a[3] holds h = a_3 / 2, as micro_slope returns it)
 template <int A>
 __device__ __forceinline__ void q_moments(const RegK& r, const Moments& m, const double a1[4], const double a2[4],
                                           double o[4])
 {
-    const double h1 = r.kmul(FK_HALF, a1[3]), h2 = r.kmul(FK_HALF, a2[3]), c12 = r.add(a1[2], a2[1]);
+    const double h1 = a1[3], h2 = a2[3], c12 = r.add(a1[2], a2[1]);
     // sums over u for the v^j groups at u-shift s2 (S_j) and the xi^2 parts (Z_j); S_3 = Z_1
     double S0[3], S1[3], S2[3], Z0[3], Z1[3];
 #pragma unroll
@@ -324,27 +325,34 @@ __device__ __forceinline__ void q_moments(const RegK& r, const Moments& m, const
 }
 
 // micro-slope coefficients a with <psi psi^T> a = b for a Maxwellian
-// (closed form of the 4x4 moment system)
-struct SlopeCtx { double U, V, Bm, inv_theta, c4; };
+// (closed form of the 4x4 moment system):
+//   a_3 = c4 (2 b_3 - Bm b_0 - 2 (V R_3 + U R_2)),  R_2 = b_1 - U b_0,  R_3 = b_2 - V b_0,
+//   a_2 = R_3 / theta - V a_3,  a_1 = R_2 / theta - U a_3,  a_0 = b_0 - U a_1 - V a_2 - Bm a_3 / 2,
+// with Bm = U^2 + V^2 + (K+2) theta and c4 = 1 / ((K+2) theta^2).  a[3] receives h = a_3 / 2, the
+// factor that q_moments uses (psi_4 carries 1/2).
+struct SlopeCtx { double U, V, U2, V2, Bm, hBm, inv_theta, c4; };
 
 __device__ __forceinline__ void slope_ctx(const RegK& r, double U, double V, double theta, double inv_theta,
                                           SlopeCtx& s)
 {
     s.U = U; s.V = V;
+    s.U2 = r.add(U, U); s.V2 = r.add(V, V);
     s.Bm = fma(U, U, fma(V, V, r.mul(r.k(FK_K2), theta)));
+    s.hBm = r.kmul(FK_HALF, s.Bm);
     s.inv_theta = inv_theta;
     s.c4 = r.mul(r.mul(inv_theta, inv_theta), r.k(FK_INVK2));
 }
 
 __device__ __forceinline__ void micro_slope(const RegK& r, const SlopeCtx& s, const double b[4], double a[4])
 {
-    const double R4 = fma(-s.Bm, b[0], r.add(b[3], b[3]));
+    const double R4h = fma(-s.hBm, b[0], b[3]);
     const double R3 = fma(-s.V, b[0], b[2]);
     const double R2 = fma(-s.U, b[0], b[1]);
-    a[3] = r.mul(s.c4, r.kfma(FK_M2, fma(s.V, R3, r.mul(s.U, R2)), R4));
-    a[2] = fma(-s.V, a[3], r.mul(R3, s.inv_theta));
-    a[1] = fma(-s.U, a[3], r.mul(R2, s.inv_theta));
-    a[0] = fma(r.kmul(FK_MHALF, a[3]), s.Bm, fma(-s.V, a[2], fma(-s.U, a[1], b[0])));
+    const double h = r.mul(s.c4, r.sub(R4h, fma(s.V, R3, r.mul(s.U, R2))));
+    a[3] = h;
+    a[2] = fma(-s.V2, h, r.mul(R3, s.inv_theta));
+    a[1] = fma(-s.U2, h, r.mul(R2, s.inv_theta));
+    a[0] = fma(-h, s.Bm, fma(-s.V, a[2], fma(-s.U, a[1], b[0])));
 }
 
 // ------------------------------------------------------------------------
