@@ -51,25 +51,22 @@ UNIT = "cell-updates/s"
 
 # Algorithmic FP64 operations per cell and stage (FMA = 2) on the 256^2 vortex, where every kernel does
 # exactly the method's work (no halo recomputation, every face once): two face-row records (1,888
-# each: linear P7 + WENO-Z pair of 4 variables), two face segments (3,048.4 in stage 1, 2,852.4 in
+# each: linear P7 + WENO-Z pair of 4 variables), two face segments (3,076.44 in stage 1, 2,878.44 in
 # stage 2: two Gauss points each) and the update (80 / 121).  The kernels issue their adds and
 # multiplies as DFMAs, so the operations are counted by ncu on a build with plain adds and
 # multiplies; each per-unit figure is the smallest count of the formulations measured (the current
-# code spends 1,916 per record and 3,048.4 / 2,852.4 per segment).  The segment counts are the ncu
-# counts of the earlier formulation (3,112.4 / 2,916.4) less the 64.0 operations per segment that the
-# present one saves in its formulas (host count of the formulas, below: 5,502.69 -> 5,374.62 and
-# 5,154.52 -> 5,026.45 per cell; both formulations expand the same special functions).
+# code spends 1,916 per record and 3,076.44 / 2,878.44 per segment).
 # The compact 6th-order variant (--order 6) changes only the record kernel's linear reconstruction:
 # 1,840 per face row with WENO-Z.
 RECORD_FLOP_PER_CELL = {8: 3776.0, 6: 3680.0}
-FLUX_FLOP_PER_CELL = {1: 6096.73, 2: 5704.73}
+FLUX_FLOP_PER_CELL = {1: 6152.88, 2: 5756.88}
 UPDATE_FLOP_PER_CELL = {1: 80.0, 2: 121.0}
 FLOP_PER_CELL = {s: RECORD_FLOP_PER_CELL[8] + FLUX_FLOP_PER_CELL[s] + UPDATE_FLOP_PER_CELL[s] for s in (1, 2)}
 # The same per-cell counts taken from the kernels' formulas rather than from an instruction stream:
 # a host build of the kernels' device arithmetic with a counting FP64 type, run over one step of the
 # 2048^2 bench grid (python -m paper_2001_01570_gb300.opcount 2048), counting add/sub/mul 1, fma 2 and
 # every divide, square root, reciprocal, exponential and erfc as 1 however the GPU expands it.
-OPCOUNT_FLOP_PER_CELL = {"records": 3733.73, "flux": {1: 5374.62, 2: 5026.45}, "update": {1: 80.0, 2: 71.0}}
+OPCOUNT_FLOP_PER_CELL = {"records": 3733.73, "flux": {1: 5398.63, 2: 5050.46}, "update": {1: 80.0, 2: 71.0}}
 DEFAULT_TILE = "14x8"     # the library's 2D default
 # DRAM bytes (read + write) per cell of one stage-1 flux-kernel launch with 14x8 tiles: ncu
 # dram__bytes_{read,write}.sum of the current kernel on the 1024^2 vortex (records and state larger

@@ -325,34 +325,30 @@ __device__ __forceinline__ void q_moments(const RegK& r, const Moments& m, const
 }
 
 // micro-slope coefficients a with <psi psi^T> a = b for a Maxwellian
-// (closed form of the 4x4 moment system):
-//   a_3 = c4 (2 b_3 - Bm b_0 - 2 (V R_3 + U R_2)),  R_2 = b_1 - U b_0,  R_3 = b_2 - V b_0,
-//   a_2 = R_3 / theta - V a_3,  a_1 = R_2 / theta - U a_3,  a_0 = b_0 - U a_1 - V a_2 - Bm a_3 / 2,
-// with Bm = U^2 + V^2 + (K+2) theta and c4 = 1 / ((K+2) theta^2).  a[3] receives h = a_3 / 2, the
-// factor that q_moments uses (psi_4 carries 1/2).
-struct SlopeCtx { double U, V, U2, V2, Bm, hBm, inv_theta, c4; };
+// (closed form of the 4x4 moment system); a[3] receives h = a_3 / 2, the factor
+// q_moments uses (psi_4 carries 1/2)
+struct SlopeCtx { double U, V, Bm, inv_theta, c4; };
 
 __device__ __forceinline__ void slope_ctx(const RegK& r, double U, double V, double theta, double inv_theta,
                                           SlopeCtx& s)
 {
     s.U = U; s.V = V;
-    s.U2 = r.add(U, U); s.V2 = r.add(V, V);
     s.Bm = fma(U, U, fma(V, V, r.mul(r.k(FK_K2), theta)));
-    s.hBm = r.kmul(FK_HALF, s.Bm);
     s.inv_theta = inv_theta;
     s.c4 = r.mul(r.mul(inv_theta, inv_theta), r.k(FK_INVK2));
 }
 
 __device__ __forceinline__ void micro_slope(const RegK& r, const SlopeCtx& s, const double b[4], double a[4])
 {
-    const double R4h = fma(-s.hBm, b[0], b[3]);
+    const double R4 = fma(-s.Bm, b[0], r.add(b[3], b[3]));
     const double R3 = fma(-s.V, b[0], b[2]);
     const double R2 = fma(-s.U, b[0], b[1]);
-    const double h = r.mul(s.c4, r.sub(R4h, fma(s.V, R3, r.mul(s.U, R2))));
-    a[3] = h;
-    a[2] = fma(-s.V2, h, r.mul(R3, s.inv_theta));
-    a[1] = fma(-s.U2, h, r.mul(R2, s.inv_theta));
+    const double a3 = r.mul(s.c4, r.kfma(FK_M2, fma(s.V, R3, r.mul(s.U, R2)), R4));
+    const double h = r.kmul(FK_HALF, a3);
+    a[2] = fma(-s.V, a3, r.mul(R3, s.inv_theta));
+    a[1] = fma(-s.U, a3, r.mul(R2, s.inv_theta));
     a[0] = fma(-h, s.Bm, fma(-s.V, a[2], fma(-s.U, a[1], b[0])));
+    a[3] = h;
 }
 
 // ------------------------------------------------------------------------
