@@ -1,7 +1,7 @@
 """The multi-process launch path of bench.py on CPU with the gloo backend (world size 2).
 
-Every GPU run of this build uses one GPU; with N GPUs bench.py runs one independent copy of the
-workload per rank (no collective on the data path) and reduces only the timings: max over ranks.
+With N GPUs bench.py runs one independent copy of the workload per rank (no collective on the
+data path) and reduces only the timings: max over ranks.
 """
 import json
 import multiprocessing as mp
