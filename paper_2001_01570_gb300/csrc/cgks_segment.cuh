@@ -166,11 +166,15 @@ struct SegmentRows {
 // stage 1: the W* and R flux combinations and the interface states W(dt/2),
 // W(dt); stage 2: dt^2/3 F_t and dt^2/3 W_tt).  rec, pa, pb, pc, r0, rstride
 // locate the segment's face rows in the tile's records; dc is this thread's
-// slice for the Gauss-point-independent derivative parts (SHARE).  Returns
+// slice for the Gauss-point-independent derivative parts (SHARE).  PARK: the
+// first point's sums are stored at park[q * park_stride] (the segment's own
+// output slots) while the second point is evaluated, and read back after it,
+// which frees their registers (the same values, the same bits).  Returns
 // false if a state was non-physical.
-template <int STAGE, bool SHARE>
+template <int STAGE, bool SHARE, bool PARK = false>
 __device__ __forceinline__ bool segment_results(const RegK& r, const double* rec, int pa, int pb, int pc, int r0,
-                                                int rstride, double iht, double* dc, double acc[FaceQ<STAGE>::n])
+                                                int rstride, double iht, double* dc, double acc[FaceQ<STAGE>::n],
+                                                double* park = nullptr, size_t park_stride = 0)
 {
     constexpr int NF = FaceQ<STAGE>::n;
     constexpr double gq = 0.28867513459481287;   // 1/(2 sqrt 3): Gauss points at +-gq
@@ -200,6 +204,10 @@ __device__ __forceinline__ bool segment_results(const RegK& r, const double* rec
                                      {sL[0], sL[1], sL[2], sL[3]}, {sR[0], sR[1], sR[2], sR[3]}, dc};
         double Fb[4], Ft[4], Wm[4], Wb[4], Wtt[4];
         bad |= !gks_point<STAGE>(r, src, Fb, Ft, Wm, Wb, Wtt);
+        if (PARK && gp == 1) {
+#pragma unroll
+            for (int q = 0; q < NF; ++q) acc[q] = park[q * park_stride];
+        }
         // Gauss average (weight 1/2 per point) times the stage's time factors
         if (STAGE == 1) {
 #pragma unroll
@@ -215,6 +223,10 @@ __device__ __forceinline__ bool segment_results(const RegK& r, const double* rec
                 acc[k] = r.kfma(FK_W3, Ft[k], acc[k]);
                 acc[4 + k] = r.kfma(FK_W3, Wtt[k], acc[4 + k]);
             }
+        }
+        if (PARK && gp == 0) {
+#pragma unroll
+            for (int q = 0; q < NF; ++q) park[q * park_stride] = acc[q];
         }
     }
     return !bad;
