@@ -70,9 +70,9 @@ OPCOUNT_FLOP_PER_CELL = {"records": 3733.73, "flux": {1: 5398.63, 2: 5050.46}, "
 DEFAULT_TILE = "14x8"     # the library's 2D default
 # DRAM bytes (read + write) per cell of one stage-1 flux-kernel launch with 14x8 tiles: ncu
 # dram__bytes_{read,write}.sum of the current kernel on the 1024^2 vortex (records and state larger
-# than L2), 477.35 + 255.52 MB, divided by the cells; the 2048^2 bench grid moves the same bytes per
+# than L2), 476.76 + 248.00 MB, divided by the cells; the 2048^2 bench grid moves the same bytes per
 # cell (its launch is too large to capture under the profiling size rule).
-FLUX_DRAM_BYTES_PER_CELL = {1: (477.34528e6 + 255.52256e6) / 1048576}
+FLUX_DRAM_BYTES_PER_CELL = {1: (476.764416e6 + 248.002304e6) / 1048576}
 # algorithmic bytes per cell of the flux kernel: the two face rows' records (2 x 28 doubles) read and
 # the two faces' results written (stage 1: 16 doubles each, stage 2: 8)
 FLUX_ALGO_BYTES_PER_CELL = {1: 448 + 256, 2: 448 + 128}
