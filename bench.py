@@ -67,7 +67,8 @@ FLOP_PER_CELL = {s: RECORD_FLOP_PER_CELL[8] + FLUX_FLOP_PER_CELL[s] + UPDATE_FLO
 # 2048^2 bench grid (python -m paper_2001_01570_gb300.opcount 2048), counting add/sub/mul 1, fma 2 and
 # every divide, square root, reciprocal, exponential and erfc as 1 however the GPU expands it.
 OPCOUNT_FLOP_PER_CELL = {"records": 3733.73, "flux": {1: 5398.63, 2: 5050.46}, "update": {1: 80.0, 2: 71.0}}
-DEFAULT_TILE = "14x8"     # the library's 2D default
+DEFAULT_TILE = "8x16"     # the library's 2D default
+TRAFFIC_TILE = "14x8"     # the tile shape the DRAM bytes below were captured on
 # DRAM bytes (read + write) per cell of one stage-1 flux-kernel launch with 14x8 tiles: ncu
 # dram__bytes_{read,write}.sum of the current kernel on the 1024^2 vortex (records and state larger
 # than L2), 476.76 + 248.00 MB, divided by the cells; the 2048^2 bench grid moves the same bytes per
@@ -267,7 +268,7 @@ def run_cgks(args, world, rank, local):
     stage1 = None if stage1_flop is None else stage1_flop * cells / ((flux_ms + rec_ms + upd_ms) * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
-                "traffic": FLUX_DRAM_BYTES_PER_CELL[1] * cells if tile == DEFAULT_TILE else None,
+                "traffic": FLUX_DRAM_BYTES_PER_CELL[1] * cells if tile == TRAFFIC_TILE else None,
                 "algorithmic_bytes": FLUX_ALGO_BYTES_PER_CELL[1] * cells,
                 "algorithmic_flop_per_cell": FLUX_FLOP_PER_CELL[1],
                 "kernel": f"stage_kernel<{tile},1>", "kernel_ms": flux_ms,

@@ -156,7 +156,7 @@ cgks_status cgks_batch_step(cgks_solver* const* solvers, int n, int nsteps);
  * 0: 16x8, 1: 8x16, 2: 32x4, 3: 64x1, 4: 16x7, 5: 7x16, 6: 14x8, 7: 24x8,
  * 8: 16x14, 9: 20x11, 10: 15x15, 11: 22x10, 12: 18x12, 13: 20x12, 14: 15x16,
  * 15: 17x14, 16: 16x16, 17: 24x16, 18: 32x12; -1
- * restores the default (14x8 in 2D, 64x1 in 1D).  The shape changes only the
+ * restores the default (8x16 in 2D, 64x1 in 1D).  The shape changes only the
  * decomposition of the work, never the results.  Errors: CGKS_E_INVAL (1D
  * solvers take only 64x1; 2D solvers any other shape). */
 cgks_status cgks_set_tile_shape(cgks_solver* s, int shape);
@@ -164,8 +164,8 @@ cgks_status cgks_set_tile_shape(cgks_solver* s, int shape);
 /* Tile shape (numbered as for cgks_set_tile_shape) that the autotuner of
  * cgks_batch_step chose for this exact batch, or -1 while it is still timing
  * the candidates.  The tuner times, on the first steps of a new batch
- * composition, the flux kernel's tile shapes 14x8, 16x8, 16x7 and 16x16 (with
- * 1.75, 2, 1.75 and 4 face segments per thread), then the update kernel at 2
+ * composition, the flux kernel's tile shapes 8x16, 14x8, 16x8 and 16x16 (with
+ * 2, 1.75, 2 and 4 face segments per thread), then the update kernel at 2
  * and 4 cells per thread with the best shape (12 steps in all); neither choice
  * changes a result. */
 int cgks_batch_tile_shape(cgks_solver* const* solvers, int n);

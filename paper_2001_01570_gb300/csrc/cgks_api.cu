@@ -88,7 +88,7 @@ cgks_status read_ctrl(cgks_solver* s, Ctrl* c)
 
 int pick_shape(const cgks_problem& p)
 {
-    return p.dim == 1 ? TILE_64x1 : TILE_14x8;
+    return p.dim == 1 ? TILE_64x1 : TILE_8x16;
 }
 
 }  // namespace

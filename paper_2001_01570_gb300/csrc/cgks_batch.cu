@@ -39,7 +39,7 @@ __global__ void dummy_ctrl_kernel(Ctrl* c)
     c->steps_target = 0;
 }
 
-constexpr int kShapeCands[] = {TILE_14x8, TILE_16x8, TILE_16x7, TILE_16x16};
+constexpr int kShapeCands[] = {TILE_8x16, TILE_14x8, TILE_16x8, TILE_16x16};
 constexpr int kCptCands[] = {2, 4};
 
 }  // namespace

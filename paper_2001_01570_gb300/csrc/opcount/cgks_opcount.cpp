@@ -12,7 +12,7 @@
 // erfc and Newton reciprocal count as one operation).  RegK's register forms
 // count as the operation they stand for.  The code below runs one step of a
 // 2D grid the way the kernels do -- every face row's record, every face
-// segment of every 14x8 tile (each face once), every cell's update, both
+// segment of every 8x16 tile (each face once), every cell's update, both
 // stages -- and reports the tally of each of the six launches.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -273,7 +273,7 @@ struct HostStep {
         return 0;
     }
 
-    // the three-kernel step (records, flux over 14 x 8 tiles, update per stage);
+    // the three-kernel step (records, flux over 8 x 16 tiles, update per stage);
     // out (may be NULL): the counts of the six launches
     bool unfused(unsigned long long* out)
     {
@@ -301,16 +301,16 @@ struct HostStep {
                 }
             }
             snapshot(o);
-            // face segments, 14 x 8 tiles
+            // face segments, 8 x 16 tiles (the 2D default)
             unsigned long long before[cgks_oc::K_N];
             memset(cgks_oc::g_tally, 0, sizeof(cgks_oc::g_tally));
-            for (int y0 = 0; y0 < ny; y0 += 8)
-                for (int x0 = 0; x0 < nx; x0 += 14) {
+            for (int y0 = 0; y0 < ny; y0 += 16)
+                for (int x0 = 0; x0 < nx; x0 += 8) {
                     snapshot(before);
-                    stage_tile<14, 8>(G, x0, y0, rx, ry);   // copies, not counted
+                    stage_tile<8, 16>(G, x0, y0, rx, ry);   // copies, not counted
                     for (int k = 0; k < cgks_oc::K_N; ++k) cgks_oc::g_tally[k] = before[k];
-                    ok &= stage == 1 ? tile_segments<14, 8, 1>(rflux, G, x0, y0, rx, ry, dc)
-                                     : tile_segments<14, 8, 2>(rflux, G, x0, y0, rx, ry, dc);
+                    ok &= stage == 1 ? tile_segments<8, 16, 1>(rflux, G, x0, y0, rx, ry, dc)
+                                     : tile_segments<8, 16, 2>(rflux, G, x0, y0, rx, ry, dc);
                 }
             snapshot(o + cgks_oc::K_N);
             // cell updates
