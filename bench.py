@@ -68,12 +68,12 @@ FLOP_PER_CELL = {s: RECORD_FLOP_PER_CELL[8] + FLUX_FLOP_PER_CELL[s] + UPDATE_FLO
 # every divide, square root, reciprocal, exponential and erfc as 1 however the GPU expands it.
 OPCOUNT_FLOP_PER_CELL = {"records": 3733.73, "flux": {1: 5398.63, 2: 5050.46}, "update": {1: 80.0, 2: 71.0}}
 DEFAULT_TILE = "8x16"     # the library's 2D default
-TRAFFIC_TILE = "14x8"     # the tile shape the DRAM bytes below were captured on
-# DRAM bytes (read + write) per cell of one stage-1 flux-kernel launch with 14x8 tiles: ncu
+TRAFFIC_TILE = "8x16"     # the tile shape the DRAM bytes below were captured on
+# DRAM bytes (read + write) per cell of one stage-1 flux-kernel launch with 8x16 tiles: ncu
 # dram__bytes_{read,write}.sum of the current kernel on the 1024^2 vortex (records and state larger
-# than L2), 476.76 + 248.00 MB, divided by the cells; the 2048^2 bench grid moves the same bytes per
+# than L2), 478.90 + 244.60 MB, divided by the cells; the 2048^2 bench grid moves the same bytes per
 # cell (its launch is too large to capture under the profiling size rule).
-FLUX_DRAM_BYTES_PER_CELL = {1: (476.764416e6 + 248.002304e6) / 1048576}
+FLUX_DRAM_BYTES_PER_CELL = {1: (478.897664e6 + 244.597504e6) / 1048576}
 # algorithmic bytes per cell of the flux kernel: the two face rows' records (2 x 28 doubles) read and
 # the two faces' results written (stage 1: 16 doubles each, stage 2: 8)
 FLUX_ALGO_BYTES_PER_CELL = {1: 448 + 256, 2: 448 + 128}
