@@ -341,7 +341,7 @@ static cgks_status enqueue_steps(cgks_solver* s, int nsteps, long* launches, boo
     const int nblocks = stage_blocks(s->ntiles, s->nsm);
     const int cv = s->prob.recon_vars;
     const int rblocks = record_blocks(s->nrchunks, s->nsm, cv);
-    const int ublocks = update_blocks(s->ncchunks, s->nsm);
+    const int ublocks = update_blocks(s->ncchunks, s->nsm, 4);
     const int fblocks = s->nftiles < s->nsm ? s->nftiles : s->nsm;
     for (int k = 0; k < nsteps; ++k) {
         CK(launch_begin_step(s->d_desc, 1, s->stream));
@@ -354,7 +354,7 @@ static cgks_status enqueue_steps(cgks_solver* s, int nsteps, long* launches, boo
         for (int stage = 1; stage <= 2; ++stage) {
             CK(launch_records(stage, cv, s->d_desc, s->d_rchunks, s->nrchunks, rblocks, s->stream));
             CK(launch_stage(s->shape, stage, s->d_desc, s->d_tiles, s->ntiles, nblocks, s->stream));
-            CK(launch_update(stage, s->d_desc, s->d_cchunks, s->ncchunks, ublocks, s->stream));
+            CK(launch_update(stage, s->d_desc, s->d_cchunks, s->ncchunks, ublocks, s->stream, nullptr, 4));
         }
         CK(launch_end_step(s->d_desc, 1, s->stream));
         *launches += 8;
@@ -436,7 +436,7 @@ cgks_status cgks_step_profiled(cgks_solver* s, int nsteps, double stage_ms[8])
     const int nblocks = stage_blocks(s->ntiles, s->nsm);
     const int cv = s->prob.recon_vars;
     const int rblocks = record_blocks(s->nrchunks, s->nsm, cv);
-    const int ublocks = update_blocks(s->ncchunks, s->nsm);
+    const int ublocks = update_blocks(s->ncchunks, s->nsm, 4);
     for (int k = 0; k < nsteps; ++k) {
         cudaEvent_t* e = &ev[(size_t)k * (NK + 1)];
         CK(cudaEventRecord(e[0], s->stream));
@@ -448,7 +448,7 @@ cgks_status cgks_step_profiled(cgks_solver* s, int nsteps, double stage_ms[8])
             CK(cudaEventRecord(f[1], s->stream));
             CK(launch_stage(s->shape, stage, s->d_desc, s->d_tiles, s->ntiles, nblocks, s->stream));
             CK(cudaEventRecord(f[2], s->stream));
-            CK(launch_update(stage, s->d_desc, s->d_cchunks, s->ncchunks, ublocks, s->stream));
+            CK(launch_update(stage, s->d_desc, s->d_cchunks, s->ncchunks, ublocks, s->stream, nullptr, 4));
             CK(cudaEventRecord(f[3], s->stream));
         }
         CK(launch_end_step(s->d_desc, 1, s->stream));
