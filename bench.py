@@ -67,7 +67,6 @@ FLOP_PER_CELL = {s: RECORD_FLOP_PER_CELL[8] + FLUX_FLOP_PER_CELL[s] + UPDATE_FLO
 # 2048^2 bench grid (python -m paper_2001_01570_gb300.opcount 2048), counting add/sub/mul 1, fma 2 and
 # every divide, square root, reciprocal, exponential and erfc as 1 however the GPU expands it.
 OPCOUNT_FLOP_PER_CELL = {"records": 3733.73, "flux": {1: 5398.63, 2: 5050.46}, "update": {1: 80.0, 2: 71.0}}
-DEFAULT_TILE = "8x16"     # the library's 2D default
 TRAFFIC_TILE = "8x16"     # the tile shape the DRAM bytes below were captured on
 # DRAM bytes (read + write) per cell of one stage-1 flux-kernel launch with 8x16 tiles: ncu
 # dram__bytes_{read,write}.sum of the current kernel on the 1024^2 vortex (records and state larger
@@ -256,7 +255,7 @@ def run_cgks(args, world, rank, local):
     # ---------------- per-kernel durations (events around every launch) for the roofline
     prof_steps = max(2, min(args.steps, 5))
     stage_ms = cgks.cgks_step_profiled(solver.handle, prof_steps)
-    tile = args.tile or DEFAULT_TILE
+    tile = args.tile or cgks.cgks_tile_shape(solver.handle)
     # stage_ms: begin, stage-1 records, flux, update, stage-2 records, flux, update, end
     flux_ms, rec_ms, upd_ms = stage_ms[2], stage_ms[1], stage_ms[3]
     nsm = torch.cuda.get_device_properties(local).multi_processor_count

@@ -156,10 +156,15 @@ cgks_status cgks_batch_step(cgks_solver* const* solvers, int n, int nsteps);
  * 0: 16x8, 1: 8x16, 2: 32x4, 3: 64x1, 4: 16x7, 5: 7x16, 6: 14x8, 7: 24x8,
  * 8: 16x14, 9: 20x11, 10: 15x15, 11: 22x10, 12: 18x12, 13: 20x12, 14: 15x16,
  * 15: 17x14, 16: 16x16, 17: 24x16, 18: 32x12; -1
- * restores the default (8x16 in 2D, 64x1 in 1D).  The shape changes only the
+ * restores the default (64x1 in 1D; in 2D 8x16, or 14x8 where it needs no more
+ * passes of the persistent grid, as on small grids).  The shape changes only the
  * decomposition of the work, never the results.  Errors: CGKS_E_INVAL (1D
  * solvers take only 64x1; 2D solvers any other shape). */
 cgks_status cgks_set_tile_shape(cgks_solver* s, int shape);
+
+/* The solver's current tile shape (numbered as for cgks_set_tile_shape); -1
+ * for a NULL solver. */
+int cgks_tile_shape(const cgks_solver* s);
 
 /* Tile shape (numbered as for cgks_set_tile_shape) that the autotuner of
  * cgks_batch_step chose for this exact batch, or -1 while it is still timing

@@ -91,6 +91,8 @@ def load():
         getattr(L, name).restype = ctypes.c_int
     L.cgks_set_tile_shape.argtypes = [vp, ctypes.c_int]
     L.cgks_set_tile_shape.restype = ctypes.c_int
+    L.cgks_tile_shape.argtypes = [vp]
+    L.cgks_tile_shape.restype = ctypes.c_int
     L.cgks_batch_tile_shape.argtypes = [ctypes.POINTER(vp), ctypes.c_int]
     L.cgks_batch_tile_shape.restype = ctypes.c_int
     L.cgks_batch_update_cpt.argtypes = [ctypes.POINTER(vp), ctypes.c_int]
@@ -245,6 +247,11 @@ def cgks_set_tile_shape(solver, shape):
     if isinstance(shape, str):
         shape = TILE_SHAPES.index(shape)
     _check(load().cgks_set_tile_shape(solver, int(shape)))
+
+
+def cgks_tile_shape(solver) -> str:
+    """The solver's current tile shape, e.g. "8x16"."""
+    return TILE_SHAPES[load().cgks_tile_shape(solver)]
 
 
 def cgks_batch_tile_shape(solvers) -> int:
